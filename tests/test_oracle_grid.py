@@ -1,0 +1,126 @@
+"""Pins of the oracle's grid kernels (Appendix C: FDTD, CIC, Esirkepov).
+
+Yee: a vacuum plane wave obeys the discrete dispersion relation
+(sin(w dt/2)/dt)^2 = sum_i (sin(k_i d_i/2)/d_i)^2; the FDTD keeps div B at
+rounding level.  CIC reproduces linear fields exactly.  Esirkepov: the
+deposited current satisfies the discrete continuity equation
+(rho^{n+1} - rho^n)/dt + div J = 0 cell by cell, and sum J dV = q w dx/dt.
+"""
+import math
+
+import numpy as np
+
+from oracle import oracle as o
+
+
+def idx(n, i, j, k):
+    return ((k % n[2]) * n[1] + (j % n[1])) * n[0] + (i % n[0])
+
+
+def test_plane_wave_dispersion():
+    n = (16, 12, 4)
+    d = (1.0, 1.3, 0.9)
+    dt = 0.4
+    m1, m2 = 3, 2
+    kx, ky = 2 * math.pi * m1 / (n[0] * d[0]), 2 * math.pi * m2 / (n[1] * d[1])
+    nc = int(np.prod(n))
+    f = [np.zeros(nc) for _ in range(6)]
+    J = [np.zeros(nc) for _ in range(3)]
+    I, Jj, K = np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]), indexing="ij")
+    flat = ((K * n[1] + Jj) * n[0] + I).ravel()
+    # E_z at (i, j, k+1/2), transverse to k in the x-y plane: div E = 0 exactly
+    f[2][flat] = np.cos(kx * I * d[0] + ky * Jj * d[1]).ravel()
+    basis = np.zeros(nc)
+    basis[flat] = np.cos(kx * I * d[0] + ky * Jj * d[1]).ravel()
+    a = []
+    for _ in range(6):
+        a.append(f[2] @ basis)
+        o.yee_step(n, d, dt, f, J)
+    a = np.array(a)
+    cos_wdt = (a[2:] + a[:-2]) / (2 * a[1:-1])
+    s = (math.sin(kx * d[0] / 2) / d[0]) ** 2 + (math.sin(ky * d[1] / 2) / d[1]) ** 2
+    expect = 1 - 2 * dt * dt * s          # cos(w dt) = 1 - 2 sin^2(w dt/2)
+    assert np.allclose(cos_wdt, expect, rtol=0, atol=1e-12)
+
+
+def test_divB_preserved():
+    rng = np.random.default_rng(0)
+    n = (8, 6, 5)
+    d = (1.0, 1.0, 1.0)
+    nc = int(np.prod(n))
+    f = [rng.standard_normal(nc) for _ in range(3)] + [np.zeros(nc) for _ in range(3)]
+    J = [rng.standard_normal(nc) * 0.1 for _ in range(3)]
+    for _ in range(5):
+        o.yee_step(n, d, 0.3, f, J)
+    Bx, By, Bz = f[3], f[4], f[5]
+    worst = 0.0
+    for k in range(n[2]):
+        for j in range(n[1]):
+            for i in range(n[0]):
+                # div B at the cell centre (i+1/2, j+1/2, k+1/2)
+                dv = (Bx[idx(n, i + 1, j, k)] - Bx[idx(n, i, j, k)]) \
+                   + (By[idx(n, i, j + 1, k)] - By[idx(n, i, j, k)]) \
+                   + (Bz[idx(n, i, j, k + 1)] - Bz[idx(n, i, j, k)])
+                worst = max(worst, abs(dv))
+    assert worst < 1e-13
+    assert np.abs(Bx).max() > 0.1
+
+
+def test_cic_linear_exact():
+    n = (6, 5, 7)
+    d = (0.5, 2.0, 1.0)
+    x0 = (-1.0, 3.0, 0.25)
+    nc = int(np.prod(n))
+    stag = [(0.5, 0, 0), (0, 0.5, 0), (0, 0, 0.5), (0, 0.5, 0.5), (0.5, 0, 0.5), (0.5, 0.5, 0)]
+    coef = [(1.0, 2.0, -1.0, 0.5), (0.3, -0.2, 0.1, 1.0), (2.0, 0.0, 0.0, -1.0),
+            (0.0, 1.0, 1.0, 0.0), (-1.0, 0.5, 2.0, 3.0), (0.7, 0.7, 0.7, 0.7)]
+    f = []
+    for c in range(6):
+        a = np.zeros(nc)
+        for k in range(n[2]):
+            for j in range(n[1]):
+                for i in range(n[0]):
+                    X = [x0[0] + (i + stag[c][0]) * d[0], x0[1] + (j + stag[c][1]) * d[1],
+                         x0[2] + (k + stag[c][2]) * d[2]]
+                    a[idx(n, i, j, k)] = coef[c][0] * X[0] + coef[c][1] * X[1] + coef[c][2] * X[2] + coef[c][3]
+        f.append(a)
+    # interior points (away from the periodic seam, where the linear field jumps)
+    for X in [(0.2, 5.1, 2.0), (-0.1, 7.9, 3.3), (0.77, 4.2, 5.5)]:
+        E, B = o.gather(n, d, x0, f, X)
+        got = list(E) + list(B)
+        for c in range(6):
+            want = coef[c][0] * X[0] + coef[c][1] * X[1] + coef[c][2] * X[2] + coef[c][3]
+            assert abs(got[c] - want) < 1e-12
+
+
+def test_esirkepov_continuity():
+    rng = np.random.default_rng(3)
+    n = (6, 7, 5)
+    d = (1.0, 0.8, 1.2)
+    x0 = (0.0, 0.0, 0.0)
+    nc = int(np.prod(n))
+    dt = 0.37
+    npart = 60
+    L = np.array(n) * np.array(d)
+    xa = rng.uniform(0, 1, (npart, 3)) * L
+    dx = rng.uniform(-0.9, 0.9, (npart, 3)) * np.array(d)
+    xb = xa + dx
+    qw = rng.uniform(-2, 2, npart)
+    J = [np.zeros(nc) for _ in range(3)]
+    for p in range(npart):
+        o.deposit(n, d, x0, J, xa[p], xb[p], qw[p], dt)
+    rho0 = o.charge_density(n, d, x0, xa[:, 0], xa[:, 1], xa[:, 2], qw)
+    rho1 = o.charge_density(n, d, x0, xb[:, 0], xb[:, 1], xb[:, 2], qw)
+    worst = 0.0
+    for k in range(n[2]):
+        for j in range(n[1]):
+            for i in range(n[0]):
+                c = idx(n, i, j, k)
+                div = (J[0][c] - J[0][idx(n, i - 1, j, k)]) / d[0] \
+                    + (J[1][c] - J[1][idx(n, i, j - 1, k)]) / d[1] \
+                    + (J[2][c] - J[2][idx(n, i, j, k - 1)]) / d[2]
+                worst = max(worst, abs((rho1[c] - rho0[c]) / dt + div))
+    assert worst < 1e-12
+    dV = np.prod(d)
+    for c in range(3):
+        assert abs(J[c].sum() * dV - (qw * dx[:, c]).sum() / dt) < 1e-11

@@ -1,0 +1,169 @@
+"""Pins of the oracle's particle step (Sec. IV.F-H, V.A).
+
+* Per-event conservation: emission and pair creation conserve 3-momentum, so in
+  a uniform E field the weighted total momentum of all species grows exactly by
+  sum q w E t of the particles present from the start (products of a pair
+  carry opposite charges and cancel).  In a uniform B field the push conserves
+  energy, so the total energy changes only by the closed-form defects of the
+  events (emission: gamma - delta|p| - sqrt(1+(1-delta)^2 p^2); pairs:
+  eps - sqrt(1+r^2 eps^2) - sqrt(1+(1-r)^2 eps^2)).
+* Adaptive sub-stepping (Sec. IV.H): a few large steps agree statistically with
+  many small steps that never subdivide (brute force), the paper's own
+  small-vs-large time step check (Sec. VII).
+* Boundaries: open boxes remove particles, periodic boxes wrap them.
+* Analytic fields: the Gaussian pulse peaks at E0 at the focus, halves its
+  intensity at +-tau/2, falls to 1/e at r = w0 and travels along -x at c.
+"""
+import math
+
+import numpy as np
+from scipy.stats import ks_2samp
+
+from oracle import oracle as o
+
+GAMMA0 = 1000.0
+B_CHI1 = 1e-3     # chi = 1 for gamma = 1000 perpendicular to B
+
+
+def electrons(n, gamma=GAMMA0, direction=(1.0, 0.0, 0.0), x=(0.0, 0.0, 0.0)):
+    p = math.sqrt(gamma ** 2 - 1)
+    return (np.tile(x, (n, 1)), np.tile(np.array(direction) * p, (n, 1)), np.ones(n),
+            np.arange(n, dtype=np.uint64))
+
+
+def big_periodic_box():
+    return dict(n=(4, 4, 4), d=(1e9, 1e9, 1e9), x0=(-2e9, -2e9, -2e9), periodic=(1, 1, 1))
+
+
+def total(run, key):
+    out = 0.0
+    for sp in run.sp:
+        x, p, w, _ = sp.get()
+        if key == "p":
+            out = out + (w[:, None] * p).sum(axis=0)
+    return out
+
+
+def test_momentum_conservation_uniform_E():
+    E = 2e-3
+    P = o.make_params(field_mode=o.FIELD_UNIFORM, fp=(0, E, 0, 0, 0, 0), kappa=0.1, **big_periodic_box())
+    run = o.Run(P, caps=(20000, 20000, 20000, 1))
+    x, p, w, ids = electrons(200, gamma=3000.0)
+    run.sp[0].set(x, p, w, ids)
+    p0 = total(run, "p")
+    dt = 2e5
+    for s in range(4):
+        run.step(s, s * dt, dt)
+    D = run.diag()
+    assert D["emissions"] > 50 and D["pairs"] > 0
+    p1 = total(run, "p")
+    expect = p0 + np.array([0.0, -1.0 * E * 4 * dt * 200, 0.0])
+    assert np.allclose(p1, expect, rtol=1e-11, atol=1e-9 * np.abs(expect).max())
+
+
+def test_energy_conservation_uniform_B():
+    P = o.make_params(field_mode=o.FIELD_UNIFORM, fp=(0, 0, 0, 0, 0, 2e-2), kappa=0.1, **big_periodic_box())
+    run = o.Run(P, caps=(20000, 20000, 20000, 1))
+    x, p, w, ids = electrons(100, gamma=500.0)
+    run.sp[0].set(x, p, w, ids)
+
+    def energy():
+        e = 0.0
+        for k, sp in enumerate(run.sp[:3]):
+            _, pp, ww, _ = sp.get()
+            m2 = 0.0 if k == 2 else 1.0
+            e += (ww * np.sqrt(m2 + (pp ** 2).sum(1))).sum()
+        return e
+    e0 = energy()
+    for s in range(3):
+        run.step(s, 0.0, 3e4)
+    D = run.diag()
+    assert D["emissions"] > 30 and D["pairs"] > 0
+    assert abs(energy() + D["energy_defect"] - e0) < 1e-10 * e0
+    # defects are tiny: at most ~ 1/gamma per event relative to the event energy
+    assert abs(D["energy_defect"]) < 1e-3 * e0
+
+
+def test_boundaries_open_and_periodic():
+    for periodic, alive in ((0, 0), (1, 1)):
+        P = o.make_params(n=(10, 10, 10), d=(1.0, 1.0, 1.0), x0=(0.0, 0.0, 0.0), periodic=(periodic,) * 3,
+                          field_mode=o.FIELD_UNIFORM, fp=(0,) * 6, pairs_on=1)
+        run = o.Run(P, caps=(1, 1, 4, 1))
+        run.sp[2].set([[9.5, 5.0, 5.0]], [[2.0, 0.0, 0.0]], [1.0], [7])
+        run.step(0, 0.0, 1.0)
+        assert run.sp[2].n == alive
+        if alive:
+            x, _, _, _ = run.sp[2].get()
+            assert abs(x[0, 0] - 0.5) < 1e-14
+        else:
+            assert run.diag()["absorbed"] == 1
+
+
+def run_stats(dt, nsteps, kappa, n=800, seed=11):
+    T_chi = dict(field_mode=o.FIELD_UNIFORM, fp=(0, 0, 0, 0, 0, B_CHI1))
+    P = o.make_params(kappa=kappa, pairs_on=0, seed=seed, **T_chi, **big_periodic_box())
+    run = o.Run(P, caps=(n, 1, 40 * n, 1))
+    x, p, w, ids = electrons(n)
+    run.sp[0].set(x, p, w, ids)
+    for s in range(nsteps):
+        run.step(s, s * dt, dt)
+    _, pe, _, _ = run.sp[0].get()
+    _, pg, _, _ = run.sp[2].get()
+    ge = np.sqrt(1 + (pe ** 2).sum(1))
+    eg = np.sqrt((pg ** 2).sum(1))
+    return run.diag(), ge, eg
+
+
+def test_adaptive_substeps_match_brute_force():
+    T = 0.02 * 2 * math.pi * GAMMA0 / B_CHI1      # 0.02 gyro periods, ~1 photon per electron
+    Da, ga, ea = run_stats(T / 2, 2, 0.1)          # AEG: N ~ 7 sub-steps per step
+    Db, gb, eb = run_stats(T / 300, 300, 1e9, seed=12)   # never subdivides, P_m ~ 1e-3
+    assert Da["substeps_lepton"] > 5 * 2 * 800
+    assert Db["substeps_lepton"] == 300 * 800
+    na, nb = Da["emissions"], Db["emissions"]
+    assert abs(na - nb) < 4 * math.sqrt(na + nb)
+    assert abs(ga.mean() - gb.mean()) < 4 * math.hypot(ga.std() / math.sqrt(len(ga)), gb.std() / math.sqrt(len(gb)))
+    assert ks_2samp(ea, eb).pvalue > 1e-3
+    # non-emitting electrons form an atom at gamma0; round away last-ulp differences of the push
+    assert ks_2samp(np.round(ga, 6), np.round(gb, 6)).pvalue > 1e-3
+
+
+def test_children_modes():
+    # with products evolving in the same step, photons born in step 0 already move in step 0
+    common = dict(field_mode=o.FIELD_UNIFORM, fp=(0, 0, 0, 0, 0, B_CHI1), kappa=0.1, pairs_on=0,
+                  **big_periodic_box())
+    res = {}
+    for mode in (0, 1):
+        P = o.make_params(same_step_children=mode, **common)
+        run = o.Run(P, caps=(300, 1, 3000, 1))
+        run.sp[0].set(*electrons(300))
+        run.step(0, 0.0, 2e5)
+        x, p, _, _ = run.sp[2].get()
+        res[mode] = (x, p)
+    # identical events (same streams), only the photon positions differ
+    assert len(res[0][0]) == len(res[1][0]) > 20
+    assert np.array_equal(res[0][1], res[1][1])
+    moved = np.linalg.norm(res[1][0] - res[0][0], axis=1)
+    assert (moved > 0).sum() > 0.5 * len(moved)
+
+
+def test_gaussian_pulse_properties():
+    E0, w, w0, tau = 6e-4, 3e-6, 5e6, 2e7
+    fp = (E0, w, w0, tau, 0.0, 0.0, 0.0, 0.0, 0.0)
+    E, B = o.field(o.FIELD_GAUSSIAN_LP, fp, (0, 0, 0), 0.0)
+    assert abs(E[1] - E0) < 1e-18 and B[2] == -E[1] and E[0] == E[2] == 0
+    # intensity half maximum at t = +-tau/2 on the envelope (carrier phase removed)
+    for t in (tau / 2, -tau / 2):
+        Et, _ = o.field(o.FIELD_GAUSSIAN_LP, fp[:8] + (-w * t,), (0, 0, 0), t)
+        assert abs((Et[1] / E0) ** 2 - 0.5) < 1e-12
+    # 1/e at r = w0 in the focal plane
+    Er, _ = o.field(o.FIELD_GAUSSIAN_LP, fp, (0, w0, 0), 0.0)
+    assert abs(Er[1] / E0 - math.exp(-1)) < 1e-12
+    # travels along -x at c: the same field value at (x - c dt, t + dt) up to diffraction
+    Ea, _ = o.field(o.FIELD_GAUSSIAN_LP, fp, (0, 0, 0), 0.0)
+    Eb, _ = o.field(o.FIELD_GAUSSIAN_LP, fp, (-1e3, 0, 0), 1e3)
+    assert abs(Eb[1] / Ea[1] - 1) < 1e-6
+    # rotating E
+    Er, Br = o.field(o.FIELD_ROTATING_E, (2.0, 0.5), (1, 2, 3), 1.3)
+    assert abs(math.hypot(Er[0], Er[1]) - 2.0) < 1e-15 and abs(math.atan2(Er[1], Er[0]) - 0.65) < 1e-15
+    assert not Br.any()
