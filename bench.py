@@ -1,0 +1,380 @@
+"""Throughput of the QED particle step: particle-steps/s with QED events.
+
+Workload (default): head-on collision of a 1 GeV electron beam (1e6
+electrons, 1% energy spread, 1 um rms radius, 3 um rms length) with a
+counter-propagating linearly polarised Gaussian pulse (lambda = 0.8 um,
+a0 = 200, 30 fs FWHM, 2 um waist), test particles in the analytic field,
+photon emission and Breit-Wheeler pairs on, dt = T_laser/100, 600 steps.
+
+One bench step = one qed_step (every live particle of every species advanced
+by dt).  W warm-up steps and K timed steps are taken from the 600-step run in
+a window centred on the collision (K + W = 600 covers the whole run, the
+default).  Between timed steps a 256 MiB buffer is written to flush L2; each
+step is bracketed by CUDA events on the stream it runs on, and the step
+kernel is bracketed separately (qed_profile_events) for the roofline.
+
+Prints one JSON line on rank 0.  --impl reference times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+RUN_STEPS = 600
+N_ELECTRONS = 1_000_000
+CAPS = (1_300_000, 200_000, 60_000_000, 0)
+COMPACT_INTERVAL = 8
+L2_FLUSH_BYTES = 256 << 20
+# algorithmic bytes per particle-step (read cell + offset + p + w + id, write
+# cell + offset + p) and per appended particle record, FP32 / FP64 forms
+BYTES_PER_STEP = {32: 68, 64: 120}
+BYTES_PER_APPEND = {32: 40, 64: 68}
+METRIC = "particle-steps/s with QED events, FP32 vs FP64 GPU path; % of HBM roofline"
+WORKLOAD_NAME = ("beam-laser head-on collision: 1e6 e- at 1 GeV (1% spread, 1 um x 3 um rms), "
+                 "LP Gaussian pulse lambda=0.8 um a0=200 30 fs FWHM w0=2 um, analytic field, "
+                 "emission + Breit-Wheeler pairs, dt=T_L/100, 600 steps")
+
+
+def window(K: int, W: int) -> int:
+    """First step of the warm-up + timed window, centred on the collision."""
+    meet = RUN_STEPS // 2
+    return max(0, min(RUN_STEPS - K - W, meet - (K + W) // 2))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+def make_workload(seed: int):
+    from paper_1412_6426_gb300 import workloads
+    return workloads.beam_laser_collision(n_particles=N_ELECTRONS, seed=seed, nsteps=RUN_STEPS)
+
+
+def time_device(w, prec: int, K: int, W: int, dist_barrier) -> dict:
+    """K timed steps of the device-resident path (inputs already in HBM)."""
+    import torch
+    from paper_1412_6426_gb300 import qed
+    from paper_1412_6426_gb300.sim import Simulation
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    s0 = window(K, W)
+    with Simulation(w, precision=prec, capacity=CAPS, compact_interval=COMPACT_INTERVAL) as sim:
+        sim.set_all()
+        if s0:
+            sim.step(s0)                      # untimed: advance to the window
+        sim.step(W)                           # warm-up steps
+        d0 = sim.diag()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for a, b in kev:                      # materialise the events before the library records them
+            a.record(stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        dist_barrier()
+        sampler = ClockSampler(int(os.environ.get("BENCH_GPU_INDEX", torch.cuda.current_device())))
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.zero_()                     # L2 flush, outside the timed events
+            qed.qed_profile_events(sim.ctx, kev[k][0].cuda_event, kev[k][1].cuda_event)
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        dist_barrier()
+        qed.qed_profile_events(sim.ctx, 0, 0)
+        d1 = sim.diag()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    psteps = d1["particle_steps"] - d0["particle_steps"]
+    appended = (d1["emissions"] - d0["emissions"]) + 2 * (d1["pairs"] - d0["pairs"])
+    algo_bytes = BYTES_PER_STEP[prec] * psteps + BYTES_PER_APPEND[prec] * appended
+    return {"precision": prec, "window_start": s0, "particle_steps": psteps, "seconds": sum(step_ms) / 1e3,
+            "kernel_seconds": sum(kern_ms) / 1e3, "ms_per_step": sum(step_ms) / K, "algo_bytes": algo_bytes,
+            "emissions": d1["emissions"] - d0["emissions"], "pairs": d1["pairs"] - d0["pairs"],
+            "launches": d1["kernel_launches"] - d0["kernel_launches"], "live_end": d1["count"],
+            "substeps": (d1["substeps_lepton"] - d0["substeps_lepton"])
+                        + (d1["substeps_photon"] - d0["substeps_photon"]),
+            "clocks": clocks}
+
+
+def time_e2e(w, prec: int, K: int, W: int) -> dict:
+    """The same steps through the public API with host buffers: each step
+    copies every species in from pinned host memory (qed_particles_set),
+    advances it (qed_step) and copies it back out (qed_particles_get)."""
+    import numpy as np
+    import torch
+    from paper_1412_6426_gb300 import qed
+    from paper_1412_6426_gb300.sim import Simulation
+
+    stream = torch.cuda.current_stream()
+    s0 = window(K, W)
+    host = {}
+    for sp in range(3):
+        cap = CAPS[sp]
+        host[sp] = (torch.empty((cap, 3), dtype=torch.float64, pin_memory=True),
+                    torch.empty((cap, 3), dtype=torch.float64, pin_memory=True),
+                    torch.empty(cap, dtype=torch.float64, pin_memory=True),
+                    torch.empty(cap, dtype=torch.int64, pin_memory=True))
+    n = {sp: 0 for sp in range(3)}
+    with Simulation(w, precision=prec, capacity=CAPS, compact_interval=COMPACT_INTERVAL) as sim:
+        sim.set_all()
+        if s0 + W:
+            sim.step(s0 + W)
+
+        def get_all():
+            for sp in range(3):
+                x, p, wt, i = host[sp]
+                n[sp] = qed.qed_particles_get(sim.ctx, sp, x.data_ptr(), p.data_ptr(), wt.data_ptr(),
+                                              i.data_ptr(), CAPS[sp], stream.cuda_stream)
+
+        get_all()
+        torch.cuda.synchronize()
+        h2d = d2h = 0
+        psteps = 0
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(K):
+            for sp in range(3):
+                x, p, wt, i = host[sp]
+                qed.qed_particles_set(sim.ctx, sp, x.data_ptr(), p.data_ptr(), wt.data_ptr(), i.data_ptr(),
+                                      n[sp], stream.cuda_stream)
+                h2d += 64 * n[sp]
+                psteps += n[sp]
+            sim.step(1)
+            get_all()                          # synchronises: the step's result is on the host
+            d2h += 64 * sum(n.values())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    secs = e0.elapsed_time(e1) / 1e3
+    return {"value": psteps / secs, "seconds": secs, "wall_seconds": wall, "particle_steps": psteps,
+            "h2d_bytes_per_step": h2d // K, "d2h_bytes_per_step": d2h // K}
+
+
+# ----------------------------------------------------------------------------
+# the FP64 CPU oracle on a bounded sample of the same workload
+def _oracle_worker(args):
+    (x, p, w, ids, wl_fields, W, K) = args
+    from oracle import drive
+    n, d, x0, periodic, field_mode, fp, dt, kappa, seed = wl_fields
+    out, diag, _, _ = drive.run(n, d, x0, periodic, field_mode, fp, dt, W + K, {0: (x, p, w, ids)},
+                                kappa=kappa, seed=seed, caps=(len(ids) * 3 + 64, 4096 + len(ids), 80 * len(ids) + 4096, 1),
+                                time_from=W)
+    return diag["timed_particle_steps"], diag["timed_seconds"], diag["overflow"]
+
+
+def oracle_sample(K: int, W: int, per_worker: int, workers: int) -> dict:
+    """Time the oracle on the first workers*per_worker electrons of the same
+    beam (same seed, same run) over the same step window, one process per
+    host core used."""
+    w = make_workload(seed=1)
+    s0 = window(K, W)
+    x, p, wt, ids = w.particles[0]
+    fields = (w.n, w.d, w.x0, w.periodic, w.field_mode, w.fp, w.dt, w.kappa, w.seed)
+    jobs = []
+    for k in range(workers):
+        sl = slice(k * per_worker, (k + 1) * per_worker)
+        jobs.append((x[sl].copy(), p[sl].copy(), wt[sl].copy(), ids[sl].copy(), fields, s0 + W, K))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t0
+    ps = sum(r[0] for r in res)
+    secs = max(r[1] for r in res)
+    return {"value": ps / secs, "unit": "particle-steps/s", "cores": workers, "kind": "oracle",
+            "sample": (f"{workers * per_worker} of the 1e6 electrons (same beam, same seed) and all their "
+                       f"products, steps {s0 + W}..{s0 + W + K - 1} of the 600-step run, FP64 oracle, "
+                       f"{workers} processes x {per_worker} electrons"),
+            "particle_steps": ps, "seconds": secs, "wall_seconds": wall,
+            "overflow": sum(r[2] for r in res)}
+
+
+def cpu_workers() -> int:
+    return max(1, min(os.cpu_count() or 1, 32))
+
+
+# ----------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=RUN_STEPS - 3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 side-by-side run")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-per-worker", type=int, default=600)
+    args = ap.parse_args()
+    K, W = args.steps, args.warmup
+    if K < 1 or W < 0 or K + W > RUN_STEPS:
+        ap.error(f"need 1 <= steps and steps + warmup <= {RUN_STEPS}")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        ref = oracle_sample(K, W, args.cpu_per_worker, cpu_workers())
+        line = {"metric": METRIC, "value": ref["value"], "unit": "particle-steps/s", "n_gpus": args.gpus,
+                "steps": K, "warmup": W, "ms_per_step": ref["seconds"] * 1e3 / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "impl": "reference",
+                "config": {"workload": WORKLOAD_NAME, "sample": ref["sample"]},
+                "cpu_baseline": {k: ref[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": ref["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import torch.distributed as tdist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    def reduce(x: float, op) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=op)
+        return float(t.item())
+
+    from paper_1412_6426_gb300 import build
+    build.build()
+    w = make_workload(seed=1 + rank)          # weak scaling: each rank its own beam
+    r32 = time_device(w, 32, K, W, barrier)
+    r64 = None if args.no_fp64 else time_device(w, 64, K, W, barrier)
+    e2e = None if args.no_e2e else time_e2e(w, 32, K, W)
+
+    tot_ps = reduce(float(r32["particle_steps"]), tdist.ReduceOp.SUM if world > 1 else None)
+    max_s = reduce(r32["seconds"], tdist.ReduceOp.MAX if world > 1 else None)
+    value = tot_ps / max_s
+    out64 = None
+    if r64 is not None:
+        tot64 = reduce(float(r64["particle_steps"]), tdist.ReduceOp.SUM if world > 1 else None)
+        max64 = reduce(r64["seconds"], tdist.ReduceOp.MAX if world > 1 else None)
+        out64 = {"value": tot64 / max64, "ms_per_step": r64["ms_per_step"]}
+    e2e_val = None
+    if e2e is not None:
+        tot_e = reduce(float(e2e["particle_steps"]), tdist.ReduceOp.SUM if world > 1 else None)
+        max_e = reduce(e2e["seconds"], tdist.ReduceOp.MAX if world > 1 else None)
+        e2e_val = tot_e / max_e
+    if rank != 0:
+        if world > 1:
+            tdist.destroy_process_group()
+        return
+
+    peak, peak_kind = peaks()
+
+    def roof(r):
+        ach = r["algo_bytes"] / r["kernel_seconds"] / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "peak_source": peak_kind,
+                "kernel": "k_step<float>" if r["precision"] == 32 else "k_step<double>",
+                "kernel_ms_per_launch": r["kernel_seconds"] * 1e3 / K,
+                "algorithmic_bytes_per_launch": r["algo_bytes"] / K}
+
+    line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "window_steps": [r32["window_start"] + W,
+                                                                   r32["window_start"] + W + K - 1],
+                       "precision": "fp32 push/rates, fp64 tables", "parallelism": f"independent beams x{world}",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "compact_interval": COMPACT_INTERVAL},
+            "roofline": roof(r32),
+            "gpu_launches": r32["launches"],
+            "clocks": r32["clocks"],
+            "events": {"emissions": r32["emissions"], "pairs": r32["pairs"], "substeps": r32["substeps"],
+                       "live_at_end": r32["live_end"]}}
+    if out64 is not None:
+        line["fp64"] = {"value": out64["value"], "ms_per_step": out64["ms_per_step"], "roofline": roof(r64),
+                        "speedup_fp32_over_fp64": value / out64["value"], "clocks": r64["clocks"]}
+    if e2e is not None:
+        line["e2e"] = {"value": e2e_val, "unit": "particle-steps/s",
+                       "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                       "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]}
+    if not args.no_cpu:
+        cb = oracle_sample(K, W, args.cpu_per_worker, cpu_workers())
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line))
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

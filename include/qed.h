@@ -1,0 +1,228 @@
+/*
+ * qed.h -- C ABI of the GB300 QED particle-step library.
+ *
+ * The library advances macro-particles (electrons, positrons, photons, ions)
+ * through one or more particle-in-cell time steps of the extended PIC scheme
+ * of Gonoskov et al. (arXiv:1412.6426):
+ *   field gather (analytic test fields or CIC on a Yee mesh),
+ *   Boris push (Appendix A),
+ *   the adaptive event generator (Sec. IV.H) around the modified event
+ *   generator for photon emission (Sec. IV.G, Eq. (25)) and the pair
+ *   generator (Sec. V.A, Eq. (30)),
+ *   creation of photons and pairs,
+ *   Esirkepov current deposit and the Yee FDTD field update (Appendix C).
+ * The calls follow the paper's statement of a PIC module (Appendix A): a
+ * module is initialised with the grid, the species and the rate tables,
+ * run once per step with the fields, the particles and the time step, and
+ * queried for diagnostics.
+ *
+ * Units ("Compton units"): momentum m c, energy m c^2, time hbar/(m c^2),
+ * length hbar/(m c), fields E_S = m^2 c^3/(e hbar).  Charges in e, masses in
+ * the electron mass.  Photons carry their momentum hbar k in m c.
+ *
+ * Conventions shared by every call:
+ *  - Every function returns a qed_status; 0 (QED_OK) is success.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All device work is ordered on it; qed_step is asynchronous.
+ *  - Pointers documented as "host or device" may be ordinary host memory,
+ *    page-locked host memory or device memory of the context's GPU; the
+ *    library detects which.
+ *  - The library never traps or aborts on the device.  Device-side failures
+ *    (capacity overflow, non-finite values, a bounded wait that timed out,
+ *    a probability above one under the strict flag, a particle moving a
+ *    cell or more in one step) set a device status word that the next
+ *    synchronising call (qed_diagnostics, qed_particles_get) returns.
+ *    After such a failure the context refuses qed_step with QED_ERR_STATE
+ *    until it is destroyed.
+ *  - The library is not thread-safe per context; distinct contexts are
+ *    independent.
+ */
+#ifndef QED_H
+#define QED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QED_ABI_VERSION 1
+
+typedef enum qed_status {
+    QED_OK = 0,
+    QED_ERR_ARG = 1,        /* invalid argument; nothing was changed */
+    QED_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    QED_ERR_CAPACITY = 3,   /* a particle or product buffer overflowed */
+    QED_ERR_NONFINITE = 4,  /* a non-finite field or momentum was seen */
+    QED_ERR_TIMEOUT = 5,    /* a bounded device wait gave up, or the
+                               products of one step nested too deeply */
+    QED_ERR_PMGT1 = 6,      /* P_m or P_p exceeded 1 with pm_strict set */
+    QED_ERR_STATE = 7,      /* the context holds an earlier device error */
+    QED_ERR_COURANT = 8     /* a charged particle moved >= 1 cell in a step
+                               with the deposit on */
+} qed_status;
+
+typedef enum qed_species {
+    QED_ELECTRON = 0,
+    QED_POSITRON = 1,
+    QED_PHOTON = 2,
+    QED_ION = 3,
+    QED_NSPECIES = 4
+} qed_species;
+
+typedef enum qed_field_mode {
+    /* E, B gathered by CIC from caller-owned Yee arrays (all axes periodic) */
+    QED_FIELD_GRID = 0,
+    /* constant fields: fp = {Ex, Ey, Ez, Bx, By, Bz} */
+    QED_FIELD_UNIFORM = 1,
+    /* linearly polarised paraxial Gaussian pulse moving along -x, E along
+     * y, B = -E along z, Gaussian temporal envelope:
+     * fp = {E0, omega, w0, tau_fwhm_of_intensity, x_focus, y_focus,
+     *       z_focus, t_focus, phase0} */
+    QED_FIELD_GAUSSIAN_LP = 2,
+    /* E = E0 (cos(omega t), sin(omega t), 0), B = 0: fp = {E0, omega} */
+    QED_FIELD_ROTATING_E = 3
+} qed_field_mode;
+
+/* Position lattice (and Yee mesh in QED_FIELD_GRID).  Particles are stored
+ * as a cell index plus an offset in [0,1) cell units; node (i,j,k) sits at
+ * x0 + (i,j,k)*d.  Yee staggering in cell units:
+ *   Ex (i+1/2,j,k)  Ey (i,j+1/2,k)  Ez (i,j,k+1/2)   (J likewise)
+ *   Bx (i,j+1/2,k+1/2)  By (i+1/2,j,k+1/2)  Bz (i+1/2,j+1/2,k)
+ * Field arrays hold n[0]*n[1]*n[2] elements, x fastest. */
+typedef struct qed_grid_desc {
+    int32_t n[3];          /* cells per axis, >= 1, product < 2^31 */
+    int32_t periodic[3];   /* per axis: 1 periodic, 0 open (particles that
+                              leave are removed and counted as absorbed) */
+    double d[3];           /* cell size, > 0 */
+    double x0[3];          /* position of node (0,0,0) */
+    int32_t field_mode;    /* qed_field_mode */
+    int32_t reserved;      /* must be 0 */
+    double fp[16];         /* analytic field parameters, see qed_field_mode */
+} qed_grid_desc;
+
+typedef struct qed_species_desc {
+    int64_t capacity[4];   /* particles each species store can hold (>= 0) */
+    double charge[4];      /* in e; normally -1, +1, 0, Z */
+    double mass[4];        /* in m_e; normally 1, 1, 0, M (photon mass ignored) */
+} qed_species_desc;
+
+typedef struct qed_params {
+    int32_t precision;          /* 32: FP32 push/gather/deposit; 64: FP64 */
+    int32_t nsub_max;           /* cap on sub-intervals of one step, >= 1 */
+    int32_t emission_on;        /* photon emission by e-/e+ (Sec. IV.G) */
+    int32_t pairs_on;           /* Breit-Wheeler pairs (Sec. V.A) */
+    int32_t same_step_children; /* 1: products evolve for the rest of the
+                                   step in which they are born; 0: they
+                                   start at the next step */
+    int32_t deposit_on;         /* grid mode: Esirkepov deposit + Yee update */
+    int32_t pm_strict;          /* 1: P_m > 1 or P_p > 1 is an error */
+    uint32_t seed;              /* enters every random stream */
+    int32_t nbins;              /* photon spectrum bins (0 = none), <= 4096 */
+    int32_t compact_interval;   /* steps between removals of dead particles
+                                   (0 = only on qed_particles_get) */
+    double kappa;               /* dt_q = kappa * bound of Eq. (28) / (33) */
+    double lg_lo, lg_hi;        /* log10 range of the spectra */
+    int64_t pending_capacity;   /* products per step that evolve within the
+                                   step (0 = 1/8 of the total capacity,
+                                   at least 65536) */
+} qed_params;
+
+/* Caller-owned Yee arrays (device memory, context precision). */
+typedef struct qed_fields {
+    void *E[3];
+    void *B[3];
+    void *J[3];   /* overwritten each step with the deposited current
+                     (number-current density: charge in e, velocity in c,
+                     per (hbar/mc)^3); Maxwell: dE/dt = curl B - 4 pi alpha J */
+} qed_fields;
+
+typedef struct qed_diag {
+    int64_t count[4];           /* live particles per species */
+    int64_t particle_steps;     /* sum over steps of the live particles at the
+                                   start of each step (all species) */
+    int64_t emissions, pairs;   /* events since qed_init */
+    int64_t substeps_lepton, substeps_photon;
+    int64_t pm_gt1, pp_gt1;     /* draws where P_m > 1 or P_p > 1 */
+    int64_t capped;             /* intervals that hit nsub_max */
+    int64_t absorbed;           /* particles removed at open boundaries */
+    int64_t overflow;           /* products lost to a full buffer */
+    int64_t nonfinite;          /* particles with non-finite field/momentum */
+    int64_t kernel_launches;    /* CUDA kernels this context has launched */
+    int64_t step;               /* steps taken */
+    double time;                /* current time */
+    int32_t status;             /* device status (qed_status) */
+    int32_t nbins;              /* in: length of the arrays below */
+    double *spectrum;           /* in: host array of nbins or NULL; out:
+                                   weighted counts of emitted photons over
+                                   log10(delta) in [lg_lo, lg_hi) */
+    double *spectrum_energy;    /* same over log10(photon energy / m c^2) */
+} qed_diag;
+
+typedef struct qed_ctx qed_ctx;
+
+/* Create a context on the current CUDA device.
+ *  grid, species, params: host structs, copied.
+ *  tables: NULL to build the FP64 rate tables of F1(z), F2(z) (Sec. IV.E,
+ *    Eq. (20)-(21)) on the device, or a host buffer of tables_bytes
+ *    previously filled by qed_tables_export (any precision).
+ *  Allocates the particle stores (capacity per species, library-owned) and
+ *  the product buffer.  Returns QED_ERR_ARG for invalid descriptors,
+ *  QED_ERR_CUDA if an allocation or launch fails; *out is NULL then. */
+int qed_init(qed_ctx **out, const qed_grid_desc *grid, const qed_species_desc *species,
+             const void *tables, size_t tables_bytes, const qed_params *params, void *stream);
+
+/* Copy the context's rate tables to host memory.  With host_buf == NULL
+ * only *needed is written.  QED_ERR_ARG if bytes < *needed. */
+int qed_tables_export(qed_ctx *ctx, void *host_buf, size_t bytes, size_t *needed);
+
+/* Replace the particles of one species (host or device pointers):
+ *  x: n x 3 absolute positions, p: n x 3 momenta (m c), w: n weights,
+ *  id: n unique 64-bit ids (they key the random streams, Sec. IV.G).
+ * Positions outside an open lattice are removed (absorbed).  QED_ERR_ARG if
+ * n exceeds the capacity or species is invalid. */
+int qed_particles_set(qed_ctx *ctx, int species, const double *x, const double *p,
+                      const double *w, const uint64_t *id, int64_t n, void *stream);
+
+/* Remove dead particles of one species and copy the live ones out (host or
+ * device pointers; layout as in qed_particles_set, FP64).  *n_out receives
+ * the live count; at most max_n are written (QED_ERR_ARG if more are live).
+ * Synchronises the stream and returns the device status. */
+int qed_particles_get(qed_ctx *ctx, int species, double *x, double *p, double *w,
+                      uint64_t *id, int64_t max_n, int64_t *n_out, void *stream);
+
+/* Advance all species by nsteps steps of dt.  fields: NULL unless
+ * field_mode is QED_FIELD_GRID, where the E, B arrays are read (gather),
+ * J is overwritten by the deposit and E, B are advanced by one symmetrised
+ * FDTD step after the particles (deposit_on).  Asynchronous; allocates
+ * nothing, so it may be captured in a CUDA graph.  QED_ERR_STATE after a
+ * device error, QED_ERR_ARG for dt <= 0 or missing fields. */
+int qed_step(qed_ctx *ctx, const qed_fields *fields, double dt, int32_t nsteps, void *stream);
+
+/* Set the step counter and time used by the next qed_step (the random
+ * streams are keyed by the step, so a restart reproduces a run exactly). */
+int qed_set_clock(qed_ctx *ctx, int64_t step, double time);
+
+/* Profiling aid: record the CUDA events start and stop (cudaEvent_t passed
+ * as void*, created by the caller on the context's device) immediately
+ * before and after the particle-step kernel of every following step, on the
+ * stream of that step.  NULL, NULL stops recording.  The events are not
+ * owned by the library. */
+int qed_profile_events(qed_ctx *ctx, void *start, void *stop);
+
+/* Synchronise the stream and read counters, live counts, spectra and the
+ * device status into *out (host struct).  Returns the device status. */
+int qed_diagnostics(qed_ctx *ctx, qed_diag *out, void *stream);
+
+/* Free every resource of the context.  NULL is accepted. */
+int qed_destroy(qed_ctx *ctx);
+
+/* Static description of a status code. */
+const char *qed_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QED_H */

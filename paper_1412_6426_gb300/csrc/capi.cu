@@ -1,0 +1,377 @@
+// C ABI of the QED particle-step library (declared in include/qed.h).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "qed_internal.h"
+
+size_t qed_record_bytes(int prec);
+size_t qed_pend_bytes(int prec);
+int qed_launch_count_live(qed_ctx *c, long long *d_live, cudaStream_t s);
+
+namespace {
+
+cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+int fold_status(int bits) {
+  if (bits & qed::kStCapacity) return QED_ERR_CAPACITY;
+  if (bits & qed::kStNonfinite) return QED_ERR_NONFINITE;
+  if (bits & qed::kStTimeout) return QED_ERR_TIMEOUT;
+  if (bits & qed::kStPmGt1) return QED_ERR_PMGT1;
+  if (bits & qed::kStCourant) return QED_ERR_COURANT;
+  return QED_OK;
+}
+
+template <typename T> int dalloc(T **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return QED_OK;
+  return cudaMalloc((void **)p, bytes) == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+size_t table_bytes(int prec) {
+  return prec == 64 ? sizeof(double) * qed::Tab<double>::kSize : sizeof(float) * qed::Tab<float>::kSize;
+}
+
+void release(qed_ctx *c) {
+  for (int sp = 0; sp < 4; ++sp)
+    for (int b = 0; b < 2; ++b) {
+      cudaFree(c->st[sp].pos[b]);
+      cudaFree(c->st[sp].mom[b]);
+      cudaFree(c->st[sp].id[b]);
+    }
+  cudaFree(c->pend[0]);
+  cudaFree(c->pend[1]);
+  cudaFree(c->d_count);
+  cudaFree(c->d_nstart);
+  cudaFree(c->d_pend_count);
+  cudaFree(c->d_counters);
+  cudaFree(c->d_spec);
+  cudaFree(c->d_spec_e);
+  cudaFree(c->d_status);
+  cudaFree(c->d_barrier);
+  cudaFree(c->d_tables);
+  cudaFree(c->d_tile);
+  cudaFree(c->stage);
+}
+
+// Classify a caller pointer: returns a device-usable alias, or nullptr when
+// it is ordinary (pageable) host memory that must be staged.
+const void *device_alias(const void *p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+  if (at.type == cudaMemoryTypeHost) {
+    void *dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, const_cast<void *>(p), 0) == cudaSuccess) return dp;
+    cudaGetLastError();
+  }
+  return nullptr;
+}
+
+int ensure_stage(qed_ctx *c, size_t bytes) {
+  if (c->stage_bytes >= bytes) return QED_OK;
+  cudaFree(c->stage);
+  c->stage = nullptr;
+  c->stage_bytes = 0;
+  if (cudaMalloc(&c->stage, bytes) != cudaSuccess) return QED_ERR_CUDA;
+  c->stage_bytes = bytes;
+  return QED_OK;
+}
+
+int read_status(qed_ctx *c, cudaStream_t s) {
+  int bits = 0;
+  if (cudaMemcpyAsync(&bits, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return QED_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return QED_ERR_CUDA;
+  int st = fold_status(bits);
+  if (st != QED_OK) c->latched = st;
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qed_error_string(int status) {
+  switch (status) {
+    case QED_OK: return "ok";
+    case QED_ERR_ARG: return "invalid argument";
+    case QED_ERR_CUDA: return "CUDA runtime call failed";
+    case QED_ERR_CAPACITY: return "particle or product buffer capacity exceeded";
+    case QED_ERR_NONFINITE: return "non-finite field or momentum";
+    case QED_ERR_TIMEOUT: return "bounded device wait gave up or products nested too deeply";
+    case QED_ERR_PMGT1: return "event probability above one with pm_strict";
+    case QED_ERR_STATE: return "context holds an earlier device error";
+    case QED_ERR_COURANT: return "charged particle moved a cell or more in one step";
+    default: return "unknown status";
+  }
+}
+
+int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, const void *tables,
+             size_t tables_bytes, const qed_params *p, void *stream) {
+  if (!out) return QED_ERR_ARG;
+  *out = nullptr;
+  if (!g || !sp || !p) return QED_ERR_ARG;
+  if (p->precision != 32 && p->precision != 64) return QED_ERR_ARG;
+  long long ncell = 1;
+  for (int k = 0; k < 3; ++k) {
+    if (g->n[k] < 1 || !(g->d[k] > 0.0) || !std::isfinite(g->d[k]) || !std::isfinite(g->x0[k]))
+      return QED_ERR_ARG;
+    ncell *= g->n[k];
+  }
+  if (ncell >= (1ll << 31)) return QED_ERR_ARG;
+  if (g->field_mode < QED_FIELD_GRID || g->field_mode > QED_FIELD_ROTATING_E || g->reserved != 0)
+    return QED_ERR_ARG;
+  if (g->field_mode == QED_FIELD_GRID)
+    for (int k = 0; k < 3; ++k)
+      if (!g->periodic[k]) return QED_ERR_ARG;
+  if (p->nsub_max < 1 || !(p->kappa > 0.0) || p->nbins < 0 || p->nbins > qed::kMaxBins)
+    return QED_ERR_ARG;
+  if (p->nbins > 0 && !(p->lg_hi > p->lg_lo)) return QED_ERR_ARG;
+  if (p->pending_capacity < 0 || p->compact_interval < 0) return QED_ERR_ARG;
+  long long total_cap = 0, max_cap = 0;
+  for (int k = 0; k < 4; ++k) {
+    if (sp->capacity[k] < 0 || sp->capacity[k] > (1ll << 40)) return QED_ERR_ARG;
+    if (k != QED_PHOTON && !(sp->mass[k] > 0.0)) return QED_ERR_ARG;
+    total_cap += sp->capacity[k];
+    max_cap = sp->capacity[k] > max_cap ? sp->capacity[k] : max_cap;
+  }
+  if (tables && tables_bytes != table_bytes(p->precision)) return QED_ERR_ARG;
+
+  qed_ctx *c = new (std::nothrow) qed_ctx();
+  if (!c) return QED_ERR_CUDA;
+  c->prec = p->precision;
+  c->grid = *g;
+  c->species = *sp;
+  c->par = *p;
+  cudaStream_t s = as_stream(stream);
+  int rc = QED_OK;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return QED_ERR_CUDA;
+  }
+  c->num_sms = prop.multiProcessorCount;
+  const size_t rec = qed_record_bytes(c->prec);  // pos + mom
+  for (int k = 0; k < 4 && rc == QED_OK; ++k) {
+    c->st[k].cap = sp->capacity[k];
+    for (int b = 0; b < 2 && rc == QED_OK; ++b) {
+      rc = dalloc(&c->st[k].pos[b], rec / 2 * sp->capacity[k]);
+      if (rc == QED_OK) rc = dalloc(&c->st[k].mom[b], rec / 2 * sp->capacity[k]);
+      if (rc == QED_OK) rc = dalloc(&c->st[k].id[b], sizeof(uint64_t) * sp->capacity[k]);
+    }
+  }
+  c->pend_cap = p->pending_capacity > 0 ? p->pending_capacity
+                                        : (total_cap / 8 > 65536 ? total_cap / 8 : 65536);
+  if (rc == QED_OK) rc = dalloc(&c->pend[0], qed_pend_bytes(c->prec) * c->pend_cap);
+  if (rc == QED_OK) rc = dalloc(&c->pend[1], qed_pend_bytes(c->prec) * c->pend_cap);
+  if (rc == QED_OK) rc = dalloc(&c->d_count, 4 * sizeof(long long));
+  if (rc == QED_OK) rc = dalloc(&c->d_nstart, 4 * sizeof(long long));
+  if (rc == QED_OK) rc = dalloc(&c->d_pend_count, sizeof(unsigned long long) * (qed::kMaxPass + 2));
+  if (rc == QED_OK) rc = dalloc(&c->d_counters, sizeof(unsigned long long) * qed::kNumCounters);
+  if (rc == QED_OK) rc = dalloc(&c->d_spec, sizeof(double) * (p->nbins > 0 ? p->nbins : 1));
+  if (rc == QED_OK) rc = dalloc(&c->d_spec_e, sizeof(double) * (p->nbins > 0 ? p->nbins : 1));
+  if (rc == QED_OK) rc = dalloc(&c->d_status, sizeof(int) * 4);
+  if (rc == QED_OK) rc = dalloc(&c->d_barrier, sizeof(unsigned) * 4);
+  c->tables_bytes = table_bytes(c->prec);
+  if (rc == QED_OK) rc = dalloc(&c->d_tables, c->tables_bytes);
+  c->tile_cap = (max_cap + qed::kCompactTile - 1) / qed::kCompactTile + 2;
+  if (rc == QED_OK) rc = dalloc(&c->d_tile, sizeof(long long) * c->tile_cap);
+  if (rc == QED_OK) {
+    cudaMemsetAsync(c->d_count, 0, 4 * sizeof(long long), s);
+    cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * qed::kNumCounters, s);
+    cudaMemsetAsync(c->d_spec, 0, sizeof(double) * (p->nbins > 0 ? p->nbins : 1), s);
+    cudaMemsetAsync(c->d_spec_e, 0, sizeof(double) * (p->nbins > 0 ? p->nbins : 1), s);
+    cudaMemsetAsync(c->d_status, 0, sizeof(int) * 4, s);
+    cudaMemsetAsync(c->d_barrier, 0, sizeof(unsigned) * 4, s);
+    if (tables)
+      rc = cudaMemcpyAsync(c->d_tables, tables, c->tables_bytes, cudaMemcpyHostToDevice, s) == cudaSuccess
+               ? QED_OK : QED_ERR_CUDA;
+    else
+      rc = qed_build_tables(c, s);
+  }
+  if (rc == QED_OK) rc = qed_step_kernel_blocks(c);
+  if (rc == QED_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = QED_ERR_CUDA;
+  if (rc != QED_OK) {
+    cudaGetLastError();
+    release(c);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return QED_OK;
+}
+
+int qed_tables_export(qed_ctx *c, void *host_buf, size_t bytes, size_t *needed) {
+  if (!c) return QED_ERR_ARG;
+  if (needed) *needed = c->tables_bytes;
+  if (!host_buf) return QED_OK;
+  if (bytes < c->tables_bytes) return QED_ERR_ARG;
+  return cudaMemcpy(host_buf, c->d_tables, c->tables_bytes, cudaMemcpyDeviceToHost) == cudaSuccess
+             ? QED_OK : QED_ERR_CUDA;
+}
+
+int qed_particles_set(qed_ctx *c, int sp, const double *x, const double *p, const double *w,
+                      const uint64_t *id, int64_t n, void *stream) {
+  if (!c || sp < 0 || sp >= QED_NSPECIES || n < 0 || n > c->st[sp].cap) return QED_ERR_ARG;
+  if (n > 0 && (!x || !p || !w || !id)) return QED_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  const void *dx = device_alias(x), *dp = device_alias(p), *dw = device_alias(w), *di = device_alias(id);
+  const size_t nn = (size_t)n;
+  if (n > 0 && (!dx || !dp || !dw || !di)) {
+    // stage pageable host arrays through device memory
+    if (ensure_stage(c, 64 * nn) != QED_OK) return QED_ERR_CUDA;
+    char *b = (char *)c->stage;
+    if (cudaMemcpyAsync(b, x, 24 * nn, cudaMemcpyDefault, s) != cudaSuccess ||
+        cudaMemcpyAsync(b + 24 * nn, p, 24 * nn, cudaMemcpyDefault, s) != cudaSuccess ||
+        cudaMemcpyAsync(b + 48 * nn, w, 8 * nn, cudaMemcpyDefault, s) != cudaSuccess ||
+        cudaMemcpyAsync(b + 56 * nn, id, 8 * nn, cudaMemcpyDefault, s) != cudaSuccess)
+      return QED_ERR_CUDA;
+    dx = b; dp = b + 24 * nn; dw = b + 48 * nn; di = b + 56 * nn;
+  }
+  return qed_launch_set(c, sp, (const double *)dx, (const double *)dp, (const double *)dw,
+                        (const uint64_t *)di, n, s);
+}
+
+int qed_particles_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t *id, int64_t max_n,
+                      int64_t *n_out, void *stream) {
+  if (!c || sp < 0 || sp >= QED_NSPECIES || !n_out || max_n < 0) return QED_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  int rc = qed_launch_compact(c, sp, s);
+  if (rc != QED_OK) return rc;
+  long long n = 0;
+  if (cudaMemcpyAsync(&n, c->d_count + sp, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return QED_ERR_CUDA;
+  *n_out = n;
+  if (n > max_n) return QED_ERR_ARG;
+  if (n > 0) {
+    if (!x || !p || !w || !id) return QED_ERR_ARG;
+    void *dx = (void *)device_alias(x), *dp = (void *)device_alias(p), *dw = (void *)device_alias(w),
+         *di = (void *)device_alias(id);
+    const size_t nn = (size_t)n;
+    bool staged = !dx || !dp || !dw || !di;
+    if (staged) {
+      if (ensure_stage(c, 64 * nn) != QED_OK) return QED_ERR_CUDA;
+      char *b = (char *)c->stage;
+      dx = b; dp = b + 24 * nn; dw = b + 48 * nn; di = b + 56 * nn;
+    }
+    rc = qed_launch_get(c, sp, (double *)dx, (double *)dp, (double *)dw, (uint64_t *)di, n, s);
+    if (rc != QED_OK) return rc;
+    if (staged) {
+      char *b = (char *)c->stage;
+      if (cudaMemcpyAsync(x, b, 24 * nn, cudaMemcpyDefault, s) != cudaSuccess ||
+          cudaMemcpyAsync(p, b + 24 * nn, 24 * nn, cudaMemcpyDefault, s) != cudaSuccess ||
+          cudaMemcpyAsync(w, b + 48 * nn, 8 * nn, cudaMemcpyDefault, s) != cudaSuccess ||
+          cudaMemcpyAsync(id, b + 56 * nn, 8 * nn, cudaMemcpyDefault, s) != cudaSuccess)
+        return QED_ERR_CUDA;
+    }
+  }
+  return read_status(c, s);
+}
+
+int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *stream) {
+  if (!c) return QED_ERR_ARG;
+  if (c->latched) return QED_ERR_STATE;
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return QED_ERR_ARG;
+  const bool grid = c->grid.field_mode == QED_FIELD_GRID;
+  if (grid) {
+    if (!f) return QED_ERR_ARG;
+    for (int k = 0; k < 3; ++k)
+      if (!f->E[k] || !f->B[k] || (c->par.deposit_on && !f->J[k])) return QED_ERR_ARG;
+  }
+  cudaStream_t s = as_stream(stream);
+  for (int n = 0; n < nsteps; ++n) {
+    int rc = qed_launch_step(c, f, dt, s);
+    if (rc == QED_OK && grid && c->par.deposit_on) rc = qed_launch_yee(c, f, dt, s);
+    if (rc != QED_OK) return rc;
+    c->step += 1;
+    c->time += dt;
+    if (c->par.compact_interval > 0 && ++c->steps_since_compact >= c->par.compact_interval) {
+      c->steps_since_compact = 0;
+      for (int sp = 0; sp < 4; ++sp) {
+        rc = qed_launch_compact(c, sp, s);
+        if (rc != QED_OK) return rc;
+      }
+    }
+  }
+  return QED_OK;
+}
+
+int qed_set_clock(qed_ctx *c, int64_t step, double time) {
+  if (!c || step < 0 || !std::isfinite(time)) return QED_ERR_ARG;
+  c->step = step;
+  c->time = time;
+  return QED_OK;
+}
+
+int qed_profile_events(qed_ctx *c, void *start, void *stop) {
+  if (!c || (start == nullptr) != (stop == nullptr)) return QED_ERR_ARG;
+  c->ev_start = (cudaEvent_t)start;
+  c->ev_stop = (cudaEvent_t)stop;
+  return QED_OK;
+}
+
+int qed_diagnostics(qed_ctx *c, qed_diag *out, void *stream) {
+  if (!c || !out) return QED_ERR_ARG;
+  if (out->nbins != 0 && out->nbins != c->par.nbins) return QED_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  long long *d_live = (long long *)c->d_nstart;  // reused: only valid inside a step
+  const int64_t launches = c->launches;           // before this call's own counting kernels
+  int rc = qed_launch_count_live(c, d_live, s);
+  if (rc != QED_OK) return rc;
+  unsigned long long cnt[qed::kNumCounters];
+  long long live[4];
+  int bits = 0;
+  if (cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(live, d_live, sizeof(live), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&bits, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return QED_ERR_CUDA;
+  if (out->nbins > 0) {
+    if (out->spectrum &&
+        cudaMemcpyAsync(out->spectrum, c->d_spec, sizeof(double) * out->nbins, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess)
+      return QED_ERR_CUDA;
+    if (out->spectrum_energy &&
+        cudaMemcpyAsync(out->spectrum_energy, c->d_spec_e, sizeof(double) * out->nbins,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return QED_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return QED_ERR_CUDA;
+  for (int k = 0; k < 4; ++k) out->count[k] = live[k];
+  out->emissions = (int64_t)cnt[qed::kCntEmissions];
+  out->pairs = (int64_t)cnt[qed::kCntPairs];
+  out->substeps_lepton = (int64_t)cnt[qed::kCntSubLepton];
+  out->substeps_photon = (int64_t)cnt[qed::kCntSubPhoton];
+  out->pm_gt1 = (int64_t)cnt[qed::kCntPmGt1];
+  out->pp_gt1 = (int64_t)cnt[qed::kCntPpGt1];
+  out->capped = (int64_t)cnt[qed::kCntCapped];
+  out->absorbed = (int64_t)cnt[qed::kCntAbsorbed];
+  out->overflow = (int64_t)cnt[qed::kCntOverflow];
+  out->nonfinite = (int64_t)cnt[qed::kCntNonfinite];
+  out->particle_steps = (int64_t)cnt[qed::kCntParticleSteps];
+  out->kernel_launches = launches;
+  out->step = c->step;
+  out->time = c->time;
+  int st = fold_status(bits);
+  out->status = st;
+  if (st != QED_OK) c->latched = st;
+  return st;
+}
+
+int qed_destroy(qed_ctx *c) {
+  if (!c) return QED_OK;
+  cudaDeviceSynchronize();
+  release(c);
+  delete c;
+  return QED_OK;
+}
+
+}  // extern "C"

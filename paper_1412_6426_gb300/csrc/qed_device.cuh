@@ -1,0 +1,271 @@
+// Device-side building blocks of the QED particle step (sm_103a).
+//
+// Units: momentum m c, time hbar/(m c^2), length hbar/(m c), fields E_S.
+// In these units the bracket [dt e^2 m c/hbar^2] of Eqs. (24), (27), (30)
+// is alpha*dt and the Lorentz force is q (E + v x B).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qed {
+
+constexpr double kAlpha = 7.2973525693e-3;          // fine-structure constant
+constexpr double kSqrt3Over2Pi = 0.27566444771089600; // sqrt(3)/(2 pi)
+constexpr double kTwoPi = 6.283185307179586;
+
+enum Species { kElectron = 0, kPositron = 1, kPhoton = 2, kIon = 3, kNSpecies = 4 };
+enum Purpose : uint32_t { kEmit = 1, kPair = 2, kChild = 3 };
+enum FieldMode { kFieldGrid = 0, kFieldUniform = 1, kFieldGaussianLP = 2, kFieldRotatingE = 3 };
+
+// Device status bits (folded into a qed_status by the host).
+enum StatusBit : int {
+  kStCapacity = 1, kStNonfinite = 2, kStTimeout = 4, kStPmGt1 = 8, kStCourant = 16
+};
+
+// ---------------------------------------------------------------------------
+// Rate tables.  g1(z) = F1(z) z^{-1/3}, g2(z) = F2(z) z^{-1/3} (Sec. IV.E,
+// F1(x) = x int_x^inf K_{5/3}, F2(x) = x K_{2/3}(x)) are stored as piecewise
+// polynomials: binade e of z (z in [2^e, 2^{e+1})) split into S equal
+// sub-intervals, each a degree-D polynomial in t in [-1, 1].  For e >= 0 the
+// stored function is g * exp(z).  Below 2^EMIN the two-term series
+// g1 = g1(0) - (pi/sqrt 3) z^{2/3}, g2 = g2(0) is used; at and above 2^EMAX
+// both are zero (exp(-512) is far below any uniform draw).
+template <typename R> struct TabCfg;
+template <> struct TabCfg<double> { static constexpr int EMIN = -60, EMAX = 9, S = 4, D = 10; };
+template <> struct TabCfg<float> { static constexpr int EMIN = -40, EMAX = 9, S = 2, D = 5; };
+
+template <typename R> struct Tab {
+  static constexpr int EMIN = TabCfg<R>::EMIN, EMAX = TabCfg<R>::EMAX;
+  static constexpr int S = TabCfg<R>::S, D = TabCfg<R>::D;
+  static constexpr int NB = EMAX - EMIN;
+  static constexpr int NC = D + 1;
+  static constexpr int kCoefs = 2 * NB * S * NC;  // both functions
+  // header: g1(0), g2(0), pi/sqrt(3), unused
+  static constexpr int kHeader = 4;
+  static constexpr int kSize = kHeader + kCoefs;
+};
+
+__device__ __forceinline__ void split_binade(double z, int &e, double &m) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(z);
+  e = (int)((b >> 52) & 0x7ffull) - 1023;
+  m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
+}
+__device__ __forceinline__ void split_binade(float z, int &e, float &m) {
+  unsigned b = __float_as_uint(z);
+  e = (int)((b >> 23) & 0xffu) - 127;
+  m = __uint_as_float((b & 0x7FFFFFu) | 0x3F800000u);
+}
+
+__device__ __forceinline__ double exp_r(double x) { return exp(x); }
+__device__ __forceinline__ float exp_r(float x) { return __expf(x); }
+__device__ __forceinline__ double cbrt_r(double x) { return cbrt(x); }
+__device__ __forceinline__ float cbrt_r(float x) { return cbrtf(x); }
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
+__device__ __forceinline__ double floor_r(double x) { return floor(x); }
+__device__ __forceinline__ float floor_r(float x) { return floorf(x); }
+
+// g1(z), g2(z) for z > 0 from the table T (layout of Tab<R>).
+template <typename R>
+__device__ __forceinline__ void syn_g(const R *__restrict__ T, R z, R &g1, R &g2) {
+  using C = Tab<R>;
+  int e;
+  R m;
+  split_binade(z, e, m);
+  if (e < C::EMIN) {
+    // two-term series (the next terms are O(z^{4/3}) relative)
+    R z23 = cbrt_r(z * z);
+    g1 = __ldg(T + 0) - __ldg(T + 2) * z23;
+    g2 = __ldg(T + 1);
+    return;
+  }
+  if (e >= C::EMAX) { g1 = R(0); g2 = R(0); return; }
+  R u = (m - R(1)) * R(C::S);
+  int s = (int)u;
+  s = s > C::S - 1 ? C::S - 1 : s;
+  R t = R(2) * (u - R(s)) - R(1);
+  const R *c1 = T + C::kHeader + (((e - C::EMIN) * C::S + s) * C::NC);
+  const R *c2 = c1 + C::NB * C::S * C::NC;
+  R a1 = __ldg(c1 + C::D), a2 = __ldg(c2 + C::D);
+#pragma unroll
+  for (int j = C::D - 1; j >= 0; --j) {
+    a1 = fma(a1, t, __ldg(c1 + j));
+    a2 = fma(a2, t, __ldg(c2 + j));
+  }
+  if (e >= 0) {
+    R ez = exp_r(-z);
+    a1 *= ez;
+    a2 *= ez;
+  }
+  g1 = a1;
+  g2 = a2;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 32x32 -> 64-bit products, with the key bumped by the Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Uniforms strictly inside (0,1).  FP64: 52 bits (top 26 of two words);
+// FP32: the top 23 bits of the first word.  Both add one half of the last
+// unit, so every value is exact and neither 0 nor 1 occurs.
+__device__ __forceinline__ double uniform_pair(unsigned a, unsigned b, double *) {
+  return ((double)(a >> 6) * 67108864.0 + (double)(b >> 6) + 0.5) * (1.0 / 4503599627370496.0);
+}
+__device__ __forceinline__ float uniform_pair(unsigned a, unsigned, float *) {
+  return ((float)(a >> 9) + 0.5f) * (1.0f / 8388608.0f);
+}
+
+// r1, r2 of the particle with this id at (step, sub-step, purpose).
+template <typename R>
+__device__ __forceinline__ void draw2(uint64_t id, unsigned step, unsigned sub, unsigned purpose,
+                                      unsigned seed, R &r1, R &r2) {
+  uint4 o = philox4x32_10(make_uint4(step, sub, purpose, seed),
+                          make_uint2((unsigned)id, (unsigned)(id >> 32)));
+  r1 = uniform_pair(o.x, o.y, (R *)nullptr);
+  r2 = uniform_pair(o.z, o.w, (R *)nullptr);
+}
+
+// Id of a product: mixes the parent id, step, sub-step and the product's
+// species, so ids (and the products' streams) do not depend on the order in
+// which threads create them.
+__device__ __forceinline__ uint64_t child_id(uint64_t parent, unsigned step, unsigned sub,
+                                             unsigned kind, unsigned seed) {
+  uint4 o = philox4x32_10(make_uint4(step, sub, kChild | (kind << 8), seed),
+                          make_uint2((unsigned)parent, (unsigned)(parent >> 32)));
+  return (uint64_t)o.x | ((uint64_t)o.y << 32);
+}
+
+// ---------------------------------------------------------------------------
+template <typename R> struct V3 { R x, y, z; };
+
+template <typename R> __device__ __forceinline__ R dot(V3<R> a, V3<R> b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <typename R> __device__ __forceinline__ V3<R> cross(V3<R> a, V3<R> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// chi of a lepton, Eq. (4): sqrt((gamma E + p x B)^2 - (p.E)^2), p in m c.
+template <typename R>
+__device__ __forceinline__ R chi_lepton(V3<R> p, R gamma, V3<R> E, V3<R> B) {
+  V3<R> c = cross(p, B);
+  R ax = gamma * E.x + c.x, ay = gamma * E.y + c.y, az = gamma * E.z + c.z;
+  R pe = dot(p, E);
+  R s = ax * ax + ay * ay + az * az - pe * pe;
+  return s > R(0) ? sqrt_r(s) : R(0);
+}
+
+// H_eff of Eq. (3): sqrt((E + v x B)^2 - (p_hat . E)^2).
+template <typename R>
+__device__ __forceinline__ R heff_lepton(V3<R> p, R gamma, V3<R> E, V3<R> B) {
+  R ig = R(1) / gamma;
+  V3<R> v = {p.x * ig, p.y * ig, p.z * ig};
+  V3<R> c = cross(v, B);
+  R ax = E.x + c.x, ay = E.y + c.y, az = E.z + c.z;
+  R pm = sqrt_r(dot(p, p));
+  R pe = pm > R(0) ? dot(p, E) / pm : R(0);
+  R s = ax * ax + ay * ay + az * az - pe * pe;
+  return s > R(0) ? sqrt_r(s) : R(0);
+}
+
+// H^gamma_eff of Eq. (32) for unit direction n.
+template <typename R>
+__device__ __forceinline__ R heff_photon(V3<R> n, V3<R> E, V3<R> B) {
+  V3<R> c = cross(n, B);
+  R ax = E.x + c.x, ay = E.y + c.y, az = E.z + c.z;
+  R ne = dot(n, E);
+  R s = ax * ax + ay * ay + az * az - ne * ne;
+  return s > R(0) ? sqrt_r(s) : R(0);
+}
+
+// Sub-interval count (Sec. IV.H): N = ceil(t_span/dt_q) in [1, nmax], with
+// dt_q from Eq. (28) for leptons and Eq. (33) for photons, scaled by kappa.
+// (137/2pi)(lambda_C/c) = 137 and 130 (lambda_C/c) = 130*2pi in these units.
+template <typename R>
+__device__ __forceinline__ int nsub_lepton(R t_span, R gamma, R heff, R kappa, int nmax,
+                                           int &capped) {
+  capped = 0;
+  if (!(heff > R(0))) return 1;
+  R ih = R(1) / heff;
+  R a = R(0.67) * cbrt_r(gamma) * cbrt_r(ih * ih);
+  R b = R(2) * ih;
+  R dtq = kappa * R(137) * (a < b ? a : b);
+  R ratio = t_span / dtq;
+  if (!(ratio > R(1))) return 1;
+  R n = ceil(ratio);
+  if (n > R(nmax)) { capped = 1; return nmax; }
+  return (int)n;
+}
+
+template <typename R>
+__device__ __forceinline__ int nsub_photon(R t_span, R heff_g, R kappa, int nmax, int &capped) {
+  capped = 0;
+  if (!(heff_g > R(0))) return 1;
+  R dtq = kappa * R(130.0 * kTwoPi) / heff_g;
+  R ratio = t_span / dtq;
+  if (!(ratio > R(1))) return 1;
+  R n = ceil(ratio);
+  if (n > R(nmax)) { capped = 1; return nmax; }
+  return (int)n;
+}
+
+// Modified event generator, Eq. (25) with f_m = r1^3 (Sec. IV.G), written in
+// terms of r1 so that no factor 1/delta appears:
+//   3 r1^2 G(r1^3) = sqrt3/(2pi) chi (1-delta) 3 c [g1(z) + 1.5 chi delta z g2(z)],
+//   z = (2/3) delta/(chi (1-delta)),  c = z^{1/3}/r1 = ((2/3)/(chi (1-delta)))^{1/3},
+// and P_m = alpha h/gamma times that.
+template <typename R>
+__device__ __forceinline__ R prob_emit(const R *__restrict__ T, R r1, R chi, R gamma, R h) {
+  if (!(chi > R(0))) return R(0);
+  R delta = r1 * r1 * r1;
+  R omd = R(1) - delta;
+  if (!(omd > R(0))) return R(0);
+  R c3 = R(2.0 / 3.0) / (chi * omd);
+  R z = delta * c3;
+  R g1, g2;
+  syn_g(T, z, g1, g2);
+  R br = g1 + R(1.5) * chi * delta * z * g2;
+  return R(kAlpha) * h / gamma * R(kSqrt3Over2Pi) * chi * omd * R(3) * cbrt_r(c3) * br;
+}
+
+// Pair generator, Eq. (30), with (3/2) chi_g z_p = 1/(de (1-de)):
+//   P_p = alpha h sqrt3/(2pi) (chi_g/eps) z^{1/3} [g2(z) - de(1-de) g1(z)].
+template <typename R>
+__device__ __forceinline__ R prob_pair(const R *__restrict__ T, R de, R chig, R eps, R h) {
+  if (!(chig > R(0)) || !(eps > R(0))) return R(0);
+  R d = de * (R(1) - de);
+  if (!(d > R(0))) return R(0);
+  R z = R(2.0 / 3.0) / (chig * d);
+  R g1, g2;
+  syn_g(T, z, g1, g2);
+  return R(kAlpha) * h * R(kSqrt3Over2Pi) * (chig / eps) * cbrt_r(z) * (g2 - d * g1);
+}
+
+// Boris push (Appendix A): half E, rotation by B, half E.
+template <typename R>
+__device__ __forceinline__ void boris(V3<R> &p, V3<R> E, V3<R> B, R q, R m, R h) {
+  R a = R(0.5) * q * h;
+  V3<R> um = {p.x + a * E.x, p.y + a * E.y, p.z + a * E.z};
+  R gm = sqrt_r(R(1) + dot(um, um) / (m * m));
+  R f = a / (m * gm);
+  V3<R> t = {f * B.x, f * B.y, f * B.z};
+  R k = R(2) / (R(1) + dot(t, t));
+  V3<R> s = {k * t.x, k * t.y, k * t.z};
+  V3<R> c1 = cross(um, t);
+  V3<R> up = {um.x + c1.x, um.y + c1.y, um.z + c1.z};
+  V3<R> c2 = cross(up, s);
+  p = {um.x + c2.x + a * E.x, um.y + c2.y + a * E.y, um.z + c2.z + a * E.z};
+}
+
+}  // namespace qed

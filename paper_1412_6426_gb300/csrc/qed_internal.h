@@ -1,0 +1,121 @@
+// Host-side context of the QED particle-step library and the launch
+// interfaces shared by its translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/qed.h"
+#include "qed_device.cuh"
+
+namespace qed {
+
+constexpr int kMaxPass = 64;        // nesting depth of products within one step
+constexpr int kNumCounters = 16;    // device diagnostic counters
+enum Counter {
+  kCntEmissions = 0, kCntPairs, kCntSubLepton, kCntSubPhoton, kCntPmGt1, kCntPpGt1, kCntCapped,
+  kCntAbsorbed, kCntOverflow, kCntNonfinite, kCntParticleSteps
+};
+constexpr int kMaxBins = 4096;
+constexpr int kCompactTile = 2048;   // particles per tile of the compaction
+
+// One species store: a structure of arrays, double-buffered for compaction.
+//   pos: {offset_x, offset_y, offset_z, weight}   (R4 = float4 or 2 x double2)
+//   mom: {p_x, p_y, p_z, cell}   cell = linear lattice index, -1 when dead;
+//        FP32 keeps the int bits in the 4th float, FP64 the value as a double
+//   id : 64-bit particle id (keys the particle's random streams)
+struct Store {
+  void *pos[2] = {nullptr, nullptr};
+  void *mom[2] = {nullptr, nullptr};
+  uint64_t *id[2] = {nullptr, nullptr};
+  int cur = 0;
+  int64_t cap = 0;
+};
+
+// Everything the step kernel reads, passed by value.
+template <typename R> struct StepArgs {
+  // stores (current buffers)
+  void *pos[4];
+  void *mom[4];
+  uint64_t *id[4];
+  long long *count;        // [4] store sizes (live + dead), appended atomically
+  const long long *nstart; // [4] sizes at the start of the step
+  long long cap[4];
+  // products evolving within the step
+  void *pend[2];
+  unsigned long long *pend_count;  // [kMaxPass + 2]
+  long long pend_cap;
+  // lattice
+  int n[3];
+  int periodic[3];
+  R d[3], inv_d[3];
+  double dd[3], x0[3];
+  // fields
+  int field_mode;
+  double fp[16];
+  double t;                // time at the start of the step
+  const R *E[3];
+  const R *B[3];
+  R *J[3];
+  int deposit;
+  // generator
+  R dt, kappa;
+  int nsub_max, emission_on, pairs_on, same_step, pm_strict;
+  unsigned seed, step;
+  R charge[4], mass[4];
+  const R *tab;
+  // diagnostics
+  unsigned long long *counters;
+  double *spectrum, *spectrum_energy;
+  int nbins;
+  double lg_lo, lg_inv_span;
+  int *status;
+  unsigned *barrier;       // [2]: arrivals, generation
+};
+
+}  // namespace qed
+
+struct qed_ctx {
+  int device = 0;
+  int prec = 32;
+  qed_grid_desc grid{};
+  qed_species_desc species{};
+  qed_params par{};
+  qed::Store st[4];
+  long long *d_count = nullptr;       // [4]
+  long long *d_nstart = nullptr;      // [4]
+  void *pend[2] = {nullptr, nullptr};
+  long long pend_cap = 0;
+  unsigned long long *d_pend_count = nullptr;
+  unsigned long long *d_counters = nullptr;
+  double *d_spec = nullptr, *d_spec_e = nullptr;
+  int *d_status = nullptr;
+  unsigned *d_barrier = nullptr;
+  void *d_tables = nullptr;
+  size_t tables_bytes = 0;
+  long long *d_tile = nullptr;        // compaction tile counts/offsets
+  long long tile_cap = 0;
+  int num_sms = 0;
+  int step_blocks = 0;
+  int step_threads = 256;
+  int64_t step = 0;
+  double time = 0.0;
+  int latched = 0;                    // a device error was observed
+  int64_t steps_since_compact = 0;
+  void *stage = nullptr;              // staging for pageable host I/O
+  size_t stage_bytes = 0;
+  cudaEvent_t ev_start = nullptr;     // recorded around the step kernel
+  cudaEvent_t ev_stop = nullptr;
+  int64_t launches = 0;               // kernels launched by this context
+};
+
+// Internal launch interfaces (implemented in the .cu files).
+int qed_build_tables(qed_ctx *c, cudaStream_t s);
+int qed_launch_step(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s);
+int qed_launch_yee(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s);
+int qed_launch_set(qed_ctx *c, int sp, const double *x, const double *p, const double *w,
+                   const uint64_t *id, int64_t n, cudaStream_t s);
+int qed_launch_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t *id, int64_t n,
+                   cudaStream_t s);
+int qed_launch_compact(qed_ctx *c, int sp, cudaStream_t s);
+int qed_step_kernel_blocks(qed_ctx *c);

@@ -1,0 +1,288 @@
+// Particle store: conversion from/to absolute FP64 positions, live counts,
+// and stable removal of dead particles (tiled stream compaction).
+#include <cmath>
+
+#include "qed_internal.h"
+
+namespace qed {
+namespace {
+
+struct alignas(16) D4 { double2 a, b; };  // 32-byte FP64 record half
+
+template <typename R> struct Rec;
+template <> struct Rec<float> { using T = float4; };
+template <> struct Rec<double> { using T = D4; };
+
+__device__ __forceinline__ void put(float4 *pos, float4 *mom, long long i, const double *off, double w,
+                                    const double *p, int cell) {
+  pos[i] = make_float4((float)off[0], (float)off[1], (float)off[2], (float)w);
+  mom[i] = make_float4((float)p[0], (float)p[1], (float)p[2], __int_as_float(cell));
+}
+__device__ __forceinline__ void put(D4 *pos, D4 *mom, long long i, const double *off, double w,
+                                    const double *p, int cell) {
+  D4 P, M;
+  P.a = make_double2(off[0], off[1]);
+  P.b = make_double2(off[2], w);
+  M.a = make_double2(p[0], p[1]);
+  M.b = make_double2(p[2], (double)cell);
+  pos[i] = P;
+  mom[i] = M;
+}
+__device__ __forceinline__ int cell_of(const float4 &m) { return __float_as_int(m.w); }
+__device__ __forceinline__ int cell_of(const D4 &m) { return (int)m.b.y; }
+
+struct Lattice {
+  int n[3], periodic[3];
+  double d[3], x0[3];
+};
+
+template <typename R>
+__global__ void k_set(typename Rec<R>::T *pos, typename Rec<R>::T *mom, uint64_t *ids, long long *count,
+                      int sp, Lattice L, const double *x, const double *p, const double *w,
+                      const uint64_t *id, long long n, unsigned long long *counters) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) count[sp] = n;
+  if (i >= n) return;
+  double off[3];
+  int ci[3];
+  bool dead = false;
+  for (int c = 0; c < 3; ++c) {
+    double u = (x[3 * i + c] - L.x0[c]) / L.d[c];
+    double f = floor(u);
+    double o = u - f;
+    long long k = (long long)f;
+    if (o >= 1.0) { o -= 1.0; k += 1; }
+    if (L.periodic[c]) {
+      k %= L.n[c];
+      if (k < 0) k += L.n[c];
+    } else if (k < 0 || k >= L.n[c]) {
+      dead = true;
+    }
+    ci[c] = (int)k;
+    off[c] = o;
+  }
+  int cell = dead ? -1 : (ci[2] * L.n[1] + ci[1]) * L.n[0] + ci[0];
+  if (dead) atomicAdd(counters + kCntAbsorbed, 1ull);
+  const double pp[3] = {p[3 * i], p[3 * i + 1], p[3 * i + 2]};
+  put(pos, mom, i, off, w[i], pp, cell);
+  ids[i] = id[i];
+}
+
+__device__ __forceinline__ void get(const float4 &P, const float4 &M, double *off, double &w, double *p) {
+  off[0] = P.x; off[1] = P.y; off[2] = P.z; w = P.w;
+  p[0] = M.x; p[1] = M.y; p[2] = M.z;
+}
+__device__ __forceinline__ void get(const D4 &P, const D4 &M, double *off, double &w, double *p) {
+  off[0] = P.a.x; off[1] = P.a.y; off[2] = P.b.x; w = P.b.y;
+  p[0] = M.a.x; p[1] = M.a.y; p[2] = M.b.x;
+}
+
+template <typename R>
+__global__ void k_get(const typename Rec<R>::T *pos, const typename Rec<R>::T *mom, const uint64_t *ids,
+                      Lattice L, double *x, double *p, double *w, uint64_t *id, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  typename Rec<R>::T P = pos[i], M = mom[i];
+  double off[3], pp[3], ww;
+  get(P, M, off, ww, pp);
+  int cell = cell_of(M);
+  int ci[3] = {cell % L.n[0], (cell / L.n[0]) % L.n[1], cell / (L.n[0] * L.n[1])};
+  for (int c = 0; c < 3; ++c) {
+    x[3 * i + c] = L.x0[c] + ((double)ci[c] + off[c]) * L.d[c];
+    p[3 * i + c] = pp[c];
+  }
+  w[i] = ww;
+  id[i] = ids[i];
+}
+
+// ----- compaction ----------------------------------------------------------
+// Tiles of kCompactTile records, processed in rounds of 256 consecutive
+// records so that loads stay coalesced and the output keeps the input order.
+template <typename T>
+__global__ void k_tile_count(const T *mom, const long long *count, int sp, long long cap, long long *tiles) {
+  __shared__ unsigned wsum[8];
+  const long long n = min(count[sp], cap);  // count exceeds cap after an overflow
+  if (blockIdx.x == 0 && threadIdx.x == 0) tiles[0] = n;
+  const long long ntiles = (n + kCompactTile - 1) / kCompactTile;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    unsigned mine = 0;
+    for (int r = 0; r < kCompactTile / 256; ++r) {
+      long long i = t * kCompactTile + r * 256 + threadIdx.x;
+      mine += (i < n && cell_of(mom[i]) >= 0) ? 1u : 0u;
+    }
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned s = 0;
+      for (int k = 0; k < 8; ++k) s += wsum[k];
+      tiles[2 + t] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Exclusive scan of the tile counts (one block); writes the live total.
+__global__ void k_tile_scan(long long *tiles, long long *count, int sp) {
+  __shared__ long long part[1024];
+  __shared__ long long carry;
+  const long long n = tiles[0];
+  const long long ntiles = (n + kCompactTile - 1) / kCompactTile;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (long long base = 0; base < ntiles; base += 1024) {
+    long long i = base + threadIdx.x;
+    long long v = i < ntiles ? tiles[2 + i] : 0;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      long long add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+      __syncthreads();
+      part[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < ntiles) tiles[2 + i] = carry + part[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    count[sp] = carry;
+    tiles[1] = carry;
+  }
+}
+
+template <typename T>
+__global__ void k_tile_scatter(const T *pos, const T *mom, const uint64_t *id, T *pos2, T *mom2,
+                               uint64_t *id2, const long long *tiles) {
+  __shared__ unsigned wcount[8];
+  const long long n = tiles[0];
+  const long long ntiles = (n + kCompactTile - 1) / kCompactTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    long long out = tiles[2 + t];
+    for (int r = 0; r < kCompactTile / 256; ++r) {
+      long long i = t * kCompactTile + r * 256 + threadIdx.x;
+      bool live = i < n && cell_of(mom[i]) >= 0;
+      unsigned b = __ballot_sync(0xffffffffu, live);
+      if (lane == 0) wcount[warp] = __popc(b);
+      __syncthreads();
+      unsigned before = 0, all = 0;
+      for (int k = 0; k < 8; ++k) {
+        before += k < warp ? wcount[k] : 0u;
+        all += wcount[k];
+      }
+      if (live) {
+        long long o = out + before + __popc(b & ((1u << lane) - 1u));
+        pos2[o] = pos[i];
+        mom2[o] = mom[i];
+        id2[o] = id[i];
+      }
+      out += all;
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_count_live(const T *mom, const long long *count, int sp, long long cap, long long *live) {
+  const long long n = min(count[sp], cap);
+  unsigned long long mine = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    mine += cell_of(mom[i]) >= 0;
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd((unsigned long long *)live + sp, mine);
+}
+
+Lattice lattice(const qed_ctx *c) {
+  Lattice L;
+  for (int k = 0; k < 3; ++k) {
+    L.n[k] = c->grid.n[k];
+    L.periodic[k] = c->grid.periodic[k];
+    L.d[k] = c->grid.d[k];
+    L.x0[k] = c->grid.x0[k];
+  }
+  return L;
+}
+
+template <typename R>
+int set(qed_ctx *c, int sp, const double *x, const double *p, const double *w, const uint64_t *id,
+        int64_t n, cudaStream_t s) {
+  using T = typename Rec<R>::T;
+  Store &st = c->st[sp];
+  int blocks = (int)((n + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  c->launches += 1;
+  k_set<R><<<blocks, 256, 0, s>>>((T *)st.pos[st.cur], (T *)st.mom[st.cur], st.id[st.cur], c->d_count,
+                                   sp, lattice(c), x, p, w, id, (long long)n, c->d_counters);
+  return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+template <typename R>
+int get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t *id, int64_t n, cudaStream_t s) {
+  using T = typename Rec<R>::T;
+  Store &st = c->st[sp];
+  if (n <= 0) return QED_OK;
+  int blocks = (int)((n + 255) / 256);
+  c->launches += 1;
+  k_get<R><<<blocks, 256, 0, s>>>((const T *)st.pos[st.cur], (const T *)st.mom[st.cur], st.id[st.cur],
+                                   lattice(c), x, p, w, id, (long long)n);
+  return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+template <typename R>
+int compact(qed_ctx *c, int sp, cudaStream_t s) {
+  using T = typename Rec<R>::T;
+  Store &st = c->st[sp];
+  if (st.cap == 0) return QED_OK;
+  int cur = st.cur, nxt = cur ^ 1;
+  long long maxtiles = (st.cap + kCompactTile - 1) / kCompactTile;
+  int g = (int)(maxtiles < (long long)c->num_sms * 8 ? maxtiles : (long long)c->num_sms * 8);
+  if (g < 1) g = 1;
+  c->launches += 3;
+  k_tile_count<T><<<g, 256, 0, s>>>((const T *)st.mom[cur], c->d_count, sp, (long long)st.cap, c->d_tile);
+  k_tile_scan<<<1, 1024, 0, s>>>(c->d_tile, c->d_count, sp);
+  k_tile_scatter<T><<<g, 256, 0, s>>>((const T *)st.pos[cur], (const T *)st.mom[cur], st.id[cur],
+                                       (T *)st.pos[nxt], (T *)st.mom[nxt], st.id[nxt], c->d_tile);
+  if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
+  st.cur = nxt;
+  return QED_OK;
+}
+
+template <typename R>
+int count_live(qed_ctx *c, long long *d_live, cudaStream_t s) {
+  using T = typename Rec<R>::T;
+  if (cudaMemsetAsync(d_live, 0, 4 * sizeof(long long), s) != cudaSuccess) return QED_ERR_CUDA;
+  for (int sp = 0; sp < 4; ++sp) {
+    const Store &st = c->st[sp];
+    if (st.cap == 0) continue;
+    c->launches += 1;
+    k_count_live<T><<<c->num_sms * 4, 256, 0, s>>>((const T *)st.mom[st.cur], c->d_count, sp,
+                                                    (long long)st.cap, d_live);
+  }
+  return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace qed
+
+size_t qed_record_bytes(int prec) { return prec == 64 ? 2 * sizeof(qed::D4) : 2 * sizeof(float4); }
+
+int qed_launch_set(qed_ctx *c, int sp, const double *x, const double *p, const double *w,
+                   const uint64_t *id, int64_t n, cudaStream_t s) {
+  return c->prec == 64 ? qed::set<double>(c, sp, x, p, w, id, n, s) : qed::set<float>(c, sp, x, p, w, id, n, s);
+}
+
+int qed_launch_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t *id, int64_t n,
+                   cudaStream_t s) {
+  return c->prec == 64 ? qed::get<double>(c, sp, x, p, w, id, n, s) : qed::get<float>(c, sp, x, p, w, id, n, s);
+}
+
+int qed_launch_compact(qed_ctx *c, int sp, cudaStream_t s) {
+  return c->prec == 64 ? qed::compact<double>(c, sp, s) : qed::compact<float>(c, sp, s);
+}
+
+int qed_launch_count_live(qed_ctx *c, long long *d_live, cudaStream_t s) {
+  return c->prec == 64 ? qed::count_live<double>(c, d_live, s) : qed::count_live<float>(c, d_live, s);
+}

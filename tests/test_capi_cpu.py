@@ -1,0 +1,153 @@
+"""CPU checks of the C ABI boundary (no GPU compute calls).
+
+The library builds for sm_103a and loads; it exports every function that
+include/qed.h declares; the ctypes mirrors of the header's structs have the
+same sizes and field offsets as the C compiler gives them; argument
+validation rejects invalid descriptors before touching the device.
+"""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qed.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1412_6426_gb300 import build, qed
+    build.build()
+    return qed.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(qed_\w+)\s*\(", text, re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_1412_6426_gb300 import qed
+    names = declared_functions()
+    assert len(names) >= 9
+    assert sorted(qed.EXPORTS) == names
+    nm = subprocess.run(["nm", "-D", "--defined-only", qed.LIB_PATH], capture_output=True, text=True,
+                        check=True).stdout
+    exported = set(re.findall(r"\bT (qed_\w+)", nm))
+    for n in names:
+        assert n in exported, n
+        assert hasattr(lib, n)
+
+
+def test_library_targets_sm103a_only():
+    from paper_1412_6426_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_error_strings(lib):
+    from paper_1412_6426_gb300 import qed
+    assert qed.qed_error_string(0) == "ok"
+    assert "capacity" in qed.qed_error_string(qed.QED_ERR_CAPACITY)
+    assert qed.qed_error_string(99) == "unknown status"
+
+
+LAYOUT_C = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "qed.h"
+#define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+int main(void) {
+  printf("qed_grid_desc %zu\nqed_species_desc %zu\nqed_params %zu\nqed_fields %zu\nqed_diag %zu\n",
+         sizeof(qed_grid_desc), sizeof(qed_species_desc), sizeof(qed_params), sizeof(qed_fields),
+         sizeof(qed_diag));
+  P(qed_grid_desc, d); P(qed_grid_desc, field_mode); P(qed_grid_desc, fp);
+  P(qed_params, seed); P(qed_params, kappa); P(qed_params, pending_capacity);
+  P(qed_diag, particle_steps); P(qed_diag, time); P(qed_diag, status); P(qed_diag, spectrum);
+  P(qed_species_desc, charge); P(qed_fields, J);
+  return 0;
+}
+"""
+
+
+def test_struct_layouts_match_header(tmp_path):
+    from paper_1412_6426_gb300 import qed
+    src = tmp_path / "layout.c"
+    src.write_text(LAYOUT_C)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(l.split() for l in lines if l.strip())
+    m = {"qed_grid_desc": qed.QedGridDesc, "qed_species_desc": qed.QedSpeciesDesc,
+         "qed_params": qed.QedParams, "qed_fields": qed.QedFields, "qed_diag": qed.QedDiag}
+    for k, v in got.items():
+        if "." in k:
+            t, f = k.split(".")
+            assert getattr(m[t], f).offset == int(v), k
+        else:
+            assert ctypes.sizeof(m[k]) == int(v), k
+
+
+def _descs():
+    from paper_1412_6426_gb300 import qed
+    g = qed.QedGridDesc()
+    g.n[:] = [4, 4, 4]
+    g.periodic[:] = [1, 1, 1]
+    g.d[:] = [1.0, 1.0, 1.0]
+    g.field_mode = qed.QED_FIELD_UNIFORM
+    s = qed.QedSpeciesDesc()
+    s.capacity[:] = [10, 10, 10, 0]
+    s.charge[:] = [-1, 1, 0, 1]
+    s.mass[:] = [1, 1, 0, 1836]
+    p = qed.QedParams()
+    p.precision = 64
+    p.nsub_max = 10
+    p.kappa = 0.1
+    return g, s, p
+
+
+@pytest.mark.parametrize("bad", ["precision", "cells", "grid_open", "kappa", "nbins", "mass", "tables"])
+def test_argument_validation(lib, bad):
+    from paper_1412_6426_gb300 import qed
+    g, s, p = _descs()
+    tables = None
+    if bad == "precision":
+        p.precision = 16
+    elif bad == "cells":
+        g.n[1] = 0
+    elif bad == "grid_open":
+        g.field_mode = qed.QED_FIELD_GRID
+        g.periodic[2] = 0
+    elif bad == "kappa":
+        p.kappa = -1.0
+    elif bad == "nbins":
+        p.nbins = 5000
+    elif bad == "mass":
+        s.mass[0] = 0.0
+    elif bad == "tables":
+        tables = b"\0" * 7
+    with pytest.raises(qed.QedError) as e:
+        qed.qed_init(g, s, p, tables=tables)
+    assert e.value.status == qed.QED_ERR_ARG
+
+
+def test_null_arguments(lib):
+    from paper_1412_6426_gb300 import qed
+    assert lib.qed_init(None, None, None, None, 0, None, None) == qed.QED_ERR_ARG
+    assert lib.qed_step(None, None, 1.0, 1, None) == qed.QED_ERR_ARG
+    assert lib.qed_destroy(None) == qed.QED_OK
+    assert lib.qed_diagnostics(None, None, None) == qed.QED_ERR_ARG
+
+
+def test_product_path_has_no_oracle_import():
+    # the product package never imports the oracle, and fails loudly without its library
+    pkg = os.path.join(ROOT, "paper_1412_6426_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            assert "oracle" not in re.sub(r'""".*?"""', "", open(os.path.join(pkg, f)).read(), flags=re.S), f
+    code = ("import paper_1412_6426_gb300.qed as q; q.LIB_PATH='/nonexistent.so'; q._lib=None\n"
+            "try:\n q.load(q.LIB_PATH)\nexcept RuntimeError: print('raised')\n")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT).stdout
+    assert "raised" in out

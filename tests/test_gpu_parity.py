@@ -1,0 +1,107 @@
+"""Parity of the CUDA particle step with the FP64 oracle (GPU tests).
+
+FP64 path: the same Philox streams drive both sides, so every particle must
+exist on both sides (same ids: identical event histories, including every
+product's birth step and sub-step) with momenta within 1e-12 relative and
+positions within 1e-12 of the box size (the tolerance the FP64 form is held
+to).  FP32 path: statistical agreement (event counts and spectrum bins within
+3 sigma, momentum relative error <= 1e-5 for particles with the same event
+history, energy conservation 1e-4).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1412_6426_gb300 import workloads
+from tests.util import box_scale, compare, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_1412_6426_gb300 import build
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    build.build()
+
+
+def assert_parity(w, nsteps=None, rtol=1e-12, **opts):
+    ora, od, _, _ = run_oracle(w, nsteps, **dict(opts))
+    assert od["overflow"] == 0
+    gpu, gd = run_gpu(w, nsteps, precision=64, **dict(opts))
+    assert gd["status"] == 0, gd
+    rep = compare(gpu, ora, rtol_p=rtol, xtol=1e-12 * box_scale(w))
+    assert rep["ok"], rep
+    for k in ("emissions", "pairs", "substeps_lepton", "substeps_photon", "capped", "pm_gt1"):
+        assert gd[k] == od[k], (k, gd[k], od[k])
+    return rep, gd, od
+
+
+def test_fp64_static_b_parity():
+    # chi = 1, gamma = 1000, dt = 0.01 gyro periods (first workload, 1000 of its electrons)
+    w = workloads.test_particles_static_b(n_particles=1000, nsteps=20)
+    rep, gd, od = assert_parity(w)
+    assert gd["emissions"] > 5000 and rep["matched"] > 6000
+
+
+def test_fp64_pairs_uniform_E():
+    # chi ~ 6: photons convert to pairs within the run
+    w = workloads.test_particles_static_b(n_particles=200, nsteps=4)
+    w.field_mode, w.fp, w.dt = workloads.FIELD_UNIFORM, (0, 2e-3, 0, 0, 0, 0), 2e5
+    x, p, wt, ids = w.particles[0]
+    p = p / np.linalg.norm(p[0]) * math.sqrt(3000.0 ** 2 - 1)
+    w.particles = {0: (x, p, wt, ids)}
+    rep, gd, od = assert_parity(w)
+    assert gd["pairs"] > 0 and gd["emissions"] > 100
+
+
+@pytest.mark.parametrize("same_step", [0, 1])
+def test_fp64_children_modes(same_step):
+    w = workloads.test_particles_static_b(n_particles=100, nsteps=6)
+    w.fp = (0, 0, 0, 0, 0, 3e-2)      # chi ~ 30: deep in-step cascades
+    w.dt = 2e4
+    rep, gd, od = assert_parity(w, same_step_children=same_step, caps=(60000, 60000, 60000, 1))
+    assert gd["pairs"] > 0
+
+
+def test_fp64_gaussian_pulse_parity():
+    # beam-laser collision (a0 = 200, 1 GeV), the pulse peak meets the beam centre at step 10
+    w = workloads.beam_laser_collision(n_particles=400, nsteps=20, seed=3)
+    rep, gd, od = assert_parity(w)
+    assert gd["emissions"] > 100
+
+
+def test_fp64_nsub_cap_and_absorbing_box():
+    w = workloads.test_particles_static_b(n_particles=200, nsteps=5)
+    w.periodic = (0, 0, 0)
+    w.n = (8, 8, 1)                    # small open box: photons leave it
+    rep, gd, od = assert_parity(w, nsub_max=3, kappa=0.01)
+    assert gd["capped"] > 0 and gd["absorbed"] == od["absorbed"] > 0
+
+
+def test_fp32_statistics():
+    w = workloads.test_particles_static_b(n_particles=4000, nsteps=20)
+    ora, od, spo, _ = run_oracle(w, nbins=24)
+    gpu, gd = run_gpu(w, precision=32, nbins=24)
+    assert gd["status"] == 0
+    n_o, n_g = od["emissions"], gd["emissions"]
+    assert abs(n_g - n_o) <= 3 * math.sqrt(n_o)
+    # spectra bin by bin within 3 sigma (Poisson, both sides)
+    sg = np.array(gd["spectrum"])
+    sig = np.sqrt(np.maximum(spo + sg, 1.0))
+    assert np.all(np.abs(sg - spo) <= 3 * sig + 1e-9), (sg, spo)
+    # same random words: most particles share their event history with the oracle
+    rep = compare(gpu, ora, rtol_p=1.0, xtol=np.inf, species=(0,))
+    assert rep["matched"] >= 0.99 * len(ora[0][3])
+    xg, pg, _, ig = gpu[0]
+    xo, po, _, io = ora[0]
+    common, a, b = np.intersect1d(ig, io, return_indices=True)
+    rel = np.linalg.norm(pg[a] - po[b], axis=1) / np.linalg.norm(po[b], axis=1)
+    assert np.median(rel) < 1e-5 and np.quantile(rel, 0.99) < 1e-4
+    # energy: the push in a static B conserves it; emission defects are ~1e-6 relative
+    e0 = 4000 * 1000.0
+    e1 = sum(np.sqrt((1.0 if sp < 2 else 0.0) + (gpu[sp][1] ** 2).sum(1)).sum() for sp in range(3))
+    assert abs(e1 / e0 - 1) < 1e-4
