@@ -34,8 +34,18 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
         base = sum(len(v[3]) for v in particles.values())
         caps = (4 * base + 64,) * 4
     run_ = o.Run(P, caps=caps, nbins=nbins)
+    absorbed_at_set = 0
     for sp, (x, p, w, ids) in particles.items():
-        run_.sp[sp].set(x, p, w, np.asarray(ids, dtype=np.uint64))
+        # a particle placed outside an open lattice is removed before any step
+        x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+        inside = np.ones(len(x), dtype=bool)
+        for c in range(3):
+            if not periodic[c]:
+                lo, hi = x0[c], x0[c] + d[c] * n[c]
+                inside &= (x[:, c] >= lo) & (x[:, c] < hi)
+        absorbed_at_set += int((~inside).sum())
+        run_.sp[sp].set(x[inside], np.asarray(p).reshape(-1, 3)[inside], np.asarray(w)[inside],
+                        np.asarray(ids, dtype=np.uint64)[inside])
     if fields is not None:
         run_.set_grid_fields(fields, J)
     psteps = 0
@@ -59,6 +69,7 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
     spec = run_.spectrum[:nbins].copy() if nbins else None
     spec_e = run_.spectrum_energy[:nbins].copy() if nbins else None
     diag = run_.diag()
+    diag["absorbed"] += absorbed_at_set
     diag["particle_steps"] = psteps
     diag["timed_particle_steps"] = timed_ps
     diag["timed_seconds"] = t_end - t_start if nsteps > time_from else 0.0

@@ -63,7 +63,11 @@ def test_fp64_children_modes(same_step):
     w = workloads.test_particles_static_b(n_particles=100, nsteps=6)
     w.fp = (0, 0, 0, 0, 0, 3e-2)      # chi ~ 30: deep in-step cascades
     w.dt = 2e4
-    rep, gd, od = assert_parity(w, same_step_children=same_step, caps=(60000, 60000, 60000, 1))
+    # Leptons cooled to gamma ~ 3 gyrate ~1000 rad in these 6 steps at ~1.4 rad
+    # per sub-interval; FMA and non-FMA roundings give a fixed per-step
+    # difference of the Boris rotation angle (|p| is constant), which grows
+    # linearly to ~2e-12 here.  Event histories are identical (same ids).
+    rep, gd, od = assert_parity(w, rtol=5e-12, same_step_children=same_step, caps=(60000, 60000, 60000, 1))
     assert gd["pairs"] > 0
 
 
@@ -77,7 +81,8 @@ def test_fp64_gaussian_pulse_parity():
 def test_fp64_nsub_cap_and_absorbing_box():
     w = workloads.test_particles_static_b(n_particles=200, nsteps=5)
     w.periodic = (0, 0, 0)
-    w.n = (8, 8, 1)                    # small open box: photons leave it
+    w.n = (8, 8, 1)                    # small open box around the origin: photons leave it
+    w.x0 = (-4 * w.d[0], -4 * w.d[1], -0.5 * w.d[2])
     rep, gd, od = assert_parity(w, nsub_max=3, kappa=0.01)
     assert gd["capped"] > 0 and gd["absorbed"] == od["absorbed"] > 0
 
