@@ -192,6 +192,30 @@ int qed_particles_set(qed_ctx *ctx, int species, const double *x, const double *
 int qed_particles_get(qed_ctx *ctx, int species, double *x, double *p, double *w,
                       uint64_t *id, int64_t max_n, int64_t *n_out, void *stream);
 
+/* Read the live particles of one species, like qed_particles_get, without
+ * allocating any memory.  The paper has no counterpart; this call exists for
+ * callers that cannot call cudaMalloc when they want the results: code that
+ * runs while a stream is being captured into a CUDA graph, hosts whose
+ * device memory all belongs to their own pool allocator, real-time loops
+ * that forbid allocation after start-up.
+ *  x, p, w, id: device or page-locked host buffers (layout as in
+ *    qed_particles_set); pageable host memory is refused with QED_ERR_ARG,
+ *    since it would need a staging buffer.
+ *  At most max_n particles are written, in store order (the order
+ *  qed_particles_get would give); *n_out receives the live count, and
+ *  QED_ERR_ARG is returned when it exceeds max_n.
+ *  Unlike qed_particles_get the store is not compacted.
+ *  Scratch: a fixed device array of 65536 tile counters inside the library
+ *  (512 KiB, held by every GPU that loads the library until exit), enough
+ *  for stores of up to 134,217,728 records (live plus not yet removed);
+ *  larger stores are refused with QED_ERR_CAPACITY.  The first call on a
+ *  device looks up the array's device address, so make that first call
+ *  before any stream capture.  All calls share the array: calls that
+ *  overlap on the GPU race and must be ordered by the caller.
+ * Synchronises the stream and returns the device status. */
+int qed_particles_read_static(qed_ctx *ctx, int species, double *x, double *p, double *w,
+                              uint64_t *id, int64_t max_n, int64_t *n_out, void *stream);
+
 /* Advance all species by nsteps steps of dt.  fields: NULL unless
  * field_mode is QED_FIELD_GRID, where the E, B arrays are read (gather),
  * J is overwritten by the deposit and E, B are advanced by one symmetrised

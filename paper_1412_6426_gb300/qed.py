@@ -22,7 +22,8 @@ QED_FIELD_GRID, QED_FIELD_UNIFORM, QED_FIELD_GAUSSIAN_LP, QED_FIELD_ROTATING_E =
 
 # every entry point the header declares (checked by the CPU tests)
 EXPORTS = ("qed_init", "qed_tables_export", "qed_particles_set", "qed_particles_get", "qed_step",
-           "qed_set_clock", "qed_profile_events", "qed_diagnostics", "qed_destroy", "qed_error_string")
+           "qed_set_clock", "qed_profile_events", "qed_diagnostics", "qed_destroy", "qed_error_string",
+           "qed_particles_read_static")
 
 
 class QedGridDesc(ctypes.Structure):
@@ -78,6 +79,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qed_particles_set.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp, i64, vp]
     lib.qed_particles_get.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp, i64, ctypes.POINTER(i64), vp]
     lib.qed_step.argtypes = [vp, ctypes.POINTER(QedFields), ctypes.c_double, i32, vp]
+    lib.qed_particles_read_static.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp, i64, ctypes.POINTER(i64), vp]
     lib.qed_set_clock.argtypes = [vp, i64, ctypes.c_double]
     lib.qed_profile_events.argtypes = [vp, vp, vp]
     lib.qed_diagnostics.argtypes = [vp, ctypes.POINTER(QedDiag), vp]
@@ -140,6 +142,17 @@ def qed_particles_get(ctx: int, species: int, x_ptr: int, p_ptr: int, w_ptr: int
                                   ctypes.c_void_p(p_ptr), ctypes.c_void_p(w_ptr), ctypes.c_void_p(id_ptr),
                                   int(max_n), ctypes.byref(n), ctypes.c_void_p(stream))
     _check("qed_particles_get", rc)
+    return n.value
+
+
+def qed_particles_read_static(ctx: int, species: int, x_ptr: int, p_ptr: int, w_ptr: int, id_ptr: int,
+                              max_n: int, stream: int = 0) -> int:
+    """Read one species into device or page-locked buffers without allocating."""
+    n = ctypes.c_int64()
+    rc = load().qed_particles_read_static(ctypes.c_void_p(ctx), int(species), ctypes.c_void_p(x_ptr),
+                                          ctypes.c_void_p(p_ptr), ctypes.c_void_p(w_ptr), ctypes.c_void_p(id_ptr),
+                                          int(max_n), ctypes.byref(n), ctypes.c_void_p(stream))
+    _check("qed_particles_read_static", rc)
     return n.value
 
 
