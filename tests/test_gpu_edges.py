@@ -67,8 +67,9 @@ def test_nonfinite_input_reported():
 
 
 def test_pm_strict():
-    # kappa = 50: sub-intervals far too long, P_m exceeds 1
+    # kappa = 50 and a step 4x the usual: one sub-interval, P_m up to ~2.8
     w = workloads.test_particles_static_b(n_particles=64, nsteps=2)
+    w.dt *= 4
     with sim_for(w, precision=64, capacity=(1000, 10, 5000, 0), kappa=50.0, pm_strict=1) as s:
         s.set_all()
         s.step(2)
