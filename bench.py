@@ -112,6 +112,14 @@ def make_workload(seed: int):
     return workloads.beam_laser_collision(n_particles=N_ELECTRONS, seed=seed, nsteps=RUN_STEPS)
 
 
+def scale_workload(n_electrons: int) -> None:
+    """Shrink the beam (and capacities) for profiling captures."""
+    global N_ELECTRONS, CAPS
+    f = n_electrons / N_ELECTRONS
+    N_ELECTRONS = n_electrons
+    CAPS = tuple(int(c * f) + (1024 if c else 0) for c in CAPS)
+
+
 def time_device(w, prec: int, K: int, W: int, dist_barrier) -> dict:
     """K timed steps of the device-resident path (inputs already in HBM)."""
     import torch
@@ -271,7 +279,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-per-worker", type=int, default=600)
+    ap.add_argument("--electrons", type=int, default=N_ELECTRONS,
+                    help="beam size (smaller beams are for profiling captures, not bench lines)")
     args = ap.parse_args()
+    if args.electrons != N_ELECTRONS:
+        scale_workload(args.electrons)
     K, W = args.steps, args.warmup
     if K < 1 or W < 0 or K + W > RUN_STEPS:
         ap.error(f"need 1 <= steps and steps + warmup <= {RUN_STEPS}")
@@ -351,7 +363,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "window_steps": [r32["window_start"] + W,
+            "config": {"workload": WORKLOAD_NAME if N_ELECTRONS == 1_000_000 else
+                       WORKLOAD_NAME.replace("1e6 e-", f"{N_ELECTRONS:.0e} e-"), "window_steps": [r32["window_start"] + W,
                                                                    r32["window_start"] + W + K - 1],
                        "precision": "fp32 push/rates, fp64 tables", "parallelism": f"independent beams x{world}",
                        "l2": "flushed between timed steps (256 MiB write)",
