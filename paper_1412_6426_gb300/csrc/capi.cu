@@ -51,6 +51,7 @@ void release(qed_ctx *c) {
   cudaFree(c->d_status);
   cudaFree(c->d_barrier);
   cudaFree(c->d_tables);
+  cudaFree(c->d_chi_star);
   cudaFree(c->d_tile);
   cudaFree(c->stage);
 }
@@ -182,6 +183,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
   if (rc == QED_OK) rc = dalloc(&c->d_barrier, sizeof(unsigned) * 4);
   c->tables_bytes = table_bytes(c->prec);
   if (rc == QED_OK) rc = dalloc(&c->d_tables, c->tables_bytes);
+  if (rc == QED_OK) rc = dalloc(&c->d_chi_star, sizeof(double));
   c->tile_cap = (max_cap + qed::kCompactTile - 1) / qed::kCompactTile + 2;
   if (rc == QED_OK) rc = dalloc(&c->d_tile, sizeof(long long) * c->tile_cap);
   if (rc == QED_OK) {
@@ -197,6 +199,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     else
       rc = qed_build_tables(c, s);
   }
+  if (rc == QED_OK) rc = qed_launch_chi_star(c, s);
   if (rc == QED_OK) rc = qed_step_kernel_blocks(c);
   if (rc == QED_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = QED_ERR_CUDA;
   if (rc != QED_OK) {

@@ -65,6 +65,12 @@ __device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
 __device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
 __device__ __forceinline__ double floor_r(double x) { return floor(x); }
 __device__ __forceinline__ float floor_r(float x) { return floorf(x); }
+__device__ __forceinline__ double ceil_r(double x) { return ceil(x); }
+__device__ __forceinline__ float ceil_r(float x) { return ceilf(x); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fabs_r(double x) { return fabs(x); }
+__device__ __forceinline__ float fabs_r(float x) { return fabsf(x); }
 
 // g1(z), g2(z) for z > 0 from the table T (layout of Tab<R>).
 template <typename R>
@@ -90,8 +96,8 @@ __device__ __forceinline__ void syn_g(const R *__restrict__ T, R z, R &g1, R &g2
   R a1 = __ldg(c1 + C::D), a2 = __ldg(c2 + C::D);
 #pragma unroll
   for (int j = C::D - 1; j >= 0; --j) {
-    a1 = fma(a1, t, __ldg(c1 + j));
-    a2 = fma(a2, t, __ldg(c2 + j));
+    a1 = fma_r(a1, t, __ldg(c1 + j));
+    a2 = fma_r(a2, t, __ldg(c2 + j));
   }
   if (e >= 0) {
     R ez = exp_r(-z);
@@ -203,7 +209,7 @@ __device__ __forceinline__ int nsub_lepton(R t_span, R gamma, R heff, R kappa, i
   R dtq = kappa * R(137) * (a < b ? a : b);
   R ratio = t_span / dtq;
   if (!(ratio > R(1))) return 1;
-  R n = ceil(ratio);
+  R n = ceil_r(ratio);
   if (n > R(nmax)) { capped = 1; return nmax; }
   return (int)n;
 }
@@ -215,7 +221,7 @@ __device__ __forceinline__ int nsub_photon(R t_span, R heff_g, R kappa, int nmax
   R dtq = kappa * R(130.0 * kTwoPi) / heff_g;
   R ratio = t_span / dtq;
   if (!(ratio > R(1))) return 1;
-  R n = ceil(ratio);
+  R n = ceil_r(ratio);
   if (n > R(nmax)) { capped = 1; return nmax; }
   return (int)n;
 }

@@ -45,7 +45,9 @@ template <typename R> struct StepArgs {
   void *pend[2];
   unsigned long long *pend_count;  // [kMaxPass + 2]
   long long pend_cap;
-  // lattice
+  // lattice; cell / n0 and cell / (n0 n1) by multiply-shift (div_m, div_l)
+  unsigned div_m[2];
+  int div_l[2];
   int n[3];
   int periodic[3];
   R d[3], inv_d[3];
@@ -64,6 +66,7 @@ template <typename R> struct StepArgs {
   unsigned seed, step;
   R charge[4], mass[4];
   const R *tab;
+  const double *chi_star;  // photons below this chi_g cannot pair (per context)
   // diagnostics
   unsigned long long *counters;
   double *spectrum, *spectrum_energy;
@@ -92,12 +95,14 @@ struct qed_ctx {
   int *d_status = nullptr;
   unsigned *d_barrier = nullptr;
   void *d_tables = nullptr;
+  double *d_chi_star = nullptr;       // pair-skip threshold derived from the tables
   size_t tables_bytes = 0;
   long long *d_tile = nullptr;        // compaction tile counts/offsets
   long long tile_cap = 0;
   int num_sms = 0;
-  int step_blocks = 0;
-  int step_threads = 256;
+  int blocks_photon = 0;              // grid sizes of the step kernels
+  int blocks_massive = 0;
+  int blocks_products = 0;
   int64_t step = 0;
   double time = 0.0;
   int latched = 0;                    // a device error was observed
@@ -119,3 +124,4 @@ int qed_launch_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t
                    cudaStream_t s);
 int qed_launch_compact(qed_ctx *c, int sp, cudaStream_t s);
 int qed_step_kernel_blocks(qed_ctx *c);
+int qed_launch_chi_star(qed_ctx *c, cudaStream_t s);

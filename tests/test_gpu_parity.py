@@ -110,3 +110,24 @@ def test_fp32_statistics():
     e0 = 4000 * 1000.0
     e1 = sum(np.sqrt((1.0 if sp < 2 else 0.0) + (gpu[sp][1] ** 2).sum(1)).sum() for sp in range(3))
     assert abs(e1 / e0 - 1) < 1e-4
+
+
+def test_fp32_gaussian_pulse_statistics():
+    # FP32 field evaluation (fixed-point carrier phase) against the FP64 oracle
+    w = workloads.beam_laser_collision(n_particles=3000, nsteps=20, seed=4)
+    ora, od, _, _ = run_oracle(w)
+    gpu, gd = run_gpu(w, precision=32)
+    assert gd["status"] == 0
+    assert abs(gd["emissions"] - od["emissions"]) <= 3 * math.sqrt(od["emissions"]) and od["emissions"] > 1000
+    xg, pg, _, ig = gpu[0]
+    xo, po, _, io = ora[0]
+    common, a, b = np.intersect1d(ig, io, return_indices=True)
+    assert len(common) >= 0.99 * len(io)
+    rel = np.linalg.norm(pg[a] - po[b], axis=1) / np.linalg.norm(po[b], axis=1)
+    assert np.median(rel) < 1e-5 and np.quantile(rel, 0.95) < 1e-4
+    # photon yield per energy decade within 3 sigma
+    eo = np.log10(np.linalg.norm(ora[2][1], axis=1))
+    eg = np.log10(np.linalg.norm(gpu[2][1], axis=1))
+    ho, edges = np.histogram(eo, bins=8, range=(-6, 2))
+    hg, _ = np.histogram(eg, bins=edges)
+    assert np.all(np.abs(hg - ho) <= 3 * np.sqrt(np.maximum(ho + hg, 1)))
