@@ -41,6 +41,11 @@ L2_FLUSH_BYTES = 256 << 20
 # cell + offset + p) and per appended particle record, FP32 / FP64 forms
 BYTES_PER_STEP = {32: 68, 64: 120}
 BYTES_PER_APPEND = {32: 40, 64: 68}
+# DRAM bytes (read + write) per photon-step of the photon kernel, from one ncu
+# capture of k_photons at the collision step of the 2.5e5-electron beam
+# (dram__bytes_read.sum + dram__bytes_write.sum / live photons); empty until
+# measured for the current kernel
+PHOTON_DRAM_BYTES_PER_STEP = {}
 METRIC = "particle-steps/s with QED events, FP32 vs FP64 GPU path; % of HBM roofline"
 WORKLOAD_NAME = ("beam-laser head-on collision: 1e6 e- at 1 GeV (1% spread, 1 um x 3 um rms), "
                  "LP Gaussian pulse lambda=0.8 um a0=200 30 fs FWHM w0=2 um, analytic field, "
@@ -136,32 +141,36 @@ def time_device(w, prec: int, K: int, W: int, dist_barrier) -> dict:
         sim.step(W)                           # warm-up steps
         d0 = sim.diag()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        for a, b in kev:                      # materialise the events before the library records them
-            a.record(stream)
-            b.record(stream)
+        kev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(K)]
+        for trio in kev:                      # materialise the events before the library records them
+            for e_ in trio:
+                e_.record(stream)
         torch.cuda.synchronize()
         dist_barrier()
         sampler = ClockSampler(int(os.environ.get("BENCH_GPU_INDEX", torch.cuda.current_device())))
         torch.cuda.synchronize()
         for k in range(K):
             flush.zero_()                     # L2 flush, outside the timed events
-            qed.qed_profile_events(sim.ctx, kev[k][0].cuda_event, kev[k][1].cuda_event)
+            qed.qed_profile_events(sim.ctx, kev[k][0].cuda_event, kev[k][1].cuda_event, kev[k][2].cuda_event)
             ev[k][0].record(stream)
             sim.step(1)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         clocks = sampler.stop()
         dist_barrier()
-        qed.qed_profile_events(sim.ctx, 0, 0)
+        qed.qed_profile_events(sim.ctx, 0, 0, 0)
         d1 = sim.diag()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    kern_ms = [a.elapsed_time(c) for a, _, c in kev]
+    phot_ms = [a.elapsed_time(b) for a, b, _ in kev]
     psteps = d1["particle_steps"] - d0["particle_steps"]
+    photon_steps = d1["species_steps"][2] - d0["species_steps"][2]
     appended = (d1["emissions"] - d0["emissions"]) + 2 * (d1["pairs"] - d0["pairs"])
     algo_bytes = BYTES_PER_STEP[prec] * psteps + BYTES_PER_APPEND[prec] * appended
     return {"precision": prec, "window_start": s0, "particle_steps": psteps, "seconds": sum(step_ms) / 1e3,
             "kernel_seconds": sum(kern_ms) / 1e3, "ms_per_step": sum(step_ms) / K, "algo_bytes": algo_bytes,
+            "photon_seconds": sum(phot_ms) / 1e3, "photon_steps": photon_steps,
+            "photon_algo_bytes": BYTES_PER_STEP[prec] * photon_steps,
             "emissions": d1["emissions"] - d0["emissions"], "pairs": d1["pairs"] - d0["pairs"],
             "launches": d1["kernel_launches"] - d0["kernel_launches"], "live_end": d1["count"],
             "substeps": (d1["substeps_lepton"] - d0["substeps_lepton"])
@@ -270,6 +279,7 @@ def cpu_workers() -> int:
 
 # ----------------------------------------------------------------------------
 def main():
+    global COMPACT_INTERVAL
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=RUN_STEPS - 3)
@@ -279,11 +289,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-per-worker", type=int, default=600)
+    ap.add_argument("--compact-interval", type=int, default=COMPACT_INTERVAL,
+                    help="steps between compactions (which also regroup photons that cannot pair)")
     ap.add_argument("--electrons", type=int, default=N_ELECTRONS,
                     help="beam size (smaller beams are for profiling captures, not bench lines)")
     args = ap.parse_args()
     if args.electrons != N_ELECTRONS:
         scale_workload(args.electrons)
+    COMPACT_INTERVAL = args.compact_interval
     K, W = args.steps, args.warmup
     if K < 1 or W < 0 or K + W > RUN_STEPS:
         ap.error(f"need 1 <= steps and steps + warmup <= {RUN_STEPS}")
@@ -353,12 +366,23 @@ def main():
     peak, peak_kind = peaks()
 
     def roof(r):
+        # the dominant kernel: the photon pass-0 kernel (photons are most of the particles)
+        ach = r["photon_algo_bytes"] / r["photon_seconds"] / 1e9
+        per_unit = PHOTON_DRAM_BYTES_PER_STEP.get(r["precision"])
+        traffic = per_unit * r["photon_steps"] / K if per_unit else None
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "k_photons<float>" if r["precision"] == 32 else "k_photons<double>",
+                "kernel_ms_per_launch": r["photon_seconds"] * 1e3 / K,
+                "algorithmic_bytes_per_launch": r["photon_algo_bytes"] / K,
+                "units_per_launch": r["photon_steps"] / K, "bytes_per_unit": BYTES_PER_STEP[r["precision"]]}
+
+    def roof_step(r):
+        # every kernel of the step (photons, electrons/positrons/ions, in-step products)
         ach = r["algo_bytes"] / r["kernel_seconds"] / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "peak_source": peak_kind,
-                "kernel": "k_step<float>" if r["precision"] == 32 else "k_step<double>",
-                "kernel_ms_per_launch": r["kernel_seconds"] * 1e3 / K,
-                "algorithmic_bytes_per_launch": r["algo_bytes"] / K}
+                "kernels_ms_per_step": r["kernel_seconds"] * 1e3 / K,
+                "algorithmic_bytes_per_step": r["algo_bytes"] / K}
 
     line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -370,12 +394,14 @@ def main():
                        "l2": "flushed between timed steps (256 MiB write)",
                        "compact_interval": COMPACT_INTERVAL},
             "roofline": roof(r32),
+            "roofline_step": roof_step(r32),
             "gpu_launches": r32["launches"],
             "clocks": r32["clocks"],
             "events": {"emissions": r32["emissions"], "pairs": r32["pairs"], "substeps": r32["substeps"],
                        "live_at_end": r32["live_end"]}}
     if out64 is not None:
         line["fp64"] = {"value": out64["value"], "ms_per_step": out64["ms_per_step"], "roofline": roof(r64),
+                        "roofline_step": roof_step(r64),
                         "speedup_fp32_over_fp64": value / out64["value"], "clocks": r64["clocks"]}
     if e2e is not None:
         line["e2e"] = {"value": e2e_val, "unit": "particle-steps/s",

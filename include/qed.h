@@ -142,6 +142,7 @@ typedef struct qed_diag {
     int64_t count[4];           /* live particles per species */
     int64_t particle_steps;     /* sum over steps of the live particles at the
                                    start of each step (all species) */
+    int64_t species_steps[4];   /* the same sum per species */
     int64_t emissions, pairs;   /* events since qed_init */
     int64_t substeps_lepton, substeps_photon;
     int64_t pm_gt1, pp_gt1;     /* draws where P_m > 1 or P_p > 1 */
@@ -228,12 +229,13 @@ int qed_step(qed_ctx *ctx, const qed_fields *fields, double dt, int32_t nsteps, 
  * streams are keyed by the step, so a restart reproduces a run exactly). */
 int qed_set_clock(qed_ctx *ctx, int64_t step, double time);
 
-/* Profiling aid: record the CUDA events start and stop (cudaEvent_t passed
- * as void*, created by the caller on the context's device) immediately
- * before and after the particle-step kernel of every following step, on the
- * stream of that step.  NULL, NULL stops recording.  The events are not
- * owned by the library. */
-int qed_profile_events(qed_ctx *ctx, void *start, void *stop);
+/* Profiling aid: record CUDA events (cudaEvent_t passed as void*, created by
+ * the caller on the context's device) around the kernels of every following
+ * step, on the stream of that step: start before the first step kernel,
+ * photon_done after the photon kernel (may be NULL), stop after the last
+ * step kernel (compaction excluded).  All NULL stops recording.  The events
+ * are not owned by the library. */
+int qed_profile_events(qed_ctx *ctx, void *start, void *photon_done, void *stop);
 
 /* Synchronise the stream and read counters, live counts, spectra and the
  * device status into *out (host struct).  Returns the device status. */

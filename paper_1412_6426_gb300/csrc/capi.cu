@@ -52,6 +52,7 @@ void release(qed_ctx *c) {
   cudaFree(c->d_barrier);
   cudaFree(c->d_tables);
   cudaFree(c->d_chi_star);
+  cudaFree(c->d_eps_star);
   cudaFree(c->d_tile);
   cudaFree(c->stage);
 }
@@ -184,7 +185,8 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
   c->tables_bytes = table_bytes(c->prec);
   if (rc == QED_OK) rc = dalloc(&c->d_tables, c->tables_bytes);
   if (rc == QED_OK) rc = dalloc(&c->d_chi_star, sizeof(double));
-  c->tile_cap = (max_cap + qed::kCompactTile - 1) / qed::kCompactTile + 2;
+  if (rc == QED_OK) rc = dalloc(&c->d_eps_star, sizeof(double));
+  c->tile_cap = 2 * ((max_cap + qed::kCompactTile - 1) / qed::kCompactTile + 2);   // two classes
   if (rc == QED_OK) rc = dalloc(&c->d_tile, sizeof(long long) * c->tile_cap);
   if (rc == QED_OK) {
     cudaMemsetAsync(c->d_count, 0, 4 * sizeof(long long), s);
@@ -247,7 +249,7 @@ int qed_particles_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint6
                       int64_t *n_out, void *stream) {
   if (!c || sp < 0 || sp >= QED_NSPECIES || !n_out || max_n < 0) return QED_ERR_ARG;
   cudaStream_t s = as_stream(stream);
-  int rc = qed_launch_compact(c, sp, s);
+  int rc = qed_launch_compact(c, sp, false, s);
   if (rc != QED_OK) return rc;
   long long n = 0;
   if (cudaMemcpyAsync(&n, c->d_count + sp, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -300,7 +302,7 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
     if (c->par.compact_interval > 0 && ++c->steps_since_compact >= c->par.compact_interval) {
       c->steps_since_compact = 0;
       for (int sp = 0; sp < 4; ++sp) {
-        rc = qed_launch_compact(c, sp, s);
+        rc = qed_launch_compact(c, sp, true, s);
         if (rc != QED_OK) return rc;
       }
     }
@@ -315,9 +317,10 @@ int qed_set_clock(qed_ctx *c, int64_t step, double time) {
   return QED_OK;
 }
 
-int qed_profile_events(qed_ctx *c, void *start, void *stop) {
-  if (!c || (start == nullptr) != (stop == nullptr)) return QED_ERR_ARG;
+int qed_profile_events(qed_ctx *c, void *start, void *photon_done, void *stop) {
+  if (!c || (start == nullptr) != (stop == nullptr) || (photon_done && !start)) return QED_ERR_ARG;
   c->ev_start = (cudaEvent_t)start;
+  c->ev_photon = (cudaEvent_t)photon_done;
   c->ev_stop = (cudaEvent_t)stop;
   return QED_OK;
 }
@@ -359,7 +362,11 @@ int qed_diagnostics(qed_ctx *c, qed_diag *out, void *stream) {
   out->absorbed = (int64_t)cnt[qed::kCntAbsorbed];
   out->overflow = (int64_t)cnt[qed::kCntOverflow];
   out->nonfinite = (int64_t)cnt[qed::kCntNonfinite];
-  out->particle_steps = (int64_t)cnt[qed::kCntParticleSteps];
+  out->particle_steps = 0;
+  for (int k = 0; k < 4; ++k) {
+    out->species_steps[k] = (int64_t)cnt[qed::kCntSpeciesSteps + k];
+    out->particle_steps += out->species_steps[k];
+  }
   out->kernel_launches = launches;
   out->step = c->step;
   out->time = c->time;

@@ -14,7 +14,7 @@ constexpr int kMaxPass = 64;        // nesting depth of products within one step
 constexpr int kNumCounters = 16;    // device diagnostic counters
 enum Counter {
   kCntEmissions = 0, kCntPairs, kCntSubLepton, kCntSubPhoton, kCntPmGt1, kCntPpGt1, kCntCapped,
-  kCntAbsorbed, kCntOverflow, kCntNonfinite, kCntParticleSteps
+  kCntAbsorbed, kCntOverflow, kCntNonfinite, kCntSpeciesSteps /* 4 slots: live particles per species */
 };
 constexpr int kMaxBins = 4096;
 constexpr int kCompactTile = 2048;   // particles per tile of the compaction
@@ -96,6 +96,7 @@ struct qed_ctx {
   unsigned *d_barrier = nullptr;
   void *d_tables = nullptr;
   double *d_chi_star = nullptr;       // pair-skip threshold derived from the tables
+  double *d_eps_star = nullptr;       // photons below this |p| cannot pair in the analytic field
   size_t tables_bytes = 0;
   long long *d_tile = nullptr;        // compaction tile counts/offsets
   long long tile_cap = 0;
@@ -109,7 +110,8 @@ struct qed_ctx {
   int64_t steps_since_compact = 0;
   void *stage = nullptr;              // staging for pageable host I/O
   size_t stage_bytes = 0;
-  cudaEvent_t ev_start = nullptr;     // recorded around the step kernel
+  cudaEvent_t ev_start = nullptr;     // recorded around the step kernels
+  cudaEvent_t ev_photon = nullptr;
   cudaEvent_t ev_stop = nullptr;
   int64_t launches = 0;               // kernels launched by this context
 };
@@ -122,6 +124,6 @@ int qed_launch_set(qed_ctx *c, int sp, const double *x, const double *p, const d
                    const uint64_t *id, int64_t n, cudaStream_t s);
 int qed_launch_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t *id, int64_t n,
                    cudaStream_t s);
-int qed_launch_compact(qed_ctx *c, int sp, cudaStream_t s);
+int qed_launch_compact(qed_ctx *c, int sp, bool partition, cudaStream_t s);
 int qed_step_kernel_blocks(qed_ctx *c);
 int qed_launch_chi_star(qed_ctx *c, cudaStream_t s);

@@ -42,7 +42,8 @@ template <typename R> struct Pend {
 };
 
 struct Cnt {
-  unsigned long long sub_l = 0, sub_g = 0, psteps = 0;
+  unsigned long long sub_l = 0, sub_g = 0;
+  unsigned psteps[4] = {0, 0, 0, 0};   // live particles advanced, per species
   unsigned emis = 0, pairs = 0, pm1 = 0, pp1 = 0, capped = 0, absorbed = 0, overflow = 0, nonfin = 0;
 };
 
@@ -122,6 +123,12 @@ struct StepConst {
   float curv;                // -omega / (4 pi): curvature phase in cycles per r^2/R
   float env_k;               // -2 ln 2 / tau^2
   float amp0, phi0_cyc;      // E0 and the phase offset in cycles
+  // Bound on a photon's effective field anywhere in this step (analytic
+  // fields only; infinite on the grid) and whether a photon with H <= hmax
+  // is always advanced in a single sub-interval.
+  double hmax;
+  float hmax_f;              // hmax rounded up, for the FP32 comparison
+  int one_interval;
 };
 
 __device__ __forceinline__ unsigned long long cycles_fixed(double cyc) {
@@ -153,6 +160,18 @@ __device__ double photon_chi_star(const R *tab, double kappa) {
 
 template <typename R>
 __device__ void step_constants(const StepArgs<R> &a, StepConst &k) {
+  // H^g_eff = |E + n x B|_perp <= |E| + |B| (Eq. (32))
+  k.hmax = INFINITY;
+  if (a.field_mode == kFieldUniform)
+    k.hmax = sqrt(a.fp[0] * a.fp[0] + a.fp[1] * a.fp[1] + a.fp[2] * a.fp[2]) +
+             sqrt(a.fp[3] * a.fp[3] + a.fp[4] * a.fp[4] + a.fp[5] * a.fp[5]);
+  else if (a.field_mode == kFieldRotatingE)
+    k.hmax = fabs(a.fp[0]);
+  else if (a.field_mode == kFieldGaussianLP)
+    k.hmax = 2.0 * fabs(a.fp[0]);             // |E| = |B| <= E0 everywhere
+  // N = ceil(dt H / (kappa 130 2 pi)) is 1 for every H <= hmax (margin 1e-3)
+  k.one_interval = (double)a.dt * k.hmax <= 0.999 * (double)a.kappa * 130.0 * kTwoPi;
+  k.hmax_f = (float)(k.hmax * 1.00001);
   for (int c = 0; c < 6; ++c) k.ud[c] = 0.0;
   if (a.field_mode == kFieldUniform) {
     for (int c = 0; c < 6; ++c) k.ud[c] = a.fp[c];
@@ -604,10 +623,11 @@ __device__ bool grid_barrier(unsigned *bar, int *status) {
 }
 
 __device__ __forceinline__ void flush(const Cnt &c, unsigned long long *g) {
-  unsigned long long v[kNumCounters] = {c.emis, c.pairs, c.sub_l, c.sub_g, c.pm1, c.pp1, c.capped,
-                                         c.absorbed, c.overflow, c.nonfin, c.psteps};
+  unsigned long long v[14] = {c.emis,     c.pairs,     c.sub_l,      c.sub_g,     c.pm1,
+                              c.pp1,      c.capped,    c.absorbed,   c.overflow,  c.nonfin,
+                              c.psteps[0], c.psteps[1], c.psteps[2], c.psteps[3]};
 #pragma unroll
-  for (int k = 0; k < 11; ++k) {
+  for (int k = 0; k < 14; ++k) {
     unsigned long long x = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -652,7 +672,7 @@ __global__ void __launch_bounds__(256, (Pass0Occ<R, PHOTON>::blocks)) k_pass0(co
     int cell;
     load(a, sp, i, q, cell);
     if (cell < 0) continue;
-    cnt.psteps++;
+    cnt.psteps[sp]++;
     const unsigned row = fast_div((unsigned)cell, a.div_m[0], a.div_l[0]);
     const unsigned slab = fast_div((unsigned)cell, a.div_m[1], a.div_l[1]);
     q.ci[0] = cell - (int)row * a.n[0];
@@ -747,21 +767,41 @@ __global__ void __launch_bounds__(kPhotonThreads, PhotonOcc<R>::blocks) k_photon
     int cell;
     unpack(slot[st][0][threadIdx.x], slot[st][1][threadIdx.x], q, cell);
     if (cell < 0) continue;
-    cnt.psteps++;
+    cnt.psteps[kPhoton]++;
     const unsigned row = fast_div((unsigned)cell, a.div_m[0], a.div_l[0]);
     const unsigned slab = fast_div((unsigned)cell, a.div_m[1], a.div_l[1]);
     q.ci[0] = cell - (int)row * a.n[0];
     q.ci[1] = (int)row - (int)slab * a.n[1];
     q.ci[2] = (int)slab;
-    V3<R> E, B;
-    if (a.field_mode == kFieldGrid) gather_grid(a, q, E, B);
-    else field_analytic(a, kc, q, E, B);
-    const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
-    if (!(probe == R(0))) {
-      cnt.nonfin++;
-      atomicOr(a.status, kStNonfinite);
+    bool alive = true;
+    const R eps = sqrt_r(dot(q.p, q.p));
+    const R hmax = sizeof(R) == 4 ? (R)kc.hmax_f : (R)kc.hmax;
+    if (!a.pairs_on || (kc.one_interval && eps * hmax < R(0.99999) * chi_star)) {
+      // This photon cannot pair in this step (chi_g <= eps hmax < chi*) and
+      // takes one sub-interval: its step is the straight flight of
+      // advance_photon with N = 1, without evaluating the field.
+      if (!(q.p.x * R(0) + q.p.y * R(0) + q.p.z * R(0) == R(0))) {
+        cnt.nonfin++;
+        atomicOr(a.status, kStNonfinite);
+      }
+      V3<R> dir = {R(0), R(0), R(0)};
+      if (eps > R(0)) {
+        const R ie = R(1) / eps;
+        dir = {q.p.x * ie, q.p.y * ie, q.p.z * ie};
+      }
+      move(a, q, dir, a.dt);
+      if (a.pairs_on) cnt.sub_g++;
+    } else {
+      V3<R> E, B;
+      if (a.field_mode == kFieldGrid) gather_grid(a, q, E, B);
+      else field_analytic(a, kc, q, E, B);
+      const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
+      if (!(probe == R(0))) {
+        cnt.nonfin++;
+        atomicOr(a.status, kStNonfinite);
+      }
+      alive = advance_photon(a, 0, q, a.dt, E, B, cnt, a.id[kPhoton] + i, chi_star);
     }
-    const bool alive = advance_photon(a, 0, q, a.dt, E, B, cnt, a.id[kPhoton] + i, chi_star);
     const int nc = alive ? finish_cell(a, q) : -1;
     if (alive && nc < 0) cnt.absorbed++;
     // a photon's momentum never changes: its momentum record is rewritten
@@ -884,6 +924,7 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   if (c->ev_start) cudaEventRecord(c->ev_start, s);
   c->launches += 2;
   e = cudaLaunchKernel((const void *)k_photons<R>, dim3(c->blocks_photon), dim3(kPhotonThreads), args, 0, s);
+  if (c->ev_photon) cudaEventRecord(c->ev_photon, s);
   if (e == cudaSuccess)
     e = cudaLaunchKernel((const void *)k_pass0<R, false>, dim3(c->blocks_massive), dim3(256), args, 0, s);
   if (e == cudaSuccess && a.same_step) {
@@ -898,9 +939,22 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
 }  // namespace qed
 
 namespace {
+// chi* of the pair skip, and eps* = chi*/H_max: photons below eps* cannot
+// pair anywhere in an analytic field whose effective field is bounded by
+// H_max (|E| + |B|); zero on the grid, where no bound is known.
 template <typename R>
-__global__ void k_chi_star(const R *tab, double kappa, double *out) {
-  *out = qed::photon_chi_star(tab, kappa);
+__global__ void k_chi_star(const R *tab, double kappa, int mode, qed_grid_desc g, double *chi, double *eps) {
+  const double cs = qed::photon_chi_star(tab, kappa);
+  *chi = cs;
+  double hmax = 0.0;
+  if (mode == qed::kFieldUniform)
+    hmax = sqrt(g.fp[0] * g.fp[0] + g.fp[1] * g.fp[1] + g.fp[2] * g.fp[2]) +
+           sqrt(g.fp[3] * g.fp[3] + g.fp[4] * g.fp[4] + g.fp[5] * g.fp[5]);
+  else if (mode == qed::kFieldRotatingE)
+    hmax = fabs(g.fp[0]);
+  else if (mode == qed::kFieldGaussianLP)
+    hmax = 2.0 * fabs(g.fp[0]);
+  *eps = hmax > 0.0 ? 0.999 * cs / hmax : 0.0;
 }
 
 template <typename R>
@@ -926,9 +980,11 @@ int qed_step_kernel_blocks(qed_ctx *c) {
 int qed_launch_chi_star(qed_ctx *c, cudaStream_t s) {
   c->launches += 1;
   if (c->prec == 64)
-    k_chi_star<double><<<1, 1, 0, s>>>((const double *)c->d_tables, c->par.kappa, c->d_chi_star);
+    k_chi_star<double><<<1, 1, 0, s>>>((const double *)c->d_tables, c->par.kappa, c->grid.field_mode, c->grid,
+                                       c->d_chi_star, c->d_eps_star);
   else
-    k_chi_star<float><<<1, 1, 0, s>>>((const float *)c->d_tables, c->par.kappa, c->d_chi_star);
+    k_chi_star<float><<<1, 1, 0, s>>>((const float *)c->d_tables, c->par.kappa, c->grid.field_mode, c->grid,
+                                      c->d_chi_star, c->d_eps_star);
   return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 

@@ -98,53 +98,84 @@ __global__ void k_get(const typename Rec<R>::T *pos, const typename Rec<R>::T *m
 // ----- compaction ----------------------------------------------------------
 // Tiles of kCompactTile records, processed in rounds of 256 consecutive
 // records so that loads stay coalesced and the output keeps the input order.
+// Optionally the live records are split into two classes, class 1 placed
+// after class 0 (each class in input order): photons whose momentum is below
+// eps_star cannot convert to pairs in the analytic field of the run, and
+// gathering them lets whole warps take the photon kernel's short path.
+// Layout of tiles: [0] records scanned, [1] live total, [2 + t] class-0
+// count/offset of tile t, [2 + maxt + t] the same for class 1.
+__device__ __forceinline__ float p2_of(const float4 &m) { return m.x * m.x + m.y * m.y + m.z * m.z; }
+__device__ __forceinline__ double p2_of(const D4 &m) { return m.a.x * m.a.x + m.a.y * m.a.y + m.b.x * m.b.x; }
+
 template <typename T>
-__global__ void k_tile_count(const T *mom, const long long *count, int sp, long long cap, long long *tiles) {
-  __shared__ unsigned wsum[8];
+__device__ __forceinline__ int record_class(const T &m, double eps2) {
+  if (cell_of(m) < 0) return -1;
+  return (double)p2_of(m) < eps2 ? 1 : 0;
+}
+
+template <typename T>
+__global__ void k_tile_count(const T *mom, const long long *count, int sp, long long cap, long long *tiles,
+                             long long maxt, const double *eps_star) {
+  __shared__ unsigned wsum[2][8];
   const long long n = min(count[sp], cap);  // count exceeds cap after an overflow
+  const double e = eps_star ? *eps_star : 0.0;
+  const double eps2 = e * e;
   if (blockIdx.x == 0 && threadIdx.x == 0) tiles[0] = n;
   const long long ntiles = (n + kCompactTile - 1) / kCompactTile;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    unsigned mine = 0;
+    unsigned c0 = 0, c1 = 0;
     for (int r = 0; r < kCompactTile / 256; ++r) {
       long long i = t * kCompactTile + r * 256 + threadIdx.x;
-      mine += (i < n && cell_of(mom[i]) >= 0) ? 1u : 0u;
+      const int cls = i < n ? record_class(mom[i], eps2) : -1;
+      c0 += cls == 0;
+      c1 += cls == 1;
     }
-    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = mine;
+    for (int o = 16; o > 0; o >>= 1) {
+      c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+      c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      wsum[0][threadIdx.x >> 5] = c0;
+      wsum[1][threadIdx.x >> 5] = c1;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      unsigned s = 0;
-      for (int k = 0; k < 8; ++k) s += wsum[k];
-      tiles[2 + t] = s;
+      unsigned s0 = 0, s1 = 0;
+      for (int k = 0; k < 8; ++k) { s0 += wsum[0][k]; s1 += wsum[1][k]; }
+      tiles[2 + t] = s0;
+      tiles[2 + maxt + t] = s1;
     }
     __syncthreads();
   }
 }
 
-// Exclusive scan of the tile counts (one block); writes the live total.
-__global__ void k_tile_scan(long long *tiles, long long *count, int sp) {
+// Exclusive scans of the tile counts of class 0, then class 1 (continuing
+// after the class-0 total), in one block; writes the live total.
+__global__ void k_tile_scan(long long *tiles, long long *count, int sp, long long maxt) {
   __shared__ long long part[1024];
   __shared__ long long carry;
   const long long n = tiles[0];
   const long long ntiles = (n + kCompactTile - 1) / kCompactTile;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (long long base = 0; base < ntiles; base += 1024) {
-    long long i = base + threadIdx.x;
-    long long v = i < ntiles ? tiles[2 + i] : 0;
-    part[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-      long long add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+  for (int cls = 0; cls < 2; ++cls) {
+    long long *arr = tiles + 2 + cls * maxt;
+    for (long long base = 0; base < ntiles; base += 1024) {
+      long long i = base + threadIdx.x;
+      long long v = i < ntiles ? arr[i] : 0;
+      part[threadIdx.x] = v;
       __syncthreads();
-      part[threadIdx.x] += add;
+      for (int o = 1; o < 1024; o <<= 1) {
+        long long add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += add;
+        __syncthreads();
+      }
+      if (i < ntiles) arr[i] = carry + part[threadIdx.x] - v;
+      __syncthreads();
+      if (threadIdx.x == 1023) carry += part[1023];
       __syncthreads();
     }
-    if (i < ntiles) tiles[2 + i] = carry + part[threadIdx.x] - v;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry += part[1023];
-    __syncthreads();
   }
   if (threadIdx.x == 0) {
     count[sp] = carry;
@@ -154,31 +185,40 @@ __global__ void k_tile_scan(long long *tiles, long long *count, int sp) {
 
 template <typename T>
 __global__ void k_tile_scatter(const T *pos, const T *mom, const uint64_t *id, T *pos2, T *mom2,
-                               uint64_t *id2, const long long *tiles) {
-  __shared__ unsigned wcount[8];
+                               uint64_t *id2, const long long *tiles, long long maxt, const double *eps_star) {
+  __shared__ unsigned wcount[2][8];
   const long long n = tiles[0];
+  const double e = eps_star ? *eps_star : 0.0;
+  const double eps2 = e * e;
   const long long ntiles = (n + kCompactTile - 1) / kCompactTile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    long long out = tiles[2 + t];
+    long long out[2] = {tiles[2 + t], tiles[2 + maxt + t]};
     for (int r = 0; r < kCompactTile / 256; ++r) {
       long long i = t * kCompactTile + r * 256 + threadIdx.x;
-      bool live = i < n && cell_of(mom[i]) >= 0;
-      unsigned b = __ballot_sync(0xffffffffu, live);
-      if (lane == 0) wcount[warp] = __popc(b);
-      __syncthreads();
-      unsigned before = 0, all = 0;
-      for (int k = 0; k < 8; ++k) {
-        before += k < warp ? wcount[k] : 0u;
-        all += wcount[k];
+      const int cls = i < n ? record_class(mom[i], eps2) : -1;
+      const unsigned b0 = __ballot_sync(0xffffffffu, cls == 0);
+      const unsigned b1 = __ballot_sync(0xffffffffu, cls == 1);
+      if (lane == 0) {
+        wcount[0][warp] = __popc(b0);
+        wcount[1][warp] = __popc(b1);
       }
-      if (live) {
-        long long o = out + before + __popc(b & ((1u << lane) - 1u));
+      __syncthreads();
+      unsigned before[2] = {0, 0}, all[2] = {0, 0};
+      for (int k = 0; k < 8; ++k)
+        for (int c = 0; c < 2; ++c) {
+          before[c] += k < warp ? wcount[c][k] : 0u;
+          all[c] += wcount[c][k];
+        }
+      if (cls >= 0) {
+        const unsigned b = cls ? b1 : b0;
+        long long o = out[cls] + before[cls] + __popc(b & ((1u << lane) - 1u));
         pos2[o] = pos[i];
         mom2[o] = mom[i];
         id2[o] = id[i];
       }
-      out += all;
+      out[0] += all[0];
+      out[1] += all[1];
       __syncthreads();
     }
   }
@@ -232,19 +272,22 @@ int get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t *id, int64
 }
 
 template <typename R>
-int compact(qed_ctx *c, int sp, cudaStream_t s) {
+int compact(qed_ctx *c, int sp, bool partition, cudaStream_t s) {
   using T = typename Rec<R>::T;
   Store &st = c->st[sp];
   if (st.cap == 0) return QED_OK;
   int cur = st.cur, nxt = cur ^ 1;
   long long maxtiles = (st.cap + kCompactTile - 1) / kCompactTile;
+  const long long maxt = c->tile_cap / 2;
   int g = (int)(maxtiles < (long long)c->num_sms * 8 ? maxtiles : (long long)c->num_sms * 8);
   if (g < 1) g = 1;
+  const double *eps = (partition && sp == kPhoton) ? c->d_eps_star : nullptr;
   c->launches += 3;
-  k_tile_count<T><<<g, 256, 0, s>>>((const T *)st.mom[cur], c->d_count, sp, (long long)st.cap, c->d_tile);
-  k_tile_scan<<<1, 1024, 0, s>>>(c->d_tile, c->d_count, sp);
+  k_tile_count<T><<<g, 256, 0, s>>>((const T *)st.mom[cur], c->d_count, sp, (long long)st.cap, c->d_tile,
+                                    maxt, eps);
+  k_tile_scan<<<1, 1024, 0, s>>>(c->d_tile, c->d_count, sp, maxt);
   k_tile_scatter<T><<<g, 256, 0, s>>>((const T *)st.pos[cur], (const T *)st.mom[cur], st.id[cur],
-                                       (T *)st.pos[nxt], (T *)st.mom[nxt], st.id[nxt], c->d_tile);
+                                       (T *)st.pos[nxt], (T *)st.mom[nxt], st.id[nxt], c->d_tile, maxt, eps);
   if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
   st.cur = nxt;
   return QED_OK;
@@ -279,8 +322,8 @@ int qed_launch_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t
   return c->prec == 64 ? qed::get<double>(c, sp, x, p, w, id, n, s) : qed::get<float>(c, sp, x, p, w, id, n, s);
 }
 
-int qed_launch_compact(qed_ctx *c, int sp, cudaStream_t s) {
-  return c->prec == 64 ? qed::compact<double>(c, sp, s) : qed::compact<float>(c, sp, s);
+int qed_launch_compact(qed_ctx *c, int sp, bool partition, cudaStream_t s) {
+  return c->prec == 64 ? qed::compact<double>(c, sp, partition, s) : qed::compact<float>(c, sp, partition, s);
 }
 
 int qed_launch_count_live(qed_ctx *c, long long *d_live, cudaStream_t s) {

@@ -53,8 +53,9 @@ class QedFields(ctypes.Structure):
 
 
 class QedDiag(ctypes.Structure):
-    _fields_ = [("count", ctypes.c_int64 * 4)] + [(k, ctypes.c_int64) for k in (
-        "particle_steps", "emissions", "pairs", "substeps_lepton", "substeps_photon", "pm_gt1",
+    _fields_ = [("count", ctypes.c_int64 * 4), ("particle_steps", ctypes.c_int64),
+                ("species_steps", ctypes.c_int64 * 4)] + [(k, ctypes.c_int64) for k in (
+        "emissions", "pairs", "substeps_lepton", "substeps_photon", "pm_gt1",
         "pp_gt1", "capped", "absorbed", "overflow", "nonfinite", "kernel_launches", "step")] + [
         ("time", ctypes.c_double), ("status", ctypes.c_int32), ("nbins", ctypes.c_int32),
         ("spectrum", ctypes.POINTER(ctypes.c_double)),
@@ -81,7 +82,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qed_step.argtypes = [vp, ctypes.POINTER(QedFields), ctypes.c_double, i32, vp]
     lib.qed_particles_read_static.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp, i64, ctypes.POINTER(i64), vp]
     lib.qed_set_clock.argtypes = [vp, i64, ctypes.c_double]
-    lib.qed_profile_events.argtypes = [vp, vp, vp]
+    lib.qed_profile_events.argtypes = [vp, vp, vp, vp]
     lib.qed_diagnostics.argtypes = [vp, ctypes.POINTER(QedDiag), vp]
     lib.qed_destroy.argtypes = [vp]
     lib.qed_error_string.argtypes = [ctypes.c_int]
@@ -165,8 +166,9 @@ def qed_set_clock(ctx: int, step: int, time: float) -> None:
     _check("qed_set_clock", load().qed_set_clock(ctypes.c_void_p(ctx), int(step), float(time)))
 
 
-def qed_profile_events(ctx: int, start_event: int, stop_event: int) -> None:
+def qed_profile_events(ctx: int, start_event: int, photon_event: int, stop_event: int) -> None:
     _check("qed_profile_events", load().qed_profile_events(ctypes.c_void_p(ctx), ctypes.c_void_p(start_event),
+                                                           ctypes.c_void_p(photon_event),
                                                            ctypes.c_void_p(stop_event)))
 
 
@@ -181,8 +183,10 @@ def qed_diagnostics(ctx: int, nbins: int = 0, stream: int = 0, check: bool = Tru
     rc = load().qed_diagnostics(ctypes.c_void_p(ctx), ctypes.byref(d), ctypes.c_void_p(stream))
     if check:
         _check("qed_diagnostics", rc)
-    out = {k: getattr(d, k) for k, _ in QedDiag._fields_[1:15]}
+    out = {k: getattr(d, k) for k, _ in QedDiag._fields_[3:16]}
     out["count"] = list(d.count)
+    out["particle_steps"] = d.particle_steps
+    out["species_steps"] = list(d.species_steps)
     out["time"] = d.time
     out["status"] = d.status
     if nbins:

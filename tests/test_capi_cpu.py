@@ -65,7 +65,8 @@ int main(void) {
          sizeof(qed_diag));
   P(qed_grid_desc, d); P(qed_grid_desc, field_mode); P(qed_grid_desc, fp);
   P(qed_params, seed); P(qed_params, kappa); P(qed_params, pending_capacity);
-  P(qed_diag, particle_steps); P(qed_diag, time); P(qed_diag, status); P(qed_diag, spectrum);
+  P(qed_diag, particle_steps); P(qed_diag, species_steps); P(qed_diag, emissions);
+  P(qed_diag, time); P(qed_diag, status); P(qed_diag, spectrum);
   P(qed_species_desc, charge); P(qed_fields, J);
   return 0;
 }
