@@ -8,6 +8,7 @@
 
 size_t qed_record_bytes(int prec);
 size_t qed_pend_bytes(int prec);
+size_t qed_step_const_bytes();
 int qed_launch_count_live(qed_ctx *c, long long *d_live, cudaStream_t s);
 
 namespace {
@@ -53,6 +54,7 @@ void release(qed_ctx *c) {
   cudaFree(c->d_tables);
   cudaFree(c->d_chi_star);
   cudaFree(c->d_eps_star);
+  cudaFree(c->d_step_const);
   cudaFree(c->d_tile);
   cudaFree(c->stage);
 }
@@ -186,6 +188,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
   if (rc == QED_OK) rc = dalloc(&c->d_tables, c->tables_bytes);
   if (rc == QED_OK) rc = dalloc(&c->d_chi_star, sizeof(double));
   if (rc == QED_OK) rc = dalloc(&c->d_eps_star, sizeof(double));
+  if (rc == QED_OK) rc = dalloc(&c->d_step_const, qed_step_const_bytes());
   c->tile_cap = 2 * ((max_cap + qed::kCompactTile - 1) / qed::kCompactTile + 2);   // two classes
   if (rc == QED_OK) rc = dalloc(&c->d_tile, sizeof(long long) * c->tile_cap);
   if (rc == QED_OK) {

@@ -67,6 +67,7 @@ template <typename R> struct StepArgs {
   R charge[4], mass[4];
   const R *tab;
   const double *chi_star;  // photons below this chi_g cannot pair (per context)
+  void *step_const;        // per-step field constants (written by k_step_constants)
   // diagnostics
   unsigned long long *counters;
   double *spectrum, *spectrum_energy;
@@ -97,6 +98,7 @@ struct qed_ctx {
   void *d_tables = nullptr;
   double *d_chi_star = nullptr;       // pair-skip threshold derived from the tables
   double *d_eps_star = nullptr;       // photons below this |p| cannot pair in the analytic field
+  void *d_step_const = nullptr;       // per-step field constants
   size_t tables_bytes = 0;
   long long *d_tile = nullptr;        // compaction tile counts/offsets
   long long tile_cap = 0;

@@ -108,7 +108,7 @@ __device__ __forceinline__ float r2_floor(float) { return 0x1p-24f; }
 // ----- fields --------------------------------------------------------------
 // Per-step constants of the analytic fields, formed once per block in FP64
 // by one thread, so that the per-particle FP32 work needs no FP64 at all.
-struct StepConst {
+struct alignas(8) StepConst {
   double ud[6];              // uniform / rotating: E and B
   float uf[6];
   // Gaussian pulse: carrier phase in cycles = frac(c0 + i * kfix) + off * kf,
@@ -639,11 +639,17 @@ __device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m, int l) {
   return (__umulhi(n, m) + n) >> l;   // exact for n < 2^31 (Granlund-Montgomery)
 }
 
+// The per-step field constants, formed once per step in FP64 by one thread.
+template <typename R>
+__global__ void k_step_constants(const StepArgs<R> a) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) step_constants(a, *(StepConst *)a.step_const);
+}
+
 // Pass 0 of one particle family.  PHOTON: the photon store; otherwise
 // electrons, positrons and ions.  Resident blocks per SM set the register
 // budget: the photon path is light enough for four 256-thread blocks.
 template <typename R, bool PHOTON> struct Pass0Occ;
-template <> struct Pass0Occ<float, false> { static constexpr int blocks = 2; };
+template <> struct Pass0Occ<float, false> { static constexpr int blocks = 3; };
 template <> struct Pass0Occ<double, false> { static constexpr int blocks = 1; };
 
 template <typename R, bool PHOTON>
@@ -651,7 +657,8 @@ __global__ void __launch_bounds__(256, (Pass0Occ<R, PHOTON>::blocks)) k_pass0(co
   Cnt cnt;
   __shared__ long long ns[4];
   __shared__ StepConst kc;
-  if (threadIdx.x == 0) step_constants(a, kc);
+  if (threadIdx.x < (int)(sizeof(StepConst) / 8))
+    ((unsigned long long *)&kc)[threadIdx.x] = ((const unsigned long long *)a.step_const)[threadIdx.x];
   // an overflowing append leaves count above the capacity: never read past it
   if (threadIdx.x < 4) ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
   __syncthreads();
@@ -735,7 +742,8 @@ __global__ void __launch_bounds__(kPhotonThreads, PhotonOcc<R>::blocks) k_photon
   __shared__ __align__(16) T slot[kStages][2][kPhotonThreads];
   __shared__ StepConst kc;
   Cnt cnt;
-  if (threadIdx.x == 0) step_constants(a, kc);
+  if (threadIdx.x < (int)(sizeof(StepConst) / 8))
+    ((unsigned long long *)&kc)[threadIdx.x] = ((const unsigned long long *)a.step_const)[threadIdx.x];
   __syncthreads();
   const long long n = min(a.nstart[kPhoton], a.cap[kPhoton]);
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -899,6 +907,7 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   a.step = (unsigned)c->step;
   a.tab = (const R *)c->d_tables;
   a.chi_star = c->d_chi_star;
+  a.step_const = c->d_step_const;
   a.counters = c->d_counters;
   a.spectrum = c->d_spec;
   a.spectrum_energy = c->d_spec_e;
@@ -922,8 +931,10 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   void *args[] = {(void *)&a};
   cudaError_t e;
   if (c->ev_start) cudaEventRecord(c->ev_start, s);
-  c->launches += 2;
-  e = cudaLaunchKernel((const void *)k_photons<R>, dim3(c->blocks_photon), dim3(kPhotonThreads), args, 0, s);
+  c->launches += 3;
+  e = cudaLaunchKernel((const void *)k_step_constants<R>, dim3(1), dim3(32), args, 0, s);
+  if (e == cudaSuccess)
+    e = cudaLaunchKernel((const void *)k_photons<R>, dim3(c->blocks_photon), dim3(kPhotonThreads), args, 0, s);
   if (c->ev_photon) cudaEventRecord(c->ev_photon, s);
   if (e == cudaSuccess)
     e = cudaLaunchKernel((const void *)k_pass0<R, false>, dim3(c->blocks_massive), dim3(256), args, 0, s);
@@ -991,6 +1002,8 @@ int qed_launch_chi_star(qed_ctx *c, cudaStream_t s) {
 int qed_launch_step(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   return c->prec == 64 ? qed::launch<double>(c, f, dt, s) : qed::launch<float>(c, f, dt, s);
 }
+
+size_t qed_step_const_bytes() { return sizeof(qed::StepConst); }
 
 size_t qed_pend_bytes(int prec) {
   return prec == 64 ? sizeof(qed::Pend<double>) : sizeof(qed::Pend<float>);
