@@ -42,10 +42,12 @@ L2_FLUSH_BYTES = 256 << 20
 BYTES_PER_STEP = {32: 68, 64: 120}
 BYTES_PER_APPEND = {32: 40, 64: 68}
 # DRAM bytes (read + write) per photon-step of the photon kernel, from one ncu
-# capture of k_photons at the collision step of the 2.5e5-electron beam
-# (dram__bytes_read.sum + dram__bytes_write.sum / live photons); empty until
-# measured for the current kernel
-PHOTON_DRAM_BYTES_PER_STEP = {}
+# capture of k_photons at the collision step (step 300) of the 2.5e5-electron
+# beam: (dram__bytes_read.sum + dram__bytes_write.sum) / live photons.  The
+# kernel's traffic is proportional to the records it touches, so the bench
+# scales it by the photons of its own launches.  Remove an entry when the
+# kernel changes until it is measured again.
+PHOTON_DRAM_BYTES_PER_STEP = {32: 258.73e6 / 5.567e6}
 METRIC = "particle-steps/s with QED events, FP32 vs FP64 GPU path; % of HBM roofline"
 WORKLOAD_NAME = ("beam-laser head-on collision: 1e6 e- at 1 GeV (1% spread, 1 um x 3 um rms), "
                  "LP Gaussian pulse lambda=0.8 um a0=200 30 fs FWHM w0=2 um, analytic field, "
