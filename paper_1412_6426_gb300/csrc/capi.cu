@@ -9,6 +9,7 @@
 size_t qed_record_bytes(int prec);
 size_t qed_pend_bytes(int prec);
 size_t qed_step_const_bytes();
+size_t qed_clock_bytes();
 int qed_launch_count_live(qed_ctx *c, long long *d_live, cudaStream_t s);
 
 namespace {
@@ -55,6 +56,7 @@ void release(qed_ctx *c) {
   cudaFree(c->d_chi_star);
   cudaFree(c->d_eps_star);
   cudaFree(c->d_step_const);
+  cudaFree(c->d_clock);
   cudaFree(c->d_tile);
   cudaFree(c->stage);
 }
@@ -189,6 +191,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
   if (rc == QED_OK) rc = dalloc(&c->d_chi_star, sizeof(double));
   if (rc == QED_OK) rc = dalloc(&c->d_eps_star, sizeof(double));
   if (rc == QED_OK) rc = dalloc(&c->d_step_const, qed_step_const_bytes());
+  if (rc == QED_OK) rc = dalloc(&c->d_clock, qed_clock_bytes());
   c->tile_cap = 2 * ((max_cap + qed::kCompactTile - 1) / qed::kCompactTile + 2);   // two classes
   if (rc == QED_OK) rc = dalloc(&c->d_tile, sizeof(long long) * c->tile_cap);
   if (rc == QED_OK) {
@@ -198,6 +201,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     cudaMemsetAsync(c->d_spec_e, 0, sizeof(double) * (p->nbins > 0 ? p->nbins : 1), s);
     cudaMemsetAsync(c->d_status, 0, sizeof(int) * 4, s);
     cudaMemsetAsync(c->d_barrier, 0, sizeof(unsigned) * 4, s);
+    cudaMemsetAsync(c->d_clock, 0, qed_clock_bytes(), s);    // t = 0, step = 0
     if (tables)
       rc = cudaMemcpyAsync(c->d_tables, tables, c->tables_bytes, cudaMemcpyHostToDevice, s) == cudaSuccess
                ? QED_OK : QED_ERR_CUDA;
@@ -301,7 +305,6 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
     if (rc == QED_OK && grid && c->par.deposit_on) rc = qed_launch_yee(c, f, dt, s);
     if (rc != QED_OK) return rc;
     c->step += 1;
-    c->time += dt;
     if (c->par.compact_interval > 0 && ++c->steps_since_compact >= c->par.compact_interval) {
       c->steps_since_compact = 0;
       for (int sp = 0; sp < 4; ++sp) {
@@ -315,8 +318,11 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
 
 int qed_set_clock(qed_ctx *c, int64_t step, double time) {
   if (!c || step < 0 || !std::isfinite(time)) return QED_ERR_ARG;
+  struct { double t; long long step; } clk = {time, (long long)step};
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(c->d_clock, &clk, sizeof(clk), cudaMemcpyHostToDevice) != cudaSuccess)
+    return QED_ERR_CUDA;
   c->step = step;
-  c->time = time;
   return QED_OK;
 }
 
@@ -339,7 +345,9 @@ int qed_diagnostics(qed_ctx *c, qed_diag *out, void *stream) {
   unsigned long long cnt[qed::kNumCounters];
   long long live[4];
   int bits = 0;
+  struct { double t; long long step; } clk = {0.0, 0};
   if (cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&clk, c->d_clock, sizeof(clk), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(live, d_live, sizeof(live), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(&bits, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return QED_ERR_CUDA;
@@ -371,8 +379,8 @@ int qed_diagnostics(qed_ctx *c, qed_diag *out, void *stream) {
     out->particle_steps += out->species_steps[k];
   }
   out->kernel_launches = launches;
-  out->step = c->step;
-  out->time = c->time;
+  out->step = clk.step;
+  out->time = clk.t;
   int st = fold_status(bits);
   out->status = st;
   if (st != QED_OK) c->latched = st;

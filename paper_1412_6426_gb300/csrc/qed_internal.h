@@ -55,7 +55,6 @@ template <typename R> struct StepArgs {
   // fields
   int field_mode;
   double fp[16];
-  double t;                // time at the start of the step
   const R *E[3];
   const R *B[3];
   R *J[3];
@@ -63,11 +62,13 @@ template <typename R> struct StepArgs {
   // generator
   R dt, kappa;
   int nsub_max, emission_on, pairs_on, same_step, pm_strict;
-  unsigned seed, step;
+  unsigned seed;
   R charge[4], mass[4];
   const R *tab;
   const double *chi_star;  // photons below this chi_g cannot pair (per context)
   void *step_const;        // per-step field constants (written by k_step_constants)
+  void *clock;             // device clock {t, step}: read and advanced once per step
+  double dt_d;             // the step in FP64 (advances the clock)
   // diagnostics
   unsigned long long *counters;
   double *spectrum, *spectrum_energy;
@@ -99,6 +100,8 @@ struct qed_ctx {
   double *d_chi_star = nullptr;       // pair-skip threshold derived from the tables
   double *d_eps_star = nullptr;       // photons below this |p| cannot pair in the analytic field
   void *d_step_const = nullptr;       // per-step field constants
+  void *d_clock = nullptr;            // {double t; long long step}: kernels advance it, so
+                                      // captured CUDA graphs replay correctly
   size_t tables_bytes = 0;
   long long *d_tile = nullptr;        // compaction tile counts/offsets
   long long tile_cap = 0;
@@ -106,8 +109,7 @@ struct qed_ctx {
   int blocks_photon = 0;              // grid sizes of the step kernels
   int blocks_massive = 0;
   int blocks_products = 0;
-  int64_t step = 0;
-  double time = 0.0;
+  int64_t step = 0;                   // host mirror of the clock (steps issued)
   int latched = 0;                    // a device error was observed
   int64_t steps_since_compact = 0;
   void *stage = nullptr;              // staging for pageable host I/O

@@ -129,6 +129,16 @@ struct alignas(8) StepConst {
   double hmax;
   float hmax_f;              // hmax rounded up, for the FP32 comparison
   int one_interval;
+  // the step's start time and index (they key the random streams)
+  double t;
+  unsigned step;
+  unsigned pad_;
+};
+
+// Device clock, advanced by the first kernel of every step.
+struct Clock {
+  double t;
+  long long step;
 };
 
 __device__ __forceinline__ unsigned long long cycles_fixed(double cyc) {
@@ -160,6 +170,9 @@ __device__ double photon_chi_star(const R *tab, double kappa) {
 
 template <typename R>
 __device__ void step_constants(const StepArgs<R> &a, StepConst &k) {
+  const Clock *clk = (const Clock *)a.clock;
+  k.t = clk->t;
+  k.step = (unsigned)clk->step;
   // H^g_eff = |E + n x B|_perp <= |E| + |B| (Eq. (32))
   k.hmax = INFINITY;
   if (a.field_mode == kFieldUniform)
@@ -176,13 +189,13 @@ __device__ void step_constants(const StepArgs<R> &a, StepConst &k) {
   if (a.field_mode == kFieldUniform) {
     for (int c = 0; c < 6; ++c) k.ud[c] = a.fp[c];
   } else if (a.field_mode == kFieldRotatingE) {
-    double cyc = a.fp[1] * a.t * (1.0 / kTwoPi);
+    double cyc = a.fp[1] * k.t * (1.0 / kTwoPi);
     double f = cyc - rint(cyc), s, c;
     sincospi(2.0 * f, &s, &c);
     k.ud[0] = a.fp[0] * c;
     k.ud[1] = a.fp[0] * s;
   } else if (a.field_mode == kFieldGaussianLP) {
-    double T0 = (a.t - a.fp[7]) - a.fp[4] + a.x0[0];
+    double T0 = (k.t - a.fp[7]) - a.fp[4] + a.x0[0];
     k.c0 = cycles_fixed(a.fp[1] * T0 * (1.0 / kTwoPi));
     double K = a.fp[1] * a.dd[0] * (1.0 / kTwoPi);
     k.kfix = cycles_fixed(K);
@@ -203,7 +216,7 @@ __device__ void step_constants(const StepArgs<R> &a, StepConst &k) {
   for (int c = 0; c < 6; ++c) k.uf[c] = (float)k.ud[c];
 }
 
-// Analytic fields at the particle position and time a.t (modes of qed.h).
+// Analytic fields at the particle position and the step's time (modes of qed.h).
 // FP32: no FP64 instruction; the carrier phase comes from StepConst.
 __device__ void field_analytic(const StepArgs<float> &a, const StepConst &k, const Pt<float> &q,
                                V3<float> &E, V3<float> &B) {
@@ -247,7 +260,7 @@ __device__ void field_analytic(const StepArgs<double> &a, const StepConst &k, co
   // zeta: distance travelled past the focus along -x; eta: retarded time
   const double xa = a.x0[0] + ((double)q.ci[0] + q.off[0]) * a.dd[0];
   const double zeta = a.fp[4] - xa;
-  const double eta = (a.t - a.fp[7]) - zeta;
+  const double eta = (k.t - a.fp[7]) - zeta;
   const double y = a.x0[1] - a.fp[5] + ((double)q.ci[1] + q.off[1]) * a.dd[1];
   const double z = a.x0[2] - a.fp[6] + ((double)q.ci[2] + q.off[2]) * a.dd[2];
   const double w = a.fp[1], w0 = a.fp[2], tau = a.fp[3];
@@ -488,7 +501,7 @@ __device__ __noinline__ void emit(const StepArgs<R> &a, int pass, int sp, Pt<R> 
 // Boris push and modified emission generator (Sec. IV.G); ions are pushed only.
 template <typename R>
 __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, R t_span,
-                                                V3<R> E, V3<R> B, Cnt &cnt, const uint64_t *idp) {
+                                                V3<R> E, V3<R> B, Cnt &cnt, const uint64_t *idp, unsigned step) {
   const int cs[3] = {q.ci[0], q.ci[1], q.ci[2]};
   const R os[3] = {q.off[0], q.off[1], q.off[2]};
   const R qc = a.charge[sp], m = a.mass[sp];
@@ -510,7 +523,7 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
     cnt.sub_l++;
     R chi = chi_lepton(q.p, g, E, B);
     R r1, r2;
-    draw2(q.id, a.step, (unsigned)s, kEmit, a.seed, r1, r2);
+    draw2(q.id, step, (unsigned)s, kEmit, a.seed, r1, r2);
     R pm = prob_emit(a.tab, r1, chi, g, h);
     if (pm > R(1)) {
       cnt.pm1++;
@@ -521,7 +534,7 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
       R delta = r1 * r1 * r1;
       Pt<R> ph = q;
       ph.p = {delta * q.p.x, delta * q.p.y, delta * q.p.z};
-      ph.id = child_id(q.id, a.step, (unsigned)s, kPhoton, a.seed);
+      ph.id = child_id(q.id, step, (unsigned)s, kPhoton, a.seed);
       R omd = R(1) - delta;
       q.p = {omd * q.p.x, omd * q.p.y, omd * q.p.z};
       cnt.emis++;
@@ -537,7 +550,7 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
 // idp: where to load the id from when a draw needs it (nullptr: q.id is set).
 template <typename R>
 __device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, Pt<R> &q, R t_span, V3<R> E,
-                                               V3<R> B, Cnt &cnt, const uint64_t *idp, R chi_star) {
+                                               V3<R> B, Cnt &cnt, const uint64_t *idp, R chi_star, unsigned step) {
   const R eps = sqrt_r(dot(q.p, q.p));
   V3<R> dir = {R(0), R(0), R(0)};
   if (eps > R(0)) {
@@ -566,7 +579,7 @@ __device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, P
     cnt.sub_g++;
     if (!may_pair) continue;
     R r1, r2;
-    draw2(q.id, a.step, (unsigned)s, kPair, a.seed, r1, r2);
+    draw2(q.id, step, (unsigned)s, kPair, a.seed, r1, r2);
     R pp = prob_pair(a.tab, r1, chig, eps, h);
     if (pp > R(1)) {
       cnt.pp1++;
@@ -578,8 +591,8 @@ __device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, P
       el.p = {r1 * q.p.x, r1 * q.p.y, r1 * q.p.z};
       R r1c = R(1) - r1;
       po.p = {r1c * q.p.x, r1c * q.p.y, r1c * q.p.z};
-      el.id = child_id(q.id, a.step, (unsigned)s, kElectron, a.seed);
-      po.id = child_id(q.id, a.step, (unsigned)s, kPositron, a.seed);
+      el.id = child_id(q.id, step, (unsigned)s, kElectron, a.seed);
+      po.id = child_id(q.id, step, (unsigned)s, kPositron, a.seed);
       cnt.pairs++;
       R trem = R(n - 1 - s) * h;
       emit(a, pass, kElectron, el, trem, E, B, cnt);
@@ -642,7 +655,12 @@ __device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m, int l) {
 // The per-step field constants, formed once per step in FP64 by one thread.
 template <typename R>
 __global__ void k_step_constants(const StepArgs<R> a) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) step_constants(a, *(StepConst *)a.step_const);
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    step_constants(a, *(StepConst *)a.step_const);
+    Clock *clk = (Clock *)a.clock;   // the next step starts dt later
+    clk->t += a.dt_d;
+    clk->step += 1;
+  }
 }
 
 // Pass 0 of one particle family.  PHOTON: the photon store; otherwise
@@ -695,8 +713,8 @@ __global__ void __launch_bounds__(256, (Pass0Occ<R, PHOTON>::blocks)) k_pass0(co
       atomicOr(a.status, kStNonfinite);
     }
     bool alive = true;
-    if (PHOTON) alive = advance_photon(a, 0, q, a.dt, E, B, cnt, a.id[sp] + i, (R)*a.chi_star);
-    else advance_massive(a, 0, sp, q, a.dt, E, B, cnt, a.id[sp] + i);
+    if (PHOTON) alive = advance_photon(a, 0, q, a.dt, E, B, cnt, a.id[sp] + i, (R)*a.chi_star, kc.step);
+    else advance_massive(a, 0, sp, q, a.dt, E, B, cnt, a.id[sp] + i, kc.step);
     int nc = alive ? finish_cell(a, q) : -1;
     if (alive && nc < 0) cnt.absorbed++;
     // a photon's momentum never changes: its momentum record is rewritten
@@ -808,7 +826,7 @@ __global__ void __launch_bounds__(kPhotonThreads, PhotonOcc<R>::blocks) k_photon
         cnt.nonfin++;
         atomicOr(a.status, kStNonfinite);
       }
-      alive = advance_photon(a, 0, q, a.dt, E, B, cnt, a.id[kPhoton] + i, chi_star);
+      alive = advance_photon(a, 0, q, a.dt, E, B, cnt, a.id[kPhoton] + i, chi_star, kc.step);
     }
     const int nc = alive ? finish_cell(a, q) : -1;
     if (alive && nc < 0) cnt.absorbed++;
@@ -828,6 +846,7 @@ template <typename R>
 __global__ void __launch_bounds__(256, 2) k_products(const StepArgs<R> a) {
   Cnt cnt;
   const R chi_star = (R)*a.chi_star;
+  const unsigned step = ((const StepConst *)a.step_const)->step;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (int pass = 1; pass <= kMaxPass; ++pass) {
     if (pass > 1 && !grid_barrier(a.barrier, a.status)) break;
@@ -843,8 +862,8 @@ __global__ void __launch_bounds__(256, 2) k_products(const StepArgs<R> a) {
       q.ci[0] = r.ci[0]; q.ci[1] = r.ci[1]; q.ci[2] = r.ci[2];
       q.p = r.p; q.w = r.w; q.id = r.id;
       bool alive = true;
-      if (r.sp == kPhoton) alive = advance_photon(a, pass, q, r.trem, r.E, r.B, cnt, nullptr, chi_star);
-      else advance_massive(a, pass, r.sp, q, r.trem, r.E, r.B, cnt, nullptr);
+      if (r.sp == kPhoton) alive = advance_photon(a, pass, q, r.trem, r.E, r.B, cnt, nullptr, chi_star, step);
+      else advance_massive(a, pass, r.sp, q, r.trem, r.E, r.B, cnt, nullptr, step);
       if (alive) append(a, r.sp, q, cnt);
     }
   }
@@ -887,7 +906,8 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   }
   a.field_mode = c->grid.field_mode;
   for (int k = 0; k < 16; ++k) a.fp[k] = c->grid.fp[k];
-  a.t = c->time;
+  a.clock = c->d_clock;
+  a.dt_d = dt;
   if (a.field_mode == kFieldGrid) {
     for (int k = 0; k < 3; ++k) {
       a.E[k] = (const R *)f->E[k];
@@ -904,7 +924,6 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   a.same_step = c->par.same_step_children;
   a.pm_strict = c->par.pm_strict;
   a.seed = c->par.seed;
-  a.step = (unsigned)c->step;
   a.tab = (const R *)c->d_tables;
   a.chi_star = c->d_chi_star;
   a.step_const = c->d_step_const;
@@ -1004,6 +1023,7 @@ int qed_launch_step(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) 
 }
 
 size_t qed_step_const_bytes() { return sizeof(qed::StepConst); }
+size_t qed_clock_bytes() { return sizeof(qed::Clock); }
 
 size_t qed_pend_bytes(int prec) {
   return prec == 64 ? sizeof(qed::Pend<double>) : sizeof(qed::Pend<float>);
