@@ -57,6 +57,8 @@ void release(qed_ctx *c) {
   cudaFree(c->d_eps_star);
   cudaFree(c->d_step_const);
   cudaFree(c->d_clock);
+  cudaFree(c->d_blk_start);
+  cudaFree(c->d_blk_cursor);
   cudaFree(c->d_tile);
   cudaFree(c->stage);
 }
@@ -178,9 +180,20 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
                                         : (total_cap / 8 > 65536 ? total_cap / 8 : 65536);
   if (rc == QED_OK) rc = dalloc(&c->pend[0], qed_pend_bytes(c->prec) * c->pend_cap);
   if (rc == QED_OK) rc = dalloc(&c->pend[1], qed_pend_bytes(c->prec) * c->pend_cap);
-  if (rc == QED_OK) rc = dalloc(&c->d_count, 4 * sizeof(long long));
+  if (rc == QED_OK) rc = dalloc(&c->d_count, 8 * sizeof(long long));   // [4 + 4]: sort totals
   if (rc == QED_OK) rc = dalloc(&c->d_nstart, 4 * sizeof(long long));
-  if (rc == QED_OK) rc = dalloc(&c->d_pend_count, sizeof(unsigned long long) * (qed::kMaxPass + 2));
+  // product counts per pass, then the work counters of the cell-block kernel
+  if (rc == QED_OK) rc = dalloc(&c->d_pend_count, sizeof(unsigned long long) * (qed::kMaxPass + 4));
+  if (g->field_mode == QED_FIELD_GRID) {
+    long long nblk = 1;
+    for (int k = 0; k < 3; ++k) {
+      c->nb[k] = (g->n[k] + qed::kBlockCells - 1) / qed::kBlockCells;
+      nblk *= c->nb[k];
+    }
+    c->nblk = (int)nblk;
+    if (rc == QED_OK) rc = dalloc(&c->d_blk_start, sizeof(unsigned) * 4 * (nblk + 1));
+    if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (nblk + 1));
+  }
   if (rc == QED_OK) rc = dalloc(&c->d_counters, sizeof(unsigned long long) * qed::kNumCounters);
   if (rc == QED_OK) rc = dalloc(&c->d_spec, sizeof(double) * (p->nbins > 0 ? p->nbins : 1));
   if (rc == QED_OK) rc = dalloc(&c->d_spec_e, sizeof(double) * (p->nbins > 0 ? p->nbins : 1));
@@ -195,7 +208,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
   c->tile_cap = 2 * ((max_cap + qed::kCompactTile - 1) / qed::kCompactTile + 2);   // two classes
   if (rc == QED_OK) rc = dalloc(&c->d_tile, sizeof(long long) * c->tile_cap);
   if (rc == QED_OK) {
-    cudaMemsetAsync(c->d_count, 0, 4 * sizeof(long long), s);
+    cudaMemsetAsync(c->d_count, 0, 8 * sizeof(long long), s);
     cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * qed::kNumCounters, s);
     cudaMemsetAsync(c->d_spec, 0, sizeof(double) * (p->nbins > 0 ? p->nbins : 1), s);
     cudaMemsetAsync(c->d_spec_e, 0, sizeof(double) * (p->nbins > 0 ? p->nbins : 1), s);
@@ -248,6 +261,7 @@ int qed_particles_set(qed_ctx *c, int sp, const double *x, const double *p, cons
       return QED_ERR_CUDA;
     dx = b; dp = b + 24 * nn; dw = b + 48 * nn; di = b + 56 * nn;
   }
+  c->sorted = 0;
   return qed_launch_set(c, sp, (const double *)dx, (const double *)dp, (const double *)dw,
                         (const uint64_t *)di, n, s);
 }
@@ -258,6 +272,7 @@ int qed_particles_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint6
   cudaStream_t s = as_stream(stream);
   int rc = qed_launch_compact(c, sp, false, s);
   if (rc != QED_OK) return rc;
+  if (sp != QED_PHOTON) c->sorted = 0;   // compaction keeps the order but not the block starts
   long long n = 0;
   if (cudaMemcpyAsync(&n, c->d_count + sp, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -301,6 +316,16 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
   }
   cudaStream_t s = as_stream(stream);
   for (int n = 0; n < nsteps; ++n) {
+    if (grid && c->nblk > 0 && !c->sorted) {
+      // records in cell-block order let electrons, positrons and ions deposit
+      // through shared-memory tiles
+      for (int sp = 0; sp < 4; ++sp) {
+        int rs = sp == QED_PHOTON ? QED_OK : qed_launch_sort(c, sp, s);
+        if (rs != QED_OK) return rs;
+      }
+      c->sorted = 1;
+      c->steps_since_compact = 0;
+    }
     int rc = qed_launch_step(c, f, dt, s);
     if (rc == QED_OK && grid && c->par.deposit_on) rc = qed_launch_yee(c, f, dt, s);
     if (rc != QED_OK) return rc;
@@ -308,7 +333,9 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
     if (c->par.compact_interval > 0 && ++c->steps_since_compact >= c->par.compact_interval) {
       c->steps_since_compact = 0;
       for (int sp = 0; sp < 4; ++sp) {
-        rc = qed_launch_compact(c, sp, true, s);
+        // grid mode: re-sort the charged species by cell block, compact photons
+        rc = (grid && c->nblk > 0 && sp != QED_PHOTON) ? qed_launch_sort(c, sp, s)
+                                                        : qed_launch_compact(c, sp, true, s);
         if (rc != QED_OK) return rc;
       }
     }

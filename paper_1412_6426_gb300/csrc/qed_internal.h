@@ -18,6 +18,9 @@ enum Counter {
 };
 constexpr int kMaxBins = 4096;
 constexpr int kCompactTile = 2048;   // particles per tile of the compaction
+constexpr int kBlockCells = 8;       // cell block edge (grid mode): 8 x 8 x 8 cells
+constexpr int kTileNodes = kBlockCells + 3;   // current tile edge: the deposit stencil of a
+                                              // particle starting in the block stays inside
 
 // One species store: a structure of arrays, double-buffered for compaction.
 //   pos: {offset_x, offset_y, offset_z, weight}   (R4 = float4 or 2 x double2)
@@ -66,6 +69,12 @@ template <typename R> struct StepArgs {
   R charge[4], mass[4];
   const R *tab;
   const double *chi_star;  // photons below this chi_g cannot pair (per context)
+  // grid mode, cell-block sort: blocks per axis, and per species the first
+  // record of every block (nblk + 1 entries; the last is the sorted count)
+  int nb[3];
+  int nblk;
+  const unsigned *blk_start[4];
+  unsigned *work;          // work-stealing counter of the cell-block kernel (zeroed per step)
   void *step_const;        // per-step field constants (written by k_step_constants)
   void *clock;             // device clock {t, step}: read and advanced once per step
   double dt_d;             // the step in FP64 (advances the clock)
@@ -100,6 +109,11 @@ struct qed_ctx {
   double *d_chi_star = nullptr;       // pair-skip threshold derived from the tables
   double *d_eps_star = nullptr;       // photons below this |p| cannot pair in the analytic field
   void *d_step_const = nullptr;       // per-step field constants
+  unsigned *d_blk_start = nullptr;    // [4][nblk + 1] first record of each cell block
+  unsigned *d_blk_cursor = nullptr;   // [nblk + 1] histogram / scatter cursors of the sort
+  int nb[3] = {0, 0, 0};
+  int nblk = 0;
+  int sorted = 0;                     // the stores are in cell-block order (up to the tail)
   void *d_clock = nullptr;            // {double t; long long step}: kernels advance it, so
                                       // captured CUDA graphs replay correctly
   size_t tables_bytes = 0;
@@ -109,6 +123,7 @@ struct qed_ctx {
   int blocks_photon = 0;              // grid sizes of the step kernels
   int blocks_massive = 0;
   int blocks_products = 0;
+  int blocks_cells = 0;
   int64_t step = 0;                   // host mirror of the clock (steps issued)
   int latched = 0;                    // a device error was observed
   int64_t steps_since_compact = 0;
@@ -129,5 +144,6 @@ int qed_launch_set(qed_ctx *c, int sp, const double *x, const double *p, const d
 int qed_launch_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t *id, int64_t n,
                    cudaStream_t s);
 int qed_launch_compact(qed_ctx *c, int sp, bool partition, cudaStream_t s);
+int qed_launch_sort(qed_ctx *c, int sp, cudaStream_t s);
 int qed_step_kernel_blocks(qed_ctx *c);
 int qed_launch_chi_star(qed_ctx *c, cudaStream_t s);

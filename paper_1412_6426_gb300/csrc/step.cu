@@ -387,6 +387,74 @@ __device__ __noinline__ void deposit(const StepArgs<R> &a, const int *cs, const 
     }
 }
 
+// Esirkepov deposit into the shared-memory current tile of a cell block
+// (tile node (0,0,0) = global node torg, kTileNodes per axis).  Returns false,
+// depositing nothing, when the particle's stencil leaves the tile (it has
+// drifted out of its block since the last sort); the caller then deposits to
+// global memory.
+template <typename R>
+__device__ bool deposit_tile(const StepArgs<R> &a, R *jt, const int *torg, const int *cs, const R *os,
+                             const Pt<R> &q, R qw) {
+  int base[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    base[c] = cs[c] - 1 - torg[c];
+    if (base[c] < 0 || base[c] + 3 >= kTileNodes) return false;
+  }
+  R S0[3][4], dS[3][4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R ua = R(1) + os[c];
+    R ub = R(q.ci[c] - cs[c] + 1) + q.off[c];
+    if (!(fabs_r(ub - ua) < R(1))) { atomicOr(a.status, kStCourant); return true; }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      R s0 = R(1) - fabs_r(ua - R(m));
+      R s1 = R(1) - fabs_r(ub - R(m));
+      s0 = s0 > R(0) ? s0 : R(0);
+      s1 = s1 > R(0) ? s1 : R(0);
+      S0[c][m] = s0;
+      dS[c][m] = s1 - s0;
+    }
+  }
+  const R inv_vol = a.inv_d[0] * a.inv_d[1] * a.inv_d[2];
+  const R pref[3] = {-qw * a.d[0] / a.dt * inv_vol, -qw * a.d[1] / a.dt * inv_vol,
+                     -qw * a.d[2] / a.dt * inv_vol};
+  constexpr int T = kTileNodes, TT = kTileNodes * kTileNodes, TTT = TT * kTileNodes;
+  const R third = R(1.0 / 3.0);
+  for (int k = 0; k < 4; ++k)
+    for (int j = 0; j < 4; ++j) {
+      R acc = R(0);
+      R wyz = S0[1][j] * S0[2][k] + R(0.5) * dS[1][j] * S0[2][k] + R(0.5) * S0[1][j] * dS[2][k] +
+              third * dS[1][j] * dS[2][k];
+      for (int i = 0; i < 4; ++i) {
+        acc += pref[0] * dS[0][i] * wyz;
+        if (acc != R(0)) atomicAdd(jt + 0 * TTT + (base[2] + k) * TT + (base[1] + j) * T + base[0] + i, acc);
+      }
+    }
+  for (int k = 0; k < 4; ++k)
+    for (int i = 0; i < 4; ++i) {
+      R acc = R(0);
+      R wxz = S0[0][i] * S0[2][k] + R(0.5) * dS[0][i] * S0[2][k] + R(0.5) * S0[0][i] * dS[2][k] +
+              third * dS[0][i] * dS[2][k];
+      for (int j = 0; j < 4; ++j) {
+        acc += pref[1] * dS[1][j] * wxz;
+        if (acc != R(0)) atomicAdd(jt + 1 * TTT + (base[2] + k) * TT + (base[1] + j) * T + base[0] + i, acc);
+      }
+    }
+  for (int j = 0; j < 4; ++j)
+    for (int i = 0; i < 4; ++i) {
+      R acc = R(0);
+      R wxy = S0[0][i] * S0[1][j] + R(0.5) * dS[0][i] * S0[1][j] + R(0.5) * S0[0][i] * dS[1][j] +
+              third * dS[0][i] * dS[1][j];
+      for (int k = 0; k < 4; ++k) {
+        acc += pref[2] * dS[2][k] * wxy;
+        if (acc != R(0)) atomicAdd(jt + 2 * TTT + (base[2] + k) * TT + (base[1] + j) * T + base[0] + i, acc);
+      }
+    }
+  return true;
+}
+
 // ----- movement and boundaries ---------------------------------------------
 template <typename R>
 __device__ __forceinline__ void move(const StepArgs<R> &a, Pt<R> &q, V3<R> v, R h) {
@@ -501,7 +569,8 @@ __device__ __noinline__ void emit(const StepArgs<R> &a, int pass, int sp, Pt<R> 
 // Boris push and modified emission generator (Sec. IV.G); ions are pushed only.
 template <typename R>
 __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, R t_span,
-                                                V3<R> E, V3<R> B, Cnt &cnt, const uint64_t *idp, unsigned step) {
+                                                V3<R> E, V3<R> B, Cnt &cnt, const uint64_t *idp, unsigned step,
+                                                R *jt = nullptr, const int *torg = nullptr) {
   const int cs[3] = {q.ci[0], q.ci[1], q.ci[2]};
   const R os[3] = {q.off[0], q.off[1], q.off[2]};
   const R qc = a.charge[sp], m = a.mass[sp];
@@ -542,7 +611,8 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
       emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B, cnt);
     }
   }
-  if (a.deposit && qc != R(0)) deposit(a, cs, os, q, qc * q.w);
+  if (a.deposit && qc != R(0))
+    if (!jt || !deposit_tile(a, jt, torg, cs, os, q, qc * q.w)) deposit(a, cs, os, q, qc * q.w);
 }
 
 // Photon: straight flight with the pair generator (Sec. V.A) in the same
@@ -677,8 +747,15 @@ __global__ void __launch_bounds__(256, (Pass0Occ<R, PHOTON>::blocks)) k_pass0(co
   __shared__ StepConst kc;
   if (threadIdx.x < (int)(sizeof(StepConst) / 8))
     ((unsigned long long *)&kc)[threadIdx.x] = ((const unsigned long long *)a.step_const)[threadIdx.x];
+  __shared__ long long nb0[4];
   // an overflowing append leaves count above the capacity: never read past it
-  if (threadIdx.x < 4) ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
+  if (threadIdx.x < 4) {
+    ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
+    // records in cell-block order are advanced by k_blocks; this kernel takes the rest
+    const unsigned *bs = a.blk_start[threadIdx.x];
+    nb0[threadIdx.x] = (!PHOTON && bs) ? min((long long)bs[a.nblk], ns[threadIdx.x]) : 0;
+    ns[threadIdx.x] -= nb0[threadIdx.x];
+  }
   __syncthreads();
   const long long total = PHOTON ? ns[kPhoton] : ns[kElectron] + ns[kPositron] + ns[kIon];
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -692,6 +769,7 @@ __global__ void __launch_bounds__(256, (Pass0Occ<R, PHOTON>::blocks)) k_pass0(co
         sp = kPositron;
         if (i >= ns[kPositron]) { i -= ns[kPositron]; sp = kIon; }
       }
+      i += nb0[sp];
     }
     Pt<R> q;
     int cell;
@@ -839,6 +917,75 @@ __global__ void __launch_bounds__(kPhotonThreads, PhotonOcc<R>::blocks) k_photon
   flush(cnt, a.counters);
 }
 
+// Grid mode: electrons, positrons and ions in cell-block order.  Blocks take
+// cell blocks by work stealing; the particles of a cell block deposit their
+// current into a shared-memory tile covering the block and the deposit
+// stencil's reach, which is then added to the global current with one atomic
+// per non-zero tile node.
+template <typename R>
+__global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
+  constexpr int TTT = kTileNodes * kTileNodes * kTileNodes;
+  __shared__ R jt[3 * TTT];
+  __shared__ int blk;
+  __shared__ long long ns[4];
+  Cnt cnt;
+  const unsigned step = ((const StepConst *)a.step_const)->step;
+  if (threadIdx.x < 4) ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
+  for (;;) {
+    if (threadIdx.x == 0) blk = (int)atomicAdd(a.work, 1u);
+    __syncthreads();
+    const int b = blk;
+    if (b >= a.nblk) break;
+    for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) jt[t] = R(0);
+    __syncthreads();
+    const int bc[3] = {b % a.nb[0], (b / a.nb[0]) % a.nb[1], b / (a.nb[0] * a.nb[1])};
+    const int torg[3] = {bc[0] * kBlockCells - 1, bc[1] * kBlockCells - 1, bc[2] * kBlockCells - 1};
+    const int fam[3] = {kElectron, kPositron, kIon};
+    for (int f = 0; f < 3; ++f) {
+      const int sp = fam[f];
+      if (!a.blk_start[sp]) continue;
+      const long long lo = min((long long)a.blk_start[sp][b], ns[sp]);
+      const long long hi = min((long long)a.blk_start[sp][b + 1], ns[sp]);
+      for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        Pt<R> q;
+        int cell;
+        load(a, sp, i, q, cell);
+        if (cell < 0) continue;
+        cnt.psteps[sp]++;
+        const unsigned row = fast_div((unsigned)cell, a.div_m[0], a.div_l[0]);
+        const unsigned slab = fast_div((unsigned)cell, a.div_m[1], a.div_l[1]);
+        q.ci[0] = cell - (int)row * a.n[0];
+        q.ci[1] = (int)row - (int)slab * a.n[1];
+        q.ci[2] = (int)slab;
+        V3<R> E, B;
+        gather_grid(a, q, E, B);
+        const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
+        if (!(probe == R(0))) {
+          cnt.nonfin++;
+          atomicOr(a.status, kStNonfinite);
+        }
+        advance_massive(a, 0, sp, q, a.dt, E, B, cnt, a.id[sp] + i, step, jt, torg);
+        const int nc = finish_cell(a, q);
+        if (nc < 0) cnt.absorbed++;
+        store(a, sp, i, q, nc, false);
+      }
+    }
+    __syncthreads();
+    const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+    for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) {
+      const R v = jt[t];
+      if (v == R(0)) continue;
+      const int c = t / TTT, r = t % TTT;
+      const int ti = r % kTileNodes, tj = (r / kTileNodes) % kTileNodes, tk = r / (kTileNodes * kTileNodes);
+      const int gi = wrapi(torg[0] + ti, a.n[0]), gj = wrapi(torg[1] + tj, a.n[1]),
+                gk = wrapi(torg[2] + tk, a.n[2]);
+      atomicAdd(a.J[c] + gk * nxy + gj * nx + gi, v);
+    }
+    __syncthreads();   // the tile and blk are reused by the next cell block
+  }
+  flush(cnt, a.counters);
+}
+
 // Passes 1, 2, ...: products evolving for the rest of the step.  All blocks
 // are co-resident (cooperative launch) and meet at a bounded grid barrier
 // between passes; pass p reads the buffer filled in pass p-1.
@@ -926,6 +1073,12 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   a.seed = c->par.seed;
   a.tab = (const R *)c->d_tables;
   a.chi_star = c->d_chi_star;
+  a.nblk = c->nblk;
+  for (int k = 0; k < 3; ++k) a.nb[k] = c->nb[k];
+  for (int sp = 0; sp < 4; ++sp)
+    a.blk_start[sp] = (c->sorted && c->nblk > 0 && sp != kPhoton)
+                          ? c->d_blk_start + (size_t)sp * (c->nblk + 1) : nullptr;
+  a.work = (unsigned *)(c->d_pend_count + kMaxPass + 2);
   a.step_const = c->d_step_const;
   a.counters = c->d_counters;
   a.spectrum = c->d_spec;
@@ -939,7 +1092,7 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   if (cudaMemcpyAsync(c->d_nstart, c->d_count, 4 * sizeof(long long), cudaMemcpyDeviceToDevice, s) !=
       cudaSuccess)
     return QED_ERR_CUDA;
-  if (cudaMemsetAsync(c->d_pend_count, 0, sizeof(unsigned long long) * (kMaxPass + 2), s) !=
+  if (cudaMemsetAsync(c->d_pend_count, 0, sizeof(unsigned long long) * (kMaxPass + 4), s) !=
       cudaSuccess)
     return QED_ERR_CUDA;
   if (a.deposit) {
@@ -955,6 +1108,10 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   if (e == cudaSuccess)
     e = cudaLaunchKernel((const void *)k_photons<R>, dim3(c->blocks_photon), dim3(kPhotonThreads), args, 0, s);
   if (c->ev_photon) cudaEventRecord(c->ev_photon, s);
+  if (e == cudaSuccess && a.blk_start[kElectron]) {
+    c->launches += 1;
+    e = cudaLaunchKernel((const void *)k_blocks<R>, dim3(c->blocks_cells), dim3(256), args, 0, s);
+  }
   if (e == cudaSuccess)
     e = cudaLaunchKernel((const void *)k_pass0<R, false>, dim3(c->blocks_massive), dim3(256), args, 0, s);
   if (e == cudaSuccess && a.same_step) {
@@ -989,7 +1146,10 @@ __global__ void k_chi_star(const R *tab, double kappa, int mode, qed_grid_desc g
 
 template <typename R>
 int step_blocks(qed_ctx *c) {
-  int a = 0, b = 0, p = 0;
+  int a = 0, b = 0, p = 0, g = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, qed::k_blocks<R>, 256, 0) != cudaSuccess || g < 1)
+    return QED_ERR_CUDA;
+  c->blocks_cells = g * c->num_sms;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, qed::k_photons<R>, qed::kPhotonThreads, 0) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, qed::k_pass0<R, false>, 256, 0) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, qed::k_products<R>, 256, 0) != cudaSuccess ||

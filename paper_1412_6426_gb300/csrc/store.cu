@@ -235,6 +235,130 @@ __global__ void k_count_live(const T *mom, const long long *count, int sp, long 
   if ((threadIdx.x & 31) == 0 && mine) atomicAdd((unsigned long long *)live + sp, mine);
 }
 
+
+// ----- sort by cell block (grid mode) ---------------------------------------
+// Counting sort of the live records by 8x8x8 cell block: histogram, one-block
+// exclusive scan into the per-species block starts, scatter through per-block
+// cursors.  Dead records are dropped.  Lanes of a warp that land in the same
+// block share one atomic.
+struct BlockGeom {
+  int n[3], nb[3];
+};
+
+__device__ __forceinline__ int block_of(int cell, const BlockGeom &g) {
+  const int i = cell % g.n[0], j = (cell / g.n[0]) % g.n[1], k = cell / (g.n[0] * g.n[1]);
+  return (i / kBlockCells) + g.nb[0] * ((j / kBlockCells) + g.nb[1] * (k / kBlockCells));
+}
+
+__device__ __forceinline__ unsigned block_atomic_add(unsigned *ctr, int key, bool on) {
+  const unsigned mask = __ballot_sync(0xffffffffu, on);
+  if (!on) return 0;
+  const unsigned peers = __match_any_sync(mask, key);
+  const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(ctr + key, (unsigned)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+template <typename T>
+__global__ void k_blk_hist(const T *mom, const long long *count, int sp, long long cap, BlockGeom g,
+                           unsigned *hist) {
+  const long long n = min(count[sp], cap);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long i = base + threadIdx.x;
+    int cell = -1;
+    if (i < n) cell = cell_of(mom[i]);
+    const bool live = cell >= 0;
+    block_atomic_add(hist, live ? block_of(cell, g) : 0, live);
+  }
+}
+
+__global__ void k_blk_scan(unsigned *hist, int nblk, unsigned *start, long long *count, int sp) {
+  __shared__ unsigned part[1024];
+  __shared__ unsigned carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nblk; base += 1024) {
+    const int i = base + threadIdx.x;
+    const unsigned v = i < nblk ? hist[i] : 0u;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const unsigned add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+      __syncthreads();
+      part[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < nblk) {
+      start[i] = carry + part[threadIdx.x] - v;
+      hist[i] = start[i];                // becomes the scatter cursor
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    start[nblk] = carry;
+    count[sp] = carry;
+  }
+}
+
+template <typename T>
+__global__ void k_blk_scatter(const T *pos, const T *mom, const uint64_t *id, T *pos2, T *mom2, uint64_t *id2,
+                              const long long *count, int sp, long long cap, BlockGeom g, unsigned *cursor) {
+  const long long n = min(count[sp], cap);   // records before the sort (the total goes elsewhere)
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long i = base + threadIdx.x;
+    int cell = -1;
+    T M;
+    if (i < n) {
+      M = mom[i];
+      cell = cell_of(M);
+    }
+    const bool live = cell >= 0;
+    const unsigned o = block_atomic_add(cursor, live ? block_of(cell, g) : 0, live);
+    if (live) {
+      pos2[o] = pos[i];
+      mom2[o] = M;
+      id2[o] = id[i];
+    }
+  }
+}
+
+template <typename R>
+int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
+  using T = typename Rec<R>::T;
+  Store &st = c->st[sp];
+  if (st.cap == 0 || c->nblk == 0) return QED_OK;
+  BlockGeom g;
+  for (int k = 0; k < 3; ++k) {
+    g.n[k] = c->grid.n[k];
+    g.nb[k] = c->nb[k];
+  }
+  const int cur = st.cur, nxt = cur ^ 1;
+  unsigned *start = c->d_blk_start + (size_t)sp * (c->nblk + 1);
+  if (cudaMemsetAsync(c->d_blk_cursor, 0, sizeof(unsigned) * (c->nblk + 1), s) != cudaSuccess) return QED_ERR_CUDA;
+  const int grid = c->num_sms * 8;
+  c->launches += 3;
+  k_blk_hist<T><<<grid, 256, 0, s>>>((const T *)st.mom[cur], c->d_count, sp, (long long)st.cap, g,
+                                     c->d_blk_cursor);
+  // the record count to scatter is read on the device: the histogram keeps it
+  k_blk_scan<<<1, 1024, 0, s>>>(c->d_blk_cursor, c->nblk, start, c->d_count + 4, sp);   // total -> [4 + sp]
+  k_blk_scatter<T><<<grid, 256, 0, s>>>((const T *)st.pos[cur], (const T *)st.mom[cur], st.id[cur],
+                                        (T *)st.pos[nxt], (T *)st.mom[nxt], st.id[nxt], c->d_count, sp,
+                                        (long long)st.cap, g, c->d_blk_cursor);
+  if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
+  // the live count becomes the store size
+  if (cudaMemcpyAsync(c->d_count + sp, c->d_count + 4 + sp, sizeof(long long), cudaMemcpyDeviceToDevice, s) !=
+      cudaSuccess)
+    return QED_ERR_CUDA;
+  st.cur = nxt;
+  return QED_OK;
+}
+
 Lattice lattice(const qed_ctx *c) {
   Lattice L;
   for (int k = 0; k < 3; ++k) {
@@ -324,6 +448,10 @@ int qed_launch_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t
 
 int qed_launch_compact(qed_ctx *c, int sp, bool partition, cudaStream_t s) {
   return c->prec == 64 ? qed::compact<double>(c, sp, partition, s) : qed::compact<float>(c, sp, partition, s);
+}
+
+int qed_launch_sort(qed_ctx *c, int sp, cudaStream_t s) {
+  return c->prec == 64 ? qed::sort_blocks<double>(c, sp, s) : qed::sort_blocks<float>(c, sp, s);
 }
 
 int qed_launch_count_live(qed_ctx *c, long long *d_live, cudaStream_t s) {

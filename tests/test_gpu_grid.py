@@ -51,6 +51,10 @@ def grid_case(seed=5, npart=300):
         dirs /= np.linalg.norm(dirs, axis=1)[:, None]
         p = dirs * rng.uniform(50, 200, npart)[:, None]
         parts[sp] = (x, p, np.ones(npart), np.arange(npart, dtype=np.uint64) + 10_000 * sp)
+    # ions (charge +1, mass 1836.15): pushed and deposited, never emit
+    xi = rng.uniform(0, 1, (npart // 3, 3)) * L
+    pi = rng.standard_normal((npart // 3, 3)) * 100.0
+    parts[3] = (xi, pi, np.ones(len(xi)), np.arange(len(xi), dtype=np.uint64) + 50_000)
     w = workloads.Workload(name="grid", n=n, d=d, x0=x0, periodic=(1, 1, 1), field_mode=workloads.FIELD_GRID,
                            fp=(), dt=dt, nsteps=5, particles=parts, seed=seed, kappa=0.1)
     return w, f
@@ -63,7 +67,7 @@ def run_gpu_grid(w, f, precision, nsteps):
     E = [torch.tensor(a, dtype=dtype, device="cuda") for a in f[:3]]
     B = [torch.tensor(a, dtype=dtype, device="cuda") for a in f[3:]]
     J = [torch.zeros(len(f[0]), dtype=dtype, device="cuda") for _ in range(3)]
-    caps = (4000, 4000, 8000, 0)
+    caps = (4000, 4000, 8000, 400)
     with Simulation(w, precision=precision, capacity=caps, deposit_on=1) as s:
         s.set_grid_fields(E, B, J)
         s.set_all()
@@ -81,7 +85,7 @@ def test_fp64_grid_parity():
     fo = [a.copy() for a in f]
     Jo = [np.zeros_like(f[0]) for _ in range(3)]
     ora, od, _, _ = drive.run(w.n, w.d, w.x0, w.periodic, w.field_mode, w.fp, w.dt, nsteps, w.particles,
-                              kappa=w.kappa, seed=w.seed, caps=(4000, 4000, 8000, 1), fields=fo, J=Jo,
+                              kappa=w.kappa, seed=w.seed, caps=(4000, 4000, 8000, 400), fields=fo, J=Jo,
                               deposit_on=1, yee=True)
     gpu, gd, fg = run_gpu_grid(w, f, 64, nsteps)
     assert gd["status"] == 0, gd
@@ -112,8 +116,9 @@ def test_fp32_grid_continuity():
             if len(x):
                 acc += o.charge_density(w.n, w.d, w.x0, x[:, 0], x[:, 1], x[:, 2], q * wt)
         return acc
-    r0 = rho(gpu0, ((0, -1.0), (1, 1.0)))
-    r1 = rho(out, ((0, -1.0), (1, 1.0)))
+    gpu0[3] = w.particles[3]
+    r0 = rho(gpu0, ((0, -1.0), (1, 1.0), (3, 1.0)))
+    r1 = rho(out, ((0, -1.0), (1, 1.0), (3, 1.0)))
     Jx, Jy, Jz = fg[6], fg[7], fg[8]
     n = w.n
     idx = lambda i, j, k: ((k % n[2]) * n[1] + (j % n[1])) * n[0] + (i % n[0])
