@@ -15,7 +15,9 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
         nsub_max: int = 1000, emission_on: int = 1, pairs_on: int = 1, same_step_children: int = 1,
         caps=None, nbins: int = 0, lg_lo: float = -12.0, lg_hi: float = 0.0, step0: int = 0,
         t0: float = 0.0, fields=None, J=None, deposit_on: int = 0, yee: bool = False,
-        ion_charge: float = 1.0, ion_mass: float = 1836.15267343, time_from: int = 0):
+        ion_charge: float = 1.0, ion_mass: float = 1836.15267343, time_from: int = 0,
+        ens_bits: int = 0, ens=None, emit_fg: float = 1.0, emit_ng: int = 1, pair_fg: float = 1.0,
+        pair_ng: int = 1, thin_interval: int = 0, thin_limit=(0, 0, 0, 0)):
     """Advance the given particles by nsteps steps of dt.
 
     particles: {species: (x[n,3], p[n,3], w[n], id[n])}.  Returns
@@ -23,13 +25,16 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
     With yee=True the grid fields (list of 6 arrays, modified in place) are
     advanced by one FDTD step after the particles, using the deposited J.
     Steps from index time_from on are timed (diag "timed_seconds" and
-    "timed_particle_steps").
+    "timed_particle_steps").  With thin_interval > 0 the stores are thinned
+    after every step s with (s + 1) % thin_interval == 0 (Sec. VI).
     """
     import time
     P = o.make_params(n=n, d=d, x0=x0, periodic=periodic, field_mode=field_mode, fp=fp, kappa=kappa,
                       nsub_max=nsub_max, emission_on=emission_on, pairs_on=pairs_on,
                       same_step_children=same_step_children, deposit_on=deposit_on, seed=seed,
-                      lg_lo=lg_lo, lg_hi=lg_hi, ion_charge=ion_charge, ion_mass=ion_mass)
+                      lg_lo=lg_lo, lg_hi=lg_hi, ion_charge=ion_charge, ion_mass=ion_mass,
+                      ens_bits=ens_bits, ens=ens, emit_fg=emit_fg, emit_ng=emit_ng, pair_fg=pair_fg,
+                      pair_ng=pair_ng, thin_interval=thin_interval, thin_limit=thin_limit)
     if caps is None:
         base = sum(len(v[3]) for v in particles.values())
         caps = (4 * base + 64,) * 4
@@ -64,6 +69,8 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
         run_.step(step0 + k, t0 + k * dt, dt)
         if yee:
             o.yee_step(n, d, dt, fields, J)
+        if thin_interval > 0 and (step0 + k + 1) % thin_interval == 0:
+            run_.thin(step0 + k)
     t_end = time.perf_counter()
     out = {sp: run_.sp[sp].get() for sp in range(4)}
     spec = run_.spectrum[:nbins].copy() if nbins else None

@@ -20,8 +20,9 @@ SRC = os.path.join(HERE, "qed_oracle.c")
 LIB = os.path.join(HERE, "libqed_oracle.so")
 
 ELECTRON, POSITRON, PHOTON, ION = 0, 1, 2, 3
-FIELD_GRID, FIELD_UNIFORM, FIELD_GAUSSIAN_LP, FIELD_ROTATING_E = 0, 1, 2, 3
-PURPOSE_EMIT, PURPOSE_PAIR, PURPOSE_CHILD = 1, 2, 3
+FIELD_GRID, FIELD_UNIFORM, FIELD_GAUSSIAN_LP, FIELD_ROTATING_E, FIELD_ENSEMBLE = 0, 1, 2, 3, 4
+PURPOSE_EMIT, PURPOSE_PAIR, PURPOSE_CHILD, PURPOSE_KEEP, PURPOSE_THIN = 1, 2, 3, 4, 5
+ENS_STRIDE = 9   # per ensemble: E0, omega, phase, Eu[3], Bu[3]
 
 
 def build(force: bool = False) -> str:
@@ -54,6 +55,16 @@ class Params(ctypes.Structure):
         ("charge", ctypes.c_double * 4),
         ("mass", ctypes.c_double * 4),
         ("fp", ctypes.c_double * 16),
+        ("ens_bits", ctypes.c_int32),
+        ("n_ens", ctypes.c_int32),
+        ("ens", ctypes.POINTER(ctypes.c_double)),
+        ("emit_fg", ctypes.c_double),
+        ("pair_fg", ctypes.c_double),
+        ("emit_ng", ctypes.c_int32),
+        ("pair_ng", ctypes.c_int32),
+        ("thin_interval", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("thin_limit", ctypes.c_int64 * 4),
     ]
 
 
@@ -66,7 +77,8 @@ class Store(ctypes.Structure):
 class Diag(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "emissions", "pairs", "substeps_lepton", "substeps_photon", "pm_gt1", "pp_gt1",
-        "capped", "absorbed", "overflow", "nonfinite")] + [
+        "capped", "absorbed", "overflow", "nonfinite", "photons_created", "pairs_created",
+        "thinned")] + [
         ("energy_defect", ctypes.c_double),
         ("spectrum", ctypes.POINTER(ctypes.c_double)),
         ("spectrum_energy", ctypes.POINTER(ctypes.c_double))]
@@ -105,6 +117,9 @@ def lib():
         _lib.or_step.restype = ctypes.c_int
         _lib.or_step.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Store), ctypes.POINTER(Diag),
                                  ctypes.POINTER(pd), ctypes.POINTER(pd), u32, d, d]
+        _lib.or_field_ensemble.argtypes = [ctypes.POINTER(Params), u64, d, pd, pd]
+        _lib.or_thin.restype = ctypes.c_int
+        _lib.or_thin.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Store), ctypes.POINTER(Diag), u32]
         _lib.or_sample_frozen.restype = i64
         _lib.or_sample_frozen.argtypes = [d, d, d, i64, u32, d, d, i32, pd, ctypes.POINTER(i64)]
         _lib.or_philox_block.argtypes = [u64, u32, u32, u32, u32, i64, ctypes.POINTER(u32)]
@@ -335,14 +350,26 @@ class Run:
         for s, c in zip(self.sp, stores):
             s.n = int(c.n)
 
+    def thin(self, step: int):
+        stores = (Store * 4)(*[s.cstore() for s in self.sp])
+        if lib().or_thin(ctypes.byref(self.P), stores, ctypes.byref(self.D), int(step)) != 0:
+            raise MemoryError("or_thin")
+        for s, c in zip(self.sp, stores):
+            s.n = int(c.n)
+
     def diag(self) -> dict:
-        return {k: getattr(self.D, k) for k, _ in Diag._fields_[:11]}
+        return {k: getattr(self.D, k) for k, _ in Diag._fields_[:14]}
 
 
 def make_params(*, n=(1, 1, 1), d=(1.0, 1.0, 1.0), x0=(0.0, 0.0, 0.0), periodic=(0, 0, 0),
                 field_mode=FIELD_UNIFORM, fp=(), kappa=0.1, nsub_max=1000, emission_on=1,
                 pairs_on=1, same_step_children=1, deposit_on=0, seed=1, lg_lo=-12.0,
-                lg_hi=0.0, ion_charge=1.0, ion_mass=1836.15267343) -> Params:
+                lg_hi=0.0, ion_charge=1.0, ion_mass=1836.15267343, ens_bits=0, ens=None,
+                emit_fg=1.0, emit_ng=1, pair_fg=1.0, pair_ng=1, thin_interval=0,
+                thin_limit=(0, 0, 0, 0)) -> Params:
+    """Oracle parameters.  ens: (n_ens, ENS_STRIDE) float64 table of the
+    ensemble fields (field_mode FIELD_ENSEMBLE); the returned Params keeps a
+    reference to it."""
     P = Params()
     P.n[:] = list(n)
     P.periodic[:] = list(periodic)
@@ -361,4 +388,21 @@ def make_params(*, n=(1, 1, 1), d=(1.0, 1.0, 1.0), x0=(0.0, 0.0, 0.0), periodic=
     P.mass[:] = [1.0, 1.0, 0.0, ion_mass]
     fpl = list(fp) + [0.0] * (16 - len(fp))
     P.fp[:] = fpl
+    P.ens_bits = int(ens_bits)
+    if ens is not None:
+        tab = np.ascontiguousarray(ens, dtype=np.float64).reshape(-1, ENS_STRIDE)
+        P._ens_keep = tab
+        P.n_ens = len(tab)
+        P.ens = _dp(tab)
+    P.emit_fg, P.pair_fg = float(emit_fg), float(pair_fg)
+    P.emit_ng, P.pair_ng = int(emit_ng), int(pair_ng)
+    P.thin_interval = int(thin_interval)
+    P.thin_limit[:] = [int(v) for v in thin_limit]
     return P
+
+
+def field_ensemble(P: Params, pid: int, t: float):
+    E = np.zeros(3)
+    B = np.zeros(3)
+    lib().or_field_ensemble(ctypes.byref(P), int(pid), float(t), _dp(E), _dp(B))
+    return E, B

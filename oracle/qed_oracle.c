@@ -38,6 +38,12 @@
  *                   form defects in uniform B
  *   Yee, CIC,       discrete dispersion relation; div B; linear fields exact;
  *   Esirkepov       discrete continuity equation
+ *   ensembles       one ensemble reproduces the single-field runs exactly;
+ *                   ensembles run together equal ensembles run alone
+ *   f_g, N_g        parents' histories identical to f_g = N_g = 1; product
+ *                   weight and spectrum unbiased (Sec. VI)
+ *   thinning        total weight of each group conserved; groups at or
+ *                   below the limit untouched; survivors binomial
  *   parity unpinned: the absolute output of Philox4x32-10 (no published
  *                   known-answer vectors are available here; uniformity and
  *                   decorrelation of the draws are checked statistically).
@@ -51,8 +57,11 @@
 #define OR_PI 3.14159265358979323846
 
 enum { OR_ELECTRON = 0, OR_POSITRON = 1, OR_PHOTON = 2, OR_ION = 3, OR_NSPECIES = 4 };
-enum { OR_PURPOSE_EMIT = 1, OR_PURPOSE_PAIR = 2, OR_PURPOSE_CHILD = 3 };
-enum { OR_FIELD_GRID = 0, OR_FIELD_UNIFORM = 1, OR_FIELD_GAUSSIAN_LP = 2, OR_FIELD_ROTATING_E = 3 };
+enum { OR_PURPOSE_EMIT = 1, OR_PURPOSE_PAIR = 2, OR_PURPOSE_CHILD = 3, OR_PURPOSE_KEEP = 4,
+       OR_PURPOSE_THIN = 5 };
+enum { OR_FIELD_GRID = 0, OR_FIELD_UNIFORM = 1, OR_FIELD_GAUSSIAN_LP = 2, OR_FIELD_ROTATING_E = 3,
+       OR_FIELD_ENSEMBLE = 4 };
+#define OR_ENS_STRIDE 9   /* per ensemble: E0, omega, phase, Eu[3], Bu[3] */
 
 /* ------------------------------------------------------------------------ */
 /* Synchrotron functions (Sec. IV.E, below Eq. (20) and Eq. (21)):
@@ -534,6 +543,18 @@ typedef struct {
     double lg_lo, lg_hi;     /* log10(delta) range of the spectrum */
     double charge[4], mass[4];
     double fp[16];           /* analytic field parameters */
+    /* independent ensembles (OR_FIELD_ENSEMBLE): the top ens_bits bits of an
+     * id name the particle's ensemble; products keep their parent's bits */
+    int32_t ens_bits;        /* 0..16; 0 = no ensembles */
+    int32_t n_ens;
+    const double *ens;       /* n_ens x OR_ENS_STRIDE */
+    /* tunable generator factors of Sec. VI (values <= 1 mean 1) */
+    double emit_fg, pair_fg; /* product kept with probability 1/f_g, weight x f_g */
+    int32_t emit_ng, pair_ng;/* N_g product samples per occasion, weight / N_g */
+    /* thinning with global even redistribution (Sec. VI) */
+    int32_t thin_interval;   /* thin after every step s with (s+1) % interval == 0 */
+    int32_t reserved;
+    int64_t thin_limit[4];   /* per species: most particles a group keeps (0 = off) */
 } or_params;
 
 typedef struct {
@@ -545,6 +566,9 @@ typedef struct {
 typedef struct {
     int64_t emissions, pairs, substeps_lepton, substeps_photon;
     int64_t pm_gt1, pp_gt1, capped, absorbed, overflow, nonfinite;
+    int64_t photons_created; /* photons made (all N_g samples, after the 1/f_g keep) */
+    int64_t pairs_created;   /* pairs made, likewise */
+    int64_t thinned;         /* particles removed by thinning */
     double energy_defect;    /* sum of w*(energy before - energy after) over events */
     double *spectrum;        /* nbins, weighted by w, over log10(delta) */
     double *spectrum_energy; /* nbins, weighted by w, over log10(photon energy) with the same range */
@@ -565,6 +589,55 @@ typedef struct {
     uint64_t id;
     int alive;
 } or_particle;
+
+/* Ensemble of a particle: the top ens_bits bits of its id (0 without). */
+static uint32_t or_ensemble(const or_params *P, uint64_t id)
+{
+    return P->ens_bits > 0 ? (uint32_t)(id >> (64 - P->ens_bits)) : 0u;
+}
+
+/* Id of a product: or_child_id of the parent, with the parent's ensemble
+ * bits kept so that products stay in their parent's ensemble.  kind is the
+ * product species plus (sample << 8) for the extra samples of N_g. */
+static uint64_t or_product_id(const or_params *P, uint64_t parent, uint32_t step, uint32_t sub,
+                              uint32_t kind)
+{
+    uint64_t mix = or_child_id(parent, step, sub, kind, P->seed);
+    if (P->ens_bits <= 0) return mix;
+    uint64_t hi = ~(uint64_t)0 << (64 - P->ens_bits);
+    return (parent & hi) | (mix & ~hi);
+}
+
+/* Field of ensemble e at time t: a uniform part plus a rotating E,
+ *   E = Eu + E0 (cos(omega t + phase), sin(omega t + phase), 0),  B = Bu.
+ * A particle whose ensemble has no table row sees no field. */
+void or_field_ensemble(const or_params *P, uint64_t id, double t, double E[3], double B[3])
+{
+    uint32_t e = or_ensemble(P, id);
+    E[0] = E[1] = E[2] = 0.0;
+    B[0] = B[1] = B[2] = 0.0;
+    if (!P->ens || e >= (uint32_t)P->n_ens) return;
+    const double *q = P->ens + (size_t)OR_ENS_STRIDE * e;
+    double ph = q[1] * t + q[2];
+    E[0] = q[3] + q[0] * cos(ph);
+    E[1] = q[4] + q[0] * sin(ph);
+    E[2] = q[5];
+    B[0] = q[6]; B[1] = q[7]; B[2] = q[8];
+}
+
+/* Generator factor f_g (Sec. VI): a product of an accepted draw is kept
+ * with probability 1/f_g.  Draws a uniform only when f_g > 1. */
+static int or_keep(const or_params *P, double fg, uint64_t id, uint32_t step, uint32_t sub,
+                   uint32_t sample, uint32_t generator)
+{
+    if (!(fg > 1.0)) return 1;
+    double u, unused;
+    or_draw(id, step, sub, OR_PURPOSE_KEEP | (sample << 8) | (generator << 16), P->seed, &u, &unused);
+    return u < 1.0 / fg;
+}
+
+static double or_fg(double fg) { return fg > 1.0 ? fg : 1.0; }
+static int or_ng(int32_t ng) { return ng > 1 ? (int)ng : 1; }
 
 static void or_spectrum_add(or_ctx *C, double delta, double eps, double w)
 {
@@ -653,23 +726,43 @@ static void or_process(or_ctx *C, int sp, or_particle *q, double t_span,
             or_draw(q->id, C->step, (uint32_t)s, OR_PURPOSE_EMIT, P->seed, &r1, &r2);
             double pm = or_Pm(r1, chi, g, h);
             if (pm > 1.0) C->D->pm_gt1++;
-            if (r2 < pm) {
-                /* Emission: photon along p carrying delta of it; the parent
-                 * keeps (1 - delta) of its momentum. */
-                double delta = r1 * r1 * r1;
+            /* Products (Sec. VI): N_g samples of the generator, sample 0 being
+             * the parent's own draw; each accepted sample makes a photon
+             * along p carrying delta = a1^3 of it, kept with probability
+             * 1/f_g, with weight w f_g / N_g. */
+            double p0[3] = {q->p[0], q->p[1], q->p[2]};
+            int ng = or_ng(P->emit_ng);
+            double fg = or_fg(P->emit_fg);
+            for (int j = 0; j < ng; ++j) {
+                double a1 = r1, a2 = r2, pmj = pm;
+                if (j > 0) {
+                    or_draw(q->id, C->step, (uint32_t)s, OR_PURPOSE_EMIT | ((uint32_t)j << 8), P->seed, &a1, &a2);
+                    pmj = or_Pm(a1, chi, g, h);
+                    if (pmj > 1.0) C->D->pm_gt1++;
+                }
+                if (!(a2 < pmj)) continue;
+                if (!or_keep(P, fg, q->id, C->step, (uint32_t)s, (uint32_t)j, 0u)) continue;
+                double delta = a1 * a1 * a1;
                 or_particle ph;
-                for (int c = 0; c < 3; ++c) { ph.x[c] = q->x[c]; ph.p[c] = delta * q->p[c]; }
-                ph.w = q->w;
-                ph.id = or_child_id(q->id, C->step, (uint32_t)s, OR_PHOTON, P->seed);
+                for (int c = 0; c < 3; ++c) { ph.x[c] = q->x[c]; ph.p[c] = delta * p0[c]; }
+                ph.w = q->w * (fg / (double)ng);
+                ph.id = or_product_id(P, q->id, C->step, (uint32_t)s, OR_PHOTON | ((uint32_t)j << 8));
                 ph.alive = 1;
-                double e_before = sqrt(m * m + q->p[0] * q->p[0] + q->p[1] * q->p[1] + q->p[2] * q->p[2]);
-                for (int c = 0; c < 3; ++c) q->p[c] = (1.0 - delta) * q->p[c];
-                C->D->emissions++;
+                C->D->photons_created++;
                 double eps = sqrt(ph.p[0] * ph.p[0] + ph.p[1] * ph.p[1] + ph.p[2] * ph.p[2]);
+                or_spectrum_add(C, delta, eps, ph.w);
+                or_emit_child(C, OR_PHOTON, &ph, (double)(n - 1 - s) * h, E, B);
+            }
+            if (r2 < pm) {
+                /* The parent's event: it keeps (1 - delta) of its momentum. */
+                double delta = r1 * r1 * r1;
+                double e_before = sqrt(m * m + p0[0] * p0[0] + p0[1] * p0[1] + p0[2] * p0[2]);
+                for (int c = 0; c < 3; ++c) q->p[c] = (1.0 - delta) * p0[c];
+                C->D->emissions++;
+                double k[3] = {delta * p0[0], delta * p0[1], delta * p0[2]};
+                double eps = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
                 double e_after = sqrt(m * m + q->p[0] * q->p[0] + q->p[1] * q->p[1] + q->p[2] * q->p[2]);
                 C->D->energy_defect += q->w * (e_before - e_after - eps);
-                or_spectrum_add(C, delta, eps, q->w);
-                or_emit_child(C, OR_PHOTON, &ph, (double)(n - 1 - s) * h, E, B);
             }
         }
     } else { /* photon */
@@ -691,27 +784,45 @@ static void or_process(or_ctx *C, int sp, or_particle *q, double t_span,
             or_draw(q->id, C->step, (uint32_t)s, OR_PURPOSE_PAIR, P->seed, &r1, &r2);
             double pp = or_Pp(r1, chig, eps, h);
             if (pp > 1.0) C->D->pp_gt1++;
-            if (r2 < pp) {
-                /* Pair: electron carries r1 of the photon momentum, the
-                 * positron 1 - r1; both inherit the weight; photon removed. */
+            /* Products (Sec. VI): N_g samples, sample 0 being the photon's own
+             * draw; each accepted sample makes an electron with a1 of the
+             * photon momentum and a positron with 1 - a1, kept with
+             * probability 1/f_g, with weight w f_g / N_g. */
+            int ng = or_ng(P->pair_ng);
+            double fg = or_fg(P->pair_fg);
+            double t_rem = (double)(n - 1 - s) * h;
+            for (int j = 0; j < ng; ++j) {
+                double a1 = r1, a2 = r2, ppj = pp;
+                if (j > 0) {
+                    or_draw(q->id, C->step, (uint32_t)s, OR_PURPOSE_PAIR | ((uint32_t)j << 8), P->seed, &a1, &a2);
+                    ppj = or_Pp(a1, chig, eps, h);
+                    if (ppj > 1.0) C->D->pp_gt1++;
+                }
+                if (!(a2 < ppj)) continue;
+                if (!or_keep(P, fg, q->id, C->step, (uint32_t)s, (uint32_t)j, 1u)) continue;
                 or_particle el, po;
                 for (int c = 0; c < 3; ++c) {
                     el.x[c] = po.x[c] = q->x[c];
-                    el.p[c] = r1 * q->p[c];
-                    po.p[c] = (1.0 - r1) * q->p[c];
+                    el.p[c] = a1 * q->p[c];
+                    po.p[c] = (1.0 - a1) * q->p[c];
                 }
-                el.w = po.w = q->w;
-                el.id = or_child_id(q->id, C->step, (uint32_t)s, OR_ELECTRON, P->seed);
-                po.id = or_child_id(q->id, C->step, (uint32_t)s, OR_POSITRON, P->seed);
+                el.w = po.w = q->w * (fg / (double)ng);
+                el.id = or_product_id(P, q->id, C->step, (uint32_t)s, OR_ELECTRON | ((uint32_t)j << 8));
+                po.id = or_product_id(P, q->id, C->step, (uint32_t)s, OR_POSITRON | ((uint32_t)j << 8));
                 el.alive = po.alive = 1;
+                C->D->pairs_created++;
+                or_emit_child(C, OR_ELECTRON, &el, t_rem, E, B);
+                or_emit_child(C, OR_POSITRON, &po, t_rem, E, B);
+            }
+            if (r2 < pp) {
+                /* The photon's event: it converts and is removed. */
+                double ke[3], kp[3];
+                for (int c = 0; c < 3; ++c) { ke[c] = r1 * q->p[c]; kp[c] = (1.0 - r1) * q->p[c]; }
                 q->alive = 0;
                 C->D->pairs++;
                 C->D->energy_defect += q->w * (eps
-                    - sqrt(1.0 + el.p[0] * el.p[0] + el.p[1] * el.p[1] + el.p[2] * el.p[2])
-                    - sqrt(1.0 + po.p[0] * po.p[0] + po.p[1] * po.p[1] + po.p[2] * po.p[2]));
-                double t_rem = (double)(n - 1 - s) * h;
-                or_emit_child(C, OR_ELECTRON, &el, t_rem, E, B);
-                or_emit_child(C, OR_POSITRON, &po, t_rem, E, B);
+                    - sqrt(1.0 + ke[0] * ke[0] + ke[1] * ke[1] + ke[2] * ke[2])
+                    - sqrt(1.0 + kp[0] * kp[0] + kp[1] * kp[1] + kp[2] * kp[2]));
                 break;
             }
         }
@@ -751,6 +862,8 @@ int or_step(const or_params *P, or_store S[4], or_diag *D, double *const f[6], d
             double E[3], B[3];
             if (P->field_mode == OR_FIELD_GRID)
                 or_gather(P->n, P->d, P->x0, f, q.x, E, B);
+            else if (P->field_mode == OR_FIELD_ENSEMBLE)
+                or_field_ensemble(P, q.id, t, E, B);
             else
                 or_field(P->field_mode, P->fp, q.x, t, E, B);
             int finite = 1;
@@ -775,6 +888,64 @@ int or_step(const or_params *P, or_store S[4], or_diag *D, double *const f[6], d
         s->n = o;
         free(alive[sp]);
     }
+    return 0;
+}
+
+/* Thinning with global even redistribution (Sec. VI), after step `step`.
+ * A group is one ensemble (or the whole species without ensembles).  For
+ * each species with a limit L and each group holding N > L particles, every
+ * particle survives with probability L/N (its own uniform, purpose THIN),
+ * and the survivors' weights are multiplied by (sum of the group's weights)
+ * / (sum of the survivors' weights), so the group's total weight is kept.
+ * A group in which nothing would survive is left as it is.  Particles whose
+ * ensemble has no table row belong to no group.  Survivors keep their order. */
+int or_thin(const or_params *P, or_store S[4], or_diag *D, uint32_t step)
+{
+    int64_t G = P->ens_bits > 0 ? (int64_t)P->n_ens : 1;
+    if (G <= 0) return 0;
+    int64_t *count = (int64_t *)malloc(sizeof(int64_t) * (size_t)G);
+    double *wall = (double *)malloc(sizeof(double) * (size_t)G);
+    double *wsurv = (double *)malloc(sizeof(double) * (size_t)G);
+    if (!count || !wall || !wsurv) { free(count); free(wall); free(wsurv); return -1; }
+    for (int sp = 0; sp < OR_NSPECIES; ++sp) {
+        int64_t L = P->thin_limit[sp];
+        if (L <= 0) continue;
+        or_store *s = &S[sp];
+        for (int64_t g = 0; g < G; ++g) { count[g] = 0; wall[g] = 0.0; wsurv[g] = 0.0; }
+        for (int64_t i = 0; i < s->n; ++i) {
+            uint32_t g = or_ensemble(P, s->id[i]);
+            if ((int64_t)g >= G) continue;
+            count[g]++;
+            wall[g] += s->w[i];
+        }
+        /* the survivors of a group, and their weight */
+        for (int64_t i = 0; i < s->n; ++i) {
+            uint32_t g = or_ensemble(P, s->id[i]);
+            if ((int64_t)g >= G || count[g] <= L) continue;
+            double u, unused;
+            or_draw(s->id[i], step, 0u, OR_PURPOSE_THIN, P->seed, &u, &unused);
+            if (u < (double)L / (double)count[g]) wsurv[g] += s->w[i];
+        }
+        int64_t o = 0;
+        for (int64_t i = 0; i < s->n; ++i) {
+            uint32_t g = or_ensemble(P, s->id[i]);
+            int keep = 1;
+            double w = s->w[i];
+            if ((int64_t)g < G && count[g] > L && wsurv[g] > 0.0) {
+                double u, unused;
+                or_draw(s->id[i], step, 0u, OR_PURPOSE_THIN, P->seed, &u, &unused);
+                if (u < (double)L / (double)count[g]) w = w * (wall[g] / wsurv[g]);
+                else keep = 0;
+            }
+            if (!keep) { D->thinned++; continue; }
+            s->x[o] = s->x[i]; s->y[o] = s->y[i]; s->z[o] = s->z[i];
+            s->px[o] = s->px[i]; s->py[o] = s->py[i]; s->pz[o] = s->pz[i];
+            s->w[o] = w; s->id[o] = s->id[i];
+            ++o;
+        }
+        s->n = o;
+    }
+    free(count); free(wall); free(wsurv);
     return 0;
 }
 
