@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define QED_ABI_VERSION 1
+#define QED_ABI_VERSION 2
 
 typedef enum qed_status {
     QED_OK = 0,
@@ -82,8 +82,21 @@ typedef enum qed_field_mode {
      *       z_focus, t_focus, phase0} */
     QED_FIELD_GAUSSIAN_LP = 2,
     /* E = E0 (cos(omega t), sin(omega t), 0), B = 0: fp = {E0, omega} */
-    QED_FIELD_ROTATING_E = 3
+    QED_FIELD_ROTATING_E = 3,
+    /* independent ensembles (batched test-particle runs): the top ens_bits
+     * bits of a particle's id name its ensemble e, whose row of the table
+     * given to qed_ensembles_set defines a uniform field plus a rotating E:
+     *   E = Eu + E0 (cos(omega t + phase), sin(omega t + phase), 0),  B = Bu,
+     *   row = {E0, omega, phase, Eu_x, Eu_y, Eu_z, Bu_x, Bu_y, Bu_z, thin_scale}.
+     * Products keep their parent's ensemble bits.  A particle whose ensemble
+     * has no row sees no field.  A 10th entry thin_scale > 0 scales the
+     * ensemble's thinning limits (floor(thin_limit[sp] * thin_scale)), so an
+     * instance keeps a budget in proportion to its size. */
+    QED_FIELD_ENSEMBLE = 4
 } qed_field_mode;
+
+#define QED_ENS_STRIDE 10    /* doubles per row of the ensemble table */
+#define QED_MAX_ENS_BITS 16
 
 /* Position lattice (and Yee mesh in QED_FIELD_GRID).  Particles are stored
  * as a cell index plus an offset in [0,1) cell units; node (i,j,k) sits at
@@ -127,7 +140,44 @@ typedef struct qed_params {
     int64_t pending_capacity;   /* products per step that evolve within the
                                    step (0 = 1/8 of the total capacity,
                                    at least 65536) */
+    /* --- independent ensembles (QED_FIELD_ENSEMBLE) --- */
+    int32_t ens_bits;           /* top id bits naming the ensemble, 0..16 */
+    /* --- controlling the particle count (Sec. VI) --- */
+    int32_t thin_interval;      /* thin after every step whose index s has
+                                   (s + 1) % thin_interval == 0 (0 = never) */
+    int64_t thin_limit[4];      /* per species: the most particles a group
+                                   (one ensemble, or the whole species
+                                   without ensembles) keeps; 0 = not thinned.
+                                   A group of N > L particles keeps each with
+                                   probability L/N and multiplies the
+                                   survivors' weights by (its total weight) /
+                                   (the survivors' weight): global even
+                                   redistribution */
+    double emit_fg, pair_fg;    /* generator factors f_g (values <= 1 mean 1):
+                                   a product of an accepted draw is kept with
+                                   probability 1/f_g and weight x f_g; the
+                                   parent's own event is unchanged */
+    int32_t emit_ng, pair_ng;   /* N_g samples of the generator per occasion
+                                   for the products (values <= 1 mean 1),
+                                   weight x 1/N_g; sample 0 is the parent's */
 } qed_params;
+
+/* Launch shapes and schedules; they change the speed, never the results
+ * (every particle's random stream is keyed by its id). */
+typedef struct qed_tuning {
+    int32_t photon_blocks_per_sm;  /* resident 256-thread blocks of the photon
+                                      pass per SM (1 .. its occupancy limit) */
+    int32_t massive_blocks_per_sm; /* likewise for electrons, positrons, ions */
+    int32_t work_chunk;            /* particles a block of the e-/e+/ion pass
+                                      takes per grab of the shared work
+                                      counter (multiple of 256); 0 = a static
+                                      grid-stride loop */
+    int32_t compact_interval;      /* steps between removals of dead records
+                                      (and re-sorts), >= 1 */
+    int32_t sort_massive;          /* QED_FIELD_ENSEMBLE: at each compaction,
+                                      order e-, e+ and ions by ensemble */
+    int32_t reserved[3];           /* must be 0 */
+} qed_tuning;
 
 /* Caller-owned Yee arrays (device memory, context precision). */
 typedef struct qed_fields {
@@ -150,6 +200,10 @@ typedef struct qed_diag {
     int64_t absorbed;           /* particles removed at open boundaries */
     int64_t overflow;           /* products lost to a full buffer */
     int64_t nonfinite;          /* particles with non-finite field/momentum */
+    int64_t photons_created;    /* photons made (equals emissions unless the
+                                   generator factors are set) */
+    int64_t pairs_created;      /* pairs made (likewise) */
+    int64_t thinned;            /* particles removed by thinning */
     int64_t kernel_launches;    /* CUDA kernels this context has launched */
     int64_t step;               /* steps taken */
     double time;                /* current time */
@@ -224,6 +278,36 @@ int qed_particles_read_static(qed_ctx *ctx, int species, double *x, double *p, d
  * nothing, so it may be captured in a CUDA graph.  QED_ERR_STATE after a
  * device error, QED_ERR_ARG for dt <= 0 or missing fields. */
 int qed_step(qed_ctx *ctx, const qed_fields *fields, double dt, int32_t nsteps, void *stream);
+
+/* Set the field table of QED_FIELD_ENSEMBLE: n_ens rows of QED_ENS_STRIDE
+ * doubles (host memory, copied; see QED_FIELD_ENSEMBLE).  n_ens must be in
+ * 1 .. 2^ens_bits (1 when ens_bits is 0) and every entry finite, else
+ * QED_ERR_ARG.  May be called between steps to change the fields.
+ * qed_step in this mode returns QED_ERR_ARG until a table is set. */
+int qed_ensembles_set(qed_ctx *ctx, int32_t n_ens, const double *table, void *stream);
+
+/* Read or replace the launch shapes and schedules (host struct).
+ * QED_ERR_ARG for values outside the documented ranges. */
+int qed_get_tuning(qed_ctx *ctx, qed_tuning *out);
+int qed_set_tuning(qed_ctx *ctx, const qed_tuning *tuning);
+
+/* Pick the tuning by measurement: advances the simulation by real steps of
+ * dt (the results are the ones untuned steps would give), trying the
+ * candidates of each field of qed_tuning in turn, each for
+ * max(steps_per_trial, its compaction interval) steps timed with CUDA
+ * events on the stream, in the order listed and then reversed, so that a
+ * workload that grows during the search does not favour the later
+ * candidates.  The cost of a candidate is its time per particle-step.
+ * Candidates: 1 .. 4 blocks per SM for each pass (up to the occupancy
+ * limit), work chunks {0, 256, 1024, 4096, 16384}, compaction intervals
+ * {c, c/2, c/4} below the current interval c (the capacities were sized
+ * for c), and with ensembles sorting on or off.  The search stops before a
+ * trial that would take more than max_steps steps in all; the fields not
+ * reached keep their values.  Applies the best tuning found, writes it to
+ * *out (may be NULL) and the number of steps taken to *steps_taken (may be
+ * NULL).  Synchronises the stream. */
+int qed_autotune(qed_ctx *ctx, const qed_fields *fields, double dt, int32_t steps_per_trial,
+                 int64_t max_steps, void *stream, qed_tuning *out, int64_t *steps_taken);
 
 /* Set the step counter and time used by the next qed_step (the random
  * streams are keyed by the step, so a restart reproduces a run exactly). */

@@ -61,7 +61,7 @@ enum { OR_PURPOSE_EMIT = 1, OR_PURPOSE_PAIR = 2, OR_PURPOSE_CHILD = 3, OR_PURPOS
        OR_PURPOSE_THIN = 5 };
 enum { OR_FIELD_GRID = 0, OR_FIELD_UNIFORM = 1, OR_FIELD_GAUSSIAN_LP = 2, OR_FIELD_ROTATING_E = 3,
        OR_FIELD_ENSEMBLE = 4 };
-#define OR_ENS_STRIDE 9   /* per ensemble: E0, omega, phase, Eu[3], Bu[3] */
+#define OR_ENS_STRIDE 10  /* per ensemble: E0, omega, phase, Eu[3], Bu[3], thin_scale */
 
 /* ------------------------------------------------------------------------ */
 /* Synchrotron functions (Sec. IV.E, below Eq. (20) and Eq. (21)):
@@ -547,7 +547,8 @@ typedef struct {
      * id name the particle's ensemble; products keep their parent's bits */
     int32_t ens_bits;        /* 0..16; 0 = no ensembles */
     int32_t n_ens;
-    const double *ens;       /* n_ens x OR_ENS_STRIDE */
+    const double *ens;       /* n_ens x OR_ENS_STRIDE; thin_scale > 0 scales the
+                              * thinning limits of the ensemble's group */
     /* tunable generator factors of Sec. VI (values <= 1 mean 1) */
     double emit_fg, pair_fg; /* product kept with probability 1/f_g, weight x f_g */
     int32_t emit_ng, pair_ng;/* N_g product samples per occasion, weight / N_g */
@@ -891,12 +892,26 @@ int or_step(const or_params *P, or_store S[4], or_diag *D, double *const f[6], d
     return 0;
 }
 
+/* Limit of species sp in group g: thin_limit[sp], scaled by the ensemble's
+ * thin_scale when that is positive (floor of the product). */
+static int64_t or_thin_limit(const or_params *P, int sp, uint32_t g)
+{
+    int64_t L = P->thin_limit[sp];
+    if (P->field_mode == OR_FIELD_ENSEMBLE && P->ens_bits > 0 && P->ens && (int64_t)g < (int64_t)P->n_ens) {
+        double sc = P->ens[(size_t)OR_ENS_STRIDE * g + 9];
+        if (sc > 0.0) L = (int64_t)floor((double)L * sc);
+    }
+    return L;
+}
+
 /* Thinning with global even redistribution (Sec. VI), after step `step`.
  * A group is one ensemble (or the whole species without ensembles).  For
  * each species with a limit L and each group holding N > L particles, every
  * particle survives with probability L/N (its own uniform, purpose THIN),
  * and the survivors' weights are multiplied by (sum of the group's weights)
  * / (sum of the survivors' weights), so the group's total weight is kept.
+ * The limit L of a group is thin_limit[sp], times the ensemble's thin_scale
+ * when that is positive (an independent instance keeps its own budget).
  * A group in which nothing would survive is left as it is.  Particles whose
  * ensemble has no table row belong to no group.  Survivors keep their order. */
 int or_thin(const or_params *P, or_store S[4], or_diag *D, uint32_t step)
@@ -908,8 +923,7 @@ int or_thin(const or_params *P, or_store S[4], or_diag *D, uint32_t step)
     double *wsurv = (double *)malloc(sizeof(double) * (size_t)G);
     if (!count || !wall || !wsurv) { free(count); free(wall); free(wsurv); return -1; }
     for (int sp = 0; sp < OR_NSPECIES; ++sp) {
-        int64_t L = P->thin_limit[sp];
-        if (L <= 0) continue;
+        if (P->thin_limit[sp] <= 0) continue;
         or_store *s = &S[sp];
         for (int64_t g = 0; g < G; ++g) { count[g] = 0; wall[g] = 0.0; wsurv[g] = 0.0; }
         for (int64_t i = 0; i < s->n; ++i) {
@@ -921,7 +935,9 @@ int or_thin(const or_params *P, or_store S[4], or_diag *D, uint32_t step)
         /* the survivors of a group, and their weight */
         for (int64_t i = 0; i < s->n; ++i) {
             uint32_t g = or_ensemble(P, s->id[i]);
-            if ((int64_t)g >= G || count[g] <= L) continue;
+            if ((int64_t)g >= G) continue;
+            int64_t L = or_thin_limit(P, sp, g);
+            if (count[g] <= L) continue;
             double u, unused;
             or_draw(s->id[i], step, 0u, OR_PURPOSE_THIN, P->seed, &u, &unused);
             if (u < (double)L / (double)count[g]) wsurv[g] += s->w[i];
@@ -931,6 +947,7 @@ int or_thin(const or_params *P, or_store S[4], or_diag *D, uint32_t step)
             uint32_t g = or_ensemble(P, s->id[i]);
             int keep = 1;
             double w = s->w[i];
+            int64_t L = (int64_t)g < G ? or_thin_limit(P, sp, g) : 0;
             if ((int64_t)g < G && count[g] > L && wsurv[g] > 0.0) {
                 double u, unused;
                 or_draw(s->id[i], step, 0u, OR_PURPOSE_THIN, P->seed, &u, &unused);

@@ -61,6 +61,29 @@ void release(qed_ctx *c) {
   cudaFree(c->d_blk_cursor);
   cudaFree(c->d_tile);
   cudaFree(c->stage);
+  cudaFree(c->d_ens);
+  cudaFree(c->d_ens_field);
+  cudaFree(c->d_thin);
+}
+
+int read_counters(qed_ctx *c, unsigned long long *cnt, cudaStream_t s) {
+  if (cudaMemcpyAsync(cnt, c->d_counters, sizeof(unsigned long long) * qed::kNumCounters, cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return QED_ERR_CUDA;
+  return QED_OK;
+}
+
+int check_tuning(const qed_ctx *c, const qed_tuning *t) {
+  int maxp = 0, maxm = 0;
+  if (qed_step_kernel_max_blocks(const_cast<qed_ctx *>(c), &maxp, &maxm) != QED_OK) return QED_ERR_CUDA;
+  if (t->photon_blocks_per_sm < 1 || t->photon_blocks_per_sm > maxp) return QED_ERR_ARG;
+  if (t->massive_blocks_per_sm < 1 || t->massive_blocks_per_sm > maxm) return QED_ERR_ARG;
+  if (t->work_chunk < 0 || t->work_chunk % 256 != 0 || t->work_chunk > (1 << 24)) return QED_ERR_ARG;
+  if (t->compact_interval < 1 || (t->sort_massive != 0 && t->sort_massive != 1)) return QED_ERR_ARG;
+  for (int k = 0; k < 3; ++k)
+    if (t->reserved[k] != 0) return QED_ERR_ARG;
+  return QED_OK;
 }
 
 // Classify a caller pointer: returns a device-usable alias, or nullptr when
@@ -133,7 +156,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     ncell *= g->n[k];
   }
   if (ncell >= (1ll << 31)) return QED_ERR_ARG;
-  if (g->field_mode < QED_FIELD_GRID || g->field_mode > QED_FIELD_ROTATING_E || g->reserved != 0)
+  if (g->field_mode < QED_FIELD_GRID || g->field_mode > QED_FIELD_ENSEMBLE || g->reserved != 0)
     return QED_ERR_ARG;
   if (g->field_mode == QED_FIELD_GRID)
     for (int k = 0; k < 3; ++k)
@@ -142,6 +165,14 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     return QED_ERR_ARG;
   if (p->nbins > 0 && !(p->lg_hi > p->lg_lo)) return QED_ERR_ARG;
   if (p->pending_capacity < 0 || p->compact_interval < 0) return QED_ERR_ARG;
+  if (p->ens_bits < 0 || p->ens_bits > QED_MAX_ENS_BITS || p->thin_interval < 0) return QED_ERR_ARG;
+  if (!std::isfinite(p->emit_fg) || !std::isfinite(p->pair_fg) || p->emit_ng > 64 || p->pair_ng > 64)
+    return QED_ERR_ARG;
+  bool thinning = false;
+  for (int k = 0; k < 4; ++k) {
+    if (p->thin_limit[k] < 0) return QED_ERR_ARG;
+    thinning |= p->thin_limit[k] > 0;
+  }
   long long total_cap = 0, max_cap = 0;
   for (int k = 0; k < 4; ++k) {
     if (sp->capacity[k] < 0 || sp->capacity[k] > (1ll << 40)) return QED_ERR_ARG;
@@ -157,6 +188,8 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
   c->grid = *g;
   c->species = *sp;
   c->par = *p;
+  c->ext = g->field_mode == QED_FIELD_ENSEMBLE || p->emit_fg > 1.0 || p->pair_fg > 1.0 || p->emit_ng > 1 ||
+           p->pair_ng > 1;
   cudaStream_t s = as_stream(stream);
   int rc = QED_OK;
   cudaDeviceProp prop;
@@ -194,6 +227,24 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     if (rc == QED_OK) rc = dalloc(&c->d_blk_start, sizeof(unsigned) * 4 * (nblk + 1));
     if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (nblk + 1));
   }
+  if (g->field_mode == QED_FIELD_ENSEMBLE) {
+    c->ens_cap = 1 << p->ens_bits;
+    if (rc == QED_OK) rc = dalloc(&c->d_ens, sizeof(double) * QED_ENS_STRIDE * c->ens_cap);
+    if (rc == QED_OK)
+      rc = dalloc(&c->d_ens_field, (c->prec == 64 ? sizeof(double) : sizeof(float)) * qed::kEnsFieldStride *
+                                       c->ens_cap);
+    if (p->ens_bits > 0) {
+      // counting sort of e-, e+ and ions by ensemble
+      c->key_ensembles = 1;
+      c->nblk = c->ens_cap;
+      if (rc == QED_OK) rc = dalloc(&c->d_blk_start, sizeof(unsigned) * 4 * (c->nblk + 1));
+      if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (c->nblk + 1));
+    }
+  }
+  if (thinning) {
+    c->thin_groups = p->ens_bits > 0 ? (1 << p->ens_bits) : 1;
+    if (rc == QED_OK) rc = dalloc(&c->d_thin, (size_t)24 * c->thin_groups);
+  }
   if (rc == QED_OK) rc = dalloc(&c->d_counters, sizeof(unsigned long long) * qed::kNumCounters);
   if (rc == QED_OK) rc = dalloc(&c->d_spec, sizeof(double) * (p->nbins > 0 ? p->nbins : 1));
   if (rc == QED_OK) rc = dalloc(&c->d_spec_e, sizeof(double) * (p->nbins > 0 ? p->nbins : 1));
@@ -223,6 +274,15 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
   }
   if (rc == QED_OK) rc = qed_launch_chi_star(c, s);
   if (rc == QED_OK) rc = qed_step_kernel_blocks(c);
+  if (rc == QED_OK) {
+    int maxp = 0, maxm = 0;
+    rc = qed_step_kernel_max_blocks(c, &maxp, &maxm);
+    c->tune.photon_blocks_per_sm = maxp;
+    c->tune.massive_blocks_per_sm = maxm;
+    c->tune.work_chunk = 0;
+    c->tune.compact_interval = p->compact_interval > 0 ? p->compact_interval : 8;
+    c->tune.sort_massive = c->key_ensembles;
+  }
   if (rc == QED_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = QED_ERR_CUDA;
   if (rc != QED_OK) {
     cudaGetLastError();
@@ -314,6 +374,7 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
     for (int k = 0; k < 3; ++k)
       if (!f->E[k] || !f->B[k] || (c->par.deposit_on && !f->J[k])) return QED_ERR_ARG;
   }
+  if (c->grid.field_mode == QED_FIELD_ENSEMBLE && c->n_ens < 1) return QED_ERR_ARG;
   cudaStream_t s = as_stream(stream);
   for (int n = 0; n < nsteps; ++n) {
     if (grid && c->nblk > 0 && !c->sorted) {
@@ -330,17 +391,166 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
     if (rc == QED_OK && grid && c->par.deposit_on) rc = qed_launch_yee(c, f, dt, s);
     if (rc != QED_OK) return rc;
     c->step += 1;
+    if (c->par.thin_interval > 0 && c->step % c->par.thin_interval == 0)
+      for (int sp = 0; sp < 4; ++sp)
+        if ((rc = qed_launch_thin(c, sp, s)) != QED_OK) return rc;
     if (c->par.compact_interval > 0 && ++c->steps_since_compact >= c->par.compact_interval) {
       c->steps_since_compact = 0;
       for (int sp = 0; sp < 4; ++sp) {
-        // grid mode: re-sort the charged species by cell block, compact photons
-        rc = (grid && c->nblk > 0 && sp != QED_PHOTON) ? qed_launch_sort(c, sp, s)
-                                                        : qed_launch_compact(c, sp, true, s);
+        // grid mode: re-sort the charged species by cell block; ensembles:
+        // optionally order e-, e+ and ions by ensemble; photons: compaction
+        const bool sort = sp != QED_PHOTON && c->nblk > 0 &&
+                          (grid || (c->key_ensembles && c->tune.sort_massive));
+        rc = sort ? qed_launch_sort(c, sp, s) : qed_launch_compact(c, sp, true, s);
         if (rc != QED_OK) return rc;
       }
     }
   }
   return QED_OK;
+}
+
+int qed_ensembles_set(qed_ctx *c, int32_t n_ens, const double *table, void *stream) {
+  if (!c || c->grid.field_mode != QED_FIELD_ENSEMBLE || !table) return QED_ERR_ARG;
+  if (n_ens < 1 || n_ens > c->ens_cap) return QED_ERR_ARG;
+  double hmax = 0.0;
+  for (long long e = 0; e < n_ens; ++e) {
+    const double *q = table + e * QED_ENS_STRIDE;
+    for (int k = 0; k < QED_ENS_STRIDE; ++k)
+      if (!std::isfinite(q[k])) return QED_ERR_ARG;
+    // |E| + |B| <= |E0| + |Eu| + |Bu|
+    const double h = std::fabs(q[0]) + std::sqrt(q[3] * q[3] + q[4] * q[4] + q[5] * q[5]) +
+                     std::sqrt(q[6] * q[6] + q[7] * q[7] + q[8] * q[8]);
+    hmax = h > hmax ? h : hmax;
+  }
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemcpyAsync(c->d_ens, table, sizeof(double) * QED_ENS_STRIDE * n_ens, cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
+    return QED_ERR_CUDA;
+  c->n_ens = n_ens;
+  c->ens_hmax = hmax;
+  int rc = qed_launch_chi_star(c, s);   // eps* = chi*/hmax changes with the fields
+  if (rc != QED_OK) return rc;
+  return cudaStreamSynchronize(s) == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+int qed_get_tuning(qed_ctx *c, qed_tuning *out) {
+  if (!c || !out) return QED_ERR_ARG;
+  *out = c->tune;
+  return QED_OK;
+}
+
+int qed_set_tuning(qed_ctx *c, const qed_tuning *t) {
+  if (!c || !t) return QED_ERR_ARG;
+  int rc = check_tuning(c, t);
+  if (rc != QED_OK) return rc;
+  if (t->sort_massive && !c->key_ensembles) return QED_ERR_ARG;
+  c->tune = *t;
+  c->par.compact_interval = t->compact_interval;
+  return QED_OK;
+}
+
+int qed_autotune(qed_ctx *c, const qed_fields *f, double dt, int32_t steps_per_trial, int64_t max_steps,
+                 void *stream, qed_tuning *out, int64_t *steps_taken) {
+  if (!c || steps_per_trial < 1 || !(dt > 0.0) || max_steps < 0) return QED_ERR_ARG;
+  if (c->latched) return QED_ERR_STATE;
+  cudaStream_t s = as_stream(stream);
+  int maxp = 0, maxm = 0;
+  int rc = qed_step_kernel_max_blocks(c, &maxp, &maxm);
+  if (rc != QED_OK) return rc;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return QED_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return QED_ERR_CUDA;
+  }
+  int64_t taken = 0;
+  qed_tuning best = c->tune;
+  // the configured compaction interval bounds the candidates: the
+  // capacities were sized for the dead records it lets accumulate
+  const int ci_max = best.compact_interval;
+  unsigned long long cnt[qed::kNumCounters];
+  // time per particle-step of tuning t over whole compaction periods
+  auto trial = [&](const qed_tuning &t, double *cost) -> int {
+    c->tune = t;
+    c->par.compact_interval = t.compact_interval;
+    c->steps_since_compact = 0;
+    const int n = steps_per_trial > t.compact_interval ? steps_per_trial : t.compact_interval;
+    int r = read_counters(c, cnt, s);
+    if (r != QED_OK) return r;
+    unsigned long long ps0 = 0, ps1 = 0;
+    for (int k = 0; k < 4; ++k) ps0 += cnt[qed::kCntSpeciesSteps + k];
+    if (cudaEventRecord(e0, s) != cudaSuccess) return QED_ERR_CUDA;
+    r = qed_step(c, f, dt, n, stream);
+    if (r != QED_OK) return r;
+    if (cudaEventRecord(e1, s) != cudaSuccess) return QED_ERR_CUDA;
+    r = read_counters(c, cnt, s);
+    if (r != QED_OK) return r;
+    for (int k = 0; k < 4; ++k) ps1 += cnt[qed::kCntSpeciesSteps + k];
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return QED_ERR_CUDA;
+    taken += n;
+    *cost = ps1 > ps0 ? (double)ms / (double)(ps1 - ps0) : (double)ms;
+    return read_status(c, s);
+  };
+  bool out_of_steps = false;
+  // one field at a time; candidates in order, then reversed
+  auto tune_field = [&](int32_t qed_tuning::*field, const int *cand, int nc) -> int {
+    if (nc < 2 || out_of_steps) return QED_OK;
+    // the whole search of this field must fit in the step budget
+    int64_t need = 0;
+    for (int j = 0; j < nc; ++j) {
+      const int ci = field == &qed_tuning::compact_interval ? cand[j] : best.compact_interval;
+      need += 2 * (steps_per_trial > ci ? steps_per_trial : ci);
+    }
+    if (taken + need > max_steps) {
+      out_of_steps = true;
+      return QED_OK;
+    }
+    double sum[16] = {0};
+    for (int pass = 0; pass < 2; ++pass)
+      for (int k = 0; k < nc; ++k) {
+        const int j = pass == 0 ? k : nc - 1 - k;
+        qed_tuning t = best;
+        t.*field = cand[j];
+        double cost = 0.0;
+        int r = trial(t, &cost);
+        if (r != QED_OK) return r;
+        sum[j] += cost;
+      }
+    int jb = 0;
+    for (int j = 1; j < nc; ++j)
+      if (sum[j] < sum[jb]) jb = j;
+    best.*field = cand[jb];
+    return QED_OK;
+  };
+  int cand[16], nc = 0;
+  for (int b = 1; b <= maxp && nc < 4; ++b) cand[nc++] = b;
+  rc = tune_field(&qed_tuning::photon_blocks_per_sm, cand, nc);
+  if (rc == QED_OK) {
+    nc = 0;
+    for (int b = 1; b <= maxm && nc < 4; ++b) cand[nc++] = b;
+    rc = tune_field(&qed_tuning::massive_blocks_per_sm, cand, nc);
+  }
+  if (rc == QED_OK) {
+    const int chunks[5] = {0, 256, 1024, 4096, 16384};
+    rc = tune_field(&qed_tuning::work_chunk, chunks, 5);
+  }
+  if (rc == QED_OK) {
+    nc = 0;
+    for (int v = ci_max; v >= 1 && nc < 3; v /= 2) cand[nc++] = v;
+    rc = tune_field(&qed_tuning::compact_interval, cand, nc);
+  }
+  if (rc == QED_OK && c->key_ensembles) {
+    const int so[2] = {1, 0};
+    rc = tune_field(&qed_tuning::sort_massive, so, 2);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->tune = best;
+  c->par.compact_interval = best.compact_interval;
+  if (out) *out = best;
+  if (steps_taken) *steps_taken = taken;
+  return rc;
 }
 
 int qed_set_clock(qed_ctx *c, int64_t step, double time) {
@@ -400,6 +610,9 @@ int qed_diagnostics(qed_ctx *c, qed_diag *out, void *stream) {
   out->absorbed = (int64_t)cnt[qed::kCntAbsorbed];
   out->overflow = (int64_t)cnt[qed::kCntOverflow];
   out->nonfinite = (int64_t)cnt[qed::kCntNonfinite];
+  out->photons_created = (int64_t)cnt[qed::kCntPhotonsMade];
+  out->pairs_created = (int64_t)cnt[qed::kCntPairsMade];
+  out->thinned = (int64_t)cnt[qed::kCntThinned];
   out->particle_steps = 0;
   for (int k = 0; k < 4; ++k) {
     out->species_steps[k] = (int64_t)cnt[qed::kCntSpeciesSteps + k];

@@ -11,11 +11,14 @@
 namespace qed {
 
 constexpr int kMaxPass = 64;        // nesting depth of products within one step
-constexpr int kNumCounters = 16;    // device diagnostic counters
+constexpr int kNumCounters = 20;    // device diagnostic counters
 enum Counter {
   kCntEmissions = 0, kCntPairs, kCntSubLepton, kCntSubPhoton, kCntPmGt1, kCntPpGt1, kCntCapped,
-  kCntAbsorbed, kCntOverflow, kCntNonfinite, kCntSpeciesSteps /* 4 slots: live particles per species */
+  kCntAbsorbed, kCntOverflow, kCntNonfinite, kCntSpeciesSteps /* 4 slots: live particles per species */,
+  kCntPhotonsMade = kCntSpeciesSteps + 4, kCntPairsMade, kCntThinned
 };
+constexpr int kWorkSlot = kMaxPass + 3;   // d_pend_count slot: work counter of the e-/e+/ion pass
+constexpr int kEnsFieldStride = 8;        // per ensemble per step: E[3], B[3], |E|+|B|, pad
 constexpr int kMaxBins = 4096;
 constexpr int kCompactTile = 2048;   // particles per tile of the compaction
 constexpr int kBlockCells = 8;       // cell block edge (grid mode): 8 x 8 x 8 cells
@@ -58,6 +61,20 @@ template <typename R> struct StepArgs {
   // fields
   int field_mode;
   double fp[16];
+  // ensembles: ensemble = id >> ens_shift (ens_shift 64: all in ensemble 0);
+  // products keep the parent's ens_mask bits; per-step fields of each ensemble
+  int ens_shift;
+  int n_ens;
+  unsigned long long ens_mask;
+  const double *ens_table;  // n_ens x QED_ENS_STRIDE
+  R *ens_field;            // n_ens x kEnsFieldStride, written by k_step_constants
+  double ens_hmax;         // bound of |E| + |B| over the ensembles
+  // generator factors (Sec. VI): keep = 1/f_g, wf = f_g / N_g
+  R emit_keep, emit_wf, pair_keep, pair_wf;
+  int emit_ng, pair_ng;
+  // work stealing of the e-/e+/ion pass: particles per grab (0 = grid-stride)
+  long long chunk;
+  unsigned long long *work_massive;
   const R *E[3];
   const R *B[3];
   R *J[3];
@@ -109,6 +126,16 @@ struct qed_ctx {
   double *d_chi_star = nullptr;       // pair-skip threshold derived from the tables
   double *d_eps_star = nullptr;       // photons below this |p| cannot pair in the analytic field
   void *d_step_const = nullptr;       // per-step field constants
+  double *d_ens = nullptr;            // ensemble table (2^ens_bits rows)
+  void *d_ens_field = nullptr;        // per-step ensemble fields (context precision)
+  int n_ens = 0;
+  int ens_cap = 0;                    // rows allocated
+  double ens_hmax = 0.0;
+  int key_ensembles = 0;              // sort keys are ensembles, not cell blocks
+  int ext = 0;                        // ensembles or generator factors: EXT kernels
+  void *d_thin = nullptr;             // thinning: per group count, weight, survivors' weight
+  int thin_groups = 0;
+  qed_tuning tune{};
   unsigned *d_blk_start = nullptr;    // [4][nblk + 1] first record of each cell block
   unsigned *d_blk_cursor = nullptr;   // [nblk + 1] histogram / scatter cursors of the sort
   int nb[3] = {0, 0, 0};
@@ -147,3 +174,8 @@ int qed_launch_compact(qed_ctx *c, int sp, bool partition, cudaStream_t s);
 int qed_launch_sort(qed_ctx *c, int sp, cudaStream_t s);
 int qed_step_kernel_blocks(qed_ctx *c);
 int qed_launch_chi_star(qed_ctx *c, cudaStream_t s);
+int qed_launch_thin(qed_ctx *c, int sp, cudaStream_t s);
+int qed_launch_step_ext(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s);
+int qed_step_kernel_blocks_ext(qed_ctx *c);
+int qed_step_kernel_max_blocks_ext(qed_ctx *c, int *photon, int *massive);
+int qed_step_kernel_max_blocks(qed_ctx *c, int *photon, int *massive);

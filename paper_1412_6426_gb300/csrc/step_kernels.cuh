@@ -1,0 +1,1339 @@
+// Kernels of the particle step, shared by two translation units: step.cu
+// instantiates them for the plain method, step_ext.cu (EXT = true) for runs
+// with independent ensembles or the generator factors of Sec. VI, so that
+// the plain kernels keep their register budget.
+#pragma once
+#include <cmath>
+
+#include "qed_internal.h"
+
+namespace qed {
+namespace {
+
+// Working state of one particle during the step: unbounded per-axis cell
+// coordinates plus offsets in [0,1).
+template <typename R> struct Pt {
+  int ci[3];
+  R off[3];
+  V3<R> p;
+  R w;
+  uint64_t id;
+};
+
+// A product waiting to evolve for the rest of the step.
+template <typename R> struct Pend {
+  R off[3];
+  R w;
+  V3<R> p;
+  R trem;
+  V3<R> E, B;
+  int ci[3];
+  int sp;
+  uint64_t id;
+};
+
+struct Cnt {
+  unsigned long long sub_l = 0, sub_g = 0;
+  unsigned psteps[4] = {0, 0, 0, 0};   // live particles advanced, per species
+  unsigned emis = 0, pairs = 0, pm1 = 0, pp1 = 0, capped = 0, absorbed = 0, overflow = 0, nonfin = 0;
+  unsigned made_ph = 0, made_pair = 0;   // products made (all N_g samples, after the 1/f_g keep)
+};
+
+// ----- store access --------------------------------------------------------
+__device__ __forceinline__ void load(const StepArgs<float> &a, int sp, long long i, Pt<float> &q,
+                                     int &cell) {
+  float4 P = __ldg((const float4 *)a.pos[sp] + i);
+  float4 M = __ldg((const float4 *)a.mom[sp] + i);
+  q.off[0] = P.x; q.off[1] = P.y; q.off[2] = P.z; q.w = P.w;
+  q.p = {M.x, M.y, M.z};
+  cell = __float_as_int(M.w);
+}
+__device__ __forceinline__ void load(const StepArgs<double> &a, int sp, long long i, Pt<double> &q,
+                                     int &cell) {
+  const double2 *P = (const double2 *)a.pos[sp] + 2 * i;
+  const double2 *M = (const double2 *)a.mom[sp] + 2 * i;
+  double2 p0 = __ldg(P), p1 = __ldg(P + 1), m0 = __ldg(M), m1 = __ldg(M + 1);
+  q.off[0] = p0.x; q.off[1] = p0.y; q.off[2] = p1.x; q.w = p1.y;
+  q.p = {m0.x, m0.y, m1.x};
+  cell = (int)m1.y;
+}
+__device__ __forceinline__ void unpack(const float4 &P, const float4 &M, Pt<float> &q, int &cell) {
+  q.off[0] = P.x; q.off[1] = P.y; q.off[2] = P.z; q.w = P.w;
+  q.p = {M.x, M.y, M.z};
+  cell = __float_as_int(M.w);
+}
+template <typename H>
+__device__ __forceinline__ void unpack(const H &P, const H &M, Pt<double> &q, int &cell) {
+  q.off[0] = P.a.x; q.off[1] = P.a.y; q.off[2] = P.b.x; q.w = P.b.y;
+  q.p = {M.a.x, M.a.y, M.b.x};
+  cell = (int)M.b.y;
+}
+__device__ __forceinline__ void store(const StepArgs<float> &a, int sp, long long i,
+                                      const Pt<float> &q, int cell, bool with_id) {
+  ((float4 *)a.pos[sp])[i] = make_float4(q.off[0], q.off[1], q.off[2], q.w);
+  ((float4 *)a.mom[sp])[i] = make_float4(q.p.x, q.p.y, q.p.z, __int_as_float(cell));
+  if (with_id) a.id[sp][i] = q.id;
+}
+__device__ __forceinline__ void store_pos(const StepArgs<float> &a, int sp, long long i, const Pt<float> &q) {
+  ((float4 *)a.pos[sp])[i] = make_float4(q.off[0], q.off[1], q.off[2], q.w);
+}
+__device__ __forceinline__ void store_pos(const StepArgs<double> &a, int sp, long long i, const Pt<double> &q) {
+  double2 *P = (double2 *)a.pos[sp] + 2 * i;
+  P[0] = make_double2(q.off[0], q.off[1]);
+  P[1] = make_double2(q.off[2], q.w);
+}
+__device__ __forceinline__ void store(const StepArgs<double> &a, int sp, long long i,
+                                      const Pt<double> &q, int cell, bool with_id) {
+  double2 *P = (double2 *)a.pos[sp] + 2 * i;
+  double2 *M = (double2 *)a.mom[sp] + 2 * i;
+  P[0] = make_double2(q.off[0], q.off[1]);
+  P[1] = make_double2(q.off[2], q.w);
+  M[0] = make_double2(q.p.x, q.p.y);
+  M[1] = make_double2(q.p.z, (double)cell);
+  if (with_id) a.id[sp][i] = q.id;
+}
+
+// Smallest uniform the generators can draw (r2 > this always).
+__device__ __forceinline__ double r2_floor(double) { return 0x1p-53; }
+__device__ __forceinline__ float r2_floor(float) { return 0x1p-24f; }
+
+// ----- fields --------------------------------------------------------------
+// Per-step constants of the analytic fields, formed once per block in FP64
+// by one thread, so that the per-particle FP32 work needs no FP64 at all.
+struct alignas(8) StepConst {
+  double ud[6];              // uniform / rotating: E and B
+  float uf[6];
+  // Gaussian pulse: carrier phase in cycles = frac(c0 + i * kfix) + off * kf,
+  // with c0 and kfix fractions of a cycle in 64-bit fixed point, so the
+  // cell-index term is exact whatever the size of the lattice
+  unsigned long long c0, kfix;
+  float kf;                  // omega dx / 2 pi (cycles per cell)
+  float eta0, zeta0;         // eta = eta0 + x_rel, zeta = zeta0 - x_rel
+  float y0, z0;              // offsets of the lattice origin from the focus
+  float zr, inv_zr;          // Rayleigh length and its inverse
+  float inv_w0sq;            // 1 / w0^2
+  float curv;                // -omega / (4 pi): curvature phase in cycles per r^2/R
+  float env_k;               // -2 ln 2 / tau^2
+  float amp0, phi0_cyc;      // E0 and the phase offset in cycles
+  // Bound on a photon's effective field anywhere in this step (analytic
+  // fields only; infinite on the grid) and whether a photon with H <= hmax
+  // is always advanced in a single sub-interval.
+  double hmax;
+  float hmax_f;              // hmax rounded up, for the FP32 comparison
+  int one_interval;
+  // the step's start time and index (they key the random streams)
+  double t;
+  unsigned step;
+  unsigned pad_;
+};
+
+// Device clock, advanced by the first kernel of every step.
+struct Clock {
+  double t;
+  long long step;
+};
+
+__device__ __forceinline__ unsigned long long cycles_fixed(double cyc) {
+  cyc -= floor(cyc);
+  if (!(cyc < 1.0)) cyc = 0.0;
+  return __double2ull_rn(ldexp(cyc, 64) > 1.8446744073709550e19 ? 0.0 : ldexp(cyc, 64));
+}
+
+// Largest chi_g for which no pair draw can succeed when the sub-interval is
+// not capped: there h <= dt_q = kappa 130 (2 pi)/H, so the bound of
+// pair_bound is at most 2 sqrt3/(2pi) alpha kappa 130 (2 pi) F2(z_min) =
+// 3.2862 kappa F2(z_min), z_min = 8/(3 chi_g).  z* solves
+// 3.2862 kappa F2(z*) = r2_floor / 2 on the decreasing branch of F2 (beyond
+// its maximum at 0.4169), by bisection on the table; chi* = 8/(3 z*).
+template <typename R>
+__device__ double photon_chi_star(const R *tab, double kappa) {
+  const double target = 0.5 * (double)r2_floor(R(0)) / (3.2862 * kappa);
+  if (!(target < 0.6)) return 0.0;
+  double lo = 0.4169, hi = 740.0;    // F2(lo) > target >= F2(hi)
+  for (int it = 0; it < 60; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    R g1, g2;
+    syn_g(tab, (R)mid, g1, g2);
+    const double f2 = cbrt(mid) * (double)g2;
+    if (f2 > target) lo = mid; else hi = mid;
+  }
+  return 8.0 / (3.0 * hi);
+}
+
+template <typename R>
+__device__ void step_constants(const StepArgs<R> &a, StepConst &k) {
+  const Clock *clk = (const Clock *)a.clock;
+  k.t = clk->t;
+  k.step = (unsigned)clk->step;
+  // H^g_eff = |E + n x B|_perp <= |E| + |B| (Eq. (32))
+  k.hmax = INFINITY;
+  if (a.field_mode == kFieldUniform)
+    k.hmax = sqrt(a.fp[0] * a.fp[0] + a.fp[1] * a.fp[1] + a.fp[2] * a.fp[2]) +
+             sqrt(a.fp[3] * a.fp[3] + a.fp[4] * a.fp[4] + a.fp[5] * a.fp[5]);
+  else if (a.field_mode == kFieldRotatingE)
+    k.hmax = fabs(a.fp[0]);
+  else if (a.field_mode == kFieldGaussianLP)
+    k.hmax = 2.0 * fabs(a.fp[0]);             // |E| = |B| <= E0 everywhere
+  else if (a.field_mode == kFieldEnsemble)
+    k.hmax = a.ens_hmax;
+  // N = ceil(dt H / (kappa 130 2 pi)) is 1 for every H <= hmax (margin 1e-3)
+  k.one_interval = (double)a.dt * k.hmax <= 0.999 * (double)a.kappa * 130.0 * kTwoPi;
+  k.hmax_f = (float)(k.hmax * 1.00001);
+  for (int c = 0; c < 6; ++c) k.ud[c] = 0.0;
+  if (a.field_mode == kFieldUniform) {
+    for (int c = 0; c < 6; ++c) k.ud[c] = a.fp[c];
+  } else if (a.field_mode == kFieldRotatingE) {
+    double cyc = a.fp[1] * k.t * (1.0 / kTwoPi);
+    double f = cyc - rint(cyc), s, c;
+    sincospi(2.0 * f, &s, &c);
+    k.ud[0] = a.fp[0] * c;
+    k.ud[1] = a.fp[0] * s;
+  } else if (a.field_mode == kFieldGaussianLP) {
+    double T0 = (k.t - a.fp[7]) - a.fp[4] + a.x0[0];
+    k.c0 = cycles_fixed(a.fp[1] * T0 * (1.0 / kTwoPi));
+    double K = a.fp[1] * a.dd[0] * (1.0 / kTwoPi);
+    k.kfix = cycles_fixed(K);
+    k.kf = (float)K;
+    k.eta0 = (float)T0;
+    k.zeta0 = (float)(a.fp[4] - a.x0[0]);
+    k.y0 = (float)(a.x0[1] - a.fp[5]);
+    k.z0 = (float)(a.x0[2] - a.fp[6]);
+    const double zr = 0.5 * a.fp[1] * a.fp[2] * a.fp[2];
+    k.zr = (float)zr;
+    k.inv_zr = (float)(1.0 / zr);
+    k.inv_w0sq = (float)(1.0 / (a.fp[2] * a.fp[2]));
+    k.curv = (float)(-0.5 * a.fp[1] / kTwoPi);
+    k.env_k = (float)(-2.0 * 0.6931471805599453 / (a.fp[3] * a.fp[3]));
+    k.amp0 = (float)a.fp[0];
+    k.phi0_cyc = (float)(a.fp[8] / kTwoPi);
+  }
+  for (int c = 0; c < 6; ++c) k.uf[c] = (float)k.ud[c];
+}
+
+// Analytic fields at the particle position and the step's time (modes of qed.h).
+// FP32: no FP64 instruction; the carrier phase comes from StepConst.
+__device__ void field_analytic(const StepArgs<float> &a, const StepConst &k, const Pt<float> &q,
+                               V3<float> &E, V3<float> &B) {
+  if (a.field_mode != kFieldGaussianLP) {
+    E = {k.uf[0], k.uf[1], k.uf[2]};
+    B = {k.uf[3], k.uf[4], k.uf[5]};
+    return;
+  }
+  E = {0.f, 0.f, 0.f};
+  B = {0.f, 0.f, 0.f};
+  const float xr = ((float)q.ci[0] + q.off[0]) * a.d[0];
+  const float zeta = k.zeta0 - xr, eta = k.eta0 + xr;
+  const float y = k.y0 + ((float)q.ci[1] + q.off[1]) * a.d[1];
+  const float z = k.z0 + ((float)q.ci[2] + q.off[2]) * a.d[2];
+  const float rz = zeta * k.inv_zr;
+  const float rs = rsqrtf(1.f + rz * rz);        // w0 / w(zeta)
+  const float iq = rs * rs;                      // w0^2 / w(zeta)^2
+  const float r2 = y * y + z * z;
+  const float invR = rz * k.inv_zr * iq;         // zeta / (zeta^2 + zr^2)
+  const unsigned long long ph = k.c0 + (unsigned long long)(unsigned)q.ci[0] * k.kfix;
+  float cyc = (float)(unsigned)(ph >> 32) * 2.3283064365386963e-10f + q.off[0] * k.kf +
+              k.curv * r2 * invR + atanf(rz) * 0.15915494309189535f + k.phi0_cyc;
+  cyc -= rintf(cyc);
+  float s, c;
+  sincospif(2.f * cyc, &s, &c);
+  const float amp = k.amp0 * rs * __expf(-r2 * k.inv_w0sq * iq + k.env_k * eta * eta);
+  E.y = amp * c;
+  B.z = -E.y;
+}
+
+// FP64: the same fields with every quantity in FP64.
+__device__ void field_analytic(const StepArgs<double> &a, const StepConst &k, const Pt<double> &q,
+                               V3<double> &E, V3<double> &B) {
+  if (a.field_mode != kFieldGaussianLP) {
+    E = {k.ud[0], k.ud[1], k.ud[2]};
+    B = {k.ud[3], k.ud[4], k.ud[5]};
+    return;
+  }
+  E = {0.0, 0.0, 0.0};
+  B = {0.0, 0.0, 0.0};
+  // zeta: distance travelled past the focus along -x; eta: retarded time
+  const double xa = a.x0[0] + ((double)q.ci[0] + q.off[0]) * a.dd[0];
+  const double zeta = a.fp[4] - xa;
+  const double eta = (k.t - a.fp[7]) - zeta;
+  const double y = a.x0[1] - a.fp[5] + ((double)q.ci[1] + q.off[1]) * a.dd[1];
+  const double z = a.x0[2] - a.fp[6] + ((double)q.ci[2] + q.off[2]) * a.dd[2];
+  const double w = a.fp[1], w0 = a.fp[2], tau = a.fp[3];
+  const double zr = 0.5 * w * w0 * w0;
+  const double rz = zeta / zr;
+  const double wz2 = w0 * w0 * (1.0 + rz * rz);
+  const double r2 = y * y + z * z;
+  const double invR = zeta / (zeta * zeta + zr * zr);
+  const double phase = w * eta - 0.5 * w * r2 * invR + atan(rz) + a.fp[8];
+  const double env = exp(-2.0 * 0.6931471805599453 * eta * eta / (tau * tau));
+  const double amp = a.fp[0] * sqrt(w0 * w0 / wz2) * exp(-r2 / wz2) * env;
+  E.y = amp * cos(phase);
+  B.z = -E.y;
+}
+
+// Ensemble mode: the field of the particle's ensemble at the step's time,
+// evaluated once per step by k_step_constants.
+template <typename R>
+__device__ __forceinline__ void field_ensemble(const StepArgs<R> &a, uint64_t id, V3<R> &E, V3<R> &B) {
+  const unsigned long long e = a.ens_shift >= 64 ? 0ull : (unsigned long long)(id >> a.ens_shift);
+  if (e >= (unsigned long long)a.n_ens) {
+    E = {R(0), R(0), R(0)};
+    B = {R(0), R(0), R(0)};
+    return;
+  }
+  const R *f = a.ens_field + e * kEnsFieldStride;
+  E = {__ldg(f), __ldg(f + 1), __ldg(f + 2)};
+  B = {__ldg(f + 3), __ldg(f + 4), __ldg(f + 5)};
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// CIC gather of one staggered component (stagger sx, sy, sz in {0, 1/2}).
+template <typename R>
+__device__ __forceinline__ R cic(const R *__restrict__ f, const StepArgs<R> &a, const int *ci,
+                                 const R *off, int sx, int sy, int sz) {
+  int b[3];
+  R fr[3];
+  const int sg[3] = {sx, sy, sz};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R v = sg[c] ? off[c] - R(0.5) : off[c];
+    int bb = ci[c];
+    if (v < R(0)) { v += R(1); bb -= 1; }
+    b[c] = bb;
+    fr[c] = v;
+  }
+  int i0 = wrapi(b[0], a.n[0]), i1 = wrapi(b[0] + 1, a.n[0]);
+  int j0 = wrapi(b[1], a.n[1]), j1 = wrapi(b[1] + 1, a.n[1]);
+  int k0 = wrapi(b[2], a.n[2]), k1 = wrapi(b[2] + 1, a.n[2]);
+  long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+  R acc = R(0);
+  acc += (R(1) - fr[0]) * (R(1) - fr[1]) * (R(1) - fr[2]) * __ldg(f + k0 * nxy + j0 * nx + i0);
+  acc += fr[0] * (R(1) - fr[1]) * (R(1) - fr[2]) * __ldg(f + k0 * nxy + j0 * nx + i1);
+  acc += (R(1) - fr[0]) * fr[1] * (R(1) - fr[2]) * __ldg(f + k0 * nxy + j1 * nx + i0);
+  acc += fr[0] * fr[1] * (R(1) - fr[2]) * __ldg(f + k0 * nxy + j1 * nx + i1);
+  acc += (R(1) - fr[0]) * (R(1) - fr[1]) * fr[2] * __ldg(f + k1 * nxy + j0 * nx + i0);
+  acc += fr[0] * (R(1) - fr[1]) * fr[2] * __ldg(f + k1 * nxy + j0 * nx + i1);
+  acc += (R(1) - fr[0]) * fr[1] * fr[2] * __ldg(f + k1 * nxy + j1 * nx + i0);
+  acc += fr[0] * fr[1] * fr[2] * __ldg(f + k1 * nxy + j1 * nx + i1);
+  return acc;
+}
+
+template <typename R>
+__device__ void gather_grid(const StepArgs<R> &a, const Pt<R> &q, V3<R> &E, V3<R> &B) {
+  E.x = cic(a.E[0], a, q.ci, q.off, 1, 0, 0);
+  E.y = cic(a.E[1], a, q.ci, q.off, 0, 1, 0);
+  E.z = cic(a.E[2], a, q.ci, q.off, 0, 0, 1);
+  B.x = cic(a.B[0], a, q.ci, q.off, 0, 1, 1);
+  B.y = cic(a.B[1], a, q.ci, q.off, 1, 0, 1);
+  B.z = cic(a.B[2], a, q.ci, q.off, 1, 1, 0);
+}
+
+// ----- Esirkepov deposit (linear shape) ------------------------------------
+template <typename R>
+__device__ __noinline__ void deposit(const StepArgs<R> &a, const int *cs, const R *os, const Pt<R> &q, R qw) {
+  R S0[3][4], dS[3][4];
+  int base[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    base[c] = cs[c] - 1;
+    R ua = R(1) + os[c];
+    R ub = R(q.ci[c] - cs[c] + 1) + q.off[c];
+    if (!(fabs_r(ub - ua) < R(1))) { atomicOr(a.status, kStCourant); return; }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      R s0 = R(1) - fabs_r(ua - R(m));
+      R s1 = R(1) - fabs_r(ub - R(m));
+      s0 = s0 > R(0) ? s0 : R(0);
+      s1 = s1 > R(0) ? s1 : R(0);
+      S0[c][m] = s0;
+      dS[c][m] = s1 - s0;
+    }
+  }
+  const R inv_vol = a.inv_d[0] * a.inv_d[1] * a.inv_d[2];
+  const R pref[3] = {-qw * a.d[0] / a.dt * inv_vol, -qw * a.d[1] / a.dt * inv_vol,
+                     -qw * a.d[2] / a.dt * inv_vol};
+  long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+  int I[4], Jj[4], K[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    I[m] = wrapi(base[0] + m, a.n[0]);
+    Jj[m] = wrapi(base[1] + m, a.n[1]);
+    K[m] = wrapi(base[2] + m, a.n[2]);
+  }
+  const R third = R(1.0 / 3.0);
+  for (int k = 0; k < 4; ++k)
+    for (int j = 0; j < 4; ++j) {
+      R acc = R(0);
+      R wyz = S0[1][j] * S0[2][k] + R(0.5) * dS[1][j] * S0[2][k] + R(0.5) * S0[1][j] * dS[2][k] +
+              third * dS[1][j] * dS[2][k];
+      for (int i = 0; i < 4; ++i) {
+        acc += pref[0] * dS[0][i] * wyz;
+        if (acc != R(0)) atomicAdd(a.J[0] + K[k] * nxy + Jj[j] * nx + I[i], acc);
+      }
+    }
+  for (int k = 0; k < 4; ++k)
+    for (int i = 0; i < 4; ++i) {
+      R acc = R(0);
+      R wxz = S0[0][i] * S0[2][k] + R(0.5) * dS[0][i] * S0[2][k] + R(0.5) * S0[0][i] * dS[2][k] +
+              third * dS[0][i] * dS[2][k];
+      for (int j = 0; j < 4; ++j) {
+        acc += pref[1] * dS[1][j] * wxz;
+        if (acc != R(0)) atomicAdd(a.J[1] + K[k] * nxy + Jj[j] * nx + I[i], acc);
+      }
+    }
+  for (int j = 0; j < 4; ++j)
+    for (int i = 0; i < 4; ++i) {
+      R acc = R(0);
+      R wxy = S0[0][i] * S0[1][j] + R(0.5) * dS[0][i] * S0[1][j] + R(0.5) * S0[0][i] * dS[1][j] +
+              third * dS[0][i] * dS[1][j];
+      for (int k = 0; k < 4; ++k) {
+        acc += pref[2] * dS[2][k] * wxy;
+        if (acc != R(0)) atomicAdd(a.J[2] + K[k] * nxy + Jj[j] * nx + I[i], acc);
+      }
+    }
+}
+
+// Esirkepov deposit into the shared-memory current tile of a cell block
+// (tile node (0,0,0) = global node torg, kTileNodes per axis).  Returns false,
+// depositing nothing, when the particle's stencil leaves the tile (it has
+// drifted out of its block since the last sort); the caller then deposits to
+// global memory.
+template <typename R>
+__device__ bool deposit_tile(const StepArgs<R> &a, R *jt, const int *torg, const int *cs, const R *os,
+                             const Pt<R> &q, R qw) {
+  int base[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    base[c] = cs[c] - 1 - torg[c];
+    if (base[c] < 0 || base[c] + 3 >= kTileNodes) return false;
+  }
+  R S0[3][4], dS[3][4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R ua = R(1) + os[c];
+    R ub = R(q.ci[c] - cs[c] + 1) + q.off[c];
+    if (!(fabs_r(ub - ua) < R(1))) { atomicOr(a.status, kStCourant); return true; }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      R s0 = R(1) - fabs_r(ua - R(m));
+      R s1 = R(1) - fabs_r(ub - R(m));
+      s0 = s0 > R(0) ? s0 : R(0);
+      s1 = s1 > R(0) ? s1 : R(0);
+      S0[c][m] = s0;
+      dS[c][m] = s1 - s0;
+    }
+  }
+  const R inv_vol = a.inv_d[0] * a.inv_d[1] * a.inv_d[2];
+  const R pref[3] = {-qw * a.d[0] / a.dt * inv_vol, -qw * a.d[1] / a.dt * inv_vol,
+                     -qw * a.d[2] / a.dt * inv_vol};
+  constexpr int T = kTileNodes, TT = kTileNodes * kTileNodes, TTT = TT * kTileNodes;
+  const R third = R(1.0 / 3.0);
+  for (int k = 0; k < 4; ++k)
+    for (int j = 0; j < 4; ++j) {
+      R acc = R(0);
+      R wyz = S0[1][j] * S0[2][k] + R(0.5) * dS[1][j] * S0[2][k] + R(0.5) * S0[1][j] * dS[2][k] +
+              third * dS[1][j] * dS[2][k];
+      for (int i = 0; i < 4; ++i) {
+        acc += pref[0] * dS[0][i] * wyz;
+        if (acc != R(0)) atomicAdd(jt + 0 * TTT + (base[2] + k) * TT + (base[1] + j) * T + base[0] + i, acc);
+      }
+    }
+  for (int k = 0; k < 4; ++k)
+    for (int i = 0; i < 4; ++i) {
+      R acc = R(0);
+      R wxz = S0[0][i] * S0[2][k] + R(0.5) * dS[0][i] * S0[2][k] + R(0.5) * S0[0][i] * dS[2][k] +
+              third * dS[0][i] * dS[2][k];
+      for (int j = 0; j < 4; ++j) {
+        acc += pref[1] * dS[1][j] * wxz;
+        if (acc != R(0)) atomicAdd(jt + 1 * TTT + (base[2] + k) * TT + (base[1] + j) * T + base[0] + i, acc);
+      }
+    }
+  for (int j = 0; j < 4; ++j)
+    for (int i = 0; i < 4; ++i) {
+      R acc = R(0);
+      R wxy = S0[0][i] * S0[1][j] + R(0.5) * dS[0][i] * S0[1][j] + R(0.5) * S0[0][i] * dS[1][j] +
+              third * dS[0][i] * dS[1][j];
+      for (int k = 0; k < 4; ++k) {
+        acc += pref[2] * dS[2][k] * wxy;
+        if (acc != R(0)) atomicAdd(jt + 2 * TTT + (base[2] + k) * TT + (base[1] + j) * T + base[0] + i, acc);
+      }
+    }
+  return true;
+}
+
+// ----- movement and boundaries ---------------------------------------------
+template <typename R>
+__device__ __forceinline__ void move(const StepArgs<R> &a, Pt<R> &q, V3<R> v, R h) {
+  const R dv[3] = {v.x, v.y, v.z};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R o = q.off[c] + dv[c] * h * a.inv_d[c];
+    R fl = floor_r(o);
+    if (fl != R(0)) {
+      q.ci[c] += (int)fl;
+      o -= fl;
+      if (o >= R(1)) { o -= R(1); q.ci[c] += 1; }
+    }
+    q.off[c] = o;
+  }
+}
+
+// Periodic wrap or removal at the end of a particle's step; returns the
+// linear cell or -1 when the particle left an open lattice.
+template <typename R>
+__device__ __forceinline__ int finish_cell(const StepArgs<R> &a, Pt<R> &q) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (a.periodic[c]) q.ci[c] = wrapi(q.ci[c], a.n[c]);
+    else if (q.ci[c] < 0 || q.ci[c] >= a.n[c]) return -1;
+  }
+  return (q.ci[2] * a.n[1] + q.ci[1]) * a.n[0] + q.ci[0];
+}
+
+__device__ __forceinline__ double log10_r(double x) { return log10(x); }
+__device__ __forceinline__ float log10_r(float x) { return log10f(x); }
+
+template <typename R>
+__device__ __noinline__ void spectrum_add(const StepArgs<R> &a, R delta, R eps, R w) {
+  if (a.nbins <= 0) return;
+  const R lo = (R)a.lg_lo, sc = (R)(a.lg_inv_span * a.nbins);
+  R u = (log10_r(delta) - lo) * sc;
+  if (u >= R(0) && u < R(a.nbins)) atomicAdd(a.spectrum + (int)u, (double)w);
+  R v = (log10_r(eps) - lo) * sc;
+  if (v >= R(0) && v < R(a.nbins)) atomicAdd(a.spectrum_energy + (int)v, (double)w);
+}
+
+// Upper bound of P_p(de) over de for one sub-interval (Eq. (30)):
+// P_p <= alpha h sqrt3/(2pi) (chi/eps) F2(z_p), and z_p >= z_min = 8/(3 chi)
+// at de = 1/2, where F2 decreases beyond its maximum 0.60705 at z = 0.4169.
+// A factor 2 covers the table's rounding.
+template <typename R>
+__device__ __forceinline__ R pair_bound(const R *__restrict__ T, R chig, R eps, R h) {
+  if (!(chig > R(0)) || !(eps > R(0))) return R(0);
+  R zmin = R(8.0 / 3.0) / chig;
+  R f2 = R(0.6071);
+  if (zmin > R(0.42)) {
+    R g1, g2;
+    syn_g(T, zmin, g1, g2);
+    f2 = cbrt_r(zmin) * g2;
+  }
+  return R(2) * R(kAlpha) * h * R(kSqrt3Over2Pi) * (chig / eps) * f2;
+}
+
+// Id of a product: child_id of the parent, keeping the parent's ensemble
+// bits.  kind = product species | (sample << 8).
+template <typename R>
+__device__ __forceinline__ uint64_t product_id(const StepArgs<R> &a, uint64_t parent, unsigned step, unsigned sub,
+                                               unsigned kind) {
+  const uint64_t mix = child_id(parent, step, sub, kind, a.seed);
+  return (parent & a.ens_mask) | (mix & ~a.ens_mask);
+}
+
+// Append a finished particle to its store (warp-aggregated slot reservation).
+template <typename R>
+__device__ __noinline__ void append(const StepArgs<R> &a, int sp, Pt<R> &q, Cnt &cnt) {
+  int cell = finish_cell(a, q);
+  if (cell < 0) { cnt.absorbed++; return; }
+  unsigned mask = __activemask();
+  // lanes appending to the same species share one atomic
+  unsigned peers = __match_any_sync(mask, sp);
+  int leader = __ffs(peers) - 1;
+  int rank = __popc(peers & ((1u << (threadIdx.x & 31)) - 1u));
+  unsigned long long base = 0;
+  if ((int)(threadIdx.x & 31) == leader)
+    base = (unsigned long long)atomicAdd((unsigned long long *)a.count + sp,
+                                         (unsigned long long)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  long long slot = (long long)base + rank;
+  if (slot >= a.cap[sp]) {
+    atomicOr(a.status, kStCapacity);
+    cnt.overflow++;
+    return;
+  }
+  store(a, sp, slot, q, cell, true);
+}
+
+// Queue a product for the rest of the step (same_step), or append it now.
+template <typename R>
+__device__ __noinline__ void emit(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, R trem, V3<R> E, V3<R> B,
+                                  Cnt &cnt) {
+  if (a.same_step && trem > R(0)) {
+    // lanes queueing products in this pass share one atomic
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(a.pend_count + pass + 1, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
+    if ((long long)slot >= a.pend_cap) {
+      atomicOr(a.status, kStCapacity);
+      cnt.overflow++;
+      return;
+    }
+    Pend<R> *r = (Pend<R> *)a.pend[(pass + 1) & 1] + slot;
+    r->off[0] = q.off[0]; r->off[1] = q.off[1]; r->off[2] = q.off[2];
+    r->w = q.w; r->p = q.p; r->trem = trem; r->E = E; r->B = B;
+    r->ci[0] = q.ci[0]; r->ci[1] = q.ci[1]; r->ci[2] = q.ci[2];
+    r->sp = sp; r->id = q.id;
+  } else {
+    append(a, sp, q, cnt);
+  }
+}
+
+// Generator factors (Sec. VI) for the emission: N_g samples of the modified
+// generator in sub-interval s (sample 0 is the parent's own draw r1, r2);
+// each accepted sample makes a photon carrying delta = r1^3 of the parent's
+// momentum before its recoil, kept with probability 1/f_g (a KEEP draw),
+// with weight w f_g / N_g.  The parent's recoil is left to the caller.
+template <typename R>
+__device__ __noinline__ void emit_samples(const StepArgs<R> &a, int pass, const Pt<R> &q, R r1, R r2, R pm, R chi,
+                                          R g, R h, int s, int n, unsigned step, V3<R> E, V3<R> B, Cnt &cnt) {
+  for (int j = 0; j < a.emit_ng; ++j) {
+    R a1 = r1, a2 = r2, pmj = pm;
+    if (j > 0) {
+      draw2(q.id, step, (unsigned)s, kEmit | ((unsigned)j << 8), a.seed, a1, a2);
+      pmj = prob_emit(a.tab, a1, chi, g, h);
+      if (pmj > R(1)) {
+        cnt.pm1++;
+        if (a.pm_strict) atomicOr(a.status, kStPmGt1);
+      }
+    }
+    if (!(a2 < pmj)) continue;
+    if (a.emit_keep < R(1)) {
+      R u, v;
+      draw2(q.id, step, (unsigned)s, kKeep | ((unsigned)j << 8), a.seed, u, v);
+      if (!(u < a.emit_keep)) continue;
+    }
+    const R delta = a1 * a1 * a1;
+    Pt<R> ph = q;
+    ph.p = {delta * q.p.x, delta * q.p.y, delta * q.p.z};
+    ph.w = q.w * a.emit_wf;
+    ph.id = product_id(a, q.id, step, (unsigned)s, kPhoton | ((unsigned)j << 8));
+    cnt.made_ph++;
+    spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), ph.w);
+    emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B, cnt);
+  }
+}
+
+// The same for the pair generator: each accepted sample makes an electron
+// with r1 of the photon momentum and a positron with 1 - r1, kept with
+// probability 1/f_g, with weight w f_g / N_g.  The photon's own conversion
+// (sample 0) is left to the caller.
+template <typename R>
+__device__ __noinline__ void pair_samples(const StepArgs<R> &a, int pass, const Pt<R> &q, R r1, R r2, R pp, R chig,
+                                          R eps, R h, int s, int n, unsigned step, V3<R> E, V3<R> B, Cnt &cnt) {
+  const R trem = R(n - 1 - s) * h;
+  for (int j = 0; j < a.pair_ng; ++j) {
+    R a1 = r1, a2 = r2, ppj = pp;
+    if (j > 0) {
+      draw2(q.id, step, (unsigned)s, kPair | ((unsigned)j << 8), a.seed, a1, a2);
+      ppj = prob_pair(a.tab, a1, chig, eps, h);
+      if (ppj > R(1)) {
+        cnt.pp1++;
+        if (a.pm_strict) atomicOr(a.status, kStPmGt1);
+      }
+    }
+    if (!(a2 < ppj)) continue;
+    if (a.pair_keep < R(1)) {
+      R u, v;
+      draw2(q.id, step, (unsigned)s, kKeep | ((unsigned)j << 8) | (1u << 16), a.seed, u, v);
+      if (!(u < a.pair_keep)) continue;
+    }
+    Pt<R> el = q, po = q;
+    el.p = {a1 * q.p.x, a1 * q.p.y, a1 * q.p.z};
+    const R c1 = R(1) - a1;
+    po.p = {c1 * q.p.x, c1 * q.p.y, c1 * q.p.z};
+    el.w = po.w = q.w * a.pair_wf;
+    el.id = product_id(a, q.id, step, (unsigned)s, kElectron | ((unsigned)j << 8));
+    po.id = product_id(a, q.id, step, (unsigned)s, kPositron | ((unsigned)j << 8));
+    cnt.made_pair++;
+    emit(a, pass, kElectron, el, trem, E, B, cnt);
+    emit(a, pass, kPositron, po, trem, E, B, cnt);
+  }
+}
+
+// Electron, positron or ion: the adaptive sub-interval loop (Sec. IV.H) of
+// Boris push and modified emission generator (Sec. IV.G); ions are pushed only.
+template <typename R, bool EXT>
+__device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, R t_span,
+                                                V3<R> E, V3<R> B, Cnt &cnt, const uint64_t *idp, unsigned step,
+                                                R *jt = nullptr, const int *torg = nullptr) {
+  const int cs[3] = {q.ci[0], q.ci[1], q.ci[2]};
+  const R os[3] = {q.off[0], q.off[1], q.off[2]};
+  const R qc = a.charge[sp], m = a.mass[sp];
+  const bool qed = (sp != kIon) && a.emission_on;
+  if (qed && idp) q.id = __ldg(idp);
+  int n = 1, capped = 0;
+  if (qed) {
+    R g0 = sqrt_r(R(1) + dot(q.p, q.p) / (m * m));
+    n = nsub_lepton(t_span, g0, heff_lepton(q.p, g0, E, B), a.kappa, a.nsub_max, capped);
+    cnt.capped += capped;
+  }
+  const R h = t_span / R(n);
+  for (int s = 0; s < n; ++s) {
+    boris(q.p, E, B, qc, m, h);
+    R g = sqrt_r(R(1) + dot(q.p, q.p) / (m * m));
+    R im = R(1) / (m * g);
+    move(a, q, V3<R>{q.p.x * im, q.p.y * im, q.p.z * im}, h);
+    if (!qed) continue;
+    cnt.sub_l++;
+    R chi = chi_lepton(q.p, g, E, B);
+    R r1, r2;
+    draw2(q.id, step, (unsigned)s, kEmit, a.seed, r1, r2);
+    R pm = prob_emit(a.tab, r1, chi, g, h);
+    if (pm > R(1)) {
+      cnt.pm1++;
+      if (a.pm_strict) atomicOr(a.status, kStPmGt1);
+    }
+    if (EXT && (a.emit_ng > 1 || a.emit_keep < R(1))) {
+      // generator factors: products from N_g samples, kept with 1/f_g
+      emit_samples(a, pass, q, r1, r2, pm, chi, g, h, s, n, step, E, B, cnt);
+      if (r2 < pm) {
+        const R omd = R(1) - r1 * r1 * r1;
+        q.p = {omd * q.p.x, omd * q.p.y, omd * q.p.z};
+        cnt.emis++;
+      }
+    } else if (r2 < pm) {
+      // photon along p with delta of it; the parent keeps (1 - delta)
+      R delta = r1 * r1 * r1;
+      Pt<R> ph = q;
+      ph.p = {delta * q.p.x, delta * q.p.y, delta * q.p.z};
+      ph.id = product_id(a, q.id, step, (unsigned)s, kPhoton);
+      R omd = R(1) - delta;
+      q.p = {omd * q.p.x, omd * q.p.y, omd * q.p.z};
+      cnt.emis++;
+      cnt.made_ph++;
+      spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), q.w);
+      emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B, cnt);
+    }
+  }
+  if (a.deposit && qc != R(0))
+    if (!jt || !deposit_tile(a, jt, torg, cs, os, q, qc * q.w)) deposit(a, cs, os, q, qc * q.w);
+}
+
+// Photon: straight flight with the pair generator (Sec. V.A) in the same
+// sub-interval loop.  Returns false when the photon converted into a pair.
+// idp: where to load the id from when a draw needs it (nullptr: q.id is set).
+template <typename R, bool EXT>
+__device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, Pt<R> &q, R t_span, V3<R> E,
+                                               V3<R> B, Cnt &cnt, const uint64_t *idp, R chi_star, unsigned step) {
+  const R eps = sqrt_r(dot(q.p, q.p));
+  V3<R> dir = {R(0), R(0), R(0)};
+  if (eps > R(0)) {
+    const R ie = R(1) / eps;
+    dir = {q.p.x * ie, q.p.y * ie, q.p.z * ie};
+  }
+  const R hg = heff_photon(dir, E, B);
+  const R chig = eps * hg;
+  int n = 1, capped = 0;
+  if (a.pairs_on) {
+    n = nsub_photon(t_span, hg, a.kappa, a.nsub_max, capped);
+    cnt.capped += capped;
+  }
+  const R h = t_span / R(n);
+  // No draw can make a pair when P_p is below the smallest uniform: below
+  // chi_star (uncapped) by the bound of photon_chi_star, else by pair_bound.
+  bool may_pair = a.pairs_on;
+  if (may_pair) {
+    if (!capped && chig < chi_star) may_pair = false;
+    else may_pair = pair_bound(a.tab, chig, eps, h) >= r2_floor(h);
+  }
+  if (may_pair && idp) q.id = __ldg(idp);
+  for (int s = 0; s < n; ++s) {
+    move(a, q, dir, h);
+    if (!a.pairs_on) continue;
+    cnt.sub_g++;
+    if (!may_pair) continue;
+    R r1, r2;
+    draw2(q.id, step, (unsigned)s, kPair, a.seed, r1, r2);
+    R pp = prob_pair(a.tab, r1, chig, eps, h);
+    if (pp > R(1)) {
+      cnt.pp1++;
+      if (a.pm_strict) atomicOr(a.status, kStPmGt1);
+    }
+    if (EXT && (a.pair_ng > 1 || a.pair_keep < R(1))) {
+      // generator factors: pairs from N_g samples, kept with 1/f_g
+      pair_samples(a, pass, q, r1, r2, pp, chig, eps, h, s, n, step, E, B, cnt);
+      if (r2 < pp) {
+        cnt.pairs++;
+        return false;
+      }
+    } else if (r2 < pp) {
+      // electron takes r1 of the photon momentum, positron 1 - r1
+      Pt<R> el = q, po = q;
+      el.p = {r1 * q.p.x, r1 * q.p.y, r1 * q.p.z};
+      R r1c = R(1) - r1;
+      po.p = {r1c * q.p.x, r1c * q.p.y, r1c * q.p.z};
+      el.id = product_id(a, q.id, step, (unsigned)s, kElectron);
+      po.id = product_id(a, q.id, step, (unsigned)s, kPositron);
+      cnt.pairs++;
+      cnt.made_pair++;
+      R trem = R(n - 1 - s) * h;
+      emit(a, pass, kElectron, el, trem, E, B, cnt);
+      emit(a, pass, kPositron, po, trem, E, B, cnt);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Bounded grid barrier (all blocks are co-resident: cooperative launch).
+// Gives up after ~1 s, sets the timeout status and returns false.
+__device__ bool grid_barrier(unsigned *bar, int *status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = bar + 1;
+    unsigned g = *gen;
+    __threadfence();
+    unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    ok = 1;
+    if (arrived == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g) {
+        __nanosleep(64);
+        if (++it > (1ll << 24)) {
+          atomicOr(status, kStTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ void flush(const Cnt &c, unsigned long long *g) {
+  unsigned long long v[16] = {c.emis,      c.pairs,       c.sub_l,       c.sub_g,     c.pm1,
+                              c.pp1,       c.capped,      c.absorbed,    c.overflow,  c.nonfin,
+                              c.psteps[0], c.psteps[1],   c.psteps[2],   c.psteps[3], c.made_ph,
+                              c.made_pair};
+  static_assert(kCntPhotonsMade == 14 && kCntPairsMade == 15, "counter layout");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    unsigned long long x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(g + k, x);
+  }
+}
+
+__device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m, int l) {
+  return (__umulhi(n, m) + n) >> l;   // exact for n < 2^31 (Granlund-Montgomery)
+}
+
+// The per-step field constants, formed once per step in FP64 by one thread.
+// Ensemble mode: every thread of the one block also evaluates the fields
+// of its ensembles at the step's time (FP64, stored in the context precision).
+template <typename R>
+__global__ void k_step_constants(const StepArgs<R> a) {
+  Clock *clk = (Clock *)a.clock;
+  const double t = clk->t;
+  if (a.field_mode == kFieldEnsemble) {
+    for (int e = threadIdx.x; e < a.n_ens; e += blockDim.x) {
+      const double *q = a.ens_table + (size_t)e * QED_ENS_STRIDE;
+      double sn, cs;
+      sincos(q[1] * t + q[2], &sn, &cs);
+      const double E[3] = {q[3] + q[0] * cs, q[4] + q[0] * sn, q[5]};
+      R *f = a.ens_field + (size_t)e * kEnsFieldStride;
+      for (int c = 0; c < 3; ++c) {
+        f[c] = (R)E[c];
+        f[3 + c] = (R)q[6 + c];
+      }
+      f[6] = (R)(sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]) +
+                 sqrt(q[6] * q[6] + q[7] * q[7] + q[8] * q[8]));
+      f[7] = R(0);
+    }
+  }
+  __syncthreads();   // every thread has read the clock
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    step_constants(a, *(StepConst *)a.step_const);
+    clk->t = t + a.dt_d;   // the next step starts dt later
+    clk->step += 1;
+  }
+}
+
+// Pass 0 of one particle family.  PHOTON: the photon store; otherwise
+// electrons, positrons and ions.  Resident blocks per SM set the register
+// budget: the photon path is light enough for four 256-thread blocks.
+template <typename R, bool PHOTON> struct Pass0Occ;
+template <> struct Pass0Occ<float, false> { static constexpr int blocks = 3; };
+template <> struct Pass0Occ<double, false> { static constexpr int blocks = 1; };
+
+template <typename R, bool PHOTON, bool EXT>
+__global__ void __launch_bounds__(256, (Pass0Occ<R, PHOTON>::blocks)) k_pass0(const StepArgs<R> a) {
+  Cnt cnt;
+  __shared__ long long ns[4];
+  __shared__ StepConst kc;
+  if (threadIdx.x < (int)(sizeof(StepConst) / 8))
+    ((unsigned long long *)&kc)[threadIdx.x] = ((const unsigned long long *)a.step_const)[threadIdx.x];
+  __shared__ long long nb0[4];
+  // an overflowing append leaves count above the capacity: never read past it
+  if (threadIdx.x < 4) {
+    ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
+    // records in cell-block order are advanced by k_blocks; this kernel takes the rest
+    const unsigned *bs = a.blk_start[threadIdx.x];
+    nb0[threadIdx.x] = (!PHOTON && bs) ? min((long long)bs[a.nblk], ns[threadIdx.x]) : 0;
+    ns[threadIdx.x] -= nb0[threadIdx.x];
+  }
+  __syncthreads();
+  const long long total = PHOTON ? ns[kPhoton] : ns[kElectron] + ns[kPositron] + ns[kIon];
+  auto body = [&](long long it) {
+    int sp = kPhoton;
+    long long i = it;
+    if (!PHOTON) {
+      sp = kElectron;
+      if (i >= ns[kElectron]) {
+        i -= ns[kElectron];
+        sp = kPositron;
+        if (i >= ns[kPositron]) { i -= ns[kPositron]; sp = kIon; }
+      }
+      i += nb0[sp];
+    }
+    Pt<R> q;
+    int cell;
+    load(a, sp, i, q, cell);
+    if (cell < 0) return;
+    cnt.psteps[sp]++;
+    const unsigned row = fast_div((unsigned)cell, a.div_m[0], a.div_l[0]);
+    const unsigned slab = fast_div((unsigned)cell, a.div_m[1], a.div_l[1]);
+    q.ci[0] = cell - (int)row * a.n[0];
+    q.ci[1] = (int)row - (int)slab * a.n[1];
+    q.ci[2] = (int)slab;
+    V3<R> E, B;
+    const uint64_t *idp = a.id[sp] + i;
+    if (a.field_mode == kFieldGrid) {
+      gather_grid(a, q, E, B);
+    } else if (EXT && a.field_mode == kFieldEnsemble) {
+      q.id = __ldg(idp);
+      idp = nullptr;
+      field_ensemble(a, q.id, E, B);
+    } else {
+      field_analytic(a, kc, q, E, B);
+    }
+    // a NaN or an infinity in any input makes this sum NaN or infinite
+    const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
+    if (!(probe == R(0))) {
+      cnt.nonfin++;
+      atomicOr(a.status, kStNonfinite);
+    }
+    bool alive = true;
+    if (PHOTON) alive = advance_photon<R, EXT>(a, 0, q, a.dt, E, B, cnt, idp, (R)*a.chi_star, kc.step);
+    else advance_massive<R, EXT>(a, 0, sp, q, a.dt, E, B, cnt, idp, kc.step);
+    int nc = alive ? finish_cell(a, q) : -1;
+    if (alive && nc < 0) cnt.absorbed++;
+    // a photon's momentum never changes: its momentum record is rewritten
+    // only when the cell changed or the photon died
+    if (PHOTON && nc == cell) store_pos(a, sp, i, q);
+    else store(a, sp, i, q, nc, false);
+  };
+  // Static: grid-stride over rows of 256.  Work stealing (chunk > 0): blocks
+  // take chunks of consecutive particles from a shared counter, so blocks
+  // that drew cheap particles take more.  One loop, one copy of the body.
+  __shared__ long long wb;
+  const bool dyn = a.chunk > 0;
+  long long next = (long long)blockIdx.x * blockDim.x;
+  for (;;) {
+    long long lo, hi;
+    if (dyn) {
+      __syncthreads();   // everyone has read the previous chunk's start
+      if (threadIdx.x == 0) wb = (long long)atomicAdd(a.work_massive, (unsigned long long)a.chunk);
+      __syncthreads();
+      lo = wb;
+      hi = min(lo + a.chunk, total);
+    } else {
+      lo = next;
+      hi = min(lo + (long long)blockDim.x, total);
+      next += (long long)gridDim.x * blockDim.x;
+    }
+    if (lo >= total) break;
+    for (long long it = lo + threadIdx.x; it < hi; it += blockDim.x) body(it);
+  }
+  flush(cnt, a.counters);
+}
+
+// ----- photon pass 0 with per-thread asynchronous staging -----------------
+// Photons are most of the particles of a cascade and their step is short, so
+// memory latency dominates.  Each thread streams its own photons (grid-stride
+// order) through kStages private shared-memory slots with cp.async: the
+// records of the next kStages-1 photons are in flight while the current one
+// is computed.  A thread only reads what it copied itself, so no barrier and
+// no spin-wait is involved (cp.async.wait_group is a hardware wait).
+constexpr int kPhotonThreads = 256;
+// slots per thread: three 32-byte FP32 records, two 64-byte FP64 records
+template <typename R> struct PhotonStages { static constexpr int n = sizeof(R) == 4 ? 3 : 2; };
+
+template <typename R> struct Half;
+template <> struct Half<float> { using T = float4; };
+template <> struct Half<double> { struct alignas(16) T { double2 a, b; }; };
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename R> struct PhotonOcc { static constexpr int blocks = sizeof(R) == 4 ? 3 : 2; };
+
+template <typename R, bool EXT>
+__global__ void __launch_bounds__(kPhotonThreads, PhotonOcc<R>::blocks) k_photons(const StepArgs<R> a) {
+  using T = typename Half<R>::T;
+  constexpr int kChunks = sizeof(T) / 16;
+  constexpr int kStages = PhotonStages<R>::n;
+  // [stage][pos | mom][thread]: consecutive threads read consecutive slots
+  __shared__ __align__(16) T slot[kStages][2][kPhotonThreads];
+  __shared__ StepConst kc;
+  Cnt cnt;
+  if (threadIdx.x < (int)(sizeof(StepConst) / 8))
+    ((unsigned long long *)&kc)[threadIdx.x] = ((const unsigned long long *)a.step_const)[threadIdx.x];
+  __syncthreads();
+  const long long n = min(a.nstart[kPhoton], a.cap[kPhoton]);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const T *gpos = (const T *)a.pos[kPhoton];
+  const T *gmom = (const T *)a.mom[kPhoton];
+  const R chi_star = (R)*a.chi_star;
+  auto issue = [&](long long k) {
+    const long long i = i0 + k * stride;
+    if (i < n) {
+      const int st = (int)(k % kStages);
+#pragma unroll
+      for (int c = 0; c < kChunks; ++c) {
+        cp_async16((char *)&slot[st][0][threadIdx.x] + 16 * c, (const char *)(gpos + i) + 16 * c);
+        cp_async16((char *)&slot[st][1][threadIdx.x] + 16 * c, (const char *)(gmom + i) + 16 * c);
+      }
+    }
+    cp_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < kStages - 1; ++k) issue(k);
+  for (long long k = 0;; ++k) {
+    const long long i = i0 + k * stride;
+    if (i >= n) break;
+    issue(k + kStages - 1);
+    cp_wait<kStages - 1>();
+    const int st = (int)(k % kStages);
+    Pt<R> q;
+    int cell;
+    unpack(slot[st][0][threadIdx.x], slot[st][1][threadIdx.x], q, cell);
+    if (cell < 0) continue;
+    cnt.psteps[kPhoton]++;
+    const unsigned row = fast_div((unsigned)cell, a.div_m[0], a.div_l[0]);
+    const unsigned slab = fast_div((unsigned)cell, a.div_m[1], a.div_l[1]);
+    q.ci[0] = cell - (int)row * a.n[0];
+    q.ci[1] = (int)row - (int)slab * a.n[1];
+    q.ci[2] = (int)slab;
+    bool alive = true;
+    const R eps = sqrt_r(dot(q.p, q.p));
+    const R hmax = sizeof(R) == 4 ? (R)kc.hmax_f : (R)kc.hmax;
+    if (!a.pairs_on || (kc.one_interval && eps * hmax < R(0.99999) * chi_star)) {
+      // This photon cannot pair in this step (chi_g <= eps hmax < chi*) and
+      // takes one sub-interval: its step is the straight flight of
+      // advance_photon with N = 1, without evaluating the field.
+      if (!(q.p.x * R(0) + q.p.y * R(0) + q.p.z * R(0) == R(0))) {
+        cnt.nonfin++;
+        atomicOr(a.status, kStNonfinite);
+      }
+      V3<R> dir = {R(0), R(0), R(0)};
+      if (eps > R(0)) {
+        const R ie = R(1) / eps;
+        dir = {q.p.x * ie, q.p.y * ie, q.p.z * ie};
+      }
+      move(a, q, dir, a.dt);
+      if (a.pairs_on) cnt.sub_g++;
+    } else {
+      V3<R> E, B;
+      const uint64_t *idp = a.id[kPhoton] + i;
+      if (a.field_mode == kFieldGrid) {
+        gather_grid(a, q, E, B);
+      } else if (EXT && a.field_mode == kFieldEnsemble) {
+        q.id = __ldg(idp);
+        idp = nullptr;
+        field_ensemble(a, q.id, E, B);
+      } else {
+        field_analytic(a, kc, q, E, B);
+      }
+      const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
+      if (!(probe == R(0))) {
+        cnt.nonfin++;
+        atomicOr(a.status, kStNonfinite);
+      }
+      alive = advance_photon<R, EXT>(a, 0, q, a.dt, E, B, cnt, idp, chi_star, kc.step);
+    }
+    const int nc = alive ? finish_cell(a, q) : -1;
+    if (alive && nc < 0) cnt.absorbed++;
+    // a photon's momentum never changes: its momentum record is rewritten
+    // only when the cell changed or the photon died
+    if (nc == cell) store_pos(a, kPhoton, i, q);
+    else store(a, kPhoton, i, q, nc, false);
+  }
+  cp_wait<0>();
+  flush(cnt, a.counters);
+}
+
+// Grid mode: electrons, positrons and ions in cell-block order.  Blocks take
+// cell blocks by work stealing; the particles of a cell block deposit their
+// current into a shared-memory tile covering the block and the deposit
+// stencil's reach, which is then added to the global current with one atomic
+// per non-zero tile node.
+template <typename R, bool EXT>
+__global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
+  constexpr int TTT = kTileNodes * kTileNodes * kTileNodes;
+  __shared__ R jt[3 * TTT];
+  __shared__ int blk;
+  __shared__ long long ns[4];
+  Cnt cnt;
+  const unsigned step = ((const StepConst *)a.step_const)->step;
+  if (threadIdx.x < 4) ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
+  for (;;) {
+    if (threadIdx.x == 0) blk = (int)atomicAdd(a.work, 1u);
+    __syncthreads();
+    const int b = blk;
+    if (b >= a.nblk) break;
+    for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) jt[t] = R(0);
+    __syncthreads();
+    const int bc[3] = {b % a.nb[0], (b / a.nb[0]) % a.nb[1], b / (a.nb[0] * a.nb[1])};
+    const int torg[3] = {bc[0] * kBlockCells - 1, bc[1] * kBlockCells - 1, bc[2] * kBlockCells - 1};
+    const int fam[3] = {kElectron, kPositron, kIon};
+    for (int f = 0; f < 3; ++f) {
+      const int sp = fam[f];
+      if (!a.blk_start[sp]) continue;
+      const long long lo = min((long long)a.blk_start[sp][b], ns[sp]);
+      const long long hi = min((long long)a.blk_start[sp][b + 1], ns[sp]);
+      for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        Pt<R> q;
+        int cell;
+        load(a, sp, i, q, cell);
+        if (cell < 0) continue;
+        cnt.psteps[sp]++;
+        const unsigned row = fast_div((unsigned)cell, a.div_m[0], a.div_l[0]);
+        const unsigned slab = fast_div((unsigned)cell, a.div_m[1], a.div_l[1]);
+        q.ci[0] = cell - (int)row * a.n[0];
+        q.ci[1] = (int)row - (int)slab * a.n[1];
+        q.ci[2] = (int)slab;
+        V3<R> E, B;
+        gather_grid(a, q, E, B);
+        const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
+        if (!(probe == R(0))) {
+          cnt.nonfin++;
+          atomicOr(a.status, kStNonfinite);
+        }
+        advance_massive<R, EXT>(a, 0, sp, q, a.dt, E, B, cnt, a.id[sp] + i, step, jt, torg);
+        const int nc = finish_cell(a, q);
+        if (nc < 0) cnt.absorbed++;
+        store(a, sp, i, q, nc, false);
+      }
+    }
+    __syncthreads();
+    const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+    for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) {
+      const R v = jt[t];
+      if (v == R(0)) continue;
+      const int c = t / TTT, r = t % TTT;
+      const int ti = r % kTileNodes, tj = (r / kTileNodes) % kTileNodes, tk = r / (kTileNodes * kTileNodes);
+      const int gi = wrapi(torg[0] + ti, a.n[0]), gj = wrapi(torg[1] + tj, a.n[1]),
+                gk = wrapi(torg[2] + tk, a.n[2]);
+      atomicAdd(a.J[c] + gk * nxy + gj * nx + gi, v);
+    }
+    __syncthreads();   // the tile and blk are reused by the next cell block
+  }
+  flush(cnt, a.counters);
+}
+
+// Passes 1, 2, ...: products evolving for the rest of the step.  All blocks
+// are co-resident (cooperative launch) and meet at a bounded grid barrier
+// between passes; pass p reads the buffer filled in pass p-1.
+template <typename R, bool EXT>
+__global__ void __launch_bounds__(256, 2) k_products(const StepArgs<R> a) {
+  Cnt cnt;
+  const R chi_star = (R)*a.chi_star;
+  const unsigned step = ((const StepConst *)a.step_const)->step;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int pass = 1; pass <= kMaxPass; ++pass) {
+    if (pass > 1 && !grid_barrier(a.barrier, a.status)) break;
+    const long long n = (long long)*((volatile unsigned long long *)(a.pend_count + pass));
+    if (n == 0) break;
+    if (pass == kMaxPass) { atomicOr(a.status, kStTimeout); break; }
+    const long long lim = n < a.pend_cap ? n : a.pend_cap;
+    const Pend<R> *buf = (const Pend<R> *)a.pend[pass & 1];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += stride) {
+      const Pend<R> r = buf[i];
+      Pt<R> q;
+      q.off[0] = r.off[0]; q.off[1] = r.off[1]; q.off[2] = r.off[2];
+      q.ci[0] = r.ci[0]; q.ci[1] = r.ci[1]; q.ci[2] = r.ci[2];
+      q.p = r.p; q.w = r.w; q.id = r.id;
+      bool alive = true;
+      if (r.sp == kPhoton) alive = advance_photon<R, EXT>(a, pass, q, r.trem, r.E, r.B, cnt, nullptr, chi_star, step);
+      else advance_massive<R, EXT>(a, pass, r.sp, q, r.trem, r.E, r.B, cnt, nullptr, step);
+      if (alive) append(a, r.sp, q, cnt);
+    }
+  }
+  flush(cnt, a.counters);
+}
+
+void fast_div_magic(unsigned d, unsigned &m, int &l) {
+  l = 0;
+  while ((1ull << l) < d) ++l;
+  m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+}
+
+template <typename R, bool EXT>
+int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
+  StepArgs<R> a{};
+  for (int sp = 0; sp < 4; ++sp) {
+    const Store &st = c->st[sp];
+    a.pos[sp] = st.pos[st.cur];
+    a.mom[sp] = st.mom[st.cur];
+    a.id[sp] = st.id[st.cur];
+    a.cap[sp] = st.cap;
+    a.charge[sp] = (R)c->species.charge[sp];
+    a.mass[sp] = (R)c->species.mass[sp];
+  }
+  a.count = c->d_count;
+  a.nstart = c->d_nstart;
+  a.pend[0] = c->pend[0];
+  a.pend[1] = c->pend[1];
+  a.pend_count = c->d_pend_count;
+  a.pend_cap = c->pend_cap;
+  fast_div_magic((unsigned)c->grid.n[0], a.div_m[0], a.div_l[0]);
+  fast_div_magic((unsigned)(c->grid.n[0] * c->grid.n[1]), a.div_m[1], a.div_l[1]);
+  for (int k = 0; k < 3; ++k) {
+    a.n[k] = c->grid.n[k];
+    a.periodic[k] = c->grid.periodic[k];
+    a.d[k] = (R)c->grid.d[k];
+    a.inv_d[k] = (R)(1.0 / c->grid.d[k]);
+    a.dd[k] = c->grid.d[k];
+    a.x0[k] = c->grid.x0[k];
+  }
+  a.field_mode = c->grid.field_mode;
+  for (int k = 0; k < 16; ++k) a.fp[k] = c->grid.fp[k];
+  a.ens_shift = c->par.ens_bits > 0 ? 64 - c->par.ens_bits : 64;
+  a.ens_mask = c->par.ens_bits > 0 ? ~0ull << (64 - c->par.ens_bits) : 0ull;
+  a.n_ens = c->n_ens;
+  a.ens_table = c->d_ens;
+  a.ens_field = (R *)c->d_ens_field;
+  a.ens_hmax = c->ens_hmax;
+  {
+    const double efg = c->par.emit_fg > 1.0 ? c->par.emit_fg : 1.0;
+    const double pfg = c->par.pair_fg > 1.0 ? c->par.pair_fg : 1.0;
+    a.emit_ng = c->par.emit_ng > 1 ? c->par.emit_ng : 1;
+    a.pair_ng = c->par.pair_ng > 1 ? c->par.pair_ng : 1;
+    a.emit_keep = (R)(1.0 / efg);
+    a.pair_keep = (R)(1.0 / pfg);
+    a.emit_wf = (R)(efg / (double)a.emit_ng);
+    a.pair_wf = (R)(pfg / (double)a.pair_ng);
+  }
+  a.chunk = c->tune.work_chunk;
+  a.work_massive = c->d_pend_count + kWorkSlot;
+  a.clock = c->d_clock;
+  a.dt_d = dt;
+  if (a.field_mode == kFieldGrid) {
+    for (int k = 0; k < 3; ++k) {
+      a.E[k] = (const R *)f->E[k];
+      a.B[k] = (const R *)f->B[k];
+      a.J[k] = (R *)f->J[k];
+    }
+  }
+  a.deposit = (a.field_mode == kFieldGrid) && c->par.deposit_on;
+  a.dt = (R)dt;
+  a.kappa = (R)c->par.kappa;
+  a.nsub_max = c->par.nsub_max;
+  a.emission_on = c->par.emission_on;
+  a.pairs_on = c->par.pairs_on;
+  a.same_step = c->par.same_step_children;
+  a.pm_strict = c->par.pm_strict;
+  a.seed = c->par.seed;
+  a.tab = (const R *)c->d_tables;
+  a.chi_star = c->d_chi_star;
+  a.nblk = c->nblk;
+  for (int k = 0; k < 3; ++k) a.nb[k] = c->nb[k];
+  for (int sp = 0; sp < 4; ++sp)
+    a.blk_start[sp] = (c->sorted && c->nblk > 0 && !c->key_ensembles && sp != kPhoton)
+                          ? c->d_blk_start + (size_t)sp * (c->nblk + 1) : nullptr;
+  a.work = (unsigned *)(c->d_pend_count + kMaxPass + 2);
+  a.step_const = c->d_step_const;
+  a.counters = c->d_counters;
+  a.spectrum = c->d_spec;
+  a.spectrum_energy = c->d_spec_e;
+  a.nbins = c->par.nbins;
+  a.lg_lo = c->par.lg_lo;
+  a.lg_inv_span = 1.0 / (c->par.lg_hi - c->par.lg_lo);
+  a.status = c->d_status;
+  a.barrier = c->d_barrier;
+
+  if (cudaMemcpyAsync(c->d_nstart, c->d_count, 4 * sizeof(long long), cudaMemcpyDeviceToDevice, s) !=
+      cudaSuccess)
+    return QED_ERR_CUDA;
+  if (cudaMemsetAsync(c->d_pend_count, 0, sizeof(unsigned long long) * (kMaxPass + 4), s) !=
+      cudaSuccess)
+    return QED_ERR_CUDA;
+  if (a.deposit) {
+    size_t nc = (size_t)a.n[0] * a.n[1] * a.n[2];
+    for (int k = 0; k < 3; ++k)
+      if (cudaMemsetAsync(a.J[k], 0, nc * sizeof(R), s) != cudaSuccess) return QED_ERR_CUDA;
+  }
+  void *args[] = {(void *)&a};
+  cudaError_t e;
+  if (c->ev_start) cudaEventRecord(c->ev_start, s);
+  c->launches += 3;
+  e = cudaLaunchKernel((const void *)k_step_constants<R>, dim3(1),
+                       dim3(a.field_mode == kFieldEnsemble ? 256 : 32), args, 0, s);
+  if (e == cudaSuccess)
+    e = cudaLaunchKernel((const void *)k_photons<R, EXT>, dim3(c->num_sms * c->tune.photon_blocks_per_sm),
+                         dim3(kPhotonThreads), args, 0, s);
+  if (c->ev_photon) cudaEventRecord(c->ev_photon, s);
+  if (e == cudaSuccess && a.blk_start[kElectron]) {
+    c->launches += 1;
+    e = cudaLaunchKernel((const void *)k_blocks<R, EXT>, dim3(c->blocks_cells), dim3(256), args, 0, s);
+  }
+  if (e == cudaSuccess)
+    e = cudaLaunchKernel((const void *)k_pass0<R, false, EXT>, dim3(c->num_sms * c->tune.massive_blocks_per_sm),
+                         dim3(256), args, 0, s);
+  if (e == cudaSuccess && a.same_step) {
+    c->launches += 1;
+    e = cudaLaunchCooperativeKernel((const void *)k_products<R, EXT>, dim3(c->blocks_products), dim3(256), args, 0, s);
+  }
+  if (c->ev_stop) cudaEventRecord(c->ev_stop, s);
+  return e == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+
+template <typename R, bool EXT>
+int step_blocks(qed_ctx *c) {
+  int a = 0, b = 0, p = 0, g = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k_blocks<R, EXT>, 256, 0) != cudaSuccess || g < 1)
+    return QED_ERR_CUDA;
+  c->blocks_cells = g * c->num_sms;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_photons<R, EXT>, qed::kPhotonThreads, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pass0<R, false, EXT>, 256, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k_products<R, EXT>, 256, 0) != cudaSuccess ||
+      a < 1 || b < 1 || p < 1)
+    return QED_ERR_CUDA;
+  c->blocks_photon = a * c->num_sms;
+  c->blocks_massive = b * c->num_sms;
+  c->blocks_products = p * c->num_sms;   // co-resident: the barrier needs every block running
+  return QED_OK;
+}
+
+// Occupancy limits of the photon and the e-/e+/ion passes (blocks per SM).
+template <typename R, bool EXT>
+int max_blocks(int *photon, int *massive) {
+  cudaError_t e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(photon, k_photons<R, EXT>, kPhotonThreads, 0);
+  cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(massive, k_pass0<R, false, EXT>, 256, 0);
+  return (e1 == cudaSuccess && e2 == cudaSuccess && *photon >= 1 && *massive >= 1) ? QED_OK : QED_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace qed

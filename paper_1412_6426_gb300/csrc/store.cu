@@ -30,6 +30,8 @@ __device__ __forceinline__ void put(D4 *pos, D4 *mom, long long i, const double 
 }
 __device__ __forceinline__ int cell_of(const float4 &m) { return __float_as_int(m.w); }
 __device__ __forceinline__ int cell_of(const D4 &m) { return (int)m.b.y; }
+__device__ __forceinline__ void set_cell_dead(float4 &m) { m.w = __int_as_float(-1); }
+__device__ __forceinline__ void set_cell_dead(D4 &m) { m.b.y = -1.0; }
 
 struct Lattice {
   int n[3], periodic[3];
@@ -236,18 +238,26 @@ __global__ void k_count_live(const T *mom, const long long *count, int sp, long 
 }
 
 
-// ----- sort by cell block (grid mode) ---------------------------------------
-// Counting sort of the live records by 8x8x8 cell block: histogram, one-block
-// exclusive scan into the per-species block starts, scatter through per-block
-// cursors.  Dead records are dropped.  Lanes of a warp that land in the same
-// block share one atomic.
+// ----- counting sort: by cell block (grid mode) or by ensemble ---------------
+// Counting sort of the live records by key: the 8x8x8 cell block of the
+// record (grid mode) or its ensemble (the top id bits): histogram, one-block
+// exclusive scan into the per-species key starts, scatter through per-key
+// cursors.  Dead records are dropped.  Lanes of a warp that land on the same
+// key share one atomic.
 struct BlockGeom {
   int n[3], nb[3];
+  int ens_shift;   // < 64: the key is id >> ens_shift
+  int nkeys;
 };
 
 __device__ __forceinline__ int block_of(int cell, const BlockGeom &g) {
   const int i = cell % g.n[0], j = (cell / g.n[0]) % g.n[1], k = cell / (g.n[0] * g.n[1]);
   return (i / kBlockCells) + g.nb[0] * ((j / kBlockCells) + g.nb[1] * (k / kBlockCells));
+}
+
+__device__ __forceinline__ int key_of(int cell, uint64_t id, const BlockGeom &g) {
+  if (g.ens_shift < 64) return (int)min((unsigned long long)(id >> g.ens_shift), (unsigned long long)(g.nkeys - 1));
+  return block_of(cell, g);
 }
 
 __device__ __forceinline__ unsigned block_atomic_add(unsigned *ctr, int key, bool on) {
@@ -262,16 +272,20 @@ __device__ __forceinline__ unsigned block_atomic_add(unsigned *ctr, int key, boo
 }
 
 template <typename T>
-__global__ void k_blk_hist(const T *mom, const long long *count, int sp, long long cap, BlockGeom g,
-                           unsigned *hist) {
+__global__ void k_blk_hist(const T *mom, const uint64_t *id, const long long *count, int sp, long long cap,
+                           BlockGeom g, unsigned *hist) {
   const long long n = min(count[sp], cap);
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
     const long long i = base + threadIdx.x;
     int cell = -1;
-    if (i < n) cell = cell_of(mom[i]);
+    uint64_t pid = 0;
+    if (i < n) {
+      cell = cell_of(mom[i]);
+      if (g.ens_shift < 64) pid = id[i];
+    }
     const bool live = cell >= 0;
-    block_atomic_add(hist, live ? block_of(cell, g) : 0, live);
+    block_atomic_add(hist, live ? key_of(cell, pid, g) : 0, live);
   }
 }
 
@@ -319,11 +333,12 @@ __global__ void k_blk_scatter(const T *pos, const T *mom, const uint64_t *id, T 
       cell = cell_of(M);
     }
     const bool live = cell >= 0;
-    const unsigned o = block_atomic_add(cursor, live ? block_of(cell, g) : 0, live);
+    const uint64_t pid = live ? id[i] : 0;
+    const unsigned o = block_atomic_add(cursor, live ? key_of(cell, pid, g) : 0, live);
     if (live) {
       pos2[o] = pos[i];
       mom2[o] = M;
-      id2[o] = id[i];
+      id2[o] = pid;
     }
   }
 }
@@ -338,12 +353,14 @@ int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
     g.n[k] = c->grid.n[k];
     g.nb[k] = c->nb[k];
   }
+  g.ens_shift = c->key_ensembles ? 64 - c->par.ens_bits : 64;
+  g.nkeys = c->nblk;
   const int cur = st.cur, nxt = cur ^ 1;
   unsigned *start = c->d_blk_start + (size_t)sp * (c->nblk + 1);
   if (cudaMemsetAsync(c->d_blk_cursor, 0, sizeof(unsigned) * (c->nblk + 1), s) != cudaSuccess) return QED_ERR_CUDA;
   const int grid = c->num_sms * 8;
   c->launches += 3;
-  k_blk_hist<T><<<grid, 256, 0, s>>>((const T *)st.mom[cur], c->d_count, sp, (long long)st.cap, g,
+  k_blk_hist<T><<<grid, 256, 0, s>>>((const T *)st.mom[cur], st.id[cur], c->d_count, sp, (long long)st.cap, g,
                                      c->d_blk_cursor);
   // the record count to scatter is read on the device: the histogram keeps it
   k_blk_scan<<<1, 1024, 0, s>>>(c->d_blk_cursor, c->nblk, start, c->d_count + 4, sp);   // total -> [4 + sp]
@@ -357,6 +374,166 @@ int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
     return QED_ERR_CUDA;
   st.cur = nxt;
   return QED_OK;
+}
+
+// ----- thinning (Sec. VI): global even redistribution per group --------------
+// Three passes over one species: (1) per group (ensemble, or the species)
+// the live count N and weight W; (2) where N > L, each record survives with
+// probability L/N (its own uniform, purpose THIN, counter = the step just
+// taken) and the survivors' weight W' is summed; (3) where N > L and W' > 0
+// the others die and the survivors' weights are multiplied by W/W'.  The
+// decision of pass 2 is drawn again in pass 3 from the same stream.
+struct ThinArgs {
+  int ens_shift;           // 64: one group
+  int groups;
+  long long limit;
+  const double *ens;       // ensemble table (thin_scale in column 9) or null
+  unsigned seed;
+  const void *clock;       // {double t; long long step}, already advanced
+  unsigned long long *n;   // [groups]
+  double *w, *wsurv;       // [groups]
+  unsigned long long *thinned;
+};
+
+__device__ __forceinline__ double weight_of(const float4 &P) { return (double)P.w; }
+__device__ __forceinline__ double weight_of(const D4 &P) { return P.b.y; }
+__device__ __forceinline__ void set_weight(float4 &P, double w) { P.w = (float)w; }
+__device__ __forceinline__ void set_weight(D4 &P, double w) { P.b.y = w; }
+
+__device__ __forceinline__ int group_of(uint64_t id, const ThinArgs &t) {
+  const unsigned long long e = t.ens_shift >= 64 ? 0ull : (unsigned long long)(id >> t.ens_shift);
+  return e < (unsigned long long)t.groups ? (int)e : -1;
+}
+
+// Limit of group g: the species limit, times the ensemble's thin_scale when positive.
+__device__ __forceinline__ long long group_limit(int g, const ThinArgs &t) {
+  long long L = t.limit;
+  if (t.ens) {
+    const double sc = t.ens[(size_t)g * QED_ENS_STRIDE + 9];
+    if (sc > 0.0) L = (long long)floor((double)L * sc);
+  }
+  return L;
+}
+
+__device__ __forceinline__ bool thin_survives(uint64_t id, const ThinArgs &t, long long L, unsigned long long N) {
+  const unsigned step = (unsigned)(((const long long *)t.clock)[1] - 1);
+  const uint4 o = philox4x32_10(make_uint4(step, 0u, kThin, t.seed), make_uint2((unsigned)id, (unsigned)(id >> 32)));
+  const double u = uniform_pair(o.x, o.y, (double *)nullptr);
+  return u < (double)L / (double)N;
+}
+
+// Lanes with the same group add their values with one atomic per group.
+__device__ __forceinline__ void group_add(int g, bool on, double w, unsigned long long *n, double *wsum) {
+  const unsigned mask = __ballot_sync(0xffffffffu, on);
+  if (!on) return;
+  const unsigned peers = __match_any_sync(mask, g);
+  const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+  double tot = 0.0;
+  for (unsigned m = peers; m; m &= m - 1) tot += __shfl_sync(peers, w, __ffs(m) - 1);
+  if (lane == leader) {
+    if (n) atomicAdd(n + g, (unsigned long long)__popc(peers));
+    atomicAdd(wsum + g, tot);
+  }
+}
+
+template <typename T>
+__global__ void k_thin_count(const T *pos, const T *mom, const uint64_t *id, const long long *count, int sp,
+                             long long cap, ThinArgs t) {
+  const long long n = min(count[sp], cap);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long i = base + threadIdx.x;
+    int g = -1;
+    double w = 0.0;
+    if (i < n && cell_of(mom[i]) >= 0) {
+      g = group_of(id[i], t);
+      w = weight_of(pos[i]);
+    }
+    group_add(g, g >= 0, w, t.n, t.w);
+  }
+}
+
+template <typename T>
+__global__ void k_thin_mark(const T *pos, const T *mom, const uint64_t *id, const long long *count, int sp,
+                            long long cap, ThinArgs t) {
+  const long long n = min(count[sp], cap);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long i = base + threadIdx.x;
+    int g = -1;
+    double w = 0.0;
+    if (i < n && cell_of(mom[i]) >= 0) {
+      const uint64_t pid = id[i];
+      g = group_of(pid, t);
+      if (g >= 0) {
+        const unsigned long long N = t.n[g];
+        const long long L = group_limit(g, t);
+        if ((long long)N > L && thin_survives(pid, t, L, N)) w = weight_of(pos[i]);
+        else g = -1;
+      }
+    }
+    group_add(g, g >= 0, w, nullptr, t.wsurv);
+  }
+}
+
+template <typename T>
+__global__ void k_thin_apply(T *pos, T *mom, const uint64_t *id, const long long *count, int sp, long long cap,
+                             ThinArgs t) {
+  const long long n = min(count[sp], cap);
+  unsigned long long removed = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    T M = mom[i];
+    if (cell_of(M) < 0) continue;
+    const uint64_t pid = id[i];
+    const int g = group_of(pid, t);
+    if (g < 0) continue;
+    const unsigned long long N = t.n[g];
+    const double ws = t.wsurv[g];
+    const long long L = group_limit(g, t);
+    if ((long long)N <= L || !(ws > 0.0)) continue;
+    if (thin_survives(pid, t, L, N)) {
+      T P = pos[i];
+      set_weight(P, weight_of(P) * (t.w[g] / ws));
+      pos[i] = P;
+    } else {
+      set_cell_dead(M);
+      mom[i] = M;
+      ++removed;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) removed += __shfl_xor_sync(0xffffffffu, removed, o);
+  if ((threadIdx.x & 31) == 0 && removed) atomicAdd(t.thinned, removed);
+}
+
+template <typename R>
+int thin(qed_ctx *c, int sp, cudaStream_t s) {
+  using T = typename Rec<R>::T;
+  Store &st = c->st[sp];
+  const long long L = c->par.thin_limit[sp];
+  if (st.cap == 0 || L <= 0 || !c->d_thin) return QED_OK;
+  ThinArgs t;
+  t.ens_shift = c->par.ens_bits > 0 ? 64 - c->par.ens_bits : 64;
+  t.groups = c->par.ens_bits > 0 ? c->n_ens : 1;
+  t.limit = L;
+  t.ens = (c->par.ens_bits > 0 && c->grid.field_mode == QED_FIELD_ENSEMBLE) ? c->d_ens : nullptr;
+  t.seed = c->par.seed;
+  t.clock = c->d_clock;
+  t.n = (unsigned long long *)c->d_thin;
+  t.w = (double *)(t.n + c->thin_groups);
+  t.wsurv = t.w + c->thin_groups;
+  t.thinned = c->d_counters + kCntThinned;
+  if (cudaMemsetAsync(c->d_thin, 0, (size_t)c->thin_groups * 24, s) != cudaSuccess) return QED_ERR_CUDA;
+  const int grid = c->num_sms * 8;
+  const int cur = st.cur;
+  c->launches += 3;
+  k_thin_count<T><<<grid, 256, 0, s>>>((const T *)st.pos[cur], (const T *)st.mom[cur], st.id[cur], c->d_count, sp,
+                                       (long long)st.cap, t);
+  k_thin_mark<T><<<grid, 256, 0, s>>>((const T *)st.pos[cur], (const T *)st.mom[cur], st.id[cur], c->d_count, sp,
+                                      (long long)st.cap, t);
+  k_thin_apply<T><<<grid, 256, 0, s>>>((T *)st.pos[cur], (T *)st.mom[cur], st.id[cur], c->d_count, sp,
+                                       (long long)st.cap, t);
+  return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 
 Lattice lattice(const qed_ctx *c) {
@@ -456,4 +633,8 @@ int qed_launch_sort(qed_ctx *c, int sp, cudaStream_t s) {
 
 int qed_launch_count_live(qed_ctx *c, long long *d_live, cudaStream_t s) {
   return c->prec == 64 ? qed::count_live<double>(c, d_live, s) : qed::count_live<float>(c, d_live, s);
+}
+
+int qed_launch_thin(qed_ctx *c, int sp, cudaStream_t s) {
+  return c->prec == 64 ? qed::thin<double>(c, sp, s) : qed::thin<float>(c, sp, s);
 }

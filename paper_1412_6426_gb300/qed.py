@@ -18,12 +18,15 @@ LIB_PATH = os.path.join(HERE, "_build", "libqed_gb300.so")
 QED_OK, QED_ERR_ARG, QED_ERR_CUDA, QED_ERR_CAPACITY, QED_ERR_NONFINITE = 0, 1, 2, 3, 4
 QED_ERR_TIMEOUT, QED_ERR_PMGT1, QED_ERR_STATE, QED_ERR_COURANT = 5, 6, 7, 8
 QED_ELECTRON, QED_POSITRON, QED_PHOTON, QED_ION = 0, 1, 2, 3
-QED_FIELD_GRID, QED_FIELD_UNIFORM, QED_FIELD_GAUSSIAN_LP, QED_FIELD_ROTATING_E = 0, 1, 2, 3
+QED_FIELD_GRID, QED_FIELD_UNIFORM, QED_FIELD_GAUSSIAN_LP, QED_FIELD_ROTATING_E, QED_FIELD_ENSEMBLE = 0, 1, 2, 3, 4
+QED_ENS_STRIDE = 10
+QED_MAX_ENS_BITS = 16
 
 # every entry point the header declares (checked by the CPU tests)
 EXPORTS = ("qed_init", "qed_tables_export", "qed_particles_set", "qed_particles_get", "qed_step",
            "qed_set_clock", "qed_profile_events", "qed_diagnostics", "qed_destroy", "qed_error_string",
-           "qed_particles_read_static")
+           "qed_particles_read_static", "qed_ensembles_set", "qed_get_tuning", "qed_set_tuning",
+           "qed_autotune")
 
 
 class QedGridDesc(ctypes.Structure):
@@ -45,7 +48,20 @@ class QedParams(ctypes.Structure):
                 ("pm_strict", ctypes.c_int32), ("seed", ctypes.c_uint32),
                 ("nbins", ctypes.c_int32), ("compact_interval", ctypes.c_int32),
                 ("kappa", ctypes.c_double), ("lg_lo", ctypes.c_double), ("lg_hi", ctypes.c_double),
-                ("pending_capacity", ctypes.c_int64)]
+                ("pending_capacity", ctypes.c_int64),
+                ("ens_bits", ctypes.c_int32), ("thin_interval", ctypes.c_int32),
+                ("thin_limit", ctypes.c_int64 * 4),
+                ("emit_fg", ctypes.c_double), ("pair_fg", ctypes.c_double),
+                ("emit_ng", ctypes.c_int32), ("pair_ng", ctypes.c_int32)]
+
+
+class QedTuning(ctypes.Structure):
+    _fields_ = [("photon_blocks_per_sm", ctypes.c_int32), ("massive_blocks_per_sm", ctypes.c_int32),
+                ("work_chunk", ctypes.c_int32), ("compact_interval", ctypes.c_int32),
+                ("sort_massive", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_[:5]}
 
 
 class QedFields(ctypes.Structure):
@@ -56,7 +72,8 @@ class QedDiag(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int64 * 4), ("particle_steps", ctypes.c_int64),
                 ("species_steps", ctypes.c_int64 * 4)] + [(k, ctypes.c_int64) for k in (
         "emissions", "pairs", "substeps_lepton", "substeps_photon", "pm_gt1",
-        "pp_gt1", "capped", "absorbed", "overflow", "nonfinite", "kernel_launches", "step")] + [
+        "pp_gt1", "capped", "absorbed", "overflow", "nonfinite", "photons_created", "pairs_created",
+        "thinned", "kernel_launches", "step")] + [
         ("time", ctypes.c_double), ("status", ctypes.c_int32), ("nbins", ctypes.c_int32),
         ("spectrum", ctypes.POINTER(ctypes.c_double)),
         ("spectrum_energy", ctypes.POINTER(ctypes.c_double))]
@@ -85,6 +102,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qed_profile_events.argtypes = [vp, vp, vp, vp]
     lib.qed_diagnostics.argtypes = [vp, ctypes.POINTER(QedDiag), vp]
     lib.qed_destroy.argtypes = [vp]
+    lib.qed_ensembles_set.argtypes = [vp, i32, dp, vp]
+    lib.qed_get_tuning.argtypes = [vp, ctypes.POINTER(QedTuning)]
+    lib.qed_set_tuning.argtypes = [vp, ctypes.POINTER(QedTuning)]
+    lib.qed_autotune.argtypes = [vp, ctypes.POINTER(QedFields), ctypes.c_double, i32, i64, vp,
+                                 ctypes.POINTER(QedTuning), ctypes.POINTER(i64)]
     lib.qed_error_string.argtypes = [ctypes.c_int]
     lib.qed_error_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -183,7 +205,7 @@ def qed_diagnostics(ctx: int, nbins: int = 0, stream: int = 0, check: bool = Tru
     rc = load().qed_diagnostics(ctypes.c_void_p(ctx), ctypes.byref(d), ctypes.c_void_p(stream))
     if check:
         _check("qed_diagnostics", rc)
-    out = {k: getattr(d, k) for k, _ in QedDiag._fields_[3:16]}
+    out = {k: getattr(d, k) for k, _ in QedDiag._fields_[3:19]}
     out["count"] = list(d.count)
     out["particle_steps"] = d.particle_steps
     out["species_steps"] = list(d.species_steps)
@@ -193,6 +215,34 @@ def qed_diagnostics(ctx: int, nbins: int = 0, stream: int = 0, check: bool = Tru
         out["spectrum"] = spec[:nbins].copy()
         out["spectrum_energy"] = spec_e[:nbins].copy()
     return out
+
+
+def qed_ensembles_set(ctx: int, table: np.ndarray, stream: int = 0) -> None:
+    """table: (n_ens, QED_ENS_STRIDE) rows {E0, omega, phase, Eu[3], Bu[3], thin_scale} (host, copied)."""
+    tab = np.ascontiguousarray(table, dtype=np.float64).reshape(-1, QED_ENS_STRIDE)
+    _check("qed_ensembles_set", load().qed_ensembles_set(ctypes.c_void_p(ctx), len(tab),
+                                                         ctypes.c_void_p(tab.ctypes.data),
+                                                         ctypes.c_void_p(stream)))
+
+
+def qed_get_tuning(ctx: int) -> QedTuning:
+    t = QedTuning()
+    _check("qed_get_tuning", load().qed_get_tuning(ctypes.c_void_p(ctx), ctypes.byref(t)))
+    return t
+
+
+def qed_set_tuning(ctx: int, tuning: QedTuning) -> None:
+    _check("qed_set_tuning", load().qed_set_tuning(ctypes.c_void_p(ctx), ctypes.byref(tuning)))
+
+
+def qed_autotune(ctx: int, fields: QedFields | None, dt: float, steps_per_trial: int, max_steps: int,
+                 stream: int = 0) -> tuple[QedTuning, int]:
+    t = QedTuning()
+    taken = ctypes.c_int64()
+    _check("qed_autotune", load().qed_autotune(ctypes.c_void_p(ctx), ctypes.byref(fields) if fields else None,
+                                               float(dt), int(steps_per_trial), int(max_steps),
+                                               ctypes.c_void_p(stream), ctypes.byref(t), ctypes.byref(taken)))
+    return t, taken.value
 
 
 def qed_destroy(ctx: int) -> None:

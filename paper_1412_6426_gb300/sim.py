@@ -22,7 +22,9 @@ class Simulation:
                  pairs_on: int = 1, same_step_children: int = 1, deposit_on: int = 0, nbins: int = 0,
                  lg_lo: float = -12.0, lg_hi: float = 0.0, nsub_max: int = 1000, kappa=None,
                  compact_interval: int = 0, pending_capacity: int = 0, seed=None, pm_strict: int = 0,
-                 ion_charge: float = 1.0, ion_mass: float = 1836.15267343, stream=None, tables=None):
+                 ion_charge: float = 1.0, ion_mass: float = 1836.15267343, stream=None, tables=None,
+                 thin_interval: int = 0, thin_limit=(0, 0, 0, 0), emit_fg: float = 1.0, emit_ng: int = 1,
+                 pair_fg: float = 1.0, pair_ng: int = 1):
         w = workload
         self.w = w
         self.prec = precision
@@ -53,10 +55,17 @@ class Simulation:
         p.kappa = w.kappa if kappa is None else kappa
         p.lg_lo, p.lg_hi = lg_lo, lg_hi
         p.pending_capacity = pending_capacity
+        p.ens_bits = int(getattr(w, "ens_bits", 0))
+        p.thin_interval = int(thin_interval)
+        p.thin_limit[:] = [int(v) for v in thin_limit]
+        p.emit_fg, p.pair_fg = float(emit_fg), float(pair_fg)
+        p.emit_ng, p.pair_ng = int(emit_ng), int(pair_ng)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ctx = qed.qed_init(g, s, p, tables=tables, stream=self.stream.cuda_stream)
         self.caps = list(s.capacity)
         self.fields = None
+        if getattr(w, "ens", None) is not None:
+            self.set_ensembles(w.ens)
 
     # -- particles ------------------------------------------------------------
     def set(self, species: int, x, p, w, ids) -> None:
@@ -98,6 +107,24 @@ class Simulation:
 
     def step(self, nsteps: int = 1, dt: float | None = None) -> None:
         qed.qed_step(self.ctx, self.fields, self.w.dt if dt is None else dt, nsteps, self.stream.cuda_stream)
+
+    def set_ensembles(self, table) -> None:
+        qed.qed_ensembles_set(self.ctx, np.asarray(table, dtype=np.float64), self.stream.cuda_stream)
+
+    def tuning(self) -> dict:
+        return qed.qed_get_tuning(self.ctx).as_dict()
+
+    def set_tuning(self, **kw) -> None:
+        t = qed.qed_get_tuning(self.ctx)
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        qed.qed_set_tuning(self.ctx, t)
+
+    def autotune(self, steps_per_trial: int, max_steps: int, dt: float | None = None) -> tuple[dict, int]:
+        """Advance by real steps while picking the tuning; returns (tuning, steps taken)."""
+        t, n = qed.qed_autotune(self.ctx, self.fields, self.w.dt if dt is None else dt, steps_per_trial,
+                                max_steps, self.stream.cuda_stream)
+        return t.as_dict(), n
 
     def set_clock(self, step: int, time: float) -> None:
         qed.qed_set_clock(self.ctx, step, time)

@@ -25,7 +25,8 @@ TAU_C = HBAR / (M_E * C_LIGHT ** 2)            # s
 E_S = M_E ** 2 * C_LIGHT ** 3 / (Q_E * HBAR)   # V/m
 MC2_EV = M_E * C_LIGHT ** 2 / Q_E
 
-FIELD_GRID, FIELD_UNIFORM, FIELD_GAUSSIAN_LP, FIELD_ROTATING_E = 0, 1, 2, 3
+FIELD_GRID, FIELD_UNIFORM, FIELD_GAUSSIAN_LP, FIELD_ROTATING_E, FIELD_ENSEMBLE = 0, 1, 2, 3, 4
+ENS_STRIDE = 10   # ensemble table row: E0, omega, phase, Eu[3], Bu[3], thin_scale
 ELECTRON, POSITRON, PHOTON, ION = 0, 1, 2, 3
 
 
@@ -69,6 +70,8 @@ class Workload:
     seed: int = 1
     kappa: float = 0.1
     meta: dict = field(default_factory=dict)
+    ens: np.ndarray | None = None      # (n_ens, ENS_STRIDE) table for FIELD_ENSEMBLE
+    ens_bits: int = 0                  # top id bits naming the ensemble
 
     def n_initial(self) -> int:
         return sum(len(v[3]) for v in self.particles.values())
@@ -134,6 +137,74 @@ def beam_laser_collision(n_particles: int = 1_000_000, seed: int = 1, nsteps: in
         particles={ELECTRON: (x, p, np.ones(n_particles), np.arange(n_particles, dtype=np.uint64))},
         seed=seed, meta={"gamma0": gamma0, "E0": E0, "omega": omega, "t_focus": t_focus,
                          "chi_headon": 2 * gamma0 * E0})
+
+
+def rotating_field_for_chi(chi: float, omega: float) -> float:
+    """E0 (units of E_S) of a rotating E field in which an electron on the
+    drift-free circular orbit, p = a0 = E0/omega perpendicular to E, has the
+    given chi = gamma E0 with gamma = sqrt(1 + a0^2):
+    E0^2 = (omega^2/2) (sqrt(1 + 4 chi^2/omega^2) - 1)."""
+    r = 2.0 * chi / omega
+    # sqrt(1 + r^2) - 1 written without cancellation
+    u = 0.5 * omega * omega * (r * r / (math.sqrt(1.0 + r * r) + 1.0))
+    return math.sqrt(u)
+
+
+def batched_ensembles(n_ens: int = 512, count_range=(1e3, 1e6), chi_range=(0.1, 100.0), nsteps: int = 500,
+                      seed: int = 1, wavelength_m: float = 0.8e-6, steps_per_period: int = 100,
+                      thin_interval: int = 4, thin_limit=(1, 1, 2, 0)) -> Workload:
+    """Independent test-particle instances in uniform rotating electric fields
+    (the field at the antinode of a circularly polarised standing wave).
+
+    Ensemble e has chi_e log-uniform in chi_range and N_e electrons with N_e
+    log-uniform in count_range (seeded).  Its field rotates at the laser
+    frequency with amplitude E0_e such that an electron on the drift-free
+    circular orbit, p = a0 (-sin phi_e, cos phi_e, 0) with a0 = E0_e/omega,
+    has chi = chi_e; the phase phi_e is random.  Positions are uniform in a
+    periodic box (the field is uniform, so they only label cells).  Every
+    ensemble keeps its own particle budget through thinning (Sec. VI): every
+    thin_interval steps a species group above thin_limit[sp] x N_e particles
+    is thinned with global even redistribution.  dt = T_laser /
+    steps_per_period.  Ids carry the ensemble in their top ens_bits bits."""
+    rng = np.random.default_rng(seed)
+    omega = laser_omega(wavelength_m)
+    t_laser = 2 * math.pi / omega
+    bits = max(1, int(math.ceil(math.log2(n_ens))))
+    lo, hi = (math.log10(v) for v in chi_range)
+    chi = 10.0 ** rng.uniform(lo, hi, n_ens)
+    clo, chi_ = (math.log10(v) for v in count_range)
+    counts = np.maximum(1, np.rint(10.0 ** rng.uniform(clo, chi_, n_ens))).astype(np.int64)
+    phase = rng.uniform(0.0, 2 * math.pi, n_ens)
+    E0 = np.array([rotating_field_for_chi(c, omega) for c in chi])
+    a0 = E0 / omega
+    table = np.zeros((n_ens, ENS_STRIDE))
+    table[:, 0] = E0
+    table[:, 1] = omega
+    table[:, 2] = phase
+    table[:, 9] = counts
+    cells = 16
+    d = length(wavelength_m) / cells
+    total = int(counts.sum())
+    x = rng.uniform(0.0, cells * d, (total, 3))
+    p = np.zeros((total, 3))
+    ids = np.empty(total, dtype=np.uint64)
+    o = 0
+    for e in range(n_ens):
+        n = int(counts[e])
+        p[o:o + n, 0] = -a0[e] * math.sin(phase[e])
+        p[o:o + n, 1] = a0[e] * math.cos(phase[e])
+        ids[o:o + n] = (np.uint64(e) << np.uint64(64 - bits)) | np.arange(n, dtype=np.uint64)
+        o += n
+    cap_e = int(2.5 * total) + 4096
+    cap_g = int(thin_limit[2] * total * 4) + 4096
+    return Workload(
+        name=f"batched_{n_ens}ens_{total}e_chi{chi_range[0]:g}-{chi_range[1]:g}",
+        n=(cells, cells, cells), d=(d, d, d), x0=(0.0, 0.0, 0.0), periodic=(1, 1, 1),
+        field_mode=FIELD_ENSEMBLE, fp=(), dt=t_laser / steps_per_period, nsteps=nsteps,
+        particles={ELECTRON: (x, p, np.ones(total), ids)},
+        capacity=(cap_e, cap_e, cap_g, 0), seed=seed, ens=table, ens_bits=bits,
+        meta={"chi": chi, "counts": counts, "E0": E0, "a0": a0, "phase": phase, "omega": omega,
+              "thin_interval": thin_interval, "thin_limit": tuple(thin_limit)})
 
 
 def subset(w: Workload, species: int, index: np.ndarray) -> Workload:

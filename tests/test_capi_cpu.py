@@ -60,11 +60,17 @@ LAYOUT_C = r"""
 #include "qed.h"
 #define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
 int main(void) {
-  printf("qed_grid_desc %zu\nqed_species_desc %zu\nqed_params %zu\nqed_fields %zu\nqed_diag %zu\n",
+  printf("qed_grid_desc %zu\nqed_species_desc %zu\nqed_params %zu\nqed_fields %zu\nqed_diag %zu\n"
+         "qed_tuning %zu\n",
          sizeof(qed_grid_desc), sizeof(qed_species_desc), sizeof(qed_params), sizeof(qed_fields),
-         sizeof(qed_diag));
+         sizeof(qed_diag), sizeof(qed_tuning));
   P(qed_grid_desc, d); P(qed_grid_desc, field_mode); P(qed_grid_desc, fp);
   P(qed_params, seed); P(qed_params, kappa); P(qed_params, pending_capacity);
+  P(qed_params, ens_bits); P(qed_params, thin_interval); P(qed_params, thin_limit);
+  P(qed_params, emit_fg); P(qed_params, pair_fg); P(qed_params, emit_ng); P(qed_params, pair_ng);
+  P(qed_diag, photons_created); P(qed_diag, pairs_created); P(qed_diag, thinned);
+  P(qed_diag, kernel_launches);
+  P(qed_tuning, work_chunk); P(qed_tuning, sort_massive); P(qed_tuning, reserved);
   P(qed_diag, particle_steps); P(qed_diag, species_steps); P(qed_diag, emissions);
   P(qed_diag, time); P(qed_diag, status); P(qed_diag, spectrum);
   P(qed_species_desc, charge); P(qed_fields, J);
@@ -82,13 +88,25 @@ def test_struct_layouts_match_header(tmp_path):
     lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     got = dict(l.split() for l in lines if l.strip())
     m = {"qed_grid_desc": qed.QedGridDesc, "qed_species_desc": qed.QedSpeciesDesc,
-         "qed_params": qed.QedParams, "qed_fields": qed.QedFields, "qed_diag": qed.QedDiag}
+         "qed_params": qed.QedParams, "qed_fields": qed.QedFields, "qed_diag": qed.QedDiag,
+         "qed_tuning": qed.QedTuning}
     for k, v in got.items():
         if "." in k:
             t, f = k.split(".")
             assert getattr(m[t], f).offset == int(v), k
         else:
             assert ctypes.sizeof(m[k]) == int(v), k
+
+
+def test_header_constants_match_binding():
+    from paper_1412_6426_gb300 import qed, workloads
+    text = open(HEADER).read()
+    consts = dict(re.findall(r"#define (QED_\w+)\s+(\d+)", text))
+    assert int(consts["QED_ENS_STRIDE"]) == qed.QED_ENS_STRIDE == workloads.ENS_STRIDE
+    assert int(consts["QED_MAX_ENS_BITS"]) == qed.QED_MAX_ENS_BITS
+    assert int(consts["QED_ABI_VERSION"]) == 2
+    modes = dict(re.findall(r"(QED_FIELD_\w+) = (\d+)", text))
+    assert int(modes["QED_FIELD_ENSEMBLE"]) == qed.QED_FIELD_ENSEMBLE == workloads.FIELD_ENSEMBLE
 
 
 def _descs():
@@ -109,7 +127,8 @@ def _descs():
     return g, s, p
 
 
-@pytest.mark.parametrize("bad", ["precision", "cells", "grid_open", "kappa", "nbins", "mass", "tables"])
+@pytest.mark.parametrize("bad", ["precision", "cells", "grid_open", "kappa", "nbins", "mass", "tables",
+                                 "ens_bits", "thin_limit", "fg_nan", "ng", "mode"])
 def test_argument_validation(lib, bad):
     from paper_1412_6426_gb300 import qed
     g, s, p = _descs()
@@ -129,6 +148,16 @@ def test_argument_validation(lib, bad):
         s.mass[0] = 0.0
     elif bad == "tables":
         tables = b"\0" * 7
+    elif bad == "ens_bits":
+        p.ens_bits = 17
+    elif bad == "thin_limit":
+        p.thin_limit[2] = -1
+    elif bad == "fg_nan":
+        p.emit_fg = float("nan")
+    elif bad == "ng":
+        p.pair_ng = 65
+    elif bad == "mode":
+        g.field_mode = 5
     with pytest.raises(qed.QedError) as e:
         qed.qed_init(g, s, p, tables=tables)
     assert e.value.status == qed.QED_ERR_ARG
@@ -138,6 +167,10 @@ def test_null_arguments(lib):
     from paper_1412_6426_gb300 import qed
     assert lib.qed_init(None, None, None, None, 0, None, None) == qed.QED_ERR_ARG
     assert lib.qed_step(None, None, 1.0, 1, None) == qed.QED_ERR_ARG
+    assert lib.qed_ensembles_set(None, 1, None, None) == qed.QED_ERR_ARG
+    assert lib.qed_get_tuning(None, None) == qed.QED_ERR_ARG
+    assert lib.qed_set_tuning(None, None) == qed.QED_ERR_ARG
+    assert lib.qed_autotune(None, None, 1.0, 1, 10, None, None, None) == qed.QED_ERR_ARG
     assert lib.qed_destroy(None) == qed.QED_OK
     assert lib.qed_diagnostics(None, None, None) == qed.QED_ERR_ARG
 

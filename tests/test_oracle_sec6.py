@@ -54,8 +54,8 @@ def same(out_a, out_b, species=range(4)):
         assert np.array_equal(wa[oa], wb[ob])
 
 
-def ens_row(E0=0.0, omega=0.0, phase=0.0, Eu=(0.0, 0.0, 0.0), Bu=(0.0, 0.0, 0.0)):
-    return [E0, omega, phase, *Eu, *Bu]
+def ens_row(E0=0.0, omega=0.0, phase=0.0, Eu=(0.0, 0.0, 0.0), Bu=(0.0, 0.0, 0.0), thin_scale=0.0):
+    return [E0, omega, phase, *Eu, *Bu, thin_scale]
 
 
 # ---- ensembles -----------------------------------------------------------
@@ -210,6 +210,7 @@ def test_thinning_conserves_group_weight_and_is_binomial():
     p = rng.normal(size=(n, 3)) * 100
     table = np.zeros((4, o.ENS_STRIDE))
     L = 300
+    table[3, 9] = 2.5          # the largest ensemble keeps floor(2.5 L)
     before, after, d = _thin_once({2: (x, p, w, ids)}, (0, 0, L, 0), bits, table)
     xb, pb, wb, ib = before[2]
     xa, pa, wa, ia = after[2]
@@ -218,11 +219,12 @@ def test_thinning_conserves_group_weight_and_is_binomial():
         gb = (ib >> np.uint64(64 - bits)) == e
         ga = (ia >> np.uint64(64 - bits)) == e
         assert math.isclose(wb[gb].sum(), wa[ga].sum(), rel_tol=1e-12)
-        if N <= L:
+        Lg = int(2.5 * L) if e == 3 else L
+        if N <= Lg:
             assert np.array_equal(ib[gb], ia[ga]) and np.array_equal(wb[gb], wa[ga])
         else:
-            q = L / N
-            assert abs(ga.sum() - L) < 5 * math.sqrt(N * q * (1 - q))
+            q = Lg / N
+            assert abs(ga.sum() - Lg) < 5 * math.sqrt(N * q * (1 - q))
             # survivors: a subsequence of the group, positions and momenta untouched
             keep = np.isin(ib, ia[ga])
             assert np.array_equal(ib[keep & gb], ia[ga])
