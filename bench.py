@@ -15,6 +15,14 @@ kernel is bracketed separately (qed_profile_events) for the roofline.
 
 Prints one JSON line on rank 0.  --impl reference times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
+
+--workload batched times the batched-ensemble workload instead: 512
+independent test-particle instances in uniform rotating E fields (chi
+log-uniform in [0.1, 100], electron counts log-uniform in [1e3, 1e6]), with
+per-ensemble thinning, 500 steps of dt = T_laser/100 in FP32.  The first
+steps run under the autotuner; the rest are replays of a CUDA graph that
+holds a whole number of thinning intervals and an even number of
+compactions.  Its working set (GBs) is far larger than L2.
 """
 from __future__ import annotations
 
@@ -280,8 +288,258 @@ def cpu_workers() -> int:
 
 
 # ----------------------------------------------------------------------------
+# batched ensembles
+BATCH_STEPS = 500
+BATCH_TUNE_MAX = 96
+BATCH_NAME = ("batched ensembles: 512 independent test-particle instances in uniform rotating E (drift-free "
+              "circular orbits), chi log-uniform in [0.1, 100], e- counts log-uniform in [1e3, 1e6] (seed 1), "
+              "emission + Breit-Wheeler pairs, per-ensemble thinning every 4 steps (e-, e+ to N_e, photons to "
+              "2 N_e), dt=T_L/100, 500 steps")
+
+
+BATCH_SCALE = 1.0     # electron counts x this (profiling captures only)
+BATCH_AUTOTUNE = True
+
+
+def make_batched(seed: int):
+    from paper_1412_6426_gb300 import workloads
+    return workloads.batched_ensembles(seed=seed, nsteps=BATCH_STEPS,
+                                       count_range=(1e3 * BATCH_SCALE, 1e6 * BATCH_SCALE))
+
+
+def batched_device(w, prec: int, K: int, W: int, dist_barrier) -> dict:
+    """Autotune on the first steps, then replay a captured CUDA graph of G
+    steps; W warm-up steps (whole replays) and then up to K timed steps."""
+    import torch
+    from paper_1412_6426_gb300 import qed
+    from paper_1412_6426_gb300.sim import Simulation
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = Simulation(w, precision=prec, capacity=w.capacity, compact_interval=4, stream=stream,
+                         thin_interval=w.meta["thin_interval"], thin_limit=w.meta["thin_limit"])
+        try:
+            sim.set_all()
+            if BATCH_AUTOTUNE:
+                tuned, n_tune = sim.autotune(2, BATCH_TUNE_MAX)
+            else:
+                tuned, n_tune = sim.tuning(), 0
+            sim.set_tuning(**tuned)                 # restarts the compaction phase
+            ci = tuned["compact_interval"]
+            G = math.lcm(w.meta["thin_interval"], 2 * ci)
+            left = BATCH_STEPS - n_tune
+            n_warm = max(1, -(-W // G))
+            n_timed = max(1, min(K // G, left // G - n_warm))
+            torch.cuda.synchronize()
+            l0 = sim.diag()["kernel_launches"]
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                qed.qed_step(sim.ctx, None, w.dt, G, stream.cuda_stream)
+            # minus the live-count kernels of the first diagnostics call (one per species store)
+            per_replay = sim.diag()["kernel_launches"] - l0 - sum(1 for c in w.capacity if c > 0)
+            for _ in range(n_warm):
+                graph.replay()
+            torch.cuda.synchronize()
+            d0 = sim.diag()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(n_timed)]
+            dist_barrier()
+            sampler = ClockSampler(int(os.environ.get("BENCH_GPU_INDEX", torch.cuda.current_device())))
+            torch.cuda.synchronize()
+            for k in range(n_timed):
+                ev[k][0].record(stream)
+                graph.replay()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            clocks = sampler.stop()
+            dist_barrier()
+            d1 = sim.diag()
+            del graph
+        finally:
+            sim.close()
+    rep_ms = [a.elapsed_time(b) for a, b in ev]
+    psteps = d1["particle_steps"] - d0["particle_steps"]
+    made = (d1["photons_created"] - d0["photons_created"]) + 2 * (d1["pairs_created"] - d0["pairs_created"])
+    lepton_steps = sum(d1["species_steps"][k] - d0["species_steps"][k] for k in (0, 1))
+    return {"precision": prec, "particle_steps": psteps, "seconds": sum(rep_ms) / 1e3,
+            "steps": n_timed * G, "warmup": n_tune + n_warm * G, "graph_steps": G, "replays": n_timed,
+            "ms_per_step": sum(rep_ms) / (n_timed * G), "tuning": tuned, "tune_steps": n_tune,
+            "algo_bytes": BYTES_PER_STEP[prec] * psteps + BYTES_PER_APPEND[prec] * made,
+            "launches": per_replay * n_timed,
+            "emissions": d1["emissions"] - d0["emissions"], "pairs": d1["pairs"] - d0["pairs"],
+            "thinned": d1["thinned"] - d0["thinned"], "live_end": d1["count"],
+            "substeps_per_lepton_step": (d1["substeps_lepton"] - d0["substeps_lepton"]) / max(lepton_steps, 1),
+            "clocks": clocks, "step_end": d1["step"]}
+
+
+def batched_e2e(w, prec: int, n_steps: int) -> dict:
+    """n_steps through the public API with pinned host buffers, right after
+    the thinning that ends step 8: per step every species is copied in
+    (qed_particles_set), advanced (qed_step) and copied out
+    (qed_particles_get).  The host buffers hold 3x (photons) and 2x
+    (leptons) the live particles at the start, which bounds two steps of
+    growth."""
+    import torch
+    from paper_1412_6426_gb300 import qed
+    from paper_1412_6426_gb300.sim import Simulation
+
+    stream = torch.cuda.current_stream()
+    with Simulation(w, precision=prec, capacity=w.capacity, compact_interval=4,
+                    thin_interval=w.meta["thin_interval"], thin_limit=w.meta["thin_limit"]) as sim:
+        sim.set_all()
+        sim.step(8)
+        live = sim.diag()["count"]
+        host, n = {}, {}
+        for sp in range(3):
+            cap = max(1, int(live[sp] * (3.0 if sp == 2 else 2.0)) + 4096)
+            host[sp] = (torch.empty((cap, 3), dtype=torch.float64, pin_memory=True),
+                        torch.empty((cap, 3), dtype=torch.float64, pin_memory=True),
+                        torch.empty(cap, dtype=torch.float64, pin_memory=True),
+                        torch.empty(cap, dtype=torch.int64, pin_memory=True))
+
+        def get_all():
+            for sp in range(3):
+                x, p, wt, i = host[sp]
+                n[sp] = qed.qed_particles_get(sim.ctx, sp, x.data_ptr(), p.data_ptr(), wt.data_ptr(),
+                                              i.data_ptr(), len(wt), stream.cuda_stream)
+
+        get_all()
+        torch.cuda.synchronize()
+        h2d = d2h = psteps = 0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_steps):
+            for sp in range(3):
+                x, p, wt, i = host[sp]
+                qed.qed_particles_set(sim.ctx, sp, x.data_ptr(), p.data_ptr(), wt.data_ptr(), i.data_ptr(),
+                                      n[sp], stream.cuda_stream)
+                h2d += 64 * n[sp]
+                psteps += n[sp]
+            sim.step(1)
+            get_all()
+            d2h += 64 * sum(n.values())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    return {"value": psteps / secs, "particle_steps": psteps, "seconds": secs,
+            "h2d_bytes_per_step": h2d // n_steps, "d2h_bytes_per_step": d2h // n_steps}
+
+
+def _batched_oracle_worker(args):
+    (parts, fields, nsteps) = args
+    from oracle import drive
+    n, d, x0, periodic, dt, kappa, seed, ens, bits, thin_interval, thin_limit = fields
+    base = len(parts[0][3])
+    out, diag, _, _ = drive.run(n, d, x0, periodic, 4, (), dt, nsteps, parts, kappa=kappa, seed=seed,
+                                caps=(60 * base + 4096, 60 * base + 4096, 200 * base + 4096, 1),
+                                ens=ens, ens_bits=bits, thin_interval=thin_interval, thin_limit=thin_limit)
+    return diag["timed_particle_steps"], diag["timed_seconds"], diag["overflow"]
+
+
+def batched_oracle_sample(nsteps: int, workers: int) -> dict:
+    """The oracle on whole ensembles (thinning couples the particles of an
+    ensemble): the smallest ensembles of the same workload, one per process,
+    over its first nsteps steps."""
+    import numpy as np
+    w = make_batched(seed=1)
+    counts = w.meta["counts"]
+    order = np.argsort(counts)[:workers]
+    x, p, wt, ids = w.particles[0]
+    ens_of = (ids >> np.uint64(64 - w.ens_bits)).astype(np.int64)
+    fields = (w.n, w.d, w.x0, w.periodic, w.dt, w.kappa, w.seed, w.ens, w.ens_bits,
+              w.meta["thin_interval"], w.meta["thin_limit"])
+    jobs = []
+    for e in order:
+        m = ens_of == e
+        jobs.append(({0: (x[m], p[m], wt[m], ids[m])}, fields, nsteps))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(jobs)) as pool:
+        res = pool.map(_batched_oracle_worker, jobs)
+    ps = sum(r[0] for r in res)
+    secs = max(r[1] for r in res)
+    return {"value": ps / secs, "unit": "particle-steps/s", "cores": len(jobs), "kind": "oracle",
+            "sample": (f"the {len(jobs)} smallest of the 512 ensembles ({int(counts[order].sum())} seed electrons "
+                       f"and all their products, with their thinning), steps 0..{nsteps - 1}, FP64 oracle, "
+                       f"one process per ensemble"),
+            "overflow": sum(r[2] for r in res)}
+
+
+def main_batched(args, world, rank, local):
+    import torch
+    import torch.distributed as tdist
+    from paper_1412_6426_gb300 import build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    def reduce(x: float, op) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=op)
+        return float(t.item())
+
+    build.build()
+    w = make_batched(seed=1 + rank)           # weak scaling: each rank its own 512 ensembles
+    r = batched_device(w, 32, args.steps, args.warmup, barrier)
+    r64 = None if args.no_fp64 else batched_device(w, 64, args.steps, args.warmup, barrier)
+    e2e = None if args.no_e2e else batched_e2e(w, 32, 2)
+    tot = reduce(float(r["particle_steps"]), tdist.ReduceOp.SUM if world > 1 else None)
+    mx = reduce(r["seconds"], tdist.ReduceOp.MAX if world > 1 else None)
+    if rank != 0:
+        if world > 1:
+            tdist.destroy_process_group()
+        return
+    value = tot / mx
+    peak, peak_kind = peaks()
+
+    def roof(rr):
+        ach = rr["algo_bytes"] / rr["seconds"] / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "peak_source": peak_kind,
+                "kernel": "whole step (graph replay: step kernels, thinning, compaction, sort)",
+                "algorithmic_bytes_per_step": rr["algo_bytes"] / rr["steps"],
+                "bytes_per_unit": BYTES_PER_STEP[rr["precision"]]}
+
+    line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+            "steps": r["steps"], "warmup": r["warmup"], "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": BATCH_NAME, "precision": "fp32 push/rates, fp64 tables",
+                       "parallelism": f"independent ensemble sets x{world}",
+                       "l2": "working set of several GB, larger than L2 (no flush)",
+                       "graph_steps": r["graph_steps"], "timed_replays": r["replays"],
+                       "autotune_steps": r["tune_steps"], "tuning": r["tuning"],
+                       "steps_taken": r["step_end"]},
+            "roofline": roof(r), "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "events": {"emissions": r["emissions"], "pairs": r["pairs"], "thinned": r["thinned"],
+                       "substeps_per_lepton_step": r["substeps_per_lepton_step"],
+                       "live_at_end": r["live_end"]}}
+    if r64 is not None:
+        line["fp64"] = {"value": r64["particle_steps"] / r64["seconds"], "ms_per_step": r64["ms_per_step"],
+                        "roofline": roof(r64), "tuning": r64["tuning"],
+                        "speedup_fp32_over_fp64": value / (r64["particle_steps"] / r64["seconds"])}
+    if e2e is not None:
+        line["e2e"] = {"value": e2e["value"], "unit": "particle-steps/s",
+                       "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                       "d2h_bytes_per_step": e2e["d2h_bytes_per_step"], "steps": 2}
+    if not args.no_cpu:
+        cb = batched_oracle_sample(40, min(16, cpu_workers()))
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line))
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
 def main():
-    global COMPACT_INTERVAL
+    global COMPACT_INTERVAL, BATCH_SCALE, BATCH_STEPS, BATCH_AUTOTUNE
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=RUN_STEPS - 3)
@@ -295,6 +553,12 @@ def main():
                     help="steps between compactions (which also regroup photons that cannot pair)")
     ap.add_argument("--electrons", type=int, default=N_ELECTRONS,
                     help="beam size (smaller beams are for profiling captures, not bench lines)")
+    ap.add_argument("--workload", choices=("collision", "batched"), default="collision",
+                    help="collision: the beam-laser collision (the headline line); batched: 512 ensembles")
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="batched: electron counts x this (smaller sets are for profiling captures)")
+    ap.add_argument("--batch-steps", type=int, default=BATCH_STEPS, help="batched: steps of the run")
+    ap.add_argument("--no-autotune", action="store_true", help="batched: keep the default tuning")
     args = ap.parse_args()
     if args.electrons != N_ELECTRONS:
         scale_workload(args.electrons)
@@ -306,6 +570,21 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "batched":
+        BATCH_SCALE, BATCH_STEPS, BATCH_AUTOTUNE = args.batch_scale, args.batch_steps, not args.no_autotune
+        if args.impl == "reference":
+            if rank == 0:
+                cb = batched_oracle_sample(40, min(16, cpu_workers()))
+                print(json.dumps({"metric": METRIC, "value": cb["value"], "unit": "particle-steps/s",
+                                  "n_gpus": args.gpus, "steps": 40, "warmup": 0, "higher_is_better": True,
+                                  "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                                  "impl": "reference", "config": {"workload": BATCH_NAME, "sample": cb["sample"]},
+                                  "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                                  "e2e": {"value": cb["value"], "unit": "particle-steps/s",
+                                          "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+            return
+        main_batched(args, world, rank, local)
+        return
 
     if args.impl == "reference":
         if rank != 0:

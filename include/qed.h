@@ -175,7 +175,10 @@ typedef struct qed_tuning {
     int32_t compact_interval;      /* steps between removals of dead records
                                       (and re-sorts), >= 1 */
     int32_t sort_massive;          /* QED_FIELD_ENSEMBLE: at each compaction,
-                                      order e-, e+ and ions by ensemble */
+                                      order e-, e+ and ions by the number of
+                                      sub-intervals (Eq. (28)) their next step
+                                      is estimated to take, so that warps run
+                                      loops of about equal length */
     int32_t reserved[3];           /* must be 0 */
 } qed_tuning;
 
@@ -287,7 +290,11 @@ int qed_step(qed_ctx *ctx, const qed_fields *fields, double dt, int32_t nsteps, 
 int qed_ensembles_set(qed_ctx *ctx, int32_t n_ens, const double *table, void *stream);
 
 /* Read or replace the launch shapes and schedules (host struct).
- * QED_ERR_ARG for values outside the documented ranges. */
+ * QED_ERR_ARG for values outside the documented ranges.  After
+ * qed_set_tuning the next compaction comes compact_interval steps later, so
+ * a captured sequence of steps that starts there and covers an even number
+ * of compactions (and a whole number of thinning intervals) replays
+ * correctly. */
 int qed_get_tuning(qed_ctx *ctx, qed_tuning *out);
 int qed_set_tuning(qed_ctx *ctx, const qed_tuning *tuning);
 

@@ -62,6 +62,7 @@ void release(qed_ctx *c) {
   cudaFree(c->d_tile);
   cudaFree(c->stage);
   cudaFree(c->d_ens);
+  cudaFree(c->d_ens_h);
   cudaFree(c->d_ens_field);
   cudaFree(c->d_thin);
 }
@@ -230,13 +231,14 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
   if (g->field_mode == QED_FIELD_ENSEMBLE) {
     c->ens_cap = 1 << p->ens_bits;
     if (rc == QED_OK) rc = dalloc(&c->d_ens, sizeof(double) * QED_ENS_STRIDE * c->ens_cap);
+    if (rc == QED_OK) rc = dalloc(&c->d_ens_h, sizeof(float) * c->ens_cap);
     if (rc == QED_OK)
       rc = dalloc(&c->d_ens_field, (c->prec == 64 ? sizeof(double) : sizeof(float)) * qed::kEnsFieldStride *
                                        c->ens_cap);
-    if (p->ens_bits > 0) {
-      // counting sort of e-, e+ and ions by ensemble
+    {
+      // counting sort of e-, e+ and ions by their estimated sub-interval count
       c->key_ensembles = 1;
-      c->nblk = c->ens_cap;
+      c->nblk = qed::kNsubKeys;
       if (rc == QED_OK) rc = dalloc(&c->d_blk_start, sizeof(unsigned) * 4 * (c->nblk + 1));
       if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (c->nblk + 1));
     }
@@ -376,6 +378,7 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
   }
   if (c->grid.field_mode == QED_FIELD_ENSEMBLE && c->n_ens < 1) return QED_ERR_ARG;
   cudaStream_t s = as_stream(stream);
+  c->last_dt = dt;
   for (int n = 0; n < nsteps; ++n) {
     if (grid && c->nblk > 0 && !c->sorted) {
       // records in cell-block order let electrons, positrons and ions deposit
@@ -413,19 +416,29 @@ int qed_ensembles_set(qed_ctx *c, int32_t n_ens, const double *table, void *stre
   if (!c || c->grid.field_mode != QED_FIELD_ENSEMBLE || !table) return QED_ERR_ARG;
   if (n_ens < 1 || n_ens > c->ens_cap) return QED_ERR_ARG;
   double hmax = 0.0;
+  float *hb = new (std::nothrow) float[n_ens];
+  if (!hb) return QED_ERR_CUDA;
   for (long long e = 0; e < n_ens; ++e) {
     const double *q = table + e * QED_ENS_STRIDE;
     for (int k = 0; k < QED_ENS_STRIDE; ++k)
-      if (!std::isfinite(q[k])) return QED_ERR_ARG;
+      if (!std::isfinite(q[k])) {
+        delete[] hb;
+        return QED_ERR_ARG;
+      }
     // |E| + |B| <= |E0| + |Eu| + |Bu|
     const double h = std::fabs(q[0]) + std::sqrt(q[3] * q[3] + q[4] * q[4] + q[5] * q[5]) +
                      std::sqrt(q[6] * q[6] + q[7] * q[7] + q[8] * q[8]);
     hmax = h > hmax ? h : hmax;
+    hb[e] = (float)h;
   }
   cudaStream_t s = as_stream(stream);
-  if (cudaMemcpyAsync(c->d_ens, table, sizeof(double) * QED_ENS_STRIDE * n_ens, cudaMemcpyHostToDevice, s) !=
-      cudaSuccess)
-    return QED_ERR_CUDA;
+  const bool ok = cudaMemcpyAsync(c->d_ens, table, sizeof(double) * QED_ENS_STRIDE * n_ens,
+                                  cudaMemcpyHostToDevice, s) == cudaSuccess &&
+                  cudaMemcpyAsync(c->d_ens_h, hb, sizeof(float) * n_ens, cudaMemcpyHostToDevice, s) ==
+                      cudaSuccess &&
+                  cudaStreamSynchronize(s) == cudaSuccess;
+  delete[] hb;
+  if (!ok) return QED_ERR_CUDA;
   c->n_ens = n_ens;
   c->ens_hmax = hmax;
   int rc = qed_launch_chi_star(c, s);   // eps* = chi*/hmax changes with the fields
@@ -446,6 +459,7 @@ int qed_set_tuning(qed_ctx *c, const qed_tuning *t) {
   if (t->sort_massive && !c->key_ensembles) return QED_ERR_ARG;
   c->tune = *t;
   c->par.compact_interval = t->compact_interval;
+  c->steps_since_compact = 0;   // the next compaction comes compact_interval steps later
   return QED_OK;
 }
 

@@ -19,6 +19,7 @@ enum Counter {
 };
 constexpr int kWorkSlot = kMaxPass + 3;   // d_pend_count slot: work counter of the e-/e+/ion pass
 constexpr int kEnsFieldStride = 8;        // per ensemble per step: E[3], B[3], |E|+|B|, pad
+constexpr int kNsubKeys = 64;             // sort keys of the sub-interval estimate (last: >= 63)
 constexpr int kMaxBins = 4096;
 constexpr int kCompactTile = 2048;   // particles per tile of the compaction
 constexpr int kBlockCells = 8;       // cell block edge (grid mode): 8 x 8 x 8 cells
@@ -127,11 +128,13 @@ struct qed_ctx {
   double *d_eps_star = nullptr;       // photons below this |p| cannot pair in the analytic field
   void *d_step_const = nullptr;       // per-step field constants
   double *d_ens = nullptr;            // ensemble table (2^ens_bits rows)
+  float *d_ens_h = nullptr;           // per ensemble |E0| + |Eu| + |Bu| (sort key)
   void *d_ens_field = nullptr;        // per-step ensemble fields (context precision)
   int n_ens = 0;
   int ens_cap = 0;                    // rows allocated
   double ens_hmax = 0.0;
-  int key_ensembles = 0;              // sort keys are ensembles, not cell blocks
+  int key_ensembles = 0;              // ensembles: sort keys are estimated sub-interval counts
+  double last_dt = 0.0;               // dt of the latest qed_step (the sort key uses it)
   int ext = 0;                        // ensembles or generator factors: EXT kernels
   void *d_thin = nullptr;             // thinning: per group count, weight, survivors' weight
   int thin_groups = 0;

@@ -32,12 +32,21 @@ template <typename R> struct Pend {
   uint64_t id;
 };
 
+// Per-thread counts of the frequent events, summed per warp at the end of a
+// kernel.  Rare events (P > 1, capped intervals, absorbed particles,
+// overflows, non-finite values) go straight to the global counters, so that
+// this struct stays small enough to live in registers.
 struct Cnt {
-  unsigned long long sub_l = 0, sub_g = 0;
+  unsigned sub_l = 0, sub_g = 0;       // sub-intervals of leptons, of photons
   unsigned psteps[4] = {0, 0, 0, 0};   // live particles advanced, per species
-  unsigned emis = 0, pairs = 0, pm1 = 0, pp1 = 0, capped = 0, absorbed = 0, overflow = 0, nonfin = 0;
+  unsigned emis = 0, pairs = 0;
   unsigned made_ph = 0, made_pair = 0;   // products made (all N_g samples, after the 1/f_g keep)
 };
+
+template <typename R>
+__device__ __forceinline__ void count_rare(const StepArgs<R> &a, int counter, unsigned v) {
+  if (v) atomicAdd(a.counters + counter, (unsigned long long)v);
+}
 
 // ----- store access --------------------------------------------------------
 __device__ __forceinline__ void load(const StepArgs<float> &a, int sp, long long i, Pt<float> &q,
@@ -533,10 +542,20 @@ __device__ __forceinline__ uint64_t product_id(const StepArgs<R> &a, uint64_t pa
 }
 
 // Append a finished particle to its store (warp-aggregated slot reservation).
+// Outcome bits of append / emit, added to the caller's counters: passing the
+// counters themselves by reference would keep them in local memory.
+constexpr unsigned kOutAbsorbed = 1u, kOutOverflow = 2u;
+
 template <typename R>
-__device__ __noinline__ void append(const StepArgs<R> &a, int sp, Pt<R> &q, Cnt &cnt) {
+__device__ __forceinline__ void count_outcome(const StepArgs<R> &a, unsigned r) {
+  count_rare(a, kCntAbsorbed, r & kOutAbsorbed);
+  count_rare(a, kCntOverflow, (r & kOutOverflow) >> 1);
+}
+
+template <typename R>
+__device__ __noinline__ unsigned append(const StepArgs<R> &a, int sp, Pt<R> &q) {
   int cell = finish_cell(a, q);
-  if (cell < 0) { cnt.absorbed++; return; }
+  if (cell < 0) return kOutAbsorbed;
   unsigned mask = __activemask();
   // lanes appending to the same species share one atomic
   unsigned peers = __match_any_sync(mask, sp);
@@ -550,16 +569,15 @@ __device__ __noinline__ void append(const StepArgs<R> &a, int sp, Pt<R> &q, Cnt 
   long long slot = (long long)base + rank;
   if (slot >= a.cap[sp]) {
     atomicOr(a.status, kStCapacity);
-    cnt.overflow++;
-    return;
+    return kOutOverflow;
   }
   store(a, sp, slot, q, cell, true);
+  return 0;
 }
 
 // Queue a product for the rest of the step (same_step), or append it now.
 template <typename R>
-__device__ __noinline__ void emit(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, R trem, V3<R> E, V3<R> B,
-                                  Cnt &cnt) {
+__device__ __noinline__ unsigned emit(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, R trem, V3<R> E, V3<R> B) {
   if (a.same_step && trem > R(0)) {
     // lanes queueing products in this pass share one atomic
     const unsigned mask = __activemask();
@@ -570,17 +588,16 @@ __device__ __noinline__ void emit(const StepArgs<R> &a, int pass, int sp, Pt<R> 
     unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
     if ((long long)slot >= a.pend_cap) {
       atomicOr(a.status, kStCapacity);
-      cnt.overflow++;
-      return;
+      return kOutOverflow;
     }
     Pend<R> *r = (Pend<R> *)a.pend[(pass + 1) & 1] + slot;
     r->off[0] = q.off[0]; r->off[1] = q.off[1]; r->off[2] = q.off[2];
     r->w = q.w; r->p = q.p; r->trem = trem; r->E = E; r->B = B;
     r->ci[0] = q.ci[0]; r->ci[1] = q.ci[1]; r->ci[2] = q.ci[2];
     r->sp = sp; r->id = q.id;
-  } else {
-    append(a, sp, q, cnt);
+    return 0;
   }
+  return append(a, sp, q);
 }
 
 // Generator factors (Sec. VI) for the emission: N_g samples of the modified
@@ -588,16 +605,21 @@ __device__ __noinline__ void emit(const StepArgs<R> &a, int pass, int sp, Pt<R> 
 // each accepted sample makes a photon carrying delta = r1^3 of the parent's
 // momentum before its recoil, kept with probability 1/f_g (a KEEP draw),
 // with weight w f_g / N_g.  The parent's recoil is left to the caller.
+struct SampleCounts {
+  unsigned made = 0, gt1 = 0, out = 0;   // products made, P > 1 draws, outcome bits
+};
+
 template <typename R>
-__device__ __noinline__ void emit_samples(const StepArgs<R> &a, int pass, const Pt<R> &q, R r1, R r2, R pm, R chi,
-                                          R g, R h, int s, int n, unsigned step, V3<R> E, V3<R> B, Cnt &cnt) {
+__device__ __noinline__ SampleCounts emit_samples(const StepArgs<R> &a, int pass, const Pt<R> &q, R r1, R r2, R pm,
+                                                  R chi, R g, R h, int s, int n, unsigned step, V3<R> E, V3<R> B) {
+  SampleCounts c;
   for (int j = 0; j < a.emit_ng; ++j) {
     R a1 = r1, a2 = r2, pmj = pm;
     if (j > 0) {
       draw2(q.id, step, (unsigned)s, kEmit | ((unsigned)j << 8), a.seed, a1, a2);
       pmj = prob_emit(a.tab, a1, chi, g, h);
       if (pmj > R(1)) {
-        cnt.pm1++;
+        c.gt1++;
         if (a.pm_strict) atomicOr(a.status, kStPmGt1);
       }
     }
@@ -612,10 +634,11 @@ __device__ __noinline__ void emit_samples(const StepArgs<R> &a, int pass, const 
     ph.p = {delta * q.p.x, delta * q.p.y, delta * q.p.z};
     ph.w = q.w * a.emit_wf;
     ph.id = product_id(a, q.id, step, (unsigned)s, kPhoton | ((unsigned)j << 8));
-    cnt.made_ph++;
+    c.made++;
     spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), ph.w);
-    emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B, cnt);
+    c.out |= emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B);
   }
+  return c;
 }
 
 // The same for the pair generator: each accepted sample makes an electron
@@ -623,8 +646,9 @@ __device__ __noinline__ void emit_samples(const StepArgs<R> &a, int pass, const 
 // probability 1/f_g, with weight w f_g / N_g.  The photon's own conversion
 // (sample 0) is left to the caller.
 template <typename R>
-__device__ __noinline__ void pair_samples(const StepArgs<R> &a, int pass, const Pt<R> &q, R r1, R r2, R pp, R chig,
-                                          R eps, R h, int s, int n, unsigned step, V3<R> E, V3<R> B, Cnt &cnt) {
+__device__ __noinline__ SampleCounts pair_samples(const StepArgs<R> &a, int pass, const Pt<R> &q, R r1, R r2, R pp,
+                                                  R chig, R eps, R h, int s, int n, unsigned step, V3<R> E, V3<R> B) {
+  SampleCounts c;
   const R trem = R(n - 1 - s) * h;
   for (int j = 0; j < a.pair_ng; ++j) {
     R a1 = r1, a2 = r2, ppj = pp;
@@ -632,7 +656,7 @@ __device__ __noinline__ void pair_samples(const StepArgs<R> &a, int pass, const 
       draw2(q.id, step, (unsigned)s, kPair | ((unsigned)j << 8), a.seed, a1, a2);
       ppj = prob_pair(a.tab, a1, chig, eps, h);
       if (ppj > R(1)) {
-        cnt.pp1++;
+        c.gt1++;
         if (a.pm_strict) atomicOr(a.status, kStPmGt1);
       }
     }
@@ -649,10 +673,11 @@ __device__ __noinline__ void pair_samples(const StepArgs<R> &a, int pass, const 
     el.w = po.w = q.w * a.pair_wf;
     el.id = product_id(a, q.id, step, (unsigned)s, kElectron | ((unsigned)j << 8));
     po.id = product_id(a, q.id, step, (unsigned)s, kPositron | ((unsigned)j << 8));
-    cnt.made_pair++;
-    emit(a, pass, kElectron, el, trem, E, B, cnt);
-    emit(a, pass, kPositron, po, trem, E, B, cnt);
+    c.made++;
+    c.out |= emit(a, pass, kElectron, el, trem, E, B);
+    c.out |= emit(a, pass, kPositron, po, trem, E, B);
   }
+  return c;
 }
 
 // Electron, positron or ion: the adaptive sub-interval loop (Sec. IV.H) of
@@ -661,8 +686,10 @@ template <typename R, bool EXT>
 __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, R t_span,
                                                 V3<R> E, V3<R> B, Cnt &cnt, const uint64_t *idp, unsigned step,
                                                 R *jt = nullptr, const int *torg = nullptr) {
-  const int cs[3] = {q.ci[0], q.ci[1], q.ci[2]};
-  const R os[3] = {q.off[0], q.off[1], q.off[2]};
+  // start position (scalars: arrays handed to the deposit would live in
+  // local memory for the whole loop)
+  const int cs0 = q.ci[0], cs1 = q.ci[1], cs2 = q.ci[2];
+  const R os0 = q.off[0], os1 = q.off[1], os2 = q.off[2];
   const R qc = a.charge[sp], m = a.mass[sp];
   const bool qed = (sp != kIon) && a.emission_on;
   if (qed && idp) q.id = __ldg(idp);
@@ -670,7 +697,7 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
   if (qed) {
     R g0 = sqrt_r(R(1) + dot(q.p, q.p) / (m * m));
     n = nsub_lepton(t_span, g0, heff_lepton(q.p, g0, E, B), a.kappa, a.nsub_max, capped);
-    cnt.capped += capped;
+    count_rare(a, kCntCapped, (unsigned)capped);
   }
   const R h = t_span / R(n);
   for (int s = 0; s < n; ++s) {
@@ -685,12 +712,15 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
     draw2(q.id, step, (unsigned)s, kEmit, a.seed, r1, r2);
     R pm = prob_emit(a.tab, r1, chi, g, h);
     if (pm > R(1)) {
-      cnt.pm1++;
+      count_rare(a, kCntPmGt1, 1u);
       if (a.pm_strict) atomicOr(a.status, kStPmGt1);
     }
     if (EXT && (a.emit_ng > 1 || a.emit_keep < R(1))) {
       // generator factors: products from N_g samples, kept with 1/f_g
-      emit_samples(a, pass, q, r1, r2, pm, chi, g, h, s, n, step, E, B, cnt);
+      const SampleCounts sc = emit_samples(a, pass, q, r1, r2, pm, chi, g, h, s, n, step, E, B);
+      cnt.made_ph += sc.made;
+      count_rare(a, kCntPmGt1, sc.gt1);
+      count_outcome(a, sc.out);
       if (r2 < pm) {
         const R omd = R(1) - r1 * r1 * r1;
         q.p = {omd * q.p.x, omd * q.p.y, omd * q.p.z};
@@ -707,11 +737,15 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
       cnt.emis++;
       cnt.made_ph++;
       spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), q.w);
-      emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B, cnt);
+      count_outcome(a, emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B));
     }
   }
-  if (a.deposit && qc != R(0))
-    if (!jt || !deposit_tile(a, jt, torg, cs, os, q, qc * q.w)) deposit(a, cs, os, q, qc * q.w);
+  if (a.deposit && qc != R(0)) {
+    const int cs[3] = {cs0, cs1, cs2};
+    const R os[3] = {os0, os1, os2};
+    const Pt<R> fin = q;
+    if (!jt || !deposit_tile(a, jt, torg, cs, os, fin, qc * q.w)) deposit(a, cs, os, fin, qc * q.w);
+  }
 }
 
 // Photon: straight flight with the pair generator (Sec. V.A) in the same
@@ -731,7 +765,7 @@ __device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, P
   int n = 1, capped = 0;
   if (a.pairs_on) {
     n = nsub_photon(t_span, hg, a.kappa, a.nsub_max, capped);
-    cnt.capped += capped;
+    count_rare(a, kCntCapped, (unsigned)capped);
   }
   const R h = t_span / R(n);
   // No draw can make a pair when P_p is below the smallest uniform: below
@@ -751,12 +785,15 @@ __device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, P
     draw2(q.id, step, (unsigned)s, kPair, a.seed, r1, r2);
     R pp = prob_pair(a.tab, r1, chig, eps, h);
     if (pp > R(1)) {
-      cnt.pp1++;
+      count_rare(a, kCntPpGt1, 1u);
       if (a.pm_strict) atomicOr(a.status, kStPmGt1);
     }
     if (EXT && (a.pair_ng > 1 || a.pair_keep < R(1))) {
       // generator factors: pairs from N_g samples, kept with 1/f_g
-      pair_samples(a, pass, q, r1, r2, pp, chig, eps, h, s, n, step, E, B, cnt);
+      const SampleCounts sc = pair_samples(a, pass, q, r1, r2, pp, chig, eps, h, s, n, step, E, B);
+      cnt.made_pair += sc.made;
+      count_rare(a, kCntPpGt1, sc.gt1);
+      count_outcome(a, sc.out);
       if (r2 < pp) {
         cnt.pairs++;
         return false;
@@ -772,8 +809,7 @@ __device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, P
       cnt.pairs++;
       cnt.made_pair++;
       R trem = R(n - 1 - s) * h;
-      emit(a, pass, kElectron, el, trem, E, B, cnt);
-      emit(a, pass, kPositron, po, trem, E, B, cnt);
+      count_outcome(a, emit(a, pass, kElectron, el, trem, E, B) | emit(a, pass, kPositron, po, trem, E, B));
       return false;
     }
   }
@@ -813,17 +849,17 @@ __device__ bool grid_barrier(unsigned *bar, int *status) {
 }
 
 __device__ __forceinline__ void flush(const Cnt &c, unsigned long long *g) {
-  unsigned long long v[16] = {c.emis,      c.pairs,       c.sub_l,       c.sub_g,     c.pm1,
-                              c.pp1,       c.capped,      c.absorbed,    c.overflow,  c.nonfin,
-                              c.psteps[0], c.psteps[1],   c.psteps[2],   c.psteps[3], c.made_ph,
-                              c.made_pair};
-  static_assert(kCntPhotonsMade == 14 && kCntPairsMade == 15, "counter layout");
+  const unsigned v[10] = {c.emis, c.pairs, c.sub_l, c.sub_g, c.psteps[0], c.psteps[1], c.psteps[2],
+                          c.psteps[3], c.made_ph, c.made_pair};
+  const int slot[10] = {kCntEmissions, kCntPairs, kCntSubLepton, kCntSubPhoton, kCntSpeciesSteps,
+                        kCntSpeciesSteps + 1, kCntSpeciesSteps + 2, kCntSpeciesSteps + 3, kCntPhotonsMade,
+                        kCntPairsMade};
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
+  for (int k = 0; k < 10; ++k) {
     unsigned long long x = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if ((threadIdx.x & 31) == 0 && x) atomicAdd(g + k, x);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(g + slot[k], x);
   }
 }
 
@@ -923,14 +959,14 @@ __global__ void __launch_bounds__(256, (Pass0Occ<R, PHOTON>::blocks)) k_pass0(co
     // a NaN or an infinity in any input makes this sum NaN or infinite
     const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
     if (!(probe == R(0))) {
-      cnt.nonfin++;
+      count_rare(a, kCntNonfinite, 1u);
       atomicOr(a.status, kStNonfinite);
     }
     bool alive = true;
     if (PHOTON) alive = advance_photon<R, EXT>(a, 0, q, a.dt, E, B, cnt, idp, (R)*a.chi_star, kc.step);
     else advance_massive<R, EXT>(a, 0, sp, q, a.dt, E, B, cnt, idp, kc.step);
     int nc = alive ? finish_cell(a, q) : -1;
-    if (alive && nc < 0) cnt.absorbed++;
+    if (alive && nc < 0) count_rare(a, kCntAbsorbed, 1u);
     // a photon's momentum never changes: its momentum record is rewritten
     // only when the cell changed or the photon died
     if (PHOTON && nc == cell) store_pos(a, sp, i, q);
@@ -1037,13 +1073,21 @@ __global__ void __launch_bounds__(kPhotonThreads, PhotonOcc<R>::blocks) k_photon
     q.ci[2] = (int)slab;
     bool alive = true;
     const R eps = sqrt_r(dot(q.p, q.p));
-    const R hmax = sizeof(R) == 4 ? (R)kc.hmax_f : (R)kc.hmax;
-    if (!a.pairs_on || (kc.one_interval && eps * hmax < R(0.99999) * chi_star)) {
+    R hmax = sizeof(R) == 4 ? (R)kc.hmax_f : (R)kc.hmax;
+    bool one = kc.one_interval;
+    if (EXT && a.field_mode == kFieldEnsemble) {
+      // the bound of the photon's own ensemble: |E| + |B| at this step
+      q.id = __ldg(a.id[kPhoton] + i);
+      const unsigned long long e = a.ens_shift >= 64 ? 0ull : (unsigned long long)(q.id >> a.ens_shift);
+      hmax = e < (unsigned long long)a.n_ens ? __ldg(a.ens_field + e * kEnsFieldStride + 6) * R(1.00001) : R(0);
+      one = a.dt * hmax <= R(0.999) * a.kappa * R(130.0 * kTwoPi);   // N = 1 for every H <= hmax
+    }
+    if (!a.pairs_on || (one && eps * hmax < R(0.99999) * chi_star)) {
       // This photon cannot pair in this step (chi_g <= eps hmax < chi*) and
       // takes one sub-interval: its step is the straight flight of
       // advance_photon with N = 1, without evaluating the field.
       if (!(q.p.x * R(0) + q.p.y * R(0) + q.p.z * R(0) == R(0))) {
-        cnt.nonfin++;
+        count_rare(a, kCntNonfinite, 1u);
         atomicOr(a.status, kStNonfinite);
       }
       V3<R> dir = {R(0), R(0), R(0)};
@@ -1059,21 +1103,20 @@ __global__ void __launch_bounds__(kPhotonThreads, PhotonOcc<R>::blocks) k_photon
       if (a.field_mode == kFieldGrid) {
         gather_grid(a, q, E, B);
       } else if (EXT && a.field_mode == kFieldEnsemble) {
-        q.id = __ldg(idp);
-        idp = nullptr;
+        idp = nullptr;                  // q.id was loaded for the bound above
         field_ensemble(a, q.id, E, B);
       } else {
         field_analytic(a, kc, q, E, B);
       }
       const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
       if (!(probe == R(0))) {
-        cnt.nonfin++;
+        count_rare(a, kCntNonfinite, 1u);
         atomicOr(a.status, kStNonfinite);
       }
       alive = advance_photon<R, EXT>(a, 0, q, a.dt, E, B, cnt, idp, chi_star, kc.step);
     }
     const int nc = alive ? finish_cell(a, q) : -1;
-    if (alive && nc < 0) cnt.absorbed++;
+    if (alive && nc < 0) count_rare(a, kCntAbsorbed, 1u);
     // a photon's momentum never changes: its momentum record is rewritten
     // only when the cell changed or the photon died
     if (nc == cell) store_pos(a, kPhoton, i, q);
@@ -1127,12 +1170,12 @@ __global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
         gather_grid(a, q, E, B);
         const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
         if (!(probe == R(0))) {
-          cnt.nonfin++;
+          count_rare(a, kCntNonfinite, 1u);
           atomicOr(a.status, kStNonfinite);
         }
         advance_massive<R, EXT>(a, 0, sp, q, a.dt, E, B, cnt, a.id[sp] + i, step, jt, torg);
         const int nc = finish_cell(a, q);
-        if (nc < 0) cnt.absorbed++;
+        if (nc < 0) count_rare(a, kCntAbsorbed, 1u);
         store(a, sp, i, q, nc, false);
       }
     }
@@ -1177,7 +1220,10 @@ __global__ void __launch_bounds__(256, 2) k_products(const StepArgs<R> a) {
       bool alive = true;
       if (r.sp == kPhoton) alive = advance_photon<R, EXT>(a, pass, q, r.trem, r.E, r.B, cnt, nullptr, chi_star, step);
       else advance_massive<R, EXT>(a, pass, r.sp, q, r.trem, r.E, r.B, cnt, nullptr, step);
-      if (alive) append(a, r.sp, q, cnt);
+      if (alive) {
+        Pt<R> fin = q;   // a copy: q itself stays in registers
+        count_outcome(a, append(a, r.sp, fin));
+      }
     }
   }
   flush(cnt, a.counters);

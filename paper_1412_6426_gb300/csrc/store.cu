@@ -238,16 +238,23 @@ __global__ void k_count_live(const T *mom, const long long *count, int sp, long 
 }
 
 
-// ----- counting sort: by cell block (grid mode) or by ensemble ---------------
+// ----- counting sort: by cell block (grid mode) or by sub-interval count ----
 // Counting sort of the live records by key: the 8x8x8 cell block of the
-// record (grid mode) or its ensemble (the top id bits): histogram, one-block
+// record (grid mode), or for independent ensembles the number of
+// sub-intervals the adaptive event generator will take for the record's next
+// step, estimated from its momentum and its ensemble's field bound, so that
+// the lanes of a warp run loops of about equal length: histogram, one-block
 // exclusive scan into the per-species key starts, scatter through per-key
 // cursors.  Dead records are dropped.  Lanes of a warp that land on the same
 // key share one atomic.
 struct BlockGeom {
   int n[3], nb[3];
-  int ens_shift;   // < 64: the key is id >> ens_shift
   int nkeys;
+  int nsub_key;            // 1: key = estimated sub-intervals (ensembles)
+  int ens_shift;           // ensemble = id >> ens_shift (64: ensemble 0)
+  int n_ens;
+  const float *ens_h;      // per ensemble: |E0| + |Eu| + |Bu|
+  float dt, kappa, mass;
 };
 
 __device__ __forceinline__ int block_of(int cell, const BlockGeom &g) {
@@ -255,8 +262,23 @@ __device__ __forceinline__ int block_of(int cell, const BlockGeom &g) {
   return (i / kBlockCells) + g.nb[0] * ((j / kBlockCells) + g.nb[1] * (k / kBlockCells));
 }
 
-__device__ __forceinline__ int key_of(int cell, uint64_t id, const BlockGeom &g) {
-  if (g.ens_shift < 64) return (int)min((unsigned long long)(id >> g.ens_shift), (unsigned long long)(g.nkeys - 1));
+// Sub-intervals of Eq. (28) with the ensemble's bound |E0| + |Eu| + |Bu| in
+// place of H_eff, in FP32: the key only orders the records, so an estimate
+// will do.
+__device__ __forceinline__ int nsub_key(uint64_t id, float p2, const BlockGeom &g) {
+  const unsigned long long e = g.ens_shift >= 64 ? 0ull : (unsigned long long)(id >> g.ens_shift);
+  if (e >= (unsigned long long)g.n_ens || !(g.mass > 0.f)) return 0;
+  const float H = __ldg(g.ens_h + e);
+  if (!(H > 0.f)) return 0;
+  const float gamma = sqrtf(1.f + p2 / (g.mass * g.mass));
+  const float dtq = g.kappa * 137.f * fminf(0.67f * cbrtf(gamma) / cbrtf(H * H), 2.f / H);
+  const float n = ceilf(g.dt / dtq);
+  return n < (float)(g.nkeys - 1) ? (int)n : g.nkeys - 1;
+}
+
+template <typename T>
+__device__ __forceinline__ int key_of(int cell, uint64_t id, const T &m, const BlockGeom &g) {
+  if (g.nsub_key) return nsub_key(id, (float)p2_of(m), g);
   return block_of(cell, g);
 }
 
@@ -280,12 +302,14 @@ __global__ void k_blk_hist(const T *mom, const uint64_t *id, const long long *co
     const long long i = base + threadIdx.x;
     int cell = -1;
     uint64_t pid = 0;
+    T M;
     if (i < n) {
-      cell = cell_of(mom[i]);
-      if (g.ens_shift < 64) pid = id[i];
+      M = mom[i];
+      cell = cell_of(M);
+      if (g.nsub_key) pid = id[i];
     }
     const bool live = cell >= 0;
-    block_atomic_add(hist, live ? key_of(cell, pid, g) : 0, live);
+    block_atomic_add(hist, live ? key_of(cell, pid, M, g) : 0, live);
   }
 }
 
@@ -334,7 +358,7 @@ __global__ void k_blk_scatter(const T *pos, const T *mom, const uint64_t *id, T 
     }
     const bool live = cell >= 0;
     const uint64_t pid = live ? id[i] : 0;
-    const unsigned o = block_atomic_add(cursor, live ? key_of(cell, pid, g) : 0, live);
+    const unsigned o = block_atomic_add(cursor, live ? key_of(cell, pid, M, g) : 0, live);
     if (live) {
       pos2[o] = pos[i];
       mom2[o] = M;
@@ -353,8 +377,14 @@ int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
     g.n[k] = c->grid.n[k];
     g.nb[k] = c->nb[k];
   }
-  g.ens_shift = c->key_ensembles ? 64 - c->par.ens_bits : 64;
   g.nkeys = c->nblk;
+  g.nsub_key = c->key_ensembles;
+  g.ens_shift = c->par.ens_bits > 0 ? 64 - c->par.ens_bits : 64;
+  g.n_ens = c->n_ens;
+  g.ens_h = c->d_ens_h;
+  g.dt = (float)c->last_dt;
+  g.kappa = (float)c->par.kappa;
+  g.mass = (sp == kIon || !c->par.emission_on) ? 0.f : (float)c->species.mass[sp];
   const int cur = st.cur, nxt = cur ^ 1;
   unsigned *start = c->d_blk_start + (size_t)sp * (c->nblk + 1);
   if (cudaMemsetAsync(c->d_blk_cursor, 0, sizeof(unsigned) * (c->nblk + 1), s) != cudaSuccess) return QED_ERR_CUDA;
@@ -422,6 +452,8 @@ __device__ __forceinline__ bool thin_survives(uint64_t id, const ThinArgs &t, lo
   return u < (double)L / (double)N;
 }
 
+constexpr int kThinShared = 2048;   // groups accumulated in shared memory first
+
 // Lanes with the same group add their values with one atomic per group.
 __device__ __forceinline__ void group_add(int g, bool on, double w, unsigned long long *n, double *wsum) {
   const unsigned mask = __ballot_sync(0xffffffffu, on);
@@ -436,9 +468,35 @@ __device__ __forceinline__ void group_add(int g, bool on, double w, unsigned lon
   }
 }
 
+// Per-block partial sums in shared memory (up to kThinShared groups), then
+// one global atomic per non-empty group and block.
+struct ThinShared {
+  unsigned long long n[kThinShared];
+  double w[kThinShared];
+};
+
+__device__ __forceinline__ void thin_shared_zero(ThinShared &sh, int groups) {
+  for (int k = threadIdx.x; k < groups; k += blockDim.x) {
+    sh.n[k] = 0;
+    sh.w[k] = 0.0;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void thin_shared_flush(ThinShared &sh, int groups, unsigned long long *n, double *w) {
+  __syncthreads();
+  for (int k = threadIdx.x; k < groups; k += blockDim.x) {
+    if (n && sh.n[k]) atomicAdd(n + k, sh.n[k]);
+    if (sh.w[k] != 0.0) atomicAdd(w + k, sh.w[k]);
+  }
+}
+
 template <typename T>
 __global__ void k_thin_count(const T *pos, const T *mom, const uint64_t *id, const long long *count, int sp,
                              long long cap, ThinArgs t) {
+  __shared__ ThinShared sh;
+  const bool priv = t.groups <= kThinShared;
+  if (priv) thin_shared_zero(sh, t.groups);
   const long long n = min(count[sp], cap);
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -449,13 +507,24 @@ __global__ void k_thin_count(const T *pos, const T *mom, const uint64_t *id, con
       g = group_of(id[i], t);
       w = weight_of(pos[i]);
     }
-    group_add(g, g >= 0, w, t.n, t.w);
+    if (priv) {
+      if (g >= 0) {
+        atomicAdd(&sh.n[g], 1ull);
+        atomicAdd(&sh.w[g], w);
+      }
+    } else {
+      group_add(g, g >= 0, w, t.n, t.w);
+    }
   }
+  if (priv) thin_shared_flush(sh, t.groups, t.n, t.w);
 }
 
 template <typename T>
 __global__ void k_thin_mark(const T *pos, const T *mom, const uint64_t *id, const long long *count, int sp,
                             long long cap, ThinArgs t) {
+  __shared__ ThinShared sh;
+  const bool priv = t.groups <= kThinShared;
+  if (priv) thin_shared_zero(sh, t.groups);
   const long long n = min(count[sp], cap);
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -472,8 +541,13 @@ __global__ void k_thin_mark(const T *pos, const T *mom, const uint64_t *id, cons
         else g = -1;
       }
     }
-    group_add(g, g >= 0, w, nullptr, t.wsurv);
+    if (priv) {
+      if (g >= 0) atomicAdd(&sh.w[g], w);
+    } else {
+      group_add(g, g >= 0, w, nullptr, t.wsurv);
+    }
   }
+  if (priv) thin_shared_flush(sh, t.groups, nullptr, t.wsurv);
 }
 
 template <typename T>
