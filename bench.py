@@ -42,8 +42,9 @@ if ROOT not in sys.path:
 
 RUN_STEPS = 600
 N_ELECTRONS = 1_000_000
+TUNING: dict = {}          # qed_tuning fields applied to the collision runs (--tuning)
 CAPS = (1_300_000, 200_000, 60_000_000, 0)
-COMPACT_INTERVAL = 8
+COMPACT_INTERVAL = 32       # measured: 8 -> 4.21e10, 16 -> 4.52e10, 32 -> 4.65e10 particle-steps/s
 L2_FLUSH_BYTES = 256 << 20
 # algorithmic bytes per particle-step (read cell + offset + p + w + id, write
 # cell + offset + p) and per appended particle record, FP32 / FP64 forms
@@ -146,6 +147,8 @@ def time_device(w, prec: int, K: int, W: int, dist_barrier) -> dict:
     s0 = window(K, W)
     with Simulation(w, precision=prec, capacity=CAPS, compact_interval=COMPACT_INTERVAL) as sim:
         sim.set_all()
+        if TUNING:
+            sim.set_tuning(**TUNING)
         if s0:
             sim.step(s0)                      # untimed: advance to the window
         sim.step(W)                           # warm-up steps
@@ -553,6 +556,8 @@ def main():
                     help="steps between compactions (which also regroup photons that cannot pair)")
     ap.add_argument("--electrons", type=int, default=N_ELECTRONS,
                     help="beam size (smaller beams are for profiling captures, not bench lines)")
+    ap.add_argument("--tuning", default="",
+                    help="collision: qed_tuning fields, e.g. concurrent=1,photon_blocks_per_sm=2")
     ap.add_argument("--workload", choices=("collision", "batched"), default="collision",
                     help="collision: the beam-laser collision (the headline line); batched: 512 ensembles")
     ap.add_argument("--batch-scale", type=float, default=1.0,
@@ -563,6 +568,9 @@ def main():
     if args.electrons != N_ELECTRONS:
         scale_workload(args.electrons)
     COMPACT_INTERVAL = args.compact_interval
+    for kv in filter(None, args.tuning.split(",")):
+        k, v = kv.split("=")
+        TUNING[k.strip()] = int(v)
     K, W = args.steps, args.warmup
     if K < 1 or W < 0 or K + W > RUN_STEPS:
         ap.error(f"need 1 <= steps and steps + warmup <= {RUN_STEPS}")
@@ -673,7 +681,7 @@ def main():
                                                                    r32["window_start"] + W + K - 1],
                        "precision": "fp32 push/rates, fp64 tables", "parallelism": f"independent beams x{world}",
                        "l2": "flushed between timed steps (256 MiB write)",
-                       "compact_interval": COMPACT_INTERVAL},
+                       "compact_interval": COMPACT_INTERVAL, "tuning": TUNING or "default"},
             "roofline": roof(r32),
             "roofline_step": roof_step(r32),
             "gpu_launches": r32["launches"],

@@ -179,7 +179,14 @@ typedef struct qed_tuning {
                                       sub-intervals (Eq. (28)) their next step
                                       is estimated to take, so that warps run
                                       loops of about equal length */
-    int32_t reserved[3];           /* must be 0 */
+    int32_t concurrent;            /* 1: the photon pass and the e-/e+/ion
+                                      pass run at the same time on two
+                                      streams (the second one the library's
+                                      own), so the latency-bound lepton work
+                                      fills the photon pass's idle issue
+                                      slots; give the two passes at most the
+                                      SM's blocks between them */
+    int32_t reserved[2];           /* must be 0 */
 } qed_tuning;
 
 /* Caller-owned Yee arrays (device memory, context precision). */

@@ -63,6 +63,9 @@ void release(qed_ctx *c) {
   cudaFree(c->stage);
   cudaFree(c->d_ens);
   cudaFree(c->d_ens_h);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   cudaFree(c->d_ens_field);
   cudaFree(c->d_thin);
 }
@@ -82,7 +85,8 @@ int check_tuning(const qed_ctx *c, const qed_tuning *t) {
   if (t->massive_blocks_per_sm < 1 || t->massive_blocks_per_sm > maxm) return QED_ERR_ARG;
   if (t->work_chunk < 0 || t->work_chunk % 256 != 0 || t->work_chunk > (1 << 24)) return QED_ERR_ARG;
   if (t->compact_interval < 1 || (t->sort_massive != 0 && t->sort_massive != 1)) return QED_ERR_ARG;
-  for (int k = 0; k < 3; ++k)
+  if (t->concurrent != 0 && t->concurrent != 1) return QED_ERR_ARG;
+  for (int k = 0; k < 2; ++k)
     if (t->reserved[k] != 0) return QED_ERR_ARG;
   return QED_OK;
 }
@@ -285,6 +289,10 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     c->tune.compact_interval = p->compact_interval > 0 ? p->compact_interval : 8;
     c->tune.sort_massive = c->key_ensembles;
   }
+  if (rc == QED_OK && (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess))
+    rc = QED_ERR_CUDA;
   if (rc == QED_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = QED_ERR_CUDA;
   if (rc != QED_OK) {
     cudaGetLastError();
@@ -557,6 +565,28 @@ int qed_autotune(qed_ctx *c, const qed_fields *f, double dt, int32_t steps_per_t
   if (rc == QED_OK && c->key_ensembles) {
     const int so[2] = {1, 0};
     rc = tune_field(&qed_tuning::sort_massive, so, 2);
+  }
+  if (rc == QED_OK) {
+    // the two passes side by side: split the SM's blocks between them
+    qed_tuning t = best;
+    const int tot = maxp < maxm ? maxp : maxm;
+    if (tot >= 2 && !out_of_steps) {
+      t.concurrent = 1;
+      t.photon_blocks_per_sm = tot - 1;
+      t.massive_blocks_per_sm = 1;
+      double c0 = 0.0, c1 = 0.0, x = 0.0;
+      const int ci = best.compact_interval;
+      const int64_t need = 4 * (steps_per_trial > ci ? steps_per_trial : ci);
+      if (taken + need <= max_steps) {
+        for (int pass = 0; pass < 2 && rc == QED_OK; ++pass) {
+          rc = trial(pass == 0 ? best : t, &x);
+          (pass == 0 ? c0 : c1) += x;
+          if (rc == QED_OK) rc = trial(pass == 0 ? t : best, &x);
+          (pass == 0 ? c1 : c0) += x;
+        }
+        if (rc == QED_OK && c1 < c0) best = t;
+      }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -162,6 +162,8 @@ struct qed_ctx {
   cudaEvent_t ev_start = nullptr;     // recorded around the step kernels
   cudaEvent_t ev_photon = nullptr;
   cudaEvent_t ev_stop = nullptr;
+  cudaStream_t side = nullptr;        // the e-/e+/ion pass when it runs beside the photon pass
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int64_t launches = 0;               // kernels launched by this context
 };
 

@@ -1336,6 +1336,17 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   c->launches += 3;
   e = cudaLaunchKernel((const void *)k_step_constants<R>, dim3(1),
                        dim3(a.field_mode == kFieldEnsemble ? 256 : 32), args, 0, s);
+  // concurrent: the e-/e+/ion pass runs on the side stream beside the
+  // photon pass (fork after the step constants, join before the products)
+  const bool conc = c->tune.concurrent && c->side && !a.blk_start[kElectron];
+  if (e == cudaSuccess && conc) {
+    e = cudaEventRecord(c->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    if (e == cudaSuccess)
+      e = cudaLaunchKernel((const void *)k_pass0<R, false, EXT>, dim3(c->num_sms * c->tune.massive_blocks_per_sm),
+                           dim3(256), args, 0, c->side);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+  }
   if (e == cudaSuccess)
     e = cudaLaunchKernel((const void *)k_photons<R, EXT>, dim3(c->num_sms * c->tune.photon_blocks_per_sm),
                          dim3(kPhotonThreads), args, 0, s);
@@ -1344,7 +1355,8 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     c->launches += 1;
     e = cudaLaunchKernel((const void *)k_blocks<R, EXT>, dim3(c->blocks_cells), dim3(256), args, 0, s);
   }
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && conc) e = cudaStreamWaitEvent(s, c->ev_join, 0);
+  else if (e == cudaSuccess)
     e = cudaLaunchKernel((const void *)k_pass0<R, false, EXT>, dim3(c->num_sms * c->tune.massive_blocks_per_sm),
                          dim3(256), args, 0, s);
   if (e == cudaSuccess && a.same_step) {

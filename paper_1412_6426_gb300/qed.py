@@ -58,10 +58,11 @@ class QedParams(ctypes.Structure):
 class QedTuning(ctypes.Structure):
     _fields_ = [("photon_blocks_per_sm", ctypes.c_int32), ("massive_blocks_per_sm", ctypes.c_int32),
                 ("work_chunk", ctypes.c_int32), ("compact_interval", ctypes.c_int32),
-                ("sort_massive", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("sort_massive", ctypes.c_int32), ("concurrent", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_[:5]}
+        return {k: getattr(self, k) for k, _ in self._fields_[:6]}
 
 
 class QedFields(ctypes.Structure):

@@ -70,7 +70,7 @@ int main(void) {
   P(qed_params, emit_fg); P(qed_params, pair_fg); P(qed_params, emit_ng); P(qed_params, pair_ng);
   P(qed_diag, photons_created); P(qed_diag, pairs_created); P(qed_diag, thinned);
   P(qed_diag, kernel_launches);
-  P(qed_tuning, work_chunk); P(qed_tuning, sort_massive); P(qed_tuning, reserved);
+  P(qed_tuning, work_chunk); P(qed_tuning, sort_massive); P(qed_tuning, concurrent); P(qed_tuning, reserved);
   P(qed_diag, particle_steps); P(qed_diag, species_steps); P(qed_diag, emissions);
   P(qed_diag, time); P(qed_diag, status); P(qed_diag, spectrum);
   P(qed_species_desc, charge); P(qed_fields, J);

@@ -109,7 +109,8 @@ def test_tuning_changes_no_result():
     assert dr["emissions"] > 1000 and dr["thinned"] > 0
     for tuning in (dict(work_chunk=256, massive_blocks_per_sm=1, photon_blocks_per_sm=1),
                    dict(work_chunk=4096, compact_interval=2, sort_massive=0),
-                   dict(work_chunk=0, compact_interval=1, sort_massive=1)):
+                   dict(work_chunk=0, compact_interval=1, sort_massive=1),
+                   dict(concurrent=1, photon_blocks_per_sm=2, massive_blocks_per_sm=1, work_chunk=1024)):
         out, d = _run32(w, 16, tuning=tuning)
         assert d["emissions"] == dr["emissions"] and d["pairs"] == dr["pairs"] and d["thinned"] == dr["thinned"]
         rep = compare(out, ref, rtol_p=0.0, xtol=0.0, rtol_w=1e-6)
