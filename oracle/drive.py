@@ -17,7 +17,7 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
         t0: float = 0.0, fields=None, J=None, deposit_on: int = 0, yee: bool = False,
         ion_charge: float = 1.0, ion_mass: float = 1836.15267343, time_from: int = 0,
         ens_bits: int = 0, ens=None, emit_fg: float = 1.0, emit_ng: int = 1, pair_fg: float = 1.0,
-        pair_ng: int = 1, thin_interval: int = 0, thin_limit=(0, 0, 0, 0)):
+        pair_ng: int = 1, thin_interval: int = 0, thin_limit=(0, 0, 0, 0), generator: int = 0):
     """Advance the given particles by nsteps steps of dt.
 
     particles: {species: (x[n,3], p[n,3], w[n], id[n])}.  Returns
@@ -34,7 +34,8 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
                       same_step_children=same_step_children, deposit_on=deposit_on, seed=seed,
                       lg_lo=lg_lo, lg_hi=lg_hi, ion_charge=ion_charge, ion_mass=ion_mass,
                       ens_bits=ens_bits, ens=ens, emit_fg=emit_fg, emit_ng=emit_ng, pair_fg=pair_fg,
-                      pair_ng=pair_ng, thin_interval=thin_interval, thin_limit=thin_limit)
+                      pair_ng=pair_ng, thin_interval=thin_interval, thin_limit=thin_limit,
+                      generator=generator)
     if caps is None:
         base = sum(len(v[3]) for v in particles.values())
         caps = (4 * base + 64,) * 4

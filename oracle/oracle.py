@@ -23,6 +23,7 @@ ELECTRON, POSITRON, PHOTON, ION = 0, 1, 2, 3
 FIELD_GRID, FIELD_UNIFORM, FIELD_GAUSSIAN_LP, FIELD_ROTATING_E, FIELD_ENSEMBLE = 0, 1, 2, 3, 4
 PURPOSE_EMIT, PURPOSE_PAIR, PURPOSE_CHILD, PURPOSE_KEEP, PURPOSE_THIN = 1, 2, 3, 4, 5
 ENS_STRIDE = 10  # per ensemble: E0, omega, phase, Eu[3], Bu[3], thin_scale
+GEN_MODIFIED, GEN_ALTERNATIVE, GEN_STANDARD = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -65,6 +66,8 @@ class Params(ctypes.Structure):
         ("thin_interval", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
         ("thin_limit", ctypes.c_int64 * 4),
+        ("generator", ctypes.c_int32),
+        ("reserved2", ctypes.c_int32),
     ]
 
 
@@ -117,6 +120,11 @@ def lib():
         _lib.or_step.restype = ctypes.c_int
         _lib.or_step.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Store), ctypes.POINTER(Diag),
                                  ctypes.POINTER(pd), ctypes.POINTER(pd), u32, d, d]
+        _lib.or_Wnorm.restype = d; _lib.or_Wnorm.argtypes = [d, d]
+        _lib.or_Pstd.restype = d; _lib.or_Pstd.argtypes = [d, d, d]
+        _lib.or_delta_std.restype = d; _lib.or_delta_std.argtypes = [d, d]
+        _lib.or_sample_frozen_gen.restype = i64
+        _lib.or_sample_frozen_gen.argtypes = [i32, d, d, d, i64, u32, d, d, i32, pd, ctypes.POINTER(i64)]
         _lib.or_field_ensemble.argtypes = [ctypes.POINTER(Params), u64, d, pd, pd]
         _lib.or_thin.restype = ctypes.c_int
         _lib.or_thin.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Store), ctypes.POINTER(Diag), u32]
@@ -245,6 +253,26 @@ def sample_frozen(chi_, gamma, h, ndraw, seed, lo, hi, nbins):
     return acc, hist, viol.value
 
 
+def sample_frozen_gen(generator, chi_, gamma, h, ndraw, seed, lo, hi, nbins):
+    hist = np.zeros(nbins)
+    viol = ctypes.c_int64(0)
+    acc = lib().or_sample_frozen_gen(int(generator), float(chi_), float(gamma), float(h), int(ndraw), int(seed),
+                                     float(lo), float(hi), int(nbins), _dp(hist), ctypes.byref(viol))
+    return acc, hist, viol.value
+
+
+def Wnorm(x, chi_):
+    return lib().or_Wnorm(float(x), float(chi_))
+
+
+def Pstd(chi_, gamma, dt):
+    return lib().or_Pstd(float(chi_), float(gamma), float(dt))
+
+
+def delta_std(chi_, r2):
+    return lib().or_delta_std(float(chi_), float(r2))
+
+
 # ---- Yee mesh, gather, deposit -------------------------------------------
 
 def yee_step(n, d, dt, f, J):
@@ -366,7 +394,7 @@ def make_params(*, n=(1, 1, 1), d=(1.0, 1.0, 1.0), x0=(0.0, 0.0, 0.0), periodic=
                 pairs_on=1, same_step_children=1, deposit_on=0, seed=1, lg_lo=-12.0,
                 lg_hi=0.0, ion_charge=1.0, ion_mass=1836.15267343, ens_bits=0, ens=None,
                 emit_fg=1.0, emit_ng=1, pair_fg=1.0, pair_ng=1, thin_interval=0,
-                thin_limit=(0, 0, 0, 0)) -> Params:
+                thin_limit=(0, 0, 0, 0), generator=0) -> Params:
     """Oracle parameters.  ens: (n_ens, ENS_STRIDE) float64 table of the
     ensemble fields (field_mode FIELD_ENSEMBLE); the returned Params keeps a
     reference to it."""
@@ -398,6 +426,7 @@ def make_params(*, n=(1, 1, 1), d=(1.0, 1.0, 1.0), x0=(0.0, 0.0, 0.0), periodic=
     P.emit_ng, P.pair_ng = int(emit_ng), int(pair_ng)
     P.thin_interval = int(thin_interval)
     P.thin_limit[:] = [int(v) for v in thin_limit]
+    P.generator = int(generator)
     return P
 
 

@@ -44,6 +44,10 @@
  *                   weight and spectrum unbiased (Sec. VI)
  *   thinning        total weight of each group conserved; groups at or
  *                   below the limit untouched; survivors binomial
+ *   generators      standard (inverse transform): W(x)/W(1) against scipy's
+ *                   K-function quadrature, total W(1) against the number
+ *                   rate; alternative: P(delta) against Eq. (24); the three
+ *                   generators' frozen spectra (the paper's Fig. "generators")
  *   parity unpinned: the absolute output of Philox4x32-10 (no published
  *                   known-answer vectors are available here; uniformity and
  *                   decorrelation of the draws are checked statistically).
@@ -62,6 +66,8 @@ enum { OR_PURPOSE_EMIT = 1, OR_PURPOSE_PAIR = 2, OR_PURPOSE_CHILD = 3, OR_PURPOS
 enum { OR_FIELD_GRID = 0, OR_FIELD_UNIFORM = 1, OR_FIELD_GAUSSIAN_LP = 2, OR_FIELD_ROTATING_E = 3,
        OR_FIELD_ENSEMBLE = 4 };
 #define OR_ENS_STRIDE 10  /* per ensemble: E0, omega, phase, Eu[3], Bu[3], thin_scale */
+/* photon-emission event generators of Sec. IV.F-G */
+enum { OR_GEN_MODIFIED = 0, OR_GEN_ALTERNATIVE = 1, OR_GEN_STANDARD = 2 };
 
 /* ------------------------------------------------------------------------ */
 /* Synchrotron functions (Sec. IV.E, below Eq. (20) and Eq. (21)):
@@ -185,6 +191,81 @@ double or_Pm(double r1, double chi, double gamma, double dt)
 {
     double delta = r1 * r1 * r1;
     return 3.0 * r1 * r1 * or_P(delta, chi, gamma, dt);
+}
+
+/* The standard event generator (Sec. IV.F): in an interval dt a photon is
+ * emitted when r1 < P = W(1), and its energy delta is the root of
+ * W(delta)/W(1) = r2, with
+ *   W(x) = dt int_{delta_min}^{x} P(delta)/dt d(delta),
+ * the emission probability density P of Eq. (24).  delta_min -> 0: the
+ * integrand is integrable (~ delta^{-2/3}) and, written in s = delta^{1/3},
+ *   W(x) = int_0^{x^{1/3}} 3 s^2 P(s^3) ds,
+ * it is finite at s = 0.  The integrals are 8-point Gauss-Legendre over
+ * panels of width 1/256 in s (the integrand is smooth in s); the root is
+ * found by bisection on s, integrating panel by panel. */
+static const double or_gl8_x[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290,
+                                   -0.1834346424956498, 0.1834346424956498, 0.5255324099163290,
+                                   0.7966664774136267, 0.9602898564975363};
+static const double or_gl8_w[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873,
+                                   0.3626837833783620, 0.3626837833783620, 0.3137066458778873,
+                                   0.2223810344533745, 0.1012285362903763};
+
+/* int_a^b 3 s^2 G(s^3, chi) ds, Gauss-Legendre on [a, b] */
+static double or_W_piece(double a, double b, double chi)
+{
+    double m = 0.5 * (a + b), r = 0.5 * (b - a), acc = 0.0;
+    for (int k = 0; k < 8; ++k) {
+        double s = m + r * or_gl8_x[k];
+        acc += or_gl8_w[k] * 3.0 * s * s * or_G(s * s * s, chi);
+    }
+    return r * acc;
+}
+
+#define OR_W_PANELS 256
+/* W(x)/(alpha dt/gamma) = int_0^{x^{1/3}} 3 s^2 G(s^3, chi) ds */
+double or_Wnorm(double x, double chi)
+{
+    if (!(x > 0.0) || !(chi > 0.0)) return 0.0;
+    if (x > 1.0) x = 1.0;
+    double sx = cbrt(x), acc = 0.0;
+    for (int k = 0; k < OR_W_PANELS; ++k) {
+        double a = (double)k / OR_W_PANELS, b = (double)(k + 1) / OR_W_PANELS;
+        if (a >= sx) break;
+        acc += or_W_piece(a, b < sx ? b : sx, chi);
+    }
+    return acc;
+}
+
+/* Total probability of the standard generator in an interval dt: W(1). */
+double or_Pstd(double chi, double gamma, double dt)
+{
+    return OR_ALPHA * dt / gamma * or_Wnorm(1.0, chi);
+}
+
+/* Photon energy of the standard generator: the root delta of
+ * W(delta) / W(1) = r2 (inverse transform sampling). */
+double or_delta_std(double chi, double r2)
+{
+    /* the panel integrals depend on chi only: kept for the latest chi */
+    static double panel[OR_W_PANELS], total = 0.0, last_chi = -1.0;
+    if (chi != last_chi) {
+        total = 0.0;
+        for (int k = 0; k < OR_W_PANELS; ++k) {
+            panel[k] = or_W_piece((double)k / OR_W_PANELS, (double)(k + 1) / OR_W_PANELS, chi);
+            total += panel[k];
+        }
+        last_chi = chi;
+    }
+    double target = r2 * total, below = 0.0;
+    int k = 0;
+    while (k < OR_W_PANELS - 1 && below + panel[k] < target) below += panel[k++];
+    double a = (double)k / OR_W_PANELS, b = (double)(k + 1) / OR_W_PANELS;
+    for (int it = 0; it < 200 && b - a > 1e-16; ++it) {
+        double m = 0.5 * (a + b);
+        if (below + or_W_piece((double)k / OR_W_PANELS, m, chi) < target) a = m; else b = m;
+    }
+    double sr = 0.5 * (a + b);
+    return sr * sr * sr;
 }
 
 /* Pair-production density, Eq. (30), as printed:
@@ -556,6 +637,8 @@ typedef struct {
     int32_t thin_interval;   /* thin after every step s with (s+1) % interval == 0 */
     int32_t reserved;
     int64_t thin_limit[4];   /* per species: most particles a group keeps (0 = off) */
+    int32_t generator;       /* OR_GEN_*: modified (default), alternative, standard */
+    int32_t reserved2;
 } or_params;
 
 typedef struct {
@@ -725,6 +808,39 @@ static void or_process(or_ctx *C, int sp, or_particle *q, double t_span,
             double chi = or_chi(q->p, E, B);
             double r1, r2;
             or_draw(q->id, C->step, (uint32_t)s, OR_PURPOSE_EMIT, P->seed, &r1, &r2);
+            if (P->generator == OR_GEN_ALTERNATIVE || P->generator == OR_GEN_STANDARD) {
+                /* the unmodified generators of Sec. IV.F */
+                double delta, pe;
+                int fire;
+                if (P->generator == OR_GEN_ALTERNATIVE) {
+                    delta = r1;                          /* r2 < P(r1), delta = r1 */
+                    pe = or_P(r1, chi, g, h);
+                    fire = r2 < pe;
+                } else {
+                    pe = or_Pstd(chi, g, h);             /* r1 < W(1), W(delta)/W(1) = r2 */
+                    fire = r1 < pe;
+                    delta = fire ? or_delta_std(chi, r2) : 0.0;
+                }
+                if (pe > 1.0) C->D->pm_gt1++;
+                if (fire) {
+                    double p0[3] = {q->p[0], q->p[1], q->p[2]};
+                    or_particle ph;
+                    for (int c = 0; c < 3; ++c) { ph.x[c] = q->x[c]; ph.p[c] = delta * p0[c]; }
+                    ph.w = q->w;
+                    ph.id = or_product_id(P, q->id, C->step, (uint32_t)s, OR_PHOTON);
+                    ph.alive = 1;
+                    double e_before = sqrt(m * m + p0[0] * p0[0] + p0[1] * p0[1] + p0[2] * p0[2]);
+                    for (int c = 0; c < 3; ++c) q->p[c] = (1.0 - delta) * p0[c];
+                    C->D->emissions++;
+                    C->D->photons_created++;
+                    double eps = sqrt(ph.p[0] * ph.p[0] + ph.p[1] * ph.p[1] + ph.p[2] * ph.p[2]);
+                    double e_after = sqrt(m * m + q->p[0] * q->p[0] + q->p[1] * q->p[1] + q->p[2] * q->p[2]);
+                    C->D->energy_defect += q->w * (e_before - e_after - eps);
+                    or_spectrum_add(C, delta, eps, ph.w);
+                    or_emit_child(C, OR_PHOTON, &ph, (double)(n - 1 - s) * h, E, B);
+                }
+                continue;
+            }
             double pm = or_Pm(r1, chi, g, h);
             if (pm > 1.0) C->D->pm_gt1++;
             /* Products (Sec. VI): N_g samples of the generator, sample 0 being
@@ -987,6 +1103,44 @@ int64_t or_sample_frozen(double chi, double gamma, double h, int64_t ndraw, uint
         }
     }
     if (pm_gt1) *pm_gt1 = viol;
+    return acc;
+}
+
+/* The same frozen-particle test for any of the three generators of
+ * Sec. IV.F-G (the paper's Fig. "generators"): modified (P_m, delta =
+ * r1^3), alternative (P(r1), delta = r1) or standard (W(1), delta from
+ * W(delta)/W(1) = r2).  P > 1 draws are counted in *p_gt1. */
+int64_t or_sample_frozen_gen(int32_t generator, double chi, double gamma, double h, int64_t ndraw,
+                             uint32_t seed, double lo, double hi, int32_t nbins, double *hist,
+                             int64_t *p_gt1)
+{
+    int64_t acc = 0, viol = 0;
+    double pstd = generator == OR_GEN_STANDARD ? or_Pstd(chi, gamma, h) : 0.0;
+    for (int64_t i = 0; i < ndraw; ++i) {
+        double r1, r2, delta = 0.0, pe;
+        int fire;
+        or_draw((uint64_t)i, 0u, 0u, OR_PURPOSE_EMIT, seed, &r1, &r2);
+        if (generator == OR_GEN_ALTERNATIVE) {
+            pe = or_P(r1, chi, gamma, h);
+            fire = r2 < pe;
+            delta = r1;
+        } else if (generator == OR_GEN_STANDARD) {
+            pe = pstd;
+            fire = r1 < pe;
+            if (fire) delta = or_delta_std(chi, r2);
+        } else {
+            pe = or_Pm(r1, chi, gamma, h);
+            fire = r2 < pe;
+            delta = r1 * r1 * r1;
+        }
+        if (pe > 1.0) ++viol;
+        if (fire) {
+            ++acc;
+            double a = (log10(delta) - lo) / (hi - lo) * nbins;
+            if (a >= 0.0 && a < nbins) hist[(long)a] += 1.0;
+        }
+    }
+    if (p_gt1) *p_gt1 = viol;
     return acc;
 }
 
