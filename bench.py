@@ -43,6 +43,7 @@ if ROOT not in sys.path:
 RUN_STEPS = 600
 N_ELECTRONS = 1_000_000
 TUNING: dict = {}          # qed_tuning fields applied to the collision runs (--tuning)
+GENERATOR = 0              # photon-emission generator: 0 modified, 1 alternative, 2 standard
 CAPS = (1_300_000, 200_000, 60_000_000, 0)
 COMPACT_INTERVAL = 32       # measured: 8 -> 4.21e10, 16 -> 4.52e10, 32 -> 4.65e10 particle-steps/s
 L2_FLUSH_BYTES = 256 << 20
@@ -145,7 +146,8 @@ def time_device(w, prec: int, K: int, W: int, dist_barrier) -> dict:
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     s0 = window(K, W)
-    with Simulation(w, precision=prec, capacity=CAPS, compact_interval=COMPACT_INTERVAL) as sim:
+    with Simulation(w, precision=prec, capacity=CAPS, compact_interval=COMPACT_INTERVAL,
+                    generator=GENERATOR) as sim:
         sim.set_all()
         if TUNING:
             sim.set_tuning(**TUNING)
@@ -542,7 +544,7 @@ def main_batched(args, world, rank, local):
 
 # ----------------------------------------------------------------------------
 def main():
-    global COMPACT_INTERVAL, BATCH_SCALE, BATCH_STEPS, BATCH_AUTOTUNE
+    global COMPACT_INTERVAL, BATCH_SCALE, BATCH_STEPS, BATCH_AUTOTUNE, GENERATOR
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=RUN_STEPS - 3)
@@ -556,6 +558,8 @@ def main():
                     help="steps between compactions (which also regroup photons that cannot pair)")
     ap.add_argument("--electrons", type=int, default=N_ELECTRONS,
                     help="beam size (smaller beams are for profiling captures, not bench lines)")
+    ap.add_argument("--generator", type=int, default=0, choices=(0, 1, 2),
+                    help="collision: emission generator (0 modified, 1 alternative, 2 standard)")
     ap.add_argument("--tuning", default="",
                     help="collision: qed_tuning fields, e.g. concurrent=1,photon_blocks_per_sm=2")
     ap.add_argument("--workload", choices=("collision", "batched"), default="collision",
@@ -568,6 +572,7 @@ def main():
     if args.electrons != N_ELECTRONS:
         scale_workload(args.electrons)
     COMPACT_INTERVAL = args.compact_interval
+    GENERATOR = args.generator
     for kv in filter(None, args.tuning.split(",")):
         k, v = kv.split("=")
         TUNING[k.strip()] = int(v)
@@ -681,7 +686,8 @@ def main():
                                                                    r32["window_start"] + W + K - 1],
                        "precision": "fp32 push/rates, fp64 tables", "parallelism": f"independent beams x{world}",
                        "l2": "flushed between timed steps (256 MiB write)",
-                       "compact_interval": COMPACT_INTERVAL, "tuning": TUNING or "default"},
+                       "compact_interval": COMPACT_INTERVAL, "tuning": TUNING or "default",
+                       "generator": ("modified", "alternative", "standard")[GENERATOR]},
             "roofline": roof(r32),
             "roofline_step": roof_step(r32),
             "gpu_launches": r32["launches"],

@@ -160,7 +160,25 @@ typedef struct qed_params {
     int32_t emit_ng, pair_ng;   /* N_g samples of the generator per occasion
                                    for the products (values <= 1 mean 1),
                                    weight x 1/N_g; sample 0 is the parent's */
+    /* --- the photon-emission event generator (Sec. IV.F-G) --- */
+    int32_t generator;          /* qed_generator; the generator factors above
+                                   apply to the modified generator only */
+    int32_t reserved_gen;       /* must be 0 */
 } qed_params;
+
+typedef enum qed_generator {
+    /* modified event generator, Eq. (25) with f_m = r1^3 (the default):
+     * emit delta = r1^3 when r2 < P_m(r1) */
+    QED_GEN_MODIFIED = 0,
+    /* alternative event generator (Sec. IV.F): emit delta = r1 when
+     * r2 < P(r1); under-samples low energies where P > 1 */
+    QED_GEN_ALTERNATIVE = 1,
+    /* standard event generator (Sec. IV.F) with delta_min -> 0: emit when
+     * r1 < W(1), delta the root of W(delta)/W(1) = r2, from inverse-CDF
+     * tables built in FP64 at init (chi 1e-6 .. 1e4, 4097 x 1025 values;
+     * relative accuracy of delta about 1e-5) */
+    QED_GEN_STANDARD = 2
+} qed_generator;
 
 /* Launch shapes and schedules; they change the speed, never the results
  * (every particle's random stream is keyed by its id). */

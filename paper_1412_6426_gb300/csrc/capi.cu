@@ -63,6 +63,8 @@ void release(qed_ctx *c) {
   cudaFree(c->stage);
   cudaFree(c->d_ens);
   cudaFree(c->d_ens_h);
+  cudaFree(c->d_std_cdf);
+  cudaFree(c->d_std_lnw);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -173,6 +175,8 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
   if (p->ens_bits < 0 || p->ens_bits > QED_MAX_ENS_BITS || p->thin_interval < 0) return QED_ERR_ARG;
   if (!std::isfinite(p->emit_fg) || !std::isfinite(p->pair_fg) || p->emit_ng > 64 || p->pair_ng > 64)
     return QED_ERR_ARG;
+  if (p->generator < QED_GEN_MODIFIED || p->generator > QED_GEN_STANDARD || p->reserved_gen != 0) return QED_ERR_ARG;
+  if (p->generator != QED_GEN_MODIFIED && (p->emit_fg > 1.0 || p->emit_ng > 1)) return QED_ERR_ARG;
   bool thinning = false;
   for (int k = 0; k < 4; ++k) {
     if (p->thin_limit[k] < 0) return QED_ERR_ARG;
@@ -194,7 +198,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
   c->species = *sp;
   c->par = *p;
   c->ext = g->field_mode == QED_FIELD_ENSEMBLE || p->emit_fg > 1.0 || p->pair_fg > 1.0 || p->emit_ng > 1 ||
-           p->pair_ng > 1;
+           p->pair_ng > 1 || p->generator != QED_GEN_MODIFIED;
   cudaStream_t s = as_stream(stream);
   int rc = QED_OK;
   cudaDeviceProp prop;
@@ -251,6 +255,11 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     c->thin_groups = p->ens_bits > 0 ? (1 << p->ens_bits) : 1;
     if (rc == QED_OK) rc = dalloc(&c->d_thin, (size_t)24 * c->thin_groups);
   }
+  if (p->generator == QED_GEN_STANDARD) {
+    const size_t r = c->prec == 64 ? sizeof(double) : sizeof(float);
+    if (rc == QED_OK) rc = dalloc(&c->d_std_cdf, r * qed::kStdRows * qed::kStdCols);
+    if (rc == QED_OK) rc = dalloc(&c->d_std_lnw, r * qed::kStdRows);
+  }
   if (rc == QED_OK) rc = dalloc(&c->d_counters, sizeof(unsigned long long) * qed::kNumCounters);
   if (rc == QED_OK) rc = dalloc(&c->d_spec, sizeof(double) * (p->nbins > 0 ? p->nbins : 1));
   if (rc == QED_OK) rc = dalloc(&c->d_spec_e, sizeof(double) * (p->nbins > 0 ? p->nbins : 1));
@@ -278,6 +287,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     else
       rc = qed_build_tables(c, s);
   }
+  if (rc == QED_OK && p->generator == QED_GEN_STANDARD) rc = qed_build_standard_tables(c, s);
   if (rc == QED_OK) rc = qed_launch_chi_star(c, s);
   if (rc == QED_OK) rc = qed_step_kernel_blocks(c);
   if (rc == QED_OK) {

@@ -59,6 +59,8 @@ __device__ __forceinline__ void split_binade(float z, int &e, float &m) {
 
 __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 __device__ __forceinline__ float exp_r(float x) { return __expf(x); }
+__device__ __forceinline__ double log_r(double x) { return log(x); }
+__device__ __forceinline__ float log_r(float x) { return __logf(x); }
 __device__ __forceinline__ double cbrt_r(double x) { return cbrt(x); }
 __device__ __forceinline__ float cbrt_r(float x) { return cbrtf(x); }
 __device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
@@ -243,6 +245,96 @@ __device__ __forceinline__ R prob_emit(const R *__restrict__ T, R r1, R chi, R g
   syn_g(T, z, g1, g2);
   R br = g1 + R(1.5) * chi * delta * z * g2;
   return R(kAlpha) * h / gamma * R(kSqrt3Over2Pi) * chi * omd * R(3) * cbrt_r(c3) * br;
+}
+
+// Alternative event generator (Sec. IV.F): the density P(delta) of Eq. (24)
+// itself at delta = r1,
+//   P = alpha h/gamma sqrt3/(2pi) chi (1-delta)/delta z^{1/3} [g1 + 1.5 chi delta z g2].
+template <typename R>
+__device__ __forceinline__ R prob_alternative(const R *__restrict__ T, R delta, R chi, R gamma, R h) {
+  if (!(chi > R(0)) || !(delta > R(0))) return R(0);
+  R omd = R(1) - delta;
+  if (!(omd > R(0))) return R(0);
+  R z = R(2.0 / 3.0) * delta / (chi * omd);
+  R g1, g2;
+  syn_g(T, z, g1, g2);
+  R br = g1 + R(1.5) * chi * delta * z * g2;
+  return R(kAlpha) * h / gamma * R(kSqrt3Over2Pi) * chi * omd / delta * cbrt_r(z) * br;
+}
+
+// Standard event generator (Sec. IV.F) from tables built in FP64 at init:
+// rows j = 0 .. kStdRows-1 at ln chi_j = kStdLnChiLo + j kStdDLn, each the
+// normalised cumulative W(s^3)/W(1) at s = i/(kStdCols-1) (s = delta^{1/3},
+// so delta_min -> 0 needs no cutoff), and ln W(1) per row.  Interpolation
+// is linear in ln chi and in s.  Below the table, chi < chi_lo, the
+// spectrum depends on delta/chi only and W(1) grows as chi: both are scaled
+// from the first row.  Above it the last row is used.
+constexpr int kStdRows = 4097, kStdCols = 1025;
+constexpr double kStdLnChiLo = -13.815510557964274;   // ln 1e-6
+constexpr double kStdDLn = 23.025850929940457 / 4096; // up to chi = 1e4
+
+template <typename R>
+__device__ __forceinline__ void std_row(R chi, int &j, R &f, R &scale) {
+  R lx = (log_r(chi) - R(kStdLnChiLo)) * R(1.0 / kStdDLn);
+  scale = R(1);
+  if (!(lx >= R(0))) {
+    scale = chi * R(1.0e6);          // chi / chi_lo
+    lx = R(0);
+  }
+  if (lx > R(kStdRows - 1)) lx = R(kStdRows - 1);
+  j = (int)lx;
+  if (j > kStdRows - 2) j = kStdRows - 2;
+  f = lx - R(j);
+}
+
+// Total probability W(1) of an interval h: alpha h/gamma times the table's W.
+template <typename R>
+__device__ __forceinline__ R std_total(const R *__restrict__ lnw, R chi, R gamma, R h) {
+  if (!(chi > R(0))) return R(0);
+  int j;
+  R f, sc;
+  std_row(chi, j, f, sc);
+  const R l = lnw[j] + f * (lnw[j + 1] - lnw[j]);
+  return R(kAlpha) * h / gamma * exp_r(l) * sc;
+}
+
+// Photon energy: the root of W(delta)/W(1) = u.  Bisection over the s grid
+// finds the cell; inside it two Newton steps on
+//   C(s) = C(s_lo) + int_{s_lo}^{s} f(t) dt / W(1),   f(t) = 3 t^2 G(t^3, chi),
+// with the integral by Simpson's rule and f from the synchrotron tables,
+// replace linear interpolation (which is poor where C flattens, delta -> 1).
+template <typename R>
+__device__ __noinline__ R std_delta(const R *__restrict__ T, const R *__restrict__ cdf, const R *__restrict__ lnw,
+                                    R chi, R u) {
+  int j;
+  R f, sc;
+  std_row(chi, j, f, sc);
+  const R *a = cdf + (size_t)j * kStdCols, *b = a + kStdCols;
+  int lo = 0, hi = kStdCols - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    const R c = a[mid] + f * (b[mid] - a[mid]);
+    if (c <= u) lo = mid; else hi = mid;
+  }
+  const R clo = a[lo] + f * (b[lo] - a[lo]), chi_ = a[hi] + f * (b[hi] - a[hi]);
+  const R ds = R(1.0 / (kStdCols - 1));
+  const R slo = R(lo) * ds, shi = R(hi) * ds;
+  R s = slo + (chi_ > clo ? (u - clo) / (chi_ - clo) : R(0)) * ds;
+  // the shape below the table is the first row's (chi_lo)
+  const R chi_e = sc != R(1) ? R(1.0e-6) : chi;
+  const R w1 = exp_r(lnw[j] + f * (lnw[j + 1] - lnw[j]));
+  const R unit = R(1) / R(kAlpha);       // prob_emit(T, t, chi, 1, 1/alpha) = f(t)
+  for (int it = 0; it < 2; ++it) {
+    const R fm = prob_emit(T, R(0.5) * (slo + s), chi_e, R(1), unit);
+    const R fs = prob_emit(T, s, chi_e, R(1), unit);
+    const R f0 = prob_emit(T, slo, chi_e, R(1), unit);
+    const R c = clo + (s - slo) * (f0 + R(4) * fm + fs) * R(1.0 / 6.0) / w1;
+    if (!(fs > R(0))) break;
+    R sn = s - (c - u) * w1 / fs;
+    sn = sn < slo ? slo : (sn > shi ? shi : sn);
+    s = sn;
+  }
+  return s * s * s * sc;
 }
 
 // Pair generator, Eq. (30), with (3/2) chi_g z_p = 1/(de (1-de)):

@@ -70,6 +70,9 @@ template <typename R> struct StepArgs {
   const double *ens_table;  // n_ens x QED_ENS_STRIDE
   R *ens_field;            // n_ens x kEnsFieldStride, written by k_step_constants
   double ens_hmax;         // bound of |E| + |B| over the ensembles
+  // event generator of the emission (Sec. IV.F-G): 0 modified, 1 alternative, 2 standard
+  int generator;
+  const R *std_cdf, *std_lnw;
   // generator factors (Sec. VI): keep = 1/f_g, wf = f_g / N_g
   R emit_keep, emit_wf, pair_keep, pair_wf;
   int emit_ng, pair_ng;
@@ -137,6 +140,8 @@ struct qed_ctx {
   double last_dt = 0.0;               // dt of the latest qed_step (the sort key uses it)
   int ext = 0;                        // ensembles or generator factors: EXT kernels
   void *d_thin = nullptr;             // thinning: per group count, weight, survivors' weight
+  void *d_std_cdf = nullptr;          // standard generator: kStdRows x kStdCols cumulative W
+  void *d_std_lnw = nullptr;          // and ln W(1) per row (context precision)
   int thin_groups = 0;
   qed_tuning tune{};
   unsigned *d_blk_start = nullptr;    // [4][nblk + 1] first record of each cell block
@@ -180,6 +185,7 @@ int qed_launch_sort(qed_ctx *c, int sp, cudaStream_t s);
 int qed_step_kernel_blocks(qed_ctx *c);
 int qed_launch_chi_star(qed_ctx *c, cudaStream_t s);
 int qed_launch_thin(qed_ctx *c, int sp, cudaStream_t s);
+int qed_build_standard_tables(qed_ctx *c, cudaStream_t s);
 int qed_launch_step_ext(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s);
 int qed_step_kernel_blocks_ext(qed_ctx *c);
 int qed_step_kernel_max_blocks_ext(qed_ctx *c, int *photon, int *massive);

@@ -710,6 +710,36 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
     R chi = chi_lepton(q.p, g, E, B);
     R r1, r2;
     draw2(q.id, step, (unsigned)s, kEmit, a.seed, r1, r2);
+    if (EXT && a.generator != 0) {
+      // the unmodified generators of Sec. IV.F
+      R delta, pe;
+      bool fire;
+      if (a.generator == 1) {
+        delta = r1;                                   // r2 < P(r1)
+        pe = prob_alternative(a.tab, r1, chi, g, h);
+        fire = r2 < pe;
+      } else {
+        pe = std_total(a.std_lnw, chi, g, h);        // r1 < W(1), W(delta)/W(1) = r2
+        fire = r1 < pe;
+        delta = fire ? std_delta(a.tab, a.std_cdf, a.std_lnw, chi, r2) : R(0);
+      }
+      if (pe > R(1)) {
+        count_rare(a, kCntPmGt1, 1u);
+        if (a.pm_strict) atomicOr(a.status, kStPmGt1);
+      }
+      if (fire) {
+        Pt<R> ph = q;
+        ph.p = {delta * q.p.x, delta * q.p.y, delta * q.p.z};
+        ph.id = product_id(a, q.id, step, (unsigned)s, kPhoton);
+        const R omd = R(1) - delta;
+        q.p = {omd * q.p.x, omd * q.p.y, omd * q.p.z};
+        cnt.emis++;
+        cnt.made_ph++;
+        spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), q.w);
+        count_outcome(a, emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B));
+      }
+      continue;
+    }
     R pm = prob_emit(a.tab, r1, chi, g, h);
     if (pm > R(1)) {
       count_rare(a, kCntPmGt1, 1u);
@@ -1281,6 +1311,9 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     a.emit_wf = (R)(efg / (double)a.emit_ng);
     a.pair_wf = (R)(pfg / (double)a.pair_ng);
   }
+  a.generator = c->par.generator;
+  a.std_cdf = (const R *)c->d_std_cdf;
+  a.std_lnw = (const R *)c->d_std_lnw;
   a.chunk = c->tune.work_chunk;
   a.work_massive = c->d_pend_count + kWorkSlot;
   a.clock = c->d_clock;

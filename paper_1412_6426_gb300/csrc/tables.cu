@@ -98,16 +98,94 @@ __global__ void k_tab_coefs(const double *nodes, R *tab) {
 }
 
 template <typename R>
-int build(qed_ctx *c, cudaStream_t s) {
+int build_into(qed_ctx *c, R *dst, cudaStream_t s) {
   using C = Tab<R>;
   const int total = C::NB * C::S * C::NC;
   double *nodes = nullptr;
   if (cudaMallocAsync(&nodes, sizeof(double) * 2 * total, s) != cudaSuccess) return QED_ERR_CUDA;
   c->launches += 2;
   k_tab_nodes<R><<<(total + 127) / 128, 128, 0, s>>>(nodes);
-  k_tab_coefs<R><<<(2 * C::NB * C::S + 127) / 128, 128, 0, s>>>(nodes, (R *)c->d_tables);
+  k_tab_coefs<R><<<(2 * C::NB * C::S + 127) / 128, 128, 0, s>>>(nodes, dst);
   cudaError_t err = cudaGetLastError();
   cudaFreeAsync(nodes, s);
+  return err == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+template <typename R>
+int build(qed_ctx *c, cudaStream_t s) {
+  return build_into<R>(c, (R *)c->d_tables, s);
+}
+
+// Standard event generator tables (Sec. IV.F), in FP64: for each chi_j the
+// cumulative W(s^3) = int_0^s 3 t^2 G(t^3, chi_j) dt over the s grid, by
+// 8-point Gauss-Legendre per cell (the integrand is smooth in s: it is the
+// modified generator's 3 r1^2 G(r1^3)), normalised by W(1), and ln W(1).
+__constant__ double kGL8x[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290,
+                                -0.1834346424956498, 0.1834346424956498,  0.5255324099163290,
+                                0.7966664774136267,  0.9602898564975363};
+__constant__ double kGL8w[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873,
+                                0.3626837833783620, 0.3626837833783620, 0.3137066458778873,
+                                0.2223810344533745, 0.1012285362903763};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_std_rows(const double *tab64, R *cdf, R *lnw) {
+  constexpr int NI = kStdCols - 1;          // cells per row
+  constexpr int PER = NI / 256;             // cells per thread (consecutive)
+  static_assert(NI % 256 == 0, "cells per row");
+  __shared__ double part[256];
+  const int j = blockIdx.x;
+  const double chi = exp(kStdLnChiLo + j * kStdDLn);
+  double cell[PER], mine = 0.0;
+  for (int k = 0; k < PER; ++k) {
+    const int i = threadIdx.x * PER + k;
+    const double a = (double)i / NI, b = (double)(i + 1) / NI, m = 0.5 * (a + b), r = 0.5 * (b - a);
+    double acc = 0.0;
+    for (int q = 0; q < 8; ++q)
+      acc += kGL8w[q] * prob_emit<double>(tab64, m + r * kGL8x[q], chi, 1.0, 1.0 / kAlpha);
+    cell[k] = r * acc;
+    mine += cell[k];
+  }
+  part[threadIdx.x] = mine;
+  __syncthreads();
+  // inclusive scan of the per-thread sums (Hillis-Steele)
+  for (int o = 1; o < 256; o <<= 1) {
+    const double v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0.0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  const double total = part[255];
+  double run = part[threadIdx.x] - mine;
+  R *row = cdf + (size_t)j * kStdCols;
+  if (threadIdx.x == 0) row[0] = R(0);
+  for (int k = 0; k < PER; ++k) {
+    run += cell[k];
+    const int i = threadIdx.x * PER + k + 1;
+    row[i] = i == NI ? R(1) : (R)(run / total);
+  }
+  if (threadIdx.x == 0) lnw[j] = (R)log(total);
+}
+
+template <typename R>
+int build_standard(qed_ctx *c, cudaStream_t s) {
+  const double *tab64 = nullptr;
+  double *tmp = nullptr;
+  if (c->prec == 64) {
+    tab64 = (const double *)c->d_tables;
+  } else {
+    // an FP64 synchrotron table only for this build
+    if (cudaMallocAsync(&tmp, sizeof(double) * Tab<double>::kSize, s) != cudaSuccess) return QED_ERR_CUDA;
+    int rc = build_into<double>(c, tmp, s);
+    if (rc != QED_OK) {
+      cudaFreeAsync(tmp, s);
+      return rc;
+    }
+    tab64 = tmp;
+  }
+  c->launches += 1;
+  k_std_rows<R><<<kStdRows, 256, 0, s>>>(tab64, (R *)c->d_std_cdf, (R *)c->d_std_lnw);
+  cudaError_t err = cudaGetLastError();
+  if (tmp) cudaFreeAsync(tmp, s);
   return err == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 
@@ -116,4 +194,8 @@ int build(qed_ctx *c, cudaStream_t s) {
 
 int qed_build_tables(qed_ctx *c, cudaStream_t s) {
   return c->prec == 64 ? qed::build<double>(c, s) : qed::build<float>(c, s);
+}
+
+int qed_build_standard_tables(qed_ctx *c, cudaStream_t s) {
+  return c->prec == 64 ? qed::build_standard<double>(c, s) : qed::build_standard<float>(c, s);
 }

@@ -20,6 +20,7 @@ QED_ERR_TIMEOUT, QED_ERR_PMGT1, QED_ERR_STATE, QED_ERR_COURANT = 5, 6, 7, 8
 QED_ELECTRON, QED_POSITRON, QED_PHOTON, QED_ION = 0, 1, 2, 3
 QED_FIELD_GRID, QED_FIELD_UNIFORM, QED_FIELD_GAUSSIAN_LP, QED_FIELD_ROTATING_E, QED_FIELD_ENSEMBLE = 0, 1, 2, 3, 4
 QED_ENS_STRIDE = 10
+QED_GEN_MODIFIED, QED_GEN_ALTERNATIVE, QED_GEN_STANDARD = 0, 1, 2
 QED_MAX_ENS_BITS = 16
 
 # every entry point the header declares (checked by the CPU tests)
@@ -52,7 +53,8 @@ class QedParams(ctypes.Structure):
                 ("ens_bits", ctypes.c_int32), ("thin_interval", ctypes.c_int32),
                 ("thin_limit", ctypes.c_int64 * 4),
                 ("emit_fg", ctypes.c_double), ("pair_fg", ctypes.c_double),
-                ("emit_ng", ctypes.c_int32), ("pair_ng", ctypes.c_int32)]
+                ("emit_ng", ctypes.c_int32), ("pair_ng", ctypes.c_int32),
+                ("generator", ctypes.c_int32), ("reserved_gen", ctypes.c_int32)]
 
 
 class QedTuning(ctypes.Structure):

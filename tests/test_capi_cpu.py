@@ -68,6 +68,7 @@ int main(void) {
   P(qed_params, seed); P(qed_params, kappa); P(qed_params, pending_capacity);
   P(qed_params, ens_bits); P(qed_params, thin_interval); P(qed_params, thin_limit);
   P(qed_params, emit_fg); P(qed_params, pair_fg); P(qed_params, emit_ng); P(qed_params, pair_ng);
+  P(qed_params, generator); P(qed_params, reserved_gen);
   P(qed_diag, photons_created); P(qed_diag, pairs_created); P(qed_diag, thinned);
   P(qed_diag, kernel_launches);
   P(qed_tuning, work_chunk); P(qed_tuning, sort_massive); P(qed_tuning, concurrent); P(qed_tuning, reserved);
@@ -128,7 +129,8 @@ def _descs():
 
 
 @pytest.mark.parametrize("bad", ["precision", "cells", "grid_open", "kappa", "nbins", "mass", "tables",
-                                 "ens_bits", "thin_limit", "fg_nan", "ng", "mode"])
+                                 "ens_bits", "thin_limit", "fg_nan", "ng", "mode", "generator",
+                                 "generator_factor"])
 def test_argument_validation(lib, bad):
     from paper_1412_6426_gb300 import qed
     g, s, p = _descs()
@@ -158,6 +160,11 @@ def test_argument_validation(lib, bad):
         p.pair_ng = 65
     elif bad == "mode":
         g.field_mode = 5
+    elif bad == "generator":
+        p.generator = 3
+    elif bad == "generator_factor":
+        p.generator = 2
+        p.emit_fg = 2.0
     with pytest.raises(qed.QedError) as e:
         qed.qed_init(g, s, p, tables=tables)
     assert e.value.status == qed.QED_ERR_ARG

@@ -1,0 +1,94 @@
+"""The three photon-emission generators of Sec. IV.F-G on the GPU.
+
+* FP64 parity with the oracle: the alternative generator (r2 < P(r1), delta
+  = r1) must give the same particles (ids, momenta within 1e-12, as the
+  modified generator: the density comes from the same FP64 tables).  The
+  standard generator (r1 < W(1), delta from W(delta)/W(1) = r2) samples
+  delta from inverse-CDF tables built in FP64 at init, so the ids must match
+  and the momenta agree to the tables' accuracy (2e-5).
+* FP32: the standard and the modified generators sample the same spectrum
+  (Sec. IV.G: both reproduce Eq. (21) with no cutoff), so their photon
+  numbers and energy distributions agree statistically; the alternative
+  generator loses photons at low delta where P > 1.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.stats import ks_2samp
+
+from paper_1412_6426_gb300 import workloads
+from tests.util import box_scale, compare, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_1412_6426_gb300 import build
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    build.build()
+
+
+def shower(n, nsteps, B=3e-3):
+    w = workloads.test_particles_static_b(n_particles=n, nsteps=nsteps)
+    w.fp = (0, 0, 0, 0, 0, B)     # chi ~ 3
+    return w
+
+
+def test_alternative_generator_fp64_parity():
+    w = shower(300, 6)
+    caps = (20_000, 20_000, 100_000, 1)
+    ora, od, _, _ = run_oracle(w, caps=caps, generator=1)
+    assert od["emissions"] > 300 and od["pm_gt1"] > 0
+    gpu, gd = run_gpu(w, precision=64, caps=caps, generator=1)
+    assert gd["status"] == 0
+    for k in ("emissions", "pairs", "pm_gt1"):
+        assert gd[k] == od[k], k
+    rep = compare(gpu, ora, rtol_p=1e-12, xtol=1e-12 * box_scale(w))
+    assert rep["ok"], rep
+
+
+def test_standard_generator_fp64_parity():
+    w = shower(40, 4)
+    caps = (4_000, 4_000, 20_000, 1)
+    ora, od, _, _ = run_oracle(w, caps=caps, generator=2, pairs_on=0)
+    assert od["emissions"] > 40
+    gpu, gd = run_gpu(w, precision=64, caps=caps, generator=2, pairs_on=0)
+    assert gd["status"] == 0 and gd["emissions"] == od["emissions"]
+    # positions follow the momenta: the same relative error over at most the box
+    rep = compare(gpu, ora, rtol_p=2e-5, xtol=2e-5 * box_scale(w))
+    assert rep["ok"], rep
+
+
+def _fp32(generator, n=20_000, nsteps=3):
+    w = shower(n, nsteps, B=1e-3)   # chi ~ 1
+    caps = (2 * n, 2 * n, 40 * n, 1)
+    out, d = run_gpu(w, precision=32, caps=caps, generator=generator, pairs_on=0)
+    assert d["status"] == 0
+    eps = np.linalg.norm(out[2][1], axis=1)
+    return d, eps
+
+
+def test_standard_and_modified_sample_the_same_spectrum_fp32():
+    dm, em = _fp32(0)
+    ds, es = _fp32(2)
+    nm, ns = dm["emissions"], ds["emissions"]
+    assert nm > 10_000
+    assert abs(nm - ns) < 5 * math.sqrt(nm + ns)
+    assert ks_2samp(np.log(em), np.log(es)).pvalue > 1e-4
+    # down to delta ~ 1e-9 of gamma = 1000: no cutoff in either
+    assert em.min() < 1e-5 and es.min() < 1e-5
+
+
+def test_alternative_generator_loses_soft_photons_fp32():
+    dm, em = _fp32(0)
+    da, ea = _fp32(1)
+    assert da["pm_gt1"] > 0
+    soft = 1e-3 * 1000.0          # photons below delta = 1e-3 of the initial gamma
+    assert (ea < soft).sum() < 0.8 * (em < soft).sum()
+    hard = 0.1 * 1000.0
+    nm, na = (em > hard).sum(), (ea > hard).sum()
+    assert abs(nm - na) < 5 * math.sqrt(nm + na)
