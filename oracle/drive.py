@@ -17,7 +17,8 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
         t0: float = 0.0, fields=None, J=None, deposit_on: int = 0, yee: bool = False,
         ion_charge: float = 1.0, ion_mass: float = 1836.15267343, time_from: int = 0,
         ens_bits: int = 0, ens=None, emit_fg: float = 1.0, emit_ng: int = 1, pair_fg: float = 1.0,
-        pair_ng: int = 1, thin_interval: int = 0, thin_limit=(0, 0, 0, 0), generator: int = 0):
+        pair_ng: int = 1, thin_interval: int = 0, thin_limit=(0, 0, 0, 0), generator: int = 0,
+        schwinger_on: int = 0, schwinger_weight: float = 1.0):
     """Advance the given particles by nsteps steps of dt.
 
     particles: {species: (x[n,3], p[n,3], w[n], id[n])}.  Returns
@@ -26,7 +27,9 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
     advanced by one FDTD step after the particles, using the deposited J.
     Steps from index time_from on are timed (diag "timed_seconds" and
     "timed_particle_steps").  With thin_interval > 0 the stores are thinned
-    after every step s with (s + 1) % thin_interval == 0 (Sec. VI).
+    after every step s with (s + 1) % thin_interval == 0 (Sec. VI).  With
+    schwinger_on, pairs from the vacuum are created per cell after the
+    particles of each step, before the field update (Sec. V.B).
     """
     import time
     P = o.make_params(n=n, d=d, x0=x0, periodic=periodic, field_mode=field_mode, fp=fp, kappa=kappa,
@@ -35,7 +38,7 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
                       lg_lo=lg_lo, lg_hi=lg_hi, ion_charge=ion_charge, ion_mass=ion_mass,
                       ens_bits=ens_bits, ens=ens, emit_fg=emit_fg, emit_ng=emit_ng, pair_fg=pair_fg,
                       pair_ng=pair_ng, thin_interval=thin_interval, thin_limit=thin_limit,
-                      generator=generator)
+                      generator=generator, schwinger_on=schwinger_on, schwinger_weight=schwinger_weight)
     if caps is None:
         base = sum(len(v[3]) for v in particles.values())
         caps = (4 * base + 64,) * 4
@@ -68,6 +71,8 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
             for a in J:
                 a[:] = 0.0
         run_.step(step0 + k, t0 + k * dt, dt)
+        if schwinger_on:
+            run_.schwinger(step0 + k, t0 + k * dt, dt)
         if yee:
             o.yee_step(n, d, dt, fields, J)
         if thin_interval > 0 and (step0 + k + 1) % thin_interval == 0:

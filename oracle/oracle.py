@@ -68,6 +68,9 @@ class Params(ctypes.Structure):
         ("thin_limit", ctypes.c_int64 * 4),
         ("generator", ctypes.c_int32),
         ("reserved2", ctypes.c_int32),
+        ("schwinger_on", ctypes.c_int32),
+        ("reserved3", ctypes.c_int32),
+        ("schwinger_weight", ctypes.c_double),
     ]
 
 
@@ -81,7 +84,7 @@ class Diag(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "emissions", "pairs", "substeps_lepton", "substeps_photon", "pm_gt1", "pp_gt1",
         "capped", "absorbed", "overflow", "nonfinite", "photons_created", "pairs_created",
-        "thinned")] + [
+        "thinned", "schwinger_pairs", "schwinger_gt1")] + [
         ("energy_defect", ctypes.c_double),
         ("spectrum", ctypes.POINTER(ctypes.c_double)),
         ("spectrum_energy", ctypes.POINTER(ctypes.c_double))]
@@ -120,6 +123,9 @@ def lib():
         _lib.or_step.restype = ctypes.c_int
         _lib.or_step.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Store), ctypes.POINTER(Diag),
                                  ctypes.POINTER(pd), ctypes.POINTER(pd), u32, d, d]
+        _lib.or_schwinger.restype = ctypes.c_int
+        _lib.or_schwinger.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Store), ctypes.POINTER(Diag),
+                                      ctypes.POINTER(pd), u32, d, d]
         _lib.or_Wnorm.restype = d; _lib.or_Wnorm.argtypes = [d, d]
         _lib.or_Pstd.restype = d; _lib.or_Pstd.argtypes = [d, d, d]
         _lib.or_delta_std.restype = d; _lib.or_delta_std.argtypes = [d, d]
@@ -378,6 +384,15 @@ class Run:
         for s, c in zip(self.sp, stores):
             s.n = int(c.n)
 
+    def schwinger(self, step: int, t: float, dt: float):
+        stores = (Store * 4)(*[s.cstore() for s in self.sp])
+        fp = None
+        if self.fields is not None:
+            fp = (ctypes.POINTER(ctypes.c_double) * 6)(*[_dp(a) for a in self.fields])
+        lib().or_schwinger(ctypes.byref(self.P), stores, ctypes.byref(self.D), fp, int(step), float(t), float(dt))
+        for s, c in zip(self.sp, stores):
+            s.n = int(c.n)
+
     def thin(self, step: int):
         stores = (Store * 4)(*[s.cstore() for s in self.sp])
         if lib().or_thin(ctypes.byref(self.P), stores, ctypes.byref(self.D), int(step)) != 0:
@@ -386,7 +401,7 @@ class Run:
             s.n = int(c.n)
 
     def diag(self) -> dict:
-        return {k: getattr(self.D, k) for k, _ in Diag._fields_[:14]}
+        return {k: getattr(self.D, k) for k, _ in Diag._fields_[:16]}
 
 
 def make_params(*, n=(1, 1, 1), d=(1.0, 1.0, 1.0), x0=(0.0, 0.0, 0.0), periodic=(0, 0, 0),
@@ -394,7 +409,7 @@ def make_params(*, n=(1, 1, 1), d=(1.0, 1.0, 1.0), x0=(0.0, 0.0, 0.0), periodic=
                 pairs_on=1, same_step_children=1, deposit_on=0, seed=1, lg_lo=-12.0,
                 lg_hi=0.0, ion_charge=1.0, ion_mass=1836.15267343, ens_bits=0, ens=None,
                 emit_fg=1.0, emit_ng=1, pair_fg=1.0, pair_ng=1, thin_interval=0,
-                thin_limit=(0, 0, 0, 0), generator=0) -> Params:
+                thin_limit=(0, 0, 0, 0), generator=0, schwinger_on=0, schwinger_weight=1.0) -> Params:
     """Oracle parameters.  ens: (n_ens, ENS_STRIDE) float64 table of the
     ensemble fields (field_mode FIELD_ENSEMBLE); the returned Params keeps a
     reference to it."""
@@ -427,6 +442,8 @@ def make_params(*, n=(1, 1, 1), d=(1.0, 1.0, 1.0), x0=(0.0, 0.0, 0.0), periodic=
     P.thin_interval = int(thin_interval)
     P.thin_limit[:] = [int(v) for v in thin_limit]
     P.generator = int(generator)
+    P.schwinger_on = int(schwinger_on)
+    P.schwinger_weight = float(schwinger_weight)
     return P
 
 

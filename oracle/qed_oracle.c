@@ -44,6 +44,10 @@
  *                   weight and spectrum unbiased (Sec. VI)
  *   thinning        total weight of each group conserved; groups at or
  *                   below the limit untouched; survivors binomial
+ *   Schwinger pairs the pair count of a uniform-field box against the sum of
+ *                   P_S (binomial), the unit conversion of R_S V c dt against
+ *                   the formula evaluated in SI units, positions uniform in
+ *                   the cells, pairs at rest, none in weak fields
  *   generators      standard (inverse transform): W(x)/W(1) against scipy's
  *                   K-function quadrature, total W(1) against the number
  *                   rate; alternative: P(delta) against Eq. (24); the three
@@ -62,7 +66,8 @@
 
 enum { OR_ELECTRON = 0, OR_POSITRON = 1, OR_PHOTON = 2, OR_ION = 3, OR_NSPECIES = 4 };
 enum { OR_PURPOSE_EMIT = 1, OR_PURPOSE_PAIR = 2, OR_PURPOSE_CHILD = 3, OR_PURPOSE_KEEP = 4,
-       OR_PURPOSE_THIN = 5 };
+       OR_PURPOSE_THIN = 5, OR_PURPOSE_SCHWINGER = 6 };
+#define OR_SCHWINGER_KIND 0x80   /* flag in the product kind of vacuum pairs */
 enum { OR_FIELD_GRID = 0, OR_FIELD_UNIFORM = 1, OR_FIELD_GAUSSIAN_LP = 2, OR_FIELD_ROTATING_E = 3,
        OR_FIELD_ENSEMBLE = 4 };
 #define OR_ENS_STRIDE 10  /* per ensemble: E0, omega, phase, Eu[3], Bu[3], thin_scale */
@@ -639,6 +644,9 @@ typedef struct {
     int64_t thin_limit[4];   /* per species: most particles a group keeps (0 = off) */
     int32_t generator;       /* OR_GEN_*: modified (default), alternative, standard */
     int32_t reserved2;
+    int32_t schwinger_on;    /* pairs from the vacuum per cell (Sec. V.B) */
+    int32_t reserved3;
+    double schwinger_weight; /* weight of those electrons and positrons */
 } or_params;
 
 typedef struct {
@@ -653,6 +661,8 @@ typedef struct {
     int64_t photons_created; /* photons made (all N_g samples, after the 1/f_g keep) */
     int64_t pairs_created;   /* pairs made, likewise */
     int64_t thinned;         /* particles removed by thinning */
+    int64_t schwinger_pairs; /* pairs created from the vacuum */
+    int64_t schwinger_gt1;   /* cells with P_S > 1 */
     double energy_defect;    /* sum of w*(energy before - energy after) over events */
     double *spectrum;        /* nbins, weighted by w, over log10(delta) */
     double *spectrum_energy; /* nbins, weighted by w, over log10(photon energy) with the same range */
@@ -1005,6 +1015,58 @@ int or_step(const or_params *P, or_store S[4], or_diag *D, double *const f[6], d
         s->n = o;
         free(alive[sp]);
     }
+    return 0;
+}
+
+/* Pairs from the vacuum (Sec. V.B): once per step, in every cell of the
+ * lattice, the field E is taken at the cell centre (the Yee mesh's CIC
+ * gather there, or the analytic field at the step's start time t) and
+ *   P_S = R_S V_cell c dt,   R_S = E^2 exp(-pi E_S/E) / (4 pi^3 lambda_C^4),
+ * which in Compton units (lambda_C = c = 1, E in E_S) is
+ *   P_S = E^2 exp(-pi/E) d0 d1 d2 dt / (4 pi^3).
+ * The magnetic field is neglected, as in the paper's statement.  If
+ * r < P_S an electron and a positron at rest are placed at one uniformly
+ * drawn point of the cell.  Draws: the cell index keys a Philox stream,
+ * counter (step, 0 or 1, SCHWINGER, seed): r, u_x from the first block, u_y,
+ * u_z from the second.  Ids: or_child_id of the cell index with the kind
+ * flagged OR_SCHWINGER_KIND.  Cells with P_S > 1 are counted. */
+int or_schwinger(const or_params *P, or_store S[4], or_diag *D, double *const f[6], uint32_t step, double t,
+                 double dt)
+{
+    const double vol = P->d[0] * P->d[1] * P->d[2];
+    for (long k = 0; k < P->n[2]; ++k)
+        for (long j = 0; j < P->n[1]; ++j)
+            for (long i = 0; i < P->n[0]; ++i) {
+                uint64_t cell = (uint64_t)((k * P->n[1] + j) * P->n[0] + i);
+                double xc[3] = {P->x0[0] + (i + 0.5) * P->d[0], P->x0[1] + (j + 0.5) * P->d[1],
+                                P->x0[2] + (k + 0.5) * P->d[2]};
+                double E[3], B[3];
+                if (P->field_mode == OR_FIELD_GRID)
+                    or_gather(P->n, P->d, P->x0, f, xc, E, B);
+                else
+                    or_field(P->field_mode, P->fp, xc, t, E, B);
+                double Em = sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
+                if (!(Em > 0.0)) continue;
+                double ps = Em * Em * exp(-OR_PI / Em) / (4.0 * OR_PI * OR_PI * OR_PI) * vol * dt;
+                if (ps > 1.0) D->schwinger_gt1++;
+                double r, ux, uy, uz;
+                or_draw(cell, step, 0u, OR_PURPOSE_SCHWINGER, P->seed, &r, &ux);
+                if (!(r < ps)) continue;
+                or_draw(cell, step, 1u, OR_PURPOSE_SCHWINGER, P->seed, &uy, &uz);
+                or_particle el, po;
+                el.x[0] = po.x[0] = P->x0[0] + ((double)i + ux) * P->d[0];
+                el.x[1] = po.x[1] = P->x0[1] + ((double)j + uy) * P->d[1];
+                el.x[2] = po.x[2] = P->x0[2] + ((double)k + uz) * P->d[2];
+                for (int c = 0; c < 3; ++c) el.p[c] = po.p[c] = 0.0;
+                el.w = po.w = P->schwinger_weight;
+                el.id = or_child_id(cell, step, 0u, OR_ELECTRON | OR_SCHWINGER_KIND, P->seed);
+                po.id = or_child_id(cell, step, 0u, OR_POSITRON | OR_SCHWINGER_KIND, P->seed);
+                el.alive = po.alive = 1;
+                or_ctx C = {P, S, D, f, NULL, step, t, dt};
+                or_append(&C, OR_ELECTRON, &el);
+                or_append(&C, OR_POSITRON, &po);
+                D->schwinger_pairs++;
+            }
     return 0;
 }
 
