@@ -164,6 +164,16 @@ typedef struct qed_params {
     int32_t generator;          /* qed_generator; the generator factors above
                                    apply to the modified generator only */
     int32_t reserved_gen;       /* must be 0 */
+    /* --- pairs from the vacuum (Sec. V.B) --- */
+    int32_t schwinger_on;       /* 1: once per step, in every cell, an electron
+                                   and a positron at rest are created at a
+                                   uniform point of the cell with probability
+                                   P_S = E^2 exp(-pi/E) V_cell dt / (4 pi^3)
+                                   (Compton units; E = |E| at the cell centre,
+                                   B neglected as in the paper); not with
+                                   QED_FIELD_ENSEMBLE */
+    int32_t reserved_s;         /* must be 0 */
+    double schwinger_weight;    /* their statistical weight, > 0 */
 } qed_params;
 
 typedef enum qed_generator {
@@ -232,6 +242,8 @@ typedef struct qed_diag {
                                    generator factors are set) */
     int64_t pairs_created;      /* pairs made (likewise) */
     int64_t thinned;            /* particles removed by thinning */
+    int64_t schwinger_pairs;    /* pairs created from the vacuum */
+    int64_t schwinger_gt1;      /* cell-steps with P_S > 1 (one pair made) */
     int64_t kernel_launches;    /* CUDA kernels this context has launched */
     int64_t step;               /* steps taken */
     double time;                /* current time */

@@ -177,6 +177,10 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     return QED_ERR_ARG;
   if (p->generator < QED_GEN_MODIFIED || p->generator > QED_GEN_STANDARD || p->reserved_gen != 0) return QED_ERR_ARG;
   if (p->generator != QED_GEN_MODIFIED && (p->emit_fg > 1.0 || p->emit_ng > 1)) return QED_ERR_ARG;
+  if ((p->schwinger_on != 0 && p->schwinger_on != 1) || p->reserved_s != 0) return QED_ERR_ARG;
+  if (p->schwinger_on && (!(p->schwinger_weight > 0.0) || !std::isfinite(p->schwinger_weight) ||
+                          g->field_mode == QED_FIELD_ENSEMBLE))
+    return QED_ERR_ARG;
   bool thinning = false;
   for (int k = 0; k < 4; ++k) {
     if (p->thin_limit[k] < 0) return QED_ERR_ARG;
@@ -667,6 +671,8 @@ int qed_diagnostics(qed_ctx *c, qed_diag *out, void *stream) {
   out->photons_created = (int64_t)cnt[qed::kCntPhotonsMade];
   out->pairs_created = (int64_t)cnt[qed::kCntPairsMade];
   out->thinned = (int64_t)cnt[qed::kCntThinned];
+  out->schwinger_pairs = (int64_t)cnt[qed::kCntSchwinger];
+  out->schwinger_gt1 = (int64_t)cnt[qed::kCntSchwingerGt1];
   out->particle_steps = 0;
   for (int k = 0; k < 4; ++k) {
     out->species_steps[k] = (int64_t)cnt[qed::kCntSpeciesSteps + k];

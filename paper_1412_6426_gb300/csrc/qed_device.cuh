@@ -13,9 +13,11 @@ namespace qed {
 constexpr double kAlpha = 7.2973525693e-3;          // fine-structure constant
 constexpr double kSqrt3Over2Pi = 0.27566444771089600; // sqrt(3)/(2 pi)
 constexpr double kTwoPi = 6.283185307179586;
+constexpr double kPi = 3.141592653589793;
 
 enum Species { kElectron = 0, kPositron = 1, kPhoton = 2, kIon = 3, kNSpecies = 4 };
-enum Purpose : uint32_t { kEmit = 1, kPair = 2, kChild = 3, kKeep = 4, kThin = 5 };
+enum Purpose : uint32_t { kEmit = 1, kPair = 2, kChild = 3, kKeep = 4, kThin = 5, kSchwinger = 6 };
+constexpr unsigned kSchwingerKind = 0x80;   // flag in the product kind of vacuum pairs
 enum FieldMode { kFieldGrid = 0, kFieldUniform = 1, kFieldGaussianLP = 2, kFieldRotatingE = 3, kFieldEnsemble = 4 };
 
 // Device status bits (folded into a qed_status by the host).

@@ -15,7 +15,7 @@ constexpr int kNumCounters = 20;    // device diagnostic counters
 enum Counter {
   kCntEmissions = 0, kCntPairs, kCntSubLepton, kCntSubPhoton, kCntPmGt1, kCntPpGt1, kCntCapped,
   kCntAbsorbed, kCntOverflow, kCntNonfinite, kCntSpeciesSteps /* 4 slots: live particles per species */,
-  kCntPhotonsMade = kCntSpeciesSteps + 4, kCntPairsMade, kCntThinned
+  kCntPhotonsMade = kCntSpeciesSteps + 4, kCntPairsMade, kCntThinned, kCntSchwinger, kCntSchwingerGt1
 };
 constexpr int kWorkSlot = kMaxPass + 3;   // d_pend_count slot: work counter of the e-/e+/ion pass
 constexpr int kEnsFieldStride = 8;        // per ensemble per step: E[3], B[3], |E|+|B|, pad
@@ -70,6 +70,9 @@ template <typename R> struct StepArgs {
   const double *ens_table;  // n_ens x QED_ENS_STRIDE
   R *ens_field;            // n_ens x kEnsFieldStride, written by k_step_constants
   double ens_hmax;         // bound of |E| + |B| over the ensembles
+  // pairs from the vacuum (Sec. V.B)
+  int schwinger;
+  R schwinger_w;
   // event generator of the emission (Sec. IV.F-G): 0 modified, 1 alternative, 2 standard
   int generator;
   const R *std_cdf, *std_lnw;

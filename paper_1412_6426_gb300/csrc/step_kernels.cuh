@@ -897,6 +897,58 @@ __device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m, int l) {
   return (__umulhi(n, m) + n) >> l;   // exact for n < 2^31 (Granlund-Montgomery)
 }
 
+// Pairs from the vacuum (Sec. V.B), once per step after the particles: in
+// every cell the field at the centre (CIC of the Yee mesh there, or the
+// analytic field at the step's time) gives
+//   P_S = E^2 exp(-pi/E) V_cell dt / (4 pi^3)   (Compton units, E = |E|);
+// with r < P_S an electron and a positron at rest are appended at one
+// uniform point of the cell.  The cell index keys the draws: (r, u_x) from
+// counter (step, 0, SCHWINGER, seed), (u_y, u_z) from (step, 1, ...).
+template <typename R>
+__global__ void __launch_bounds__(256) k_schwinger(const StepArgs<R> a) {
+  __shared__ StepConst kc;
+  if (threadIdx.x < (int)(sizeof(StepConst) / 8))
+    ((unsigned long long *)&kc)[threadIdx.x] = ((const unsigned long long *)a.step_const)[threadIdx.x];
+  __syncthreads();
+  const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
+  const R vol = R(a.dd[0] * a.dd[1] * a.dd[2]);
+  unsigned pairs = 0, gt1 = 0;
+  for (long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; cidx < ncell;
+       cidx += (long long)gridDim.x * blockDim.x) {
+    const unsigned cell = (unsigned)cidx;
+    const unsigned row = fast_div(cell, a.div_m[0], a.div_l[0]);
+    const unsigned slab = fast_div(cell, a.div_m[1], a.div_l[1]);
+    Pt<R> q;
+    q.ci[0] = (int)(cell - row * a.n[0]);
+    q.ci[1] = (int)(row - slab * a.n[1]);
+    q.ci[2] = (int)slab;
+    q.off[0] = q.off[1] = q.off[2] = R(0.5);
+    V3<R> E, B;
+    if (a.field_mode == kFieldGrid) gather_grid(a, q, E, B);
+    else field_analytic(a, kc, q, E, B);
+    const R em = sqrt_r(E.x * E.x + E.y * E.y + E.z * E.z);
+    if (!(em > R(0))) continue;
+    const R ps = em * em * exp_r(-R(kPi) / em) / R(4.0 * kPi * kPi * kPi) * vol * a.dt;
+    gt1 += ps > R(1);
+    R r, ux;
+    draw2((uint64_t)cell, kc.step, 0u, kSchwinger, a.seed, r, ux);
+    if (!(r < ps)) continue;
+    R uy, uz;
+    draw2((uint64_t)cell, kc.step, 1u, kSchwinger, a.seed, uy, uz);
+    Pt<R> el = q;
+    el.off[0] = ux; el.off[1] = uy; el.off[2] = uz;
+    el.p = {R(0), R(0), R(0)};
+    el.w = a.schwinger_w;
+    Pt<R> po = el;
+    el.id = child_id((uint64_t)cell, kc.step, 0u, kElectron | kSchwingerKind, a.seed);
+    po.id = child_id((uint64_t)cell, kc.step, 0u, kPositron | kSchwingerKind, a.seed);
+    count_outcome(a, append(a, kElectron, el) | append(a, kPositron, po));
+    ++pairs;
+  }
+  count_rare(a, kCntSchwinger, pairs);
+  count_rare(a, kCntSchwingerGt1, gt1);
+}
+
 // The per-step field constants, formed once per step in FP64 by one thread.
 // Ensemble mode: every thread of the one block also evaluates the fields
 // of its ensembles at the step's time (FP64, stored in the context precision).
@@ -1311,6 +1363,8 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     a.emit_wf = (R)(efg / (double)a.emit_ng);
     a.pair_wf = (R)(pfg / (double)a.pair_ng);
   }
+  a.schwinger = c->par.schwinger_on;
+  a.schwinger_w = (R)c->par.schwinger_weight;
   a.generator = c->par.generator;
   a.std_cdf = (const R *)c->d_std_cdf;
   a.std_lnw = (const R *)c->d_std_lnw;
@@ -1395,6 +1449,10 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   if (e == cudaSuccess && a.same_step) {
     c->launches += 1;
     e = cudaLaunchCooperativeKernel((const void *)k_products<R, EXT>, dim3(c->blocks_products), dim3(256), args, 0, s);
+  }
+  if (e == cudaSuccess && a.schwinger) {
+    c->launches += 1;
+    e = cudaLaunchKernel((const void *)k_schwinger<R>, dim3(c->num_sms * 8), dim3(256), args, 0, s);
   }
   if (c->ev_stop) cudaEventRecord(c->ev_stop, s);
   return e == cudaSuccess ? QED_OK : QED_ERR_CUDA;

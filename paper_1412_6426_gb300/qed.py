@@ -54,7 +54,9 @@ class QedParams(ctypes.Structure):
                 ("thin_limit", ctypes.c_int64 * 4),
                 ("emit_fg", ctypes.c_double), ("pair_fg", ctypes.c_double),
                 ("emit_ng", ctypes.c_int32), ("pair_ng", ctypes.c_int32),
-                ("generator", ctypes.c_int32), ("reserved_gen", ctypes.c_int32)]
+                ("generator", ctypes.c_int32), ("reserved_gen", ctypes.c_int32),
+                ("schwinger_on", ctypes.c_int32), ("reserved_s", ctypes.c_int32),
+                ("schwinger_weight", ctypes.c_double)]
 
 
 class QedTuning(ctypes.Structure):
@@ -76,7 +78,7 @@ class QedDiag(ctypes.Structure):
                 ("species_steps", ctypes.c_int64 * 4)] + [(k, ctypes.c_int64) for k in (
         "emissions", "pairs", "substeps_lepton", "substeps_photon", "pm_gt1",
         "pp_gt1", "capped", "absorbed", "overflow", "nonfinite", "photons_created", "pairs_created",
-        "thinned", "kernel_launches", "step")] + [
+        "thinned", "schwinger_pairs", "schwinger_gt1", "kernel_launches", "step")] + [
         ("time", ctypes.c_double), ("status", ctypes.c_int32), ("nbins", ctypes.c_int32),
         ("spectrum", ctypes.POINTER(ctypes.c_double)),
         ("spectrum_energy", ctypes.POINTER(ctypes.c_double))]
@@ -208,7 +210,7 @@ def qed_diagnostics(ctx: int, nbins: int = 0, stream: int = 0, check: bool = Tru
     rc = load().qed_diagnostics(ctypes.c_void_p(ctx), ctypes.byref(d), ctypes.c_void_p(stream))
     if check:
         _check("qed_diagnostics", rc)
-    out = {k: getattr(d, k) for k, _ in QedDiag._fields_[3:19]}
+    out = {k: getattr(d, k) for k, _ in QedDiag._fields_[3:21]}
     out["count"] = list(d.count)
     out["particle_steps"] = d.particle_steps
     out["species_steps"] = list(d.species_steps)

@@ -24,7 +24,8 @@ class Simulation:
                  compact_interval: int = 0, pending_capacity: int = 0, seed=None, pm_strict: int = 0,
                  ion_charge: float = 1.0, ion_mass: float = 1836.15267343, stream=None, tables=None,
                  thin_interval: int = 0, thin_limit=(0, 0, 0, 0), emit_fg: float = 1.0, emit_ng: int = 1,
-                 pair_fg: float = 1.0, pair_ng: int = 1, generator: int = 0):
+                 pair_fg: float = 1.0, pair_ng: int = 1, generator: int = 0, schwinger_on: int = 0,
+                 schwinger_weight: float = 1.0):
         w = workload
         self.w = w
         self.prec = precision
@@ -61,6 +62,8 @@ class Simulation:
         p.emit_fg, p.pair_fg = float(emit_fg), float(pair_fg)
         p.emit_ng, p.pair_ng = int(emit_ng), int(pair_ng)
         p.generator = int(generator)
+        p.schwinger_on = int(schwinger_on)
+        p.schwinger_weight = float(schwinger_weight)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ctx = qed.qed_init(g, s, p, tables=tables, stream=self.stream.cuda_stream)
         self.caps = list(s.capacity)

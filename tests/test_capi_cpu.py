@@ -68,7 +68,8 @@ int main(void) {
   P(qed_params, seed); P(qed_params, kappa); P(qed_params, pending_capacity);
   P(qed_params, ens_bits); P(qed_params, thin_interval); P(qed_params, thin_limit);
   P(qed_params, emit_fg); P(qed_params, pair_fg); P(qed_params, emit_ng); P(qed_params, pair_ng);
-  P(qed_params, generator); P(qed_params, reserved_gen);
+  P(qed_params, generator); P(qed_params, reserved_gen); P(qed_params, schwinger_on);
+  P(qed_params, schwinger_weight); P(qed_diag, schwinger_pairs); P(qed_diag, schwinger_gt1);
   P(qed_diag, photons_created); P(qed_diag, pairs_created); P(qed_diag, thinned);
   P(qed_diag, kernel_launches);
   P(qed_tuning, work_chunk); P(qed_tuning, sort_massive); P(qed_tuning, concurrent); P(qed_tuning, reserved);
@@ -130,7 +131,7 @@ def _descs():
 
 @pytest.mark.parametrize("bad", ["precision", "cells", "grid_open", "kappa", "nbins", "mass", "tables",
                                  "ens_bits", "thin_limit", "fg_nan", "ng", "mode", "generator",
-                                 "generator_factor"])
+                                 "generator_factor", "schwinger_weight", "schwinger_ensemble"])
 def test_argument_validation(lib, bad):
     from paper_1412_6426_gb300 import qed
     g, s, p = _descs()
@@ -165,6 +166,13 @@ def test_argument_validation(lib, bad):
     elif bad == "generator_factor":
         p.generator = 2
         p.emit_fg = 2.0
+    elif bad == "schwinger_weight":
+        p.schwinger_on = 1
+        p.schwinger_weight = 0.0
+    elif bad == "schwinger_ensemble":
+        p.schwinger_on = 1
+        p.schwinger_weight = 1.0
+        g.field_mode = qed.QED_FIELD_ENSEMBLE
     with pytest.raises(qed.QedError) as e:
         qed.qed_init(g, s, p, tables=tables)
     assert e.value.status == qed.QED_ERR_ARG
