@@ -64,6 +64,8 @@ void release(qed_ctx *c) {
   cudaFree(c->d_ens);
   cudaFree(c->d_ens_h);
   cudaFree(c->d_std_cdf);
+  cudaFree(c->d_grid_max);
+  cudaFree(c->d_blk_chunk);
   cudaFree(c->d_std_lnw);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -239,6 +241,8 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     c->nblk = (int)nblk;
     if (rc == QED_OK) rc = dalloc(&c->d_blk_start, sizeof(unsigned) * 4 * (nblk + 1));
     if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (nblk + 1));
+    if (rc == QED_OK) rc = dalloc(&c->d_grid_max, sizeof(unsigned long long) * 6);
+    if (rc == QED_OK) rc = dalloc(&c->d_blk_chunk, sizeof(unsigned) * (nblk + 1));
   }
   if (g->field_mode == QED_FIELD_ENSEMBLE) {
     c->ens_cap = 1 << p->ens_bits;
@@ -409,6 +413,8 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
         int rs = sp == QED_PHOTON ? QED_OK : qed_launch_sort(c, sp, s);
         if (rs != QED_OK) return rs;
       }
+      int rs = qed_launch_block_chunks(c, s);
+      if (rs != QED_OK) return rs;
       c->sorted = 1;
       c->steps_since_compact = 0;
     }
@@ -429,6 +435,7 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
         rc = sort ? qed_launch_sort(c, sp, s) : qed_launch_compact(c, sp, true, s);
         if (rc != QED_OK) return rc;
       }
+      if (grid && c->nblk > 0 && (rc = qed_launch_block_chunks(c, s)) != QED_OK) return rc;
     }
   }
   return QED_OK;

@@ -23,6 +23,7 @@ constexpr int kNsubKeys = 64;             // sort keys of the sub-interval estim
 constexpr int kMaxBins = 4096;
 constexpr int kCompactTile = 2048;   // particles per tile of the compaction
 constexpr int kBlockCells = 8;       // cell block edge (grid mode): 8 x 8 x 8 cells
+constexpr int kBlockChunk = 1024;    // particles per work item of the cell-block kernel
 constexpr int kTileNodes = kBlockCells + 3;   // current tile edge: the deposit stencil of a
                                               // particle starting in the block stays inside
 
@@ -70,6 +71,10 @@ template <typename R> struct StepArgs {
   const double *ens_table;  // n_ens x QED_ENS_STRIDE
   R *ens_field;            // n_ens x kEnsFieldStride, written by k_step_constants
   double ens_hmax;         // bound of |E| + |B| over the ensembles
+  // Yee mesh: per-step maxima of |Ex| .. |Bz| (bit patterns), and where the
+  // photon split threshold of the next compaction goes
+  unsigned long long *grid_max;
+  double *eps_star_out;
   // pairs from the vacuum (Sec. V.B)
   int schwinger;
   R schwinger_w;
@@ -98,6 +103,7 @@ template <typename R> struct StepArgs {
   int nb[3];
   int nblk;
   const unsigned *blk_start[4];
+  const unsigned *blk_chunk;   // nblk + 1: first work item of each cell block (kBlockChunk particles)
   unsigned *work;          // work-stealing counter of the cell-block kernel (zeroed per step)
   void *step_const;        // per-step field constants (written by k_step_constants)
   void *clock;             // device clock {t, step}: read and advanced once per step
@@ -143,12 +149,14 @@ struct qed_ctx {
   double last_dt = 0.0;               // dt of the latest qed_step (the sort key uses it)
   int ext = 0;                        // ensembles or generator factors: EXT kernels
   void *d_thin = nullptr;             // thinning: per group count, weight, survivors' weight
+  unsigned long long *d_grid_max = nullptr;   // Yee mesh: |E|, |B| component maxima per step
   void *d_std_cdf = nullptr;          // standard generator: kStdRows x kStdCols cumulative W
   void *d_std_lnw = nullptr;          // and ln W(1) per row (context precision)
   int thin_groups = 0;
   qed_tuning tune{};
   unsigned *d_blk_start = nullptr;    // [4][nblk + 1] first record of each cell block
   unsigned *d_blk_cursor = nullptr;   // [nblk + 1] histogram / scatter cursors of the sort
+  unsigned *d_blk_chunk = nullptr;    // [nblk + 1] first work item of each cell block
   int nb[3] = {0, 0, 0};
   int nblk = 0;
   int sorted = 0;                     // the stores are in cell-block order (up to the tail)
@@ -185,6 +193,7 @@ int qed_launch_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t
                    cudaStream_t s);
 int qed_launch_compact(qed_ctx *c, int sp, bool partition, cudaStream_t s);
 int qed_launch_sort(qed_ctx *c, int sp, cudaStream_t s);
+int qed_launch_block_chunks(qed_ctx *c, cudaStream_t s);
 int qed_step_kernel_blocks(qed_ctx *c);
 int qed_launch_chi_star(qed_ctx *c, cudaStream_t s);
 int qed_launch_thin(qed_ctx *c, int sp, cudaStream_t s);

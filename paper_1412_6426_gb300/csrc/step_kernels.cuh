@@ -124,9 +124,12 @@ struct alignas(8) StepConst {
   float curv;                // -omega / (4 pi): curvature phase in cycles per r^2/R
   float env_k;               // -2 ln 2 / tau^2
   float amp0, phi0_cyc;      // E0 and the phase offset in cycles
-  // Bound on a photon's effective field anywhere in this step (analytic
-  // fields only; infinite on the grid) and whether a photon with H <= hmax
-  // is always advanced in a single sub-interval.
+  // Bound on a photon's effective field anywhere in this step and whether a
+  // photon that cannot pair (eps hmax < chi*) may take the straight flight:
+  // analytic fields, when every H <= hmax gives one sub-interval (the
+  // flight is then the general path's bit for bit); the Yee mesh, when no
+  // H <= hmax caps the sub-intervals (the flight then differs from N
+  // sub-interval moves by rounding only, and no field is gathered).
   double hmax;
   float hmax_f;              // hmax rounded up, for the FP32 comparison
   int one_interval;
@@ -185,8 +188,22 @@ __device__ void step_constants(const StepArgs<R> &a, StepConst &k) {
     k.hmax = 2.0 * fabs(a.fp[0]);             // |E| = |B| <= E0 everywhere
   else if (a.field_mode == kFieldEnsemble)
     k.hmax = a.ens_hmax;
-  // N = ceil(dt H / (kappa 130 2 pi)) is 1 for every H <= hmax (margin 1e-3)
-  k.one_interval = (double)a.dt * k.hmax <= 0.999 * (double)a.kappa * 130.0 * kTwoPi;
+  else if (a.field_mode == kFieldGrid && a.grid_max) {
+    // CIC weights are a convex combination: |E| <= |(max|Ex|, max|Ey|, max|Ez|)|
+    double m[6];
+    for (int c = 0; c < 6; ++c) m[c] = sizeof(R) == 4 ? (double)__uint_as_float((unsigned)a.grid_max[c])
+                                                       : __longlong_as_double((long long)a.grid_max[c]);
+    k.hmax = (sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) + sqrt(m[3] * m[3] + m[4] * m[4] + m[5] * m[5])) *
+             (1.0 + 1e-6);
+    // compaction groups the photons that cannot pair (two-class split)
+    if (a.eps_star_out) *a.eps_star_out = k.hmax > 0.0 ? 0.999 * (*a.chi_star) / k.hmax : 0.0;
+  }
+  // N = ceil(dt H / (kappa 130 2 pi)) is 1 for every H <= hmax (margin 1e-3);
+  // on the mesh: N stays below nsub_max for every H <= hmax
+  if (a.field_mode == kFieldGrid)
+    k.one_interval = (double)a.dt * k.hmax <= 0.999 * (double)a.nsub_max * (double)a.kappa * 130.0 * kTwoPi;
+  else
+    k.one_interval = (double)a.dt * k.hmax <= 0.999 * (double)a.kappa * 130.0 * kTwoPi;
   k.hmax_f = (float)(k.hmax * 1.00001);
   for (int c = 0; c < 6; ++c) k.ud[c] = 0.0;
   if (a.field_mode == kFieldUniform) {
@@ -949,6 +966,33 @@ __global__ void __launch_bounds__(256) k_schwinger(const StepArgs<R> a) {
   count_rare(a, kCntSchwingerGt1, gt1);
 }
 
+// Yee mesh: the largest |value| of each field component this step (a
+// bound on every gathered |E| and |B|), reduced per warp and merged by
+// atomicMax on the bit patterns (monotonic for non-negative values).
+__device__ __forceinline__ unsigned long long abs_bits(float v) { return __float_as_uint(fabsf(v)); }
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(fabs(v));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_grid_max(const StepArgs<R> a) {
+  const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
+  for (int c = 0; c < 6; ++c) {
+    const R *f = c < 3 ? a.E[c] : a.B[c - 3];
+    unsigned long long m = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * blockDim.x) {
+      const unsigned long long b = abs_bits(__ldg(f + i));
+      m = b > m ? b : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long x = __shfl_xor_sync(0xffffffffu, m, o);
+      m = x > m ? x : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(a.grid_max + c, m);
+  }
+}
+
 // The per-step field constants, formed once per step in FP64 by one thread.
 // Ensemble mode: every thread of the one block also evaluates the fields
 // of its ensembles at the step's time (FP64, stored in the context precision).
@@ -1222,22 +1266,37 @@ __global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
   Cnt cnt;
   const unsigned step = ((const StepConst *)a.step_const)->step;
   if (threadIdx.x < 4) ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
+  const unsigned items = a.blk_chunk[a.nblk];
   for (;;) {
     if (threadIdx.x == 0) blk = (int)atomicAdd(a.work, 1u);
     __syncthreads();
-    const int b = blk;
-    if (b >= a.nblk) break;
+    const unsigned item = (unsigned)blk;
+    if (item >= items) break;
+    // the cell block of this item: the last b with blk_chunk[b] <= item
+    int lo = 0, hi = a.nblk;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (a.blk_chunk[mid] <= item) lo = mid; else hi = mid;
+    }
+    const int b = lo;
+    const long long first = (long long)(item - a.blk_chunk[b]) * kBlockChunk;   // within the block's records
+    const long long last = first + kBlockChunk;
     for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) jt[t] = R(0);
     __syncthreads();
     const int bc[3] = {b % a.nb[0], (b / a.nb[0]) % a.nb[1], b / (a.nb[0] * a.nb[1])};
     const int torg[3] = {bc[0] * kBlockCells - 1, bc[1] * kBlockCells - 1, bc[2] * kBlockCells - 1};
     const int fam[3] = {kElectron, kPositron, kIon};
+    long long off = 0;   // records of the block's earlier species
     for (int f = 0; f < 3; ++f) {
       const int sp = fam[f];
       if (!a.blk_start[sp]) continue;
-      const long long lo = min((long long)a.blk_start[sp][b], ns[sp]);
-      const long long hi = min((long long)a.blk_start[sp][b + 1], ns[sp]);
-      for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const long long s0 = a.blk_start[sp][b], s1 = a.blk_start[sp][b + 1];
+      // this item's part of the species' records of the block
+      const long long lo_i = max(s0, s0 + first - off), hi_i = min(s1, s0 + last - off);
+      off += s1 - s0;
+      const long long lo2 = min(lo_i, ns[sp]);
+      const long long hi2 = min(hi_i, ns[sp]);
+      for (long long i = lo2 + threadIdx.x; i < hi2; i += blockDim.x) {
         Pt<R> q;
         int cell;
         load(a, sp, i, q, cell);
@@ -1393,9 +1452,10 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   a.nblk = c->nblk;
   for (int k = 0; k < 3; ++k) a.nb[k] = c->nb[k];
   for (int sp = 0; sp < 4; ++sp)
-    a.blk_start[sp] = (c->sorted && c->nblk > 0 && !c->key_ensembles && sp != kPhoton)
+    a.blk_start[sp] = (c->sorted && c->nblk > 0 && !c->key_ensembles && sp != kPhoton && c->st[sp].cap > 0)
                           ? c->d_blk_start + (size_t)sp * (c->nblk + 1) : nullptr;
   a.work = (unsigned *)(c->d_pend_count + kMaxPass + 2);
+  a.blk_chunk = c->d_blk_chunk;
   a.step_const = c->d_step_const;
   a.counters = c->d_counters;
   a.spectrum = c->d_spec;
@@ -1417,11 +1477,20 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     for (int k = 0; k < 3; ++k)
       if (cudaMemsetAsync(a.J[k], 0, nc * sizeof(R), s) != cudaSuccess) return QED_ERR_CUDA;
   }
+  a.grid_max = a.field_mode == kFieldGrid ? c->d_grid_max : nullptr;
+  a.eps_star_out = a.field_mode == kFieldGrid ? c->d_eps_star : nullptr;
+  if (a.grid_max && cudaMemsetAsync(c->d_grid_max, 0, sizeof(unsigned long long) * 6, s) != cudaSuccess)
+    return QED_ERR_CUDA;
   void *args[] = {(void *)&a};
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
   if (c->ev_start) cudaEventRecord(c->ev_start, s);
+  if (a.grid_max) {
+    c->launches += 1;
+    e = cudaLaunchKernel((const void *)k_grid_max<R>, dim3(c->num_sms * 4), dim3(256), args, 0, s);
+  }
   c->launches += 3;
-  e = cudaLaunchKernel((const void *)k_step_constants<R>, dim3(1),
+  if (e == cudaSuccess)
+    e = cudaLaunchKernel((const void *)k_step_constants<R>, dim3(1),
                        dim3(a.field_mode == kFieldEnsemble ? 256 : 32), args, 0, s);
   // concurrent: the e-/e+/ion pass runs on the side stream beside the
   // photon pass (fork after the step constants, join before the products)

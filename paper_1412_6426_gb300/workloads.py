@@ -207,6 +207,75 @@ def batched_ensembles(n_ens: int = 512, count_range=(1e3, 1e6), chi_range=(0.1, 
               "thin_interval": thin_interval, "thin_limit": tuple(thin_limit)})
 
 
+def self_consistent_cascade(n: int = 256, seed: int = 1, nsteps: int = 2000, wavelength_m: float = 0.8e-6,
+                            cells_per_lambda: int = 32, steps_per_period: int = 64,
+                            intensity_w_cm2: float = 1e24, n_seed: int = 100_000, seed_cube_m: float = 1e-6,
+                            precision: int = 32):
+    """A self-consistent QED cascade on a periodic Yee mesh: two counter-
+    propagating circularly polarised plane-wave pulses along +-x with a sin^2
+    envelope of 2 lambda intensity FWHM (4 lambda full width), each at the
+    given intensity, meeting at the box centre after 2 lambda of travel; a
+    cold seed of n_seed electrons and n_seed positrons uniform in a cube at the
+    centre.  Returns (workload, fields) with fields = [Ex, Ey, Ez, Bx, By, Bz]
+    on the Yee staggering at t = 0 (numpy arrays, x fastest)."""
+    rng = np.random.default_rng(seed)
+    lam = length(wavelength_m)
+    d = lam / cells_per_lambda
+    omega = laser_omega(wavelength_m)
+    t_laser = 2 * math.pi / omega
+    dt = t_laser / steps_per_period
+    a0 = a0_from_intensity(intensity_w_cm2, wavelength_m, circular=True)
+    E0 = a0_to_field(a0, wavelength_m)
+    L = n * d
+    xc = 0.5 * L
+    W = 4.0 * lam                              # full width of the sin^2 envelope (FWHM 2 lambda)
+    ftype = np.float32 if precision == 32 else np.float64
+
+    def envelope(u):
+        # sin^2 envelope centred at u = 0, zero outside |u| < W/2
+        e = np.sin(math.pi * (u / W + 0.5)) ** 2
+        return np.where(np.abs(u) < 0.5 * W, e, 0.0)
+
+    def wrap(u):
+        return (u + 0.5 * L) % L - 0.5 * L
+
+    def pulses(x, comp):
+        # pulse A moves +x from xc - 2 lam, pulse B moves -x from xc + 2 lam (t = 0)
+        ua = wrap(x - (xc - 2 * lam))
+        ub = wrap(x - (xc + 2 * lam))
+        pa = omega * ua
+        pb = omega * ub
+        fa, fb = E0 * envelope(ua), E0 * envelope(ub)
+        if comp == "Ey":
+            return fa * np.cos(pa) + fb * np.cos(pb)
+        if comp == "Ez":
+            return fa * np.sin(pa) + fb * np.sin(pb)
+        if comp == "By":      # B = +x x E for A, -x x E for B
+            return -fa * np.sin(pa) + fb * np.sin(pb)
+        if comp == "Bz":
+            return fa * np.cos(pa) - fb * np.cos(pb)
+        raise ValueError(comp)
+
+    xi = np.arange(n) * d                      # Ey, Ez at x = i d
+    xh = (np.arange(n) + 0.5) * d              # By, Bz at x = (i + 1/2) d
+    nc = n ** 3
+    f = [np.zeros(nc, dtype=ftype) for _ in range(6)]
+    for k, (comp, xs) in enumerate((("Ey", xi), ("Ez", xi))):
+        f[1 + k][:] = np.broadcast_to(pulses(xs, comp)[None, None, :], (n, n, n)).ravel()
+    for k, (comp, xs) in enumerate((("By", xh), ("Bz", xh))):
+        f[4 + k][:] = np.broadcast_to(pulses(xs, comp)[None, None, :], (n, n, n)).ravel()
+    side = length(seed_cube_m)
+    parts = {}
+    for sp in (ELECTRON, POSITRON):
+        x = xc + (rng.uniform(-0.5, 0.5, (n_seed, 3)) * side)
+        parts[sp] = (x, np.zeros((n_seed, 3)), np.ones(n_seed),
+                     np.arange(n_seed, dtype=np.uint64) + np.uint64(sp * n_seed))
+    w = Workload(name=f"cascade_{n}cubed_{intensity_w_cm2:g}Wcm2", n=(n, n, n), d=(d, d, d), x0=(0.0, 0.0, 0.0),
+                 periodic=(1, 1, 1), field_mode=FIELD_GRID, fp=(), dt=dt, nsteps=nsteps, particles=parts, seed=seed,
+                 meta={"a0": a0, "E0": E0, "omega": omega, "lambda": lam, "meet_step": 2 * steps_per_period})
+    return w, f
+
+
 def subset(w: Workload, species: int, index: np.ndarray) -> Workload:
     """The same workload restricted to the listed particles of one species."""
     x, p, wt, ids = w.particles[species]
