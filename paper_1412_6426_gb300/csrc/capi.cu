@@ -66,6 +66,7 @@ void release(qed_ctx *c) {
   cudaFree(c->d_std_cdf);
   cudaFree(c->d_grid_max);
   cudaFree(c->d_blk_chunk);
+  cudaFree(c->d_phot_start);
   cudaFree(c->d_std_lnw);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -240,7 +241,8 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     }
     c->nblk = (int)nblk;
     if (rc == QED_OK) rc = dalloc(&c->d_blk_start, sizeof(unsigned) * 4 * (nblk + 1));
-    if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (nblk + 1));
+    if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (nblk + 2));
+    if (rc == QED_OK) rc = dalloc(&c->d_phot_start, sizeof(unsigned) * (nblk + 2));
     if (rc == QED_OK) rc = dalloc(&c->d_grid_max, sizeof(unsigned long long) * 6);
     if (rc == QED_OK) rc = dalloc(&c->d_blk_chunk, sizeof(unsigned) * (nblk + 1));
   }
@@ -428,10 +430,10 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
     if (c->par.compact_interval > 0 && ++c->steps_since_compact >= c->par.compact_interval) {
       c->steps_since_compact = 0;
       for (int sp = 0; sp < 4; ++sp) {
-        // grid mode: re-sort the charged species by cell block; ensembles:
-        // optionally order e-, e+ and ions by ensemble; photons: compaction
-        const bool sort = sp != QED_PHOTON && c->nblk > 0 &&
-                          (grid || (c->key_ensembles && c->tune.sort_massive));
+        // grid mode: re-sort every species by cell block (photons that may
+        // pair by block, the others after them); ensembles: optionally order
+        // e-, e+ and ions by estimated sub-intervals; otherwise compaction
+        const bool sort = c->nblk > 0 && (grid || (sp != QED_PHOTON && c->key_ensembles && c->tune.sort_massive));
         rc = sort ? qed_launch_sort(c, sp, s) : qed_launch_compact(c, sp, true, s);
         if (rc != QED_OK) return rc;
       }

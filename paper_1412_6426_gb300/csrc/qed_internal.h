@@ -157,6 +157,7 @@ struct qed_ctx {
   unsigned *d_blk_start = nullptr;    // [4][nblk + 1] first record of each cell block
   unsigned *d_blk_cursor = nullptr;   // [nblk + 1] histogram / scatter cursors of the sort
   unsigned *d_blk_chunk = nullptr;    // [nblk + 1] first work item of each cell block
+  unsigned *d_phot_start = nullptr;   // [nblk + 2] photon sort starts (grid mode)
   int nb[3] = {0, 0, 0};
   int nblk = 0;
   int sorted = 0;                     // the stores are in cell-block order (up to the tail)

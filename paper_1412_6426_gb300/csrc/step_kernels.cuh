@@ -1262,6 +1262,7 @@ __global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
   constexpr int TTT = kTileNodes * kTileNodes * kTileNodes;
   __shared__ R jt[3 * TTT];
   __shared__ int blk;
+  __shared__ int next;
   __shared__ long long ns[4];
   Cnt cnt;
   const unsigned step = ((const StepConst *)a.step_const)->step;
@@ -1286,17 +1287,38 @@ __global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
     const int bc[3] = {b % a.nb[0], (b / a.nb[0]) % a.nb[1], b / (a.nb[0] * a.nb[1])};
     const int torg[3] = {bc[0] * kBlockCells - 1, bc[1] * kBlockCells - 1, bc[2] * kBlockCells - 1};
     const int fam[3] = {kElectron, kPositron, kIon};
-    long long off = 0;   // records of the block's earlier species
+    // this item's part of each species' records of the block
+    long long r0[3], rlen[3], off = 0;
     for (int f = 0; f < 3; ++f) {
       const int sp = fam[f];
+      r0[f] = 0;
+      rlen[f] = 0;
       if (!a.blk_start[sp]) continue;
       const long long s0 = a.blk_start[sp][b], s1 = a.blk_start[sp][b + 1];
-      // this item's part of the species' records of the block
-      const long long lo_i = max(s0, s0 + first - off), hi_i = min(s1, s0 + last - off);
+      const long long lo_i = min(max(s0, s0 + first - off), ns[sp]);
+      const long long hi_i = min(min(s1, s0 + last - off), ns[sp]);
       off += s1 - s0;
-      const long long lo2 = min(lo_i, ns[sp]);
-      const long long hi2 = min(hi_i, ns[sp]);
-      for (long long i = lo2 + threadIdx.x; i < hi2; i += blockDim.x) {
+      r0[f] = lo_i;
+      rlen[f] = hi_i > lo_i ? hi_i - lo_i : 0;
+    }
+    const int total = (int)(rlen[0] + rlen[1] + rlen[2]);
+    // warps take 32 records at a time, so fast warps take more
+    if (threadIdx.x == 0) next = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(&next, 32);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= total) break;
+      const int pos = base + lane;
+      if (pos >= total) continue;
+      int f = 0;
+      long long k = pos;
+      while (k >= rlen[f]) { k -= rlen[f]; ++f; }
+      const int sp = fam[f];
+      const long long i = r0[f] + k;
+      {
         Pt<R> q;
         int cell;
         load(a, sp, i, q, cell);

@@ -255,6 +255,11 @@ struct BlockGeom {
   int n_ens;
   const float *ens_h;      // per ensemble: |E0| + |Eu| + |Bu|
   float dt, kappa, mass;
+  // photons on the Yee mesh: those that may pair (|p| >= eps*) by cell
+  // block, so that their field gathers hit cached lines; the others, which
+  // take the straight flight, after them (key nkeys - 1)
+  int photon_split;
+  const double *eps_star;
 };
 
 __device__ __forceinline__ int block_of(int cell, const BlockGeom &g) {
@@ -279,6 +284,10 @@ __device__ __forceinline__ int nsub_key(uint64_t id, float p2, const BlockGeom &
 template <typename T>
 __device__ __forceinline__ int key_of(int cell, uint64_t id, const T &m, const BlockGeom &g) {
   if (g.nsub_key) return nsub_key(id, (float)p2_of(m), g);
+  if (g.photon_split) {
+    const double e = *g.eps_star;
+    if ((double)p2_of(m) < e * e) return g.nkeys - 1;
+  }
   return block_of(cell, g);
 }
 
@@ -385,15 +394,18 @@ int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
   g.dt = (float)c->last_dt;
   g.kappa = (float)c->par.kappa;
   g.mass = (sp == kIon || !c->par.emission_on) ? 0.f : (float)c->species.mass[sp];
+  g.photon_split = sp == kPhoton && !c->key_ensembles;
+  g.eps_star = c->d_eps_star;
+  if (g.photon_split) g.nkeys = c->nblk + 1;
   const int cur = st.cur, nxt = cur ^ 1;
-  unsigned *start = c->d_blk_start + (size_t)sp * (c->nblk + 1);
-  if (cudaMemsetAsync(c->d_blk_cursor, 0, sizeof(unsigned) * (c->nblk + 1), s) != cudaSuccess) return QED_ERR_CUDA;
+  unsigned *start = g.photon_split ? c->d_phot_start : c->d_blk_start + (size_t)sp * (c->nblk + 1);
+  if (cudaMemsetAsync(c->d_blk_cursor, 0, sizeof(unsigned) * (g.nkeys + 1), s) != cudaSuccess) return QED_ERR_CUDA;
   const int grid = c->num_sms * 8;
   c->launches += 3;
   k_blk_hist<T><<<grid, 256, 0, s>>>((const T *)st.mom[cur], st.id[cur], c->d_count, sp, (long long)st.cap, g,
                                      c->d_blk_cursor);
   // the record count to scatter is read on the device: the histogram keeps it
-  k_blk_scan<<<1, 1024, 0, s>>>(c->d_blk_cursor, c->nblk, start, c->d_count + 4, sp);   // total -> [4 + sp]
+  k_blk_scan<<<1, 1024, 0, s>>>(c->d_blk_cursor, g.nkeys, start, c->d_count + 4, sp);   // total -> [4 + sp]
   k_blk_scatter<T><<<grid, 256, 0, s>>>((const T *)st.pos[cur], (const T *)st.mom[cur], st.id[cur],
                                         (T *)st.pos[nxt], (T *)st.mom[nxt], st.id[nxt], c->d_count, sp,
                                         (long long)st.cap, g, c->d_blk_cursor);
