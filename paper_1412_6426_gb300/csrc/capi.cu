@@ -65,7 +65,6 @@ void release(qed_ctx *c) {
   cudaFree(c->d_ens_h);
   cudaFree(c->d_std_cdf);
   cudaFree(c->d_grid_max);
-  cudaFree(c->d_blk_chunk);
   cudaFree(c->d_phot_start);
   cudaFree(c->d_std_lnw);
   if (c->side) cudaStreamDestroy(c->side);
@@ -244,7 +243,6 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (nblk + 2));
     if (rc == QED_OK) rc = dalloc(&c->d_phot_start, sizeof(unsigned) * (nblk + 2));
     if (rc == QED_OK) rc = dalloc(&c->d_grid_max, sizeof(unsigned long long) * 6);
-    if (rc == QED_OK) rc = dalloc(&c->d_blk_chunk, sizeof(unsigned) * (nblk + 1));
   }
   if (g->field_mode == QED_FIELD_ENSEMBLE) {
     c->ens_cap = 1 << p->ens_bits;
@@ -415,8 +413,6 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
         int rs = sp == QED_PHOTON ? QED_OK : qed_launch_sort(c, sp, s);
         if (rs != QED_OK) return rs;
       }
-      int rs = qed_launch_block_chunks(c, s);
-      if (rs != QED_OK) return rs;
       c->sorted = 1;
       c->steps_since_compact = 0;
     }
@@ -437,7 +433,6 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
         rc = sort ? qed_launch_sort(c, sp, s) : qed_launch_compact(c, sp, true, s);
         if (rc != QED_OK) return rc;
       }
-      if (grid && c->nblk > 0 && (rc = qed_launch_block_chunks(c, s)) != QED_OK) return rc;
     }
   }
   return QED_OK;

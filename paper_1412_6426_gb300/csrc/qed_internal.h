@@ -23,7 +23,7 @@ constexpr int kNsubKeys = 64;             // sort keys of the sub-interval estim
 constexpr int kMaxBins = 4096;
 constexpr int kCompactTile = 2048;   // particles per tile of the compaction
 constexpr int kBlockCells = 8;       // cell block edge (grid mode): 8 x 8 x 8 cells
-constexpr int kBlockChunk = 1024;    // particles per work item of the cell-block kernel
+constexpr int kBlockChunk = 1024;    // records per work item of the cell-block kernel
 constexpr int kTileNodes = kBlockCells + 3;   // current tile edge: the deposit stencil of a
                                               // particle starting in the block stays inside
 
@@ -42,9 +42,12 @@ struct Store {
 
 // Everything the step kernel reads, passed by value.
 template <typename R> struct StepArgs {
-  // stores (current buffers)
+  // stores (current buffers), and the second buffers (free between
+  // compactions: the cell-block pass keeps its start records there)
   void *pos[4];
   void *mom[4];
+  void *pos_scratch[4];
+  void *mom_scratch[4];
   uint64_t *id[4];
   long long *count;        // [4] store sizes (live + dead), appended atomically
   const long long *nstart; // [4] sizes at the start of the step
@@ -103,7 +106,6 @@ template <typename R> struct StepArgs {
   int nb[3];
   int nblk;
   const unsigned *blk_start[4];
-  const unsigned *blk_chunk;   // nblk + 1: first work item of each cell block (kBlockChunk particles)
   unsigned *work;          // work-stealing counter of the cell-block kernel (zeroed per step)
   void *step_const;        // per-step field constants (written by k_step_constants)
   void *clock;             // device clock {t, step}: read and advanced once per step
@@ -156,7 +158,6 @@ struct qed_ctx {
   qed_tuning tune{};
   unsigned *d_blk_start = nullptr;    // [4][nblk + 1] first record of each cell block
   unsigned *d_blk_cursor = nullptr;   // [nblk + 1] histogram / scatter cursors of the sort
-  unsigned *d_blk_chunk = nullptr;    // [nblk + 1] first work item of each cell block
   unsigned *d_phot_start = nullptr;   // [nblk + 2] photon sort starts (grid mode)
   int nb[3] = {0, 0, 0};
   int nblk = 0;
@@ -194,7 +195,6 @@ int qed_launch_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t
                    cudaStream_t s);
 int qed_launch_compact(qed_ctx *c, int sp, bool partition, cudaStream_t s);
 int qed_launch_sort(qed_ctx *c, int sp, cudaStream_t s);
-int qed_launch_block_chunks(qed_ctx *c, cudaStream_t s);
 int qed_step_kernel_blocks(qed_ctx *c);
 int qed_launch_chi_star(qed_ctx *c, cudaStream_t s);
 int qed_launch_thin(qed_ctx *c, int sp, cudaStream_t s);

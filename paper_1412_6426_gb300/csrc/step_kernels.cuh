@@ -702,7 +702,7 @@ __device__ __noinline__ SampleCounts pair_samples(const StepArgs<R> &a, int pass
 template <typename R, bool EXT>
 __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, R t_span,
                                                 V3<R> E, V3<R> B, Cnt &cnt, const uint64_t *idp, unsigned step,
-                                                R *jt = nullptr, const int *torg = nullptr) {
+                                                bool deposit_later = false) {
   // start position (scalars: arrays handed to the deposit would live in
   // local memory for the whole loop)
   const int cs0 = q.ci[0], cs1 = q.ci[1], cs2 = q.ci[2];
@@ -787,11 +787,11 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
       count_outcome(a, emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B));
     }
   }
-  if (a.deposit && qc != R(0)) {
+  if (a.deposit && qc != R(0) && !deposit_later) {
     const int cs[3] = {cs0, cs1, cs2};
     const R os[3] = {os0, os1, os2};
     const Pt<R> fin = q;
-    if (!jt || !deposit_tile(a, jt, torg, cs, os, fin, qc * q.w)) deposit(a, cs, os, fin, qc * q.w);
+    deposit(a, cs, os, fin, qc * q.w);
   }
 }
 
@@ -913,6 +913,46 @@ __device__ __forceinline__ void flush(const Cnt &c, unsigned long long *g) {
 __device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m, int l) {
   return (__umulhi(n, m) + n) >> l;   // exact for n < 2^31 (Granlund-Montgomery)
 }
+
+// ----- the start records of the cell-block pass (second store buffer) ------
+__device__ __forceinline__ void copy_record(const StepArgs<float> &a, int sp, long long i) {
+  ((float4 *)a.pos_scratch[sp])[i] = ((const float4 *)a.pos[sp])[i];
+  ((float4 *)a.mom_scratch[sp])[i] = ((const float4 *)a.mom[sp])[i];
+}
+__device__ __forceinline__ void copy_record(const StepArgs<double> &a, int sp, long long i) {
+  const double2 *P = (const double2 *)a.pos[sp] + 2 * i, *M = (const double2 *)a.mom[sp] + 2 * i;
+  double2 *P2 = (double2 *)a.pos_scratch[sp] + 2 * i, *M2 = (double2 *)a.mom_scratch[sp] + 2 * i;
+  P2[0] = P[0]; P2[1] = P[1];
+  M2[0] = M[0]; M2[1] = M[1];
+}
+__device__ __forceinline__ void load_scratch(const StepArgs<float> &a, int sp, long long i, Pt<float> &q,
+                                             int &cell) {
+  unpack(__ldg((const float4 *)a.pos_scratch[sp] + i), __ldg((const float4 *)a.mom_scratch[sp] + i), q, cell);
+}
+__device__ __forceinline__ void load_scratch(const StepArgs<double> &a, int sp, long long i, Pt<double> &q,
+                                             int &cell) {
+  const double2 *P = (const double2 *)a.pos_scratch[sp] + 2 * i;
+  const double2 *M = (const double2 *)a.mom_scratch[sp] + 2 * i;
+  double2 p0 = __ldg(P), p1 = __ldg(P + 1), m0 = __ldg(M), m1 = __ldg(M + 1);
+  q.off[0] = p0.x; q.off[1] = p0.y; q.off[2] = p1.x; q.w = p1.y;
+  q.p = {m0.x, m0.y, m1.x};
+  cell = (int)m1.y;
+}
+template <typename R>
+__device__ __forceinline__ void decode_cell(const StepArgs<R> &a, int cell, int *ci) {
+  const unsigned row = fast_div((unsigned)cell, a.div_m[0], a.div_l[0]);
+  const unsigned slab = fast_div((unsigned)cell, a.div_m[1], a.div_l[1]);
+  ci[0] = cell - (int)row * a.n[0];
+  ci[1] = (int)row - (int)slab * a.n[1];
+  ci[2] = (int)slab;
+}
+template <typename R>
+__device__ __forceinline__ int block_of_cell(const StepArgs<R> &a, int cell) {
+  int ci[3];
+  decode_cell(a, cell, ci);
+  return ci[0] / kBlockCells + a.nb[0] * (ci[1] / kBlockCells + a.nb[1] * (ci[2] / kBlockCells));
+}
+
 
 // Pairs from the vacuum (Sec. V.B), once per step after the particles: in
 // every cell the field at the centre (CIC of the Yee mesh there, or the
@@ -1257,55 +1297,58 @@ __global__ void __launch_bounds__(kPhotonThreads, PhotonOcc<R>::blocks) k_photon
 // current into a shared-memory tile covering the block and the deposit
 // stencil's reach, which is then added to the global current with one atomic
 // per non-zero tile node.
+// Work items of the cell-block kernels: kBlockChunk consecutive records of
+// one species in cell-block order (the sorted prefix of each store).
+struct BlockItems {
+  long long nsort[3], nitem[3];
+  unsigned items;
+};
+
+template <typename R>
+__device__ __forceinline__ BlockItems block_items(const StepArgs<R> &a, const long long *ns) {
+  BlockItems b;
+  const int fam[3] = {kElectron, kPositron, kIon};
+  b.items = 0;
+  for (int f = 0; f < 3; ++f) {
+    const int sp = fam[f];
+    b.nsort[f] = a.blk_start[sp] ? min((long long)a.blk_start[sp][a.nblk], ns[sp]) : 0;
+    b.nitem[f] = (b.nsort[f] + kBlockChunk - 1) / kBlockChunk;
+    b.items += (unsigned)b.nitem[f];
+  }
+  return b;
+}
+
+// Grid mode: electrons, positrons and ions in cell-block order, advanced in
+// work items taken by work stealing; warps take 32 records at a time inside
+// an item, so fast warps take more.  The current is deposited afterwards by
+// k_deposit_blocks, from the start record each thread leaves in the store's
+// second buffer (free between compactions): keeping the Esirkepov stencil
+// out of this kernel keeps its code within the instruction cache.
 template <typename R, bool EXT>
 __global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
-  constexpr int TTT = kTileNodes * kTileNodes * kTileNodes;
-  __shared__ R jt[3 * TTT];
   __shared__ int blk;
   __shared__ int next;
   __shared__ long long ns[4];
   Cnt cnt;
   const unsigned step = ((const StepConst *)a.step_const)->step;
   if (threadIdx.x < 4) ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
-  const unsigned items = a.blk_chunk[a.nblk];
+  __syncthreads();
+  const BlockItems bi = block_items(a, ns);
+  const int fam[3] = {kElectron, kPositron, kIon};
+  const int lane = threadIdx.x & 31;
   for (;;) {
-    if (threadIdx.x == 0) blk = (int)atomicAdd(a.work, 1u);
-    __syncthreads();
-    const unsigned item = (unsigned)blk;
-    if (item >= items) break;
-    // the cell block of this item: the last b with blk_chunk[b] <= item
-    int lo = 0, hi = a.nblk;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (a.blk_chunk[mid] <= item) lo = mid; else hi = mid;
+    if (threadIdx.x == 0) {
+      blk = (int)atomicAdd(a.work, 1u);
+      next = 0;
     }
-    const int b = lo;
-    const long long first = (long long)(item - a.blk_chunk[b]) * kBlockChunk;   // within the block's records
-    const long long last = first + kBlockChunk;
-    for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) jt[t] = R(0);
     __syncthreads();
-    const int bc[3] = {b % a.nb[0], (b / a.nb[0]) % a.nb[1], b / (a.nb[0] * a.nb[1])};
-    const int torg[3] = {bc[0] * kBlockCells - 1, bc[1] * kBlockCells - 1, bc[2] * kBlockCells - 1};
-    const int fam[3] = {kElectron, kPositron, kIon};
-    // this item's part of each species' records of the block
-    long long r0[3], rlen[3], off = 0;
-    for (int f = 0; f < 3; ++f) {
-      const int sp = fam[f];
-      r0[f] = 0;
-      rlen[f] = 0;
-      if (!a.blk_start[sp]) continue;
-      const long long s0 = a.blk_start[sp][b], s1 = a.blk_start[sp][b + 1];
-      const long long lo_i = min(max(s0, s0 + first - off), ns[sp]);
-      const long long hi_i = min(min(s1, s0 + last - off), ns[sp]);
-      off += s1 - s0;
-      r0[f] = lo_i;
-      rlen[f] = hi_i > lo_i ? hi_i - lo_i : 0;
-    }
-    const int total = (int)(rlen[0] + rlen[1] + rlen[2]);
-    // warps take 32 records at a time, so fast warps take more
-    if (threadIdx.x == 0) next = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
+    unsigned item = (unsigned)blk;
+    if (item >= bi.items) break;
+    int f = 0;
+    while (item >= bi.nitem[f]) { item -= (unsigned)bi.nitem[f]; ++f; }
+    const int sp = fam[f];
+    const long long lo = (long long)item * kBlockChunk, hi = min(lo + kBlockChunk, bi.nsort[f]);
+    const int total = (int)(hi - lo);
     for (;;) {
       int base = 0;
       if (lane == 0) base = atomicAdd(&next, 32);
@@ -1313,49 +1356,114 @@ __global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
       if (base >= total) break;
       const int pos = base + lane;
       if (pos >= total) continue;
-      int f = 0;
-      long long k = pos;
-      while (k >= rlen[f]) { k -= rlen[f]; ++f; }
-      const int sp = fam[f];
-      const long long i = r0[f] + k;
-      {
-        Pt<R> q;
-        int cell;
-        load(a, sp, i, q, cell);
-        if (cell < 0) continue;
-        cnt.psteps[sp]++;
-        const unsigned row = fast_div((unsigned)cell, a.div_m[0], a.div_l[0]);
-        const unsigned slab = fast_div((unsigned)cell, a.div_m[1], a.div_l[1]);
-        q.ci[0] = cell - (int)row * a.n[0];
-        q.ci[1] = (int)row - (int)slab * a.n[1];
-        q.ci[2] = (int)slab;
-        V3<R> E, B;
-        gather_grid(a, q, E, B);
-        const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
-        if (!(probe == R(0))) {
-          count_rare(a, kCntNonfinite, 1u);
-          atomicOr(a.status, kStNonfinite);
-        }
-        advance_massive<R, EXT>(a, 0, sp, q, a.dt, E, B, cnt, a.id[sp] + i, step, jt, torg);
-        const int nc = finish_cell(a, q);
-        if (nc < 0) count_rare(a, kCntAbsorbed, 1u);
-        store(a, sp, i, q, nc, false);
+      const long long i = lo + pos;
+      Pt<R> q;
+      int cell;
+      load(a, sp, i, q, cell);
+      if (cell < 0) continue;
+      if (a.deposit) copy_record(a, sp, i);
+      cnt.psteps[sp]++;
+      const unsigned row = fast_div((unsigned)cell, a.div_m[0], a.div_l[0]);
+      const unsigned slab = fast_div((unsigned)cell, a.div_m[1], a.div_l[1]);
+      q.ci[0] = cell - (int)row * a.n[0];
+      q.ci[1] = (int)row - (int)slab * a.n[1];
+      q.ci[2] = (int)slab;
+      V3<R> E, B;
+      gather_grid(a, q, E, B);
+      const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
+      if (!(probe == R(0))) {
+        count_rare(a, kCntNonfinite, 1u);
+        atomicOr(a.status, kStNonfinite);
       }
+      advance_massive<R, EXT>(a, 0, sp, q, a.dt, E, B, cnt, a.id[sp] + i, step, true);
+      const int nc = finish_cell(a, q);
+      if (nc < 0) count_rare(a, kCntAbsorbed, 1u);
+      store(a, sp, i, q, nc, false);
     }
-    __syncthreads();
-    const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
-    for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) {
-      const R v = jt[t];
-      if (v == R(0)) continue;
-      const int c = t / TTT, r = t % TTT;
-      const int ti = r % kTileNodes, tj = (r / kTileNodes) % kTileNodes, tk = r / (kTileNodes * kTileNodes);
-      const int gi = wrapi(torg[0] + ti, a.n[0]), gj = wrapi(torg[1] + tj, a.n[1]),
-                gk = wrapi(torg[2] + tk, a.n[2]);
-      atomicAdd(a.J[c] + gk * nxy + gj * nx + gi, v);
-    }
-    __syncthreads();   // the tile and blk are reused by the next cell block
+    __syncthreads();   // blk and next are reused by the next item
   }
   flush(cnt, a.counters);
+}
+
+// The Esirkepov deposit of the records k_blocks advanced: start from the
+// second buffer, end from the store.  An item whose records all lie in one
+// cell block deposits into a shared tile of that block (the block plus the
+// stencil's reach), flushed with one global atomic per non-zero node; a
+// sparse item (several blocks) deposits straight into J.
+template <typename R>
+__global__ void __launch_bounds__(256, 2) k_deposit_blocks(const StepArgs<R> a) {
+  constexpr int TTT = kTileNodes * kTileNodes * kTileNodes;
+  __shared__ R jt[3 * TTT];
+  __shared__ int blk;
+  __shared__ long long ns[4];
+  if (threadIdx.x < 4) ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
+  __syncthreads();
+  const BlockItems bi = block_items(a, ns);
+  const int fam[3] = {kElectron, kPositron, kIon};
+  const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+  for (;;) {
+    if (threadIdx.x == 0) blk = (int)atomicAdd(a.work + 1, 1u);
+    __syncthreads();
+    unsigned item = (unsigned)blk;
+    if (item >= bi.items) break;
+    int f = 0;
+    while (item >= bi.nitem[f]) { item -= (unsigned)bi.nitem[f]; ++f; }
+    const int sp = fam[f];
+    const R qc = a.charge[sp];
+    const long long lo = (long long)item * kBlockChunk, hi = min(lo + kBlockChunk, bi.nsort[f]);
+    // one cell block for the whole item (start positions)?
+    Pt<R> qa, qb;
+    int ca, cb;
+    load_scratch(a, sp, lo, qa, ca);
+    load_scratch(a, sp, hi - 1, qb, cb);
+    int bl = -1;
+    if (ca >= 0 && cb >= 0) {
+      const int ba = block_of_cell(a, ca), bb = block_of_cell(a, cb);
+      if (ba == bb) bl = ba;
+    }
+    const bool tile = bl >= 0 && qc != R(0);
+    int torg[3] = {0, 0, 0};
+    if (tile) {
+      const int bc[3] = {bl % a.nb[0], (bl / a.nb[0]) % a.nb[1], bl / (a.nb[0] * a.nb[1])};
+      for (int c = 0; c < 3; ++c) torg[c] = bc[c] * kBlockCells - 1;
+      for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) jt[t] = R(0);
+    }
+    __syncthreads();
+    if (qc != R(0))
+      for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        Pt<R> q0, q1;
+        int c0, c1;
+        load_scratch(a, sp, i, q0, c0);
+        load(a, sp, i, q1, c1);
+        if (c0 < 0 || c1 < 0) continue;
+        int cs[3], ce[3];
+        decode_cell(a, c0, cs);
+        decode_cell(a, c1, ce);
+        // the end cell unwrapped next to the start (a step moves < 1 cell)
+        for (int c = 0; c < 3; ++c) {
+          int dc = ce[c] - cs[c];
+          const R disp = R(dc) + q1.off[c] - q0.off[c];
+          if (disp >= R(1)) dc -= a.n[c];
+          else if (disp <= R(-1)) dc += a.n[c];
+          q1.ci[c] = cs[c] + dc;
+        }
+        const R os[3] = {q0.off[0], q0.off[1], q0.off[2]};
+        if (!tile || !deposit_tile(a, jt, torg, cs, os, q1, qc * q1.w)) deposit(a, cs, os, q1, qc * q1.w);
+      }
+    __syncthreads();
+    if (tile) {
+      for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) {
+        const R v = jt[t];
+        if (v == R(0)) continue;
+        const int c = t / TTT, r = t % TTT;
+        const int ti = r % kTileNodes, tj = (r / kTileNodes) % kTileNodes, tk = r / (kTileNodes * kTileNodes);
+        const int gi = wrapi(torg[0] + ti, a.n[0]), gj = wrapi(torg[1] + tj, a.n[1]),
+                  gk = wrapi(torg[2] + tk, a.n[2]);
+        atomicAdd(a.J[c] + gk * nxy + gj * nx + gi, v);
+      }
+    }
+    __syncthreads();   // the tile and blk are reused by the next item
+  }
 }
 
 // Passes 1, 2, ...: products evolving for the rest of the step.  All blocks
@@ -1405,6 +1513,8 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     const Store &st = c->st[sp];
     a.pos[sp] = st.pos[st.cur];
     a.mom[sp] = st.mom[st.cur];
+    a.pos_scratch[sp] = st.pos[st.cur ^ 1];
+    a.mom_scratch[sp] = st.mom[st.cur ^ 1];
     a.id[sp] = st.id[st.cur];
     a.cap[sp] = st.cap;
     a.charge[sp] = (R)c->species.charge[sp];
@@ -1477,7 +1587,6 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     a.blk_start[sp] = (c->sorted && c->nblk > 0 && !c->key_ensembles && sp != kPhoton && c->st[sp].cap > 0)
                           ? c->d_blk_start + (size_t)sp * (c->nblk + 1) : nullptr;
   a.work = (unsigned *)(c->d_pend_count + kMaxPass + 2);
-  a.blk_chunk = c->d_blk_chunk;
   a.step_const = c->d_step_const;
   a.counters = c->d_counters;
   a.spectrum = c->d_spec;
@@ -1532,6 +1641,10 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   if (e == cudaSuccess && a.blk_start[kElectron]) {
     c->launches += 1;
     e = cudaLaunchKernel((const void *)k_blocks<R, EXT>, dim3(c->blocks_cells), dim3(256), args, 0, s);
+    if (e == cudaSuccess && a.deposit) {
+      c->launches += 1;
+      e = cudaLaunchKernel((const void *)k_deposit_blocks<R>, dim3(c->blocks_cells), dim3(256), args, 0, s);
+    }
   }
   if (e == cudaSuccess && conc) e = cudaStreamWaitEvent(s, c->ev_join, 0);
   else if (e == cudaSuccess)

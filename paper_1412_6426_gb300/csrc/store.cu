@@ -622,43 +622,6 @@ int thin(qed_ctx *c, int sp, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 
-// Work items of the cell-block kernel: block b holds n_b = the sum over the
-// sorted species of its records and gets ceil(n_b / kBlockChunk) items, so
-// that a crowded block (a cascade's centre) is shared by several CUDA
-// blocks; chunk[b] = first item of block b, chunk[nblk] = all items.
-__global__ void k_blk_chunks(const unsigned *start, int nblk, unsigned sorted_mask, unsigned *chunk) {
-  __shared__ unsigned part[1024];
-  __shared__ unsigned carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < nblk; base += 1024) {
-    const int i = base + threadIdx.x;
-    unsigned v = 0;
-    if (i < nblk) {
-      unsigned nb = 0;
-      for (int sp = 0; sp < 4; ++sp)
-        if (sorted_mask >> sp & 1u) {
-          const unsigned *st = start + (size_t)sp * (nblk + 1);
-          nb += st[i + 1] - st[i];
-        }
-      v = (nb + kBlockChunk - 1) / kBlockChunk;
-    }
-    part[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-      const unsigned add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-      __syncthreads();
-      part[threadIdx.x] += add;
-      __syncthreads();
-    }
-    if (i < nblk) chunk[i] = carry + part[threadIdx.x] - v;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry += part[1023];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) chunk[nblk] = carry;
-}
-
 Lattice lattice(const qed_ctx *c) {
   Lattice L;
   for (int k = 0; k < 3; ++k) {
@@ -756,15 +719,6 @@ int qed_launch_sort(qed_ctx *c, int sp, cudaStream_t s) {
 
 int qed_launch_count_live(qed_ctx *c, long long *d_live, cudaStream_t s) {
   return c->prec == 64 ? qed::count_live<double>(c, d_live, s) : qed::count_live<float>(c, d_live, s);
-}
-
-int qed_launch_block_chunks(qed_ctx *c, cudaStream_t s) {
-  unsigned mask = 0;
-  for (int sp = 0; sp < 4; ++sp)
-    if (sp != qed::kPhoton && c->st[sp].cap > 0) mask |= 1u << sp;
-  c->launches += 1;
-  qed::k_blk_chunks<<<1, 1024, 0, s>>>(c->d_blk_start, c->nblk, mask, c->d_blk_chunk);
-  return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 
 int qed_launch_thin(qed_ctx *c, int sp, cudaStream_t s) {
