@@ -470,6 +470,190 @@ def batched_oracle_sample(nsteps: int, workers: int) -> dict:
             "overflow": sum(r[2] for r in res)}
 
 
+# ----------------------------------------------------------------------------
+# the self-consistent cascade on the 256^3 Yee mesh
+CASCADE_STEPS = 2000
+CASCADE_CAPS = (30_000_000, 30_000_000, 1_200_000_000, 0)
+CASCADE_NAME = ("self-consistent 3D QED cascade: 256^3 periodic Yee mesh, dx = lambda/32 (lambda = 0.8 um), "
+                "dt = T_L/64, two counter-propagating CP plane-wave pulses at 1e24 W/cm^2 (sin^2 envelope, "
+                "2 lambda FWHM), seed 1e5 e- + 1e5 e+ cold in a 1 um cube, Esirkepov deposit + FDTD, "
+                "emission + Breit-Wheeler pairs, 2000 steps")
+
+
+def cascade_run(K: int, W: int, dist_barrier, e2e_at: int = 1200, e2e_steps: int = 2) -> dict:
+    """The 2000-step cascade: W warm-up steps, then K timed steps (each with
+    CUDA events on the stream; the fields alone, 600 MB, exceed L2).  The
+    step kernels are bracketed separately (qed_profile_events)."""
+    import numpy as np
+    import torch
+    from paper_1412_6426_gb300 import qed, workloads
+    from paper_1412_6426_gb300.sim import Simulation
+
+    w, f = workloads.self_consistent_cascade(nsteps=CASCADE_STEPS)
+    nc = len(f[0])
+    E = [torch.from_numpy(a).cuda() for a in f[:3]]
+    B = [torch.from_numpy(a).cuda() for a in f[3:]]
+    J = [torch.zeros(nc, dtype=torch.float32, device="cuda") for _ in range(3)]
+    stream = torch.cuda.current_stream()
+    K = min(K, CASCADE_STEPS - W)
+    with Simulation(w, precision=32, capacity=CASCADE_CAPS, deposit_on=1, compact_interval=8) as sim:
+        sim.set_grid_fields(E, B, J)
+        sim.set_all()
+        sim.step(W)
+        d0 = sim.diag()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        kev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(K)]
+        for trio in kev:
+            for e_ in trio:
+                e_.record(stream)
+        torch.cuda.synchronize()
+        dist_barrier()
+        sampler = ClockSampler(int(os.environ.get("BENCH_GPU_INDEX", torch.cuda.current_device())))
+        for k in range(K):
+            qed.qed_profile_events(sim.ctx, kev[k][0].cuda_event, kev[k][1].cuda_event, kev[k][2].cuda_event)
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        dist_barrier()
+        qed.qed_profile_events(sim.ctx, 0, 0, 0)
+        d1 = sim.diag()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = [a.elapsed_time(c) for a, _, c in kev]
+    psteps = d1["particle_steps"] - d0["particle_steps"]
+    appended = (d1["photons_created"] - d0["photons_created"]) + 2 * (d1["pairs_created"] - d0["pairs_created"])
+    out = {"particle_steps": psteps, "seconds": sum(step_ms) / 1e3, "kernel_seconds": sum(kern_ms) / 1e3,
+           "ms_per_step": sum(step_ms) / K, "steps": K, "ncell": nc, "appended": appended,
+           "launches": d1["kernel_launches"] - d0["kernel_launches"], "live_end": d1["count"],
+           "emissions": d1["emissions"] - d0["emissions"], "pairs": d1["pairs"] - d0["pairs"], "clocks": clocks,
+           "last_ms": step_ms[-50:]}
+    # end to end through the C ABI with host buffers, a few steps into the cascade
+    out["e2e"] = None
+    if e2e_steps:
+        w2, f2 = workloads.self_consistent_cascade(nsteps=CASCADE_STEPS)
+        E2 = [torch.from_numpy(a).cuda() for a in f2[:3]]
+        B2 = [torch.from_numpy(a).cuda() for a in f2[3:]]
+        J2 = [torch.zeros(nc, dtype=torch.float32, device="cuda") for _ in range(3)]
+        with Simulation(w2, precision=32, capacity=CASCADE_CAPS, deposit_on=1, compact_interval=8) as sim:
+            sim.set_grid_fields(E2, B2, J2)
+            sim.set_all()
+            sim.step(e2e_at)
+            live = sim.diag()["count"]
+            host, n = {}, {}
+            for sp in range(3):
+                cap = max(1, int(live[sp] * 1.5) + 4096)
+                host[sp] = tuple(torch.empty(sh, dtype=dt_, pin_memory=True) for sh, dt_ in
+                                 (((cap, 3), torch.float64), ((cap, 3), torch.float64), ((cap,), torch.float64),
+                                  ((cap,), torch.int64)))
+            def get_all():
+                for sp in range(3):
+                    x, p, wt, i = host[sp]
+                    n[sp] = qed.qed_particles_get(sim.ctx, sp, x.data_ptr(), p.data_ptr(), wt.data_ptr(),
+                                                  i.data_ptr(), len(wt), stream.cuda_stream)
+            get_all()
+            torch.cuda.synchronize()
+            h2d = d2h = ps = 0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(e2e_steps):
+                for sp in range(3):
+                    x, p, wt, i = host[sp]
+                    qed.qed_particles_set(sim.ctx, sp, x.data_ptr(), p.data_ptr(), wt.data_ptr(), i.data_ptr(),
+                                          n[sp], stream.cuda_stream)
+                    h2d += 64 * n[sp]
+                    ps += n[sp]
+                sim.step(1)
+                get_all()
+                d2h += 64 * sum(n.values())
+            e1.record(stream)
+            torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        out["e2e"] = {"value": ps / secs, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d // e2e_steps,
+                      "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps, "at_step": e2e_at}
+    return out
+
+
+def cascade_oracle_sample(nsteps: int) -> dict:
+    """The oracle on the same cascade, one core (the particles share the
+    mesh), over its first nsteps steps: all 2e5 seeds and the full 256^3
+    Yee mesh."""
+    import numpy as np
+    from oracle import drive
+    from paper_1412_6426_gb300 import workloads
+    w, f = workloads.self_consistent_cascade(nsteps=CASCADE_STEPS, precision=64)
+    fo = [a.astype(np.float64) for a in f]
+    Jo = [np.zeros_like(fo[0]) for _ in range(3)]
+    n0 = w.n_initial()
+    t0 = time.perf_counter()
+    _, diag, _, _ = drive.run(w.n, w.d, w.x0, w.periodic, w.field_mode, w.fp, w.dt, nsteps, w.particles,
+                              kappa=w.kappa, seed=w.seed, caps=(4 * n0, 4 * n0, 40 * n0, 1), fields=fo, J=Jo,
+                              deposit_on=1, yee=True)
+    secs = time.perf_counter() - t0
+    return {"value": diag["particle_steps"] / secs, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": (f"steps 0..{nsteps - 1} of the cascade (all 2e5 seeds and their products, the full 256^3 "
+                       f"Yee mesh with deposit and field update), FP64 oracle, one process (the particles share "
+                       f"the mesh)")}
+
+
+def main_cascade(args, world, rank, local):
+    import torch
+    import torch.distributed as tdist
+    from paper_1412_6426_gb300 import build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    build.build()
+    W = args.warmup
+    K = CASCADE_STEPS - W if args.steps == RUN_STEPS - 3 else args.steps
+    r = cascade_run(K, W, barrier, e2e_steps=0 if args.no_e2e else 2)
+    tot = float(r["particle_steps"])
+    mx = r["seconds"]
+    if world > 1:
+        t = torch.tensor([tot, mx], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t[:1], op=tdist.ReduceOp.SUM)
+        tdist.all_reduce(t[1:], op=tdist.ReduceOp.MAX)
+        tot, mx = float(t[0]), float(t[1])
+    if rank != 0:
+        if world > 1:
+            tdist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    # algorithmic bytes: particles (68 B per particle-step, 40 B per append)
+    # and the mesh (FDTD: 9 reads + 6 writes of 4 B per cell-step; J zeroed
+    # and accumulated: 12 + 12 B per cell-step)
+    algo = 68 * r["particle_steps"] + 40 * r["appended"] + (60 + 24) * r["ncell"] * r["steps"]
+    ach = algo / r["seconds"] / 1e9
+    line = {"metric": METRIC, "value": tot / mx, "unit": "particle-steps/s", "n_gpus": world, "steps": r["steps"],
+            "warmup": W, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": CASCADE_NAME, "precision": "fp32 fields, particles, push/rates; fp64 tables",
+                       "parallelism": f"independent boxes x{world}",
+                       "l2": "fields alone 600 MB, larger than L2 (no flush)", "compact_and_sort_interval": 8},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "traffic": None, "peak_source": peak_kind,
+                         "kernel": "whole step (all kernels: particles, deposit, FDTD, sort)",
+                         "algorithmic_bytes_per_step": algo / r["steps"]},
+            "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "events": {"emissions": r["emissions"], "pairs": r["pairs"], "live_at_end": r["live_end"],
+                       "step_kernels_ms_per_step": r["kernel_seconds"] * 1e3 / r["steps"],
+                       "last_steps_ms": round(sum(r["last_ms"]) / len(r["last_ms"]), 3)}}
+    if r["e2e"] is not None:
+        line["e2e"] = r["e2e"]
+    if not args.no_cpu:
+        cb = cascade_oracle_sample(6)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line))
+    if world > 1:
+        tdist.destroy_process_group()
+
+
 def main_batched(args, world, rank, local):
     import torch
     import torch.distributed as tdist
@@ -562,8 +746,9 @@ def main():
                     help="collision: emission generator (0 modified, 1 alternative, 2 standard)")
     ap.add_argument("--tuning", default="",
                     help="collision: qed_tuning fields, e.g. concurrent=1,photon_blocks_per_sm=2")
-    ap.add_argument("--workload", choices=("collision", "batched"), default="collision",
-                    help="collision: the beam-laser collision (the headline line); batched: 512 ensembles")
+    ap.add_argument("--workload", choices=("collision", "batched", "cascade"), default="collision",
+                    help="collision: the beam-laser collision (the headline line); batched: 512 ensembles; "
+                         "cascade: the self-consistent 256^3 cascade")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="batched: electron counts x this (smaller sets are for profiling captures)")
     ap.add_argument("--batch-steps", type=int, default=BATCH_STEPS, help="batched: steps of the run")
@@ -583,6 +768,20 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "cascade":
+        if args.impl == "reference":
+            if rank == 0:
+                cb = cascade_oracle_sample(6)
+                print(json.dumps({"metric": METRIC, "value": cb["value"], "unit": "particle-steps/s",
+                                  "n_gpus": args.gpus, "steps": 6, "warmup": 0, "higher_is_better": True,
+                                  "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                                  "impl": "reference", "config": {"workload": CASCADE_NAME, "sample": cb["sample"]},
+                                  "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                                  "e2e": {"value": cb["value"], "unit": "particle-steps/s",
+                                          "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+            return
+        main_cascade(args, world, rank, local)
+        return
     if args.workload == "batched":
         BATCH_SCALE, BATCH_STEPS, BATCH_AUTOTUNE = args.batch_scale, args.batch_steps, not args.no_autotune
         if args.impl == "reference":
