@@ -596,10 +596,44 @@ def cascade_oracle_sample(nsteps: int) -> dict:
                        f"the mesh)")}
 
 
+def cascade_profile_window(start: int, count: int, caps) -> None:
+    """For profiling captures: run the cascade to step `start`, then `count`
+    steps inside a CUDA profiler range (ncu --profile-from-start off)."""
+    import torch
+    from paper_1412_6426_gb300 import workloads
+    from paper_1412_6426_gb300.sim import Simulation
+    w, f = workloads.self_consistent_cascade(nsteps=CASCADE_STEPS)
+    nc = len(f[0])
+    E = [torch.from_numpy(a).cuda() for a in f[:3]]
+    B = [torch.from_numpy(a).cuda() for a in f[3:]]
+    J = [torch.zeros(nc, dtype=torch.float32, device="cuda") for _ in range(3)]
+    with Simulation(w, precision=32, capacity=caps, deposit_on=1, compact_interval=8) as sim:
+        sim.set_grid_fields(E, B, J)
+        sim.set_all()
+        sim.step(start)
+        torch.cuda.synchronize()
+        live0 = sim.diag()["count"]
+        torch.cuda.profiler.start()
+        sim.step(count)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        d = sim.diag()
+    print(json.dumps({"profile_window": [start, count], "live_before": live0, "live_after": d["count"],
+                      "status": d["status"]}))
+
+
 def main_cascade(args, world, rank, local):
     import torch
     import torch.distributed as tdist
     from paper_1412_6426_gb300 import build
+    if args.profile_window:
+        build.build()
+        torch.cuda.set_device(local)
+        a, b = (int(v) for v in args.profile_window.split(":"))
+        caps = tuple(int(float(v)) for v in args.cascade_caps.split(",")) + (0,) if args.cascade_caps \
+            else CASCADE_CAPS
+        cascade_profile_window(a, b, caps)
+        return
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -753,6 +787,9 @@ def main():
                     help="batched: electron counts x this (smaller sets are for profiling captures)")
     ap.add_argument("--batch-steps", type=int, default=BATCH_STEPS, help="batched: steps of the run")
     ap.add_argument("--no-autotune", action="store_true", help="batched: keep the default tuning")
+    ap.add_argument("--profile-window", default="",
+                    help="cascade: START:COUNT, run to START and profile COUNT steps (for ncu captures)")
+    ap.add_argument("--cascade-caps", default="", help="cascade: e-,e+,photon capacities (profiling)")
     args = ap.parse_args()
     if args.electrons != N_ELECTRONS:
         scale_workload(args.electrons)
