@@ -20,7 +20,7 @@ SRC = os.path.join(HERE, "qed_oracle.c")
 LIB = os.path.join(HERE, "libqed_oracle.so")
 
 ELECTRON, POSITRON, PHOTON, ION = 0, 1, 2, 3
-FIELD_GRID, FIELD_UNIFORM, FIELD_GAUSSIAN_LP, FIELD_ROTATING_E, FIELD_ENSEMBLE = 0, 1, 2, 3, 4
+FIELD_GRID, FIELD_UNIFORM, FIELD_GAUSSIAN_LP, FIELD_ROTATING_E, FIELD_ENSEMBLE, FIELD_STANDING_WAVE = 0, 1, 2, 3, 4, 5
 PURPOSE_EMIT, PURPOSE_PAIR, PURPOSE_CHILD, PURPOSE_KEEP, PURPOSE_THIN = 1, 2, 3, 4, 5
 ENS_STRIDE = 10  # per ensemble: E0, omega, phase, Eu[3], Bu[3], thin_scale
 GEN_MODIFIED, GEN_ALTERNATIVE, GEN_STANDARD = 0, 1, 2

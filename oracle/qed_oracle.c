@@ -69,7 +69,7 @@ enum { OR_PURPOSE_EMIT = 1, OR_PURPOSE_PAIR = 2, OR_PURPOSE_CHILD = 3, OR_PURPOS
        OR_PURPOSE_THIN = 5, OR_PURPOSE_SCHWINGER = 6 };
 #define OR_SCHWINGER_KIND 0x80   /* flag in the product kind of vacuum pairs */
 enum { OR_FIELD_GRID = 0, OR_FIELD_UNIFORM = 1, OR_FIELD_GAUSSIAN_LP = 2, OR_FIELD_ROTATING_E = 3,
-       OR_FIELD_ENSEMBLE = 4 };
+       OR_FIELD_ENSEMBLE = 4, OR_FIELD_STANDING_WAVE = 5 };
 #define OR_ENS_STRIDE 10  /* per ensemble: E0, omega, phase, Eu[3], Bu[3], thin_scale */
 /* photon-emission event generators of Sec. IV.F-G */
 enum { OR_GEN_MODIFIED = 0, OR_GEN_ALTERNATIVE = 1, OR_GEN_STANDARD = 2 };
@@ -400,7 +400,11 @@ void or_boris(double p[3], const double E[3], const double B[3], double q, doubl
  *  GAUSSIAN_LP  linearly polarised paraxial Gaussian pulse travelling along
  *               -x, E along y, B = -E along z:
  *               fp = {E0, omega, w0, tau_fwhm_intensity, xf, yf, zf, tf, phi0}
- *  ROTATING_E   E = E0 (cos wt, sin wt, 0), B = 0: fp = {E0, omega}      */
+ *  ROTATING_E   E = E0 (cos wt, sin wt, 0), B = 0: fp = {E0, omega}
+ *  STANDING_WAVE  plane standing wave along x of the avalanche cascade
+ *               (Sec. V): E_y = E0 sin(omega x) cos(omega t),
+ *               B_z = -E0 cos(omega x) sin(omega t) (so that at t = 0 only
+ *               E_y = E0 sin(2 pi x / lambda) is present): fp = {E0, omega} */
 void or_field(int mode, const double *fp, const double x[3], double t, double E[3], double B[3])
 {
     E[0] = E[1] = E[2] = 0.0;
@@ -426,6 +430,9 @@ void or_field(int mode, const double *fp, const double x[3], double t, double E[
     } else if (mode == OR_FIELD_ROTATING_E) {
         E[0] = fp[0] * cos(fp[1] * t);
         E[1] = fp[0] * sin(fp[1] * t);
+    } else if (mode == OR_FIELD_STANDING_WAVE) {
+        E[1] = fp[0] * sin(fp[1] * x[0]) * cos(fp[1] * t);
+        B[2] = -fp[0] * cos(fp[1] * x[0]) * sin(fp[1] * t);
     }
 }
 
@@ -1094,7 +1101,10 @@ static int64_t or_thin_limit(const or_params *P, int sp, uint32_t g)
  * ensemble has no table row belong to no group.  Survivors keep their order. */
 int or_thin(const or_params *P, or_store S[4], or_diag *D, uint32_t step)
 {
-    int64_t G = P->ens_bits > 0 ? (int64_t)P->n_ens : 1;
+    /* groups are ensembles only in the ensemble field mode; elsewhere the
+     * id bits only record a product's lineage and a species is one group */
+    const int by_ens = P->field_mode == OR_FIELD_ENSEMBLE && P->ens_bits > 0;
+    int64_t G = by_ens ? (int64_t)P->n_ens : 1;
     if (G <= 0) return 0;
     int64_t *count = (int64_t *)malloc(sizeof(int64_t) * (size_t)G);
     double *wall = (double *)malloc(sizeof(double) * (size_t)G);
@@ -1105,14 +1115,14 @@ int or_thin(const or_params *P, or_store S[4], or_diag *D, uint32_t step)
         or_store *s = &S[sp];
         for (int64_t g = 0; g < G; ++g) { count[g] = 0; wall[g] = 0.0; wsurv[g] = 0.0; }
         for (int64_t i = 0; i < s->n; ++i) {
-            uint32_t g = or_ensemble(P, s->id[i]);
+            uint32_t g = by_ens ? or_ensemble(P, s->id[i]) : 0;
             if ((int64_t)g >= G) continue;
             count[g]++;
             wall[g] += s->w[i];
         }
         /* the survivors of a group, and their weight */
         for (int64_t i = 0; i < s->n; ++i) {
-            uint32_t g = or_ensemble(P, s->id[i]);
+            uint32_t g = by_ens ? or_ensemble(P, s->id[i]) : 0;
             if ((int64_t)g >= G) continue;
             int64_t L = or_thin_limit(P, sp, g);
             if (count[g] <= L) continue;
@@ -1122,7 +1132,7 @@ int or_thin(const or_params *P, or_store S[4], or_diag *D, uint32_t step)
         }
         int64_t o = 0;
         for (int64_t i = 0; i < s->n; ++i) {
-            uint32_t g = or_ensemble(P, s->id[i]);
+            uint32_t g = by_ens ? or_ensemble(P, s->id[i]) : 0;
             int keep = 1;
             double w = s->w[i];
             int64_t L = (int64_t)g < G ? or_thin_limit(P, sp, g) : 0;

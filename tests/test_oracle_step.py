@@ -167,3 +167,32 @@ def test_gaussian_pulse_properties():
     Er, Br = o.field(o.FIELD_ROTATING_E, (2.0, 0.5), (1, 2, 3), 1.3)
     assert abs(math.hypot(Er[0], Er[1]) - 2.0) < 1e-15 and abs(math.atan2(Er[1], Er[0]) - 0.65) < 1e-15
     assert not Br.any()
+
+
+def test_standing_wave_field():
+    """The standing wave of the avalanche benchmark (Sec. VII.C): at t = 0
+    only E_y = E0 sin(2 pi x/lambda); at all times a vacuum solution of
+    Maxwell's equations (checked by central differences, c = 1):
+    dBz/dt = -dEy/dx and dEy/dt = -dBz/dx; |E| + |B| <= E0."""
+    lam = 2.5896e6
+    w = 2 * math.pi / lam
+    E0 = 1e-2
+    fp = (E0, w)
+    E, B = o.field(o.FIELD_STANDING_WAVE, fp, (lam / 8, 7.0, -3.0), 0.0)
+    assert abs(E[1] - E0 * math.sqrt(0.5)) < 1e-17 and E[0] == E[2] == 0 and not np.any(B)
+    E, B = o.field(o.FIELD_STANDING_WAVE, fp, (lam / 4, 0, 0), 0.0)
+    assert abs(E[1] - E0) < 1e-17
+    rng = np.random.default_rng(3)
+    h = lam * 1e-5
+    for x, t in rng.uniform(0, 3 * lam, (20, 2)):
+        Ey = lambda xx, tt: o.field(o.FIELD_STANDING_WAVE, fp, (xx, 0, 0), tt)[0][1]
+        Bz = lambda xx, tt: o.field(o.FIELD_STANDING_WAVE, fp, (xx, 0, 0), tt)[1][2]
+        dEdx = (Ey(x + h, t) - Ey(x - h, t)) / (2 * h)
+        dEdt = (Ey(x, t + h) - Ey(x, t - h)) / (2 * h)
+        dBdx = (Bz(x + h, t) - Bz(x - h, t)) / (2 * h)
+        dBdt = (Bz(x, t + h) - Bz(x, t - h)) / (2 * h)
+        scale = E0 * w
+        assert abs(dBdt + dEdx) < 1e-6 * scale and abs(dEdt + dBdx) < 1e-6 * scale
+        E, B = o.field(o.FIELD_STANDING_WAVE, fp, (x, 0, 0), t)
+        assert abs(E[1]) + abs(B[2]) <= E0 * (1 + 1e-15)
+        assert E[0] == E[2] == B[0] == B[1] == 0
