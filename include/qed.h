@@ -92,7 +92,11 @@ typedef enum qed_field_mode {
      * has no row sees no field.  A 10th entry thin_scale > 0 scales the
      * ensemble's thinning limits (floor(thin_limit[sp] * thin_scale)), so an
      * instance keeps a budget in proportion to its size. */
-    QED_FIELD_ENSEMBLE = 4
+    QED_FIELD_ENSEMBLE = 4,
+    /* plane standing wave along x (the avalanche cascade of Sec. V):
+     * E_y = E0 sin(omega x) cos(omega t), B_z = -E0 cos(omega x) sin(omega t),
+     * x the absolute position (lattice origin included): fp = {E0, omega} */
+    QED_FIELD_STANDING_WAVE = 5
 } qed_field_mode;
 
 #define QED_ENS_STRIDE 10    /* doubles per row of the ensemble table */
@@ -141,7 +145,12 @@ typedef struct qed_params {
                                    step (0 = 1/8 of the total capacity,
                                    at least 65536) */
     /* --- independent ensembles (QED_FIELD_ENSEMBLE) --- */
-    int32_t ens_bits;           /* top id bits naming the ensemble, 0..16 */
+    int32_t ens_bits;           /* top id bits naming the ensemble, 0..16;
+                                   products keep their parent's top bits.
+                                   In the other field modes the bits only
+                                   record lineage (which seed a product
+                                   descends from) and thinning treats each
+                                   species as one group */
     /* --- controlling the particle count (Sec. VI) --- */
     int32_t thin_interval;      /* thin after every step whose index s has
                                    (s + 1) % thin_interval == 0 (0 = never) */

@@ -165,7 +165,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     ncell *= g->n[k];
   }
   if (ncell >= (1ll << 31)) return QED_ERR_ARG;
-  if (g->field_mode < QED_FIELD_GRID || g->field_mode > QED_FIELD_ENSEMBLE || g->reserved != 0)
+  if (g->field_mode < QED_FIELD_GRID || g->field_mode > QED_FIELD_STANDING_WAVE || g->reserved != 0)
     return QED_ERR_ARG;
   if (g->field_mode == QED_FIELD_GRID)
     for (int k = 0; k < 3; ++k)
@@ -260,7 +260,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     }
   }
   if (thinning) {
-    c->thin_groups = p->ens_bits > 0 ? (1 << p->ens_bits) : 1;
+    c->thin_groups = (p->ens_bits > 0 && g->field_mode == QED_FIELD_ENSEMBLE) ? (1 << p->ens_bits) : 1;
     if (rc == QED_OK) rc = dalloc(&c->d_thin, (size_t)24 * c->thin_groups);
   }
   if (p->generator == QED_GEN_STANDARD) {

@@ -18,7 +18,10 @@ constexpr double kPi = 3.141592653589793;
 enum Species { kElectron = 0, kPositron = 1, kPhoton = 2, kIon = 3, kNSpecies = 4 };
 enum Purpose : uint32_t { kEmit = 1, kPair = 2, kChild = 3, kKeep = 4, kThin = 5, kSchwinger = 6 };
 constexpr unsigned kSchwingerKind = 0x80;   // flag in the product kind of vacuum pairs
-enum FieldMode { kFieldGrid = 0, kFieldUniform = 1, kFieldGaussianLP = 2, kFieldRotatingE = 3, kFieldEnsemble = 4 };
+enum FieldMode {
+  kFieldGrid = 0, kFieldUniform = 1, kFieldGaussianLP = 2, kFieldRotatingE = 3, kFieldEnsemble = 4,
+  kFieldStandingWave = 5
+};
 
 // Device status bits (folded into a qed_status by the host).
 enum StatusBit : int {

@@ -27,7 +27,7 @@ __global__ void k_chi_star(const R *tab, double kappa, int mode, qed_grid_desc g
   if (mode == qed::kFieldUniform)
     hmax = sqrt(g.fp[0] * g.fp[0] + g.fp[1] * g.fp[1] + g.fp[2] * g.fp[2]) +
            sqrt(g.fp[3] * g.fp[3] + g.fp[4] * g.fp[4] + g.fp[5] * g.fp[5]);
-  else if (mode == qed::kFieldRotatingE)
+  else if (mode == qed::kFieldRotatingE || mode == qed::kFieldStandingWave)
     hmax = fabs(g.fp[0]);
   else if (mode == qed::kFieldGaussianLP)
     hmax = 2.0 * fabs(g.fp[0]);

@@ -184,6 +184,9 @@ __device__ void step_constants(const StepArgs<R> &a, StepConst &k) {
              sqrt(a.fp[3] * a.fp[3] + a.fp[4] * a.fp[4] + a.fp[5] * a.fp[5]);
   else if (a.field_mode == kFieldRotatingE)
     k.hmax = fabs(a.fp[0]);
+  else if (a.field_mode == kFieldStandingWave)
+    // |E| + |B| = |E0| (|sin wx cos wt| + |cos wx sin wt|) <= |E0| (Cauchy-Schwarz)
+    k.hmax = fabs(a.fp[0]);
   else if (a.field_mode == kFieldGaussianLP)
     k.hmax = 2.0 * fabs(a.fp[0]);             // |E| = |B| <= E0 everywhere
   else if (a.field_mode == kFieldEnsemble)
@@ -214,6 +217,18 @@ __device__ void step_constants(const StepArgs<R> &a, StepConst &k) {
     sincospi(2.0 * f, &s, &c);
     k.ud[0] = a.fp[0] * c;
     k.ud[1] = a.fp[0] * s;
+  } else if (a.field_mode == kFieldStandingWave) {
+    // amplitudes of E_y (times sin wx) and B_z (times cos wx) at this step
+    double cyc = a.fp[1] * k.t * (1.0 / kTwoPi);
+    double f = cyc - rint(cyc), s, c;
+    sincospi(2.0 * f, &s, &c);
+    k.ud[1] = a.fp[0] * c;
+    k.ud[5] = -a.fp[0] * s;
+    // FP32 phase of wx in cycles, lattice part in 64-bit fixed point
+    k.c0 = cycles_fixed(a.fp[1] * a.x0[0] * (1.0 / kTwoPi));
+    const double K = a.fp[1] * a.dd[0] * (1.0 / kTwoPi);
+    k.kfix = cycles_fixed(K);
+    k.kf = (float)K;
   } else if (a.field_mode == kFieldGaussianLP) {
     double T0 = (k.t - a.fp[7]) - a.fp[4] + a.x0[0];
     k.c0 = cycles_fixed(a.fp[1] * T0 * (1.0 / kTwoPi));
@@ -240,6 +255,16 @@ __device__ void step_constants(const StepArgs<R> &a, StepConst &k) {
 // FP32: no FP64 instruction; the carrier phase comes from StepConst.
 __device__ void field_analytic(const StepArgs<float> &a, const StepConst &k, const Pt<float> &q,
                                V3<float> &E, V3<float> &B) {
+  if (a.field_mode == kFieldStandingWave) {
+    const unsigned long long ph = k.c0 + (unsigned long long)(unsigned)q.ci[0] * k.kfix;
+    float cyc = (float)(unsigned)(ph >> 32) * 2.3283064365386963e-10f + q.off[0] * k.kf;
+    cyc -= rintf(cyc);
+    float s, c;
+    sincospif(2.f * cyc, &s, &c);
+    E = {0.f, k.uf[1] * s, 0.f};
+    B = {0.f, 0.f, k.uf[5] * c};
+    return;
+  }
   if (a.field_mode != kFieldGaussianLP) {
     E = {k.uf[0], k.uf[1], k.uf[2]};
     B = {k.uf[3], k.uf[4], k.uf[5]};
@@ -270,6 +295,14 @@ __device__ void field_analytic(const StepArgs<float> &a, const StepConst &k, con
 // FP64: the same fields with every quantity in FP64.
 __device__ void field_analytic(const StepArgs<double> &a, const StepConst &k, const Pt<double> &q,
                                V3<double> &E, V3<double> &B) {
+  if (a.field_mode == kFieldStandingWave) {
+    const double xa = a.x0[0] + ((double)q.ci[0] + q.off[0]) * a.dd[0];
+    double s, c;
+    sincos(a.fp[1] * xa, &s, &c);
+    E = {0.0, k.ud[1] * s, 0.0};
+    B = {0.0, 0.0, k.ud[5] * c};
+    return;
+  }
   if (a.field_mode != kFieldGaussianLP) {
     E = {k.ud[0], k.ud[1], k.ud[2]};
     B = {k.ud[3], k.ud[4], k.ud[5]};

@@ -599,10 +599,13 @@ int thin(qed_ctx *c, int sp, cudaStream_t s) {
   const long long L = c->par.thin_limit[sp];
   if (st.cap == 0 || L <= 0 || !c->d_thin) return QED_OK;
   ThinArgs t;
-  t.ens_shift = c->par.ens_bits > 0 ? 64 - c->par.ens_bits : 64;
-  t.groups = c->par.ens_bits > 0 ? c->n_ens : 1;
+  // groups are ensembles only in the ensemble field mode; elsewhere the id
+  // bits only record lineage and the species is one group
+  const bool by_ens = c->par.ens_bits > 0 && c->grid.field_mode == QED_FIELD_ENSEMBLE;
+  t.ens_shift = by_ens ? 64 - c->par.ens_bits : 64;
+  t.groups = by_ens ? c->n_ens : 1;
   t.limit = L;
-  t.ens = (c->par.ens_bits > 0 && c->grid.field_mode == QED_FIELD_ENSEMBLE) ? c->d_ens : nullptr;
+  t.ens = by_ens ? c->d_ens : nullptr;
   t.seed = c->par.seed;
   t.clock = c->d_clock;
   t.n = (unsigned long long *)c->d_thin;

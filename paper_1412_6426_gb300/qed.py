@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libqed_gb300.so")
 QED_OK, QED_ERR_ARG, QED_ERR_CUDA, QED_ERR_CAPACITY, QED_ERR_NONFINITE = 0, 1, 2, 3, 4
 QED_ERR_TIMEOUT, QED_ERR_PMGT1, QED_ERR_STATE, QED_ERR_COURANT = 5, 6, 7, 8
 QED_ELECTRON, QED_POSITRON, QED_PHOTON, QED_ION = 0, 1, 2, 3
-QED_FIELD_GRID, QED_FIELD_UNIFORM, QED_FIELD_GAUSSIAN_LP, QED_FIELD_ROTATING_E, QED_FIELD_ENSEMBLE = 0, 1, 2, 3, 4
+QED_FIELD_GRID, QED_FIELD_UNIFORM, QED_FIELD_GAUSSIAN_LP, QED_FIELD_ROTATING_E, QED_FIELD_ENSEMBLE, QED_FIELD_STANDING_WAVE = (
+    0, 1, 2, 3, 4, 5)
 QED_ENS_STRIDE = 10
 QED_GEN_MODIFIED, QED_GEN_ALTERNATIVE, QED_GEN_STANDARD = 0, 1, 2
 QED_MAX_ENS_BITS = 16

@@ -24,8 +24,9 @@ LAMBDA_C_BAR = HBAR / (M_E * C_LIGHT)          # m
 TAU_C = HBAR / (M_E * C_LIGHT ** 2)            # s
 E_S = M_E ** 2 * C_LIGHT ** 3 / (Q_E * HBAR)   # V/m
 MC2_EV = M_E * C_LIGHT ** 2 / Q_E
+ALPHA = 7.2973525693e-3                        # fine-structure constant
 
-FIELD_GRID, FIELD_UNIFORM, FIELD_GAUSSIAN_LP, FIELD_ROTATING_E, FIELD_ENSEMBLE = 0, 1, 2, 3, 4
+FIELD_GRID, FIELD_UNIFORM, FIELD_GAUSSIAN_LP, FIELD_ROTATING_E, FIELD_ENSEMBLE, FIELD_STANDING_WAVE = 0, 1, 2, 3, 4, 5
 ENS_STRIDE = 10   # ensemble table row: E0, omega, phase, Eu[3], Bu[3], thin_scale
 ELECTRON, POSITRON, PHOTON, ION = 0, 1, 2, 3
 
@@ -274,6 +275,83 @@ def self_consistent_cascade(n: int = 256, seed: int = 1, nsteps: int = 2000, wav
                  periodic=(1, 1, 1), field_mode=FIELD_GRID, fp=(), dt=dt, nsteps=nsteps, particles=parts, seed=seed,
                  meta={"a0": a0, "E0": E0, "omega": omega, "lambda": lam, "meet_step": 2 * steps_per_period})
     return w, f
+
+
+def shower_t_rad(gamma0: float, H0: float) -> float:
+    """Radiation time of the shower benchmark (Sec. VII.A):
+    t_rad = 3.85 gamma0^(1/3) (E_S/H0)^(2/3) hbar^2/(m c e^2), and
+    hbar^2/(m c e^2) = (hbar/(m c^2)) / alpha in Compton units."""
+    return 3.85 * gamma0 ** (1.0 / 3.0) * (1.0 / H0) ** (2.0 / 3.0) / ALPHA
+
+
+def shower_cascade(n_seeds: int = 1000, gamma0: float = 2e5, H0: float = 0.2, dt_per_trad: float = 1e-3,
+                   t_end_trad: float = 2.0, seed: int = 1) -> Workload:
+    """Shower-type cascade of Sec. VII.A: n_seeds independent electrons with
+    gamma0 along +x in a constant magnetic field H0 (units of E_S) along z,
+    perpendicular to the motion.  The field is uniform and the particles are
+    test particles, so one run of n_seeds electrons is n_seeds independent
+    cascades (the benchmark averages 10^3 runs).  dt = dt_per_trad t_rad;
+    nsteps reaches t_end_trad t_rad.  The periodic box is larger than the
+    gyro-radius (uniform field: the wrap changes nothing)."""
+    t_rad = shower_t_rad(gamma0, H0)
+    dt = dt_per_trad * t_rad
+    nsteps = int(round(t_end_trad / dt_per_trad))
+    p0 = math.sqrt(gamma0 ** 2 - 1.0)
+    cells = 16
+    d = 4.0 * p0 / H0 / cells
+    x = np.zeros((n_seeds, 3))
+    x[:, 0] = 0.5 * cells * d
+    x[:, 1] = 0.5 * cells * d - p0 / H0          # orbit centred in the box
+    x[:, 2] = 0.5 * d
+    p = np.zeros((n_seeds, 3))
+    p[:, 0] = p0
+    return Workload(
+        name=f"shower_{n_seeds}e_gamma{gamma0:g}_H{H0:g}_dt{dt_per_trad:g}trad",
+        n=(cells, cells, 1), d=(d, d, d), x0=(0.0, 0.0, 0.0), periodic=(1, 1, 1),
+        field_mode=FIELD_UNIFORM, fp=(0.0, 0.0, 0.0, 0.0, 0.0, H0), dt=dt, nsteps=nsteps,
+        particles={ELECTRON: (x, p, np.ones(n_seeds), np.arange(n_seeds, dtype=np.uint64))},
+        seed=seed, meta={"t_rad": t_rad, "gamma0": gamma0, "H0": H0, "eps_cut": 1e-3 * gamma0})
+
+
+def avalanche_t_rad(E0: float) -> float:
+    """t_rad of the avalanche benchmark (Sec. VII.C): 14 (E_S/H0)^(2/3)
+    lambda_C/c, lambda_C = 2 pi hbar/(m c) the Compton wavelength, so
+    lambda_C/c is 2 pi Compton time units."""
+    return 14.0 * (1.0 / E0) ** (2.0 / 3.0) * 2.0 * math.pi
+
+
+def avalanche_cascade(n_seeds: int = 256, E0: float = 1e-2, wavelength_m: float = 1e-6,
+                      dt_large_trad: float = 173.0, substeps: int = 1, periods: float = 1.0,
+                      cells: int = 64, seed: int = 1) -> Workload:
+    """Avalanche-type cascade of Sec. VII.C: seed electrons at x = lambda/8
+    with p_y = 1000 (gamma0 ~ 1000) in the plane standing wave whose only
+    field at t = 0 is E_y = E0 sin(2 pi x/lambda) (FIELD_STANDING_WAVE).
+    The large step is dt_large_trad t_rad (173 t_rad: about 8 steps per
+    cycle); substeps > 1 divides it (substeps = 1018 gives 0.17 t_rad), so
+    both runs reach the same times.  The box is one wavelength, periodic (the
+    wave's period); y and z are one periodic cell.  Test particles: one run
+    holds n_seeds independent avalanches."""
+    lam = length(wavelength_m)
+    omega = laser_omega(wavelength_m)
+    t_rad = avalanche_t_rad(E0)
+    dt_large = dt_large_trad * t_rad
+    dt = dt_large / substeps
+    t_period = 2.0 * math.pi / omega
+    n_large = int(math.ceil(periods * t_period / dt_large))
+    d = lam / cells
+    x = np.empty((n_seeds, 3))
+    x[:, 0] = lam / 8.0
+    x[:, 1] = 0.5 * lam
+    x[:, 2] = 0.5 * lam
+    p = np.zeros((n_seeds, 3))
+    p[:, 1] = 1000.0
+    return Workload(
+        name=f"avalanche_{n_seeds}e_E{E0:g}_dt{dt / t_rad:.4g}trad",
+        n=(cells, 1, 1), d=(d, lam, lam), x0=(0.0, 0.0, 0.0), periodic=(1, 1, 1),
+        field_mode=FIELD_STANDING_WAVE, fp=(E0, omega), dt=dt, nsteps=n_large * substeps,
+        particles={ELECTRON: (x, p, np.ones(n_seeds), np.arange(n_seeds, dtype=np.uint64))},
+        seed=seed, meta={"t_rad": t_rad, "dt_large": dt_large, "substeps": substeps, "n_large": n_large,
+                         "omega": omega, "lambda": lam, "t_period": t_period})
 
 
 def subset(w: Workload, species: int, index: np.ndarray) -> Workload:

@@ -109,6 +109,7 @@ def test_header_constants_match_binding():
     assert int(consts["QED_ABI_VERSION"]) == 2
     modes = dict(re.findall(r"(QED_FIELD_\w+) = (\d+)", text))
     assert int(modes["QED_FIELD_ENSEMBLE"]) == qed.QED_FIELD_ENSEMBLE == workloads.FIELD_ENSEMBLE
+    assert int(modes["QED_FIELD_STANDING_WAVE"]) == qed.QED_FIELD_STANDING_WAVE == workloads.FIELD_STANDING_WAVE
 
 
 def _descs():
@@ -160,7 +161,7 @@ def test_argument_validation(lib, bad):
     elif bad == "ng":
         p.pair_ng = 65
     elif bad == "mode":
-        g.field_mode = 5
+        g.field_mode = 6
     elif bad == "generator":
         p.generator = 3
     elif bad == "generator_factor":

@@ -1,0 +1,217 @@
+"""Cascade benchmarks of Sec. VII run as self-consistency tests of the
+adaptive event generator (Sec. IV.H): a run whose time step needs no
+subdivision and a run whose time step the generator subdivides at almost
+every occasion must develop the same cascade.  The literature curves the
+paper compares with are not reproduced here; the paper's own check, small
+against large time step, is.
+
+Standing-wave field (the avalanche's field): FP64 parity with the oracle
+(same ids, momenta within 1e-12) and FP32 statistics.
+
+Shower (Sec. VII.A): 256 electrons with gamma0 = 2e5 in H0 = 0.2 E_S
+perpendicular to the motion; the number of particles with energy above
+1e-3 gamma0 per seed at t = 0.5, 1, 1.5, 2 t_rad with dt = 1e-3 t_rad (no
+subdivision above gamma ~ 130) and dt = 0.5 t_rad (hundreds of
+sub-intervals).  The uniform
+field makes the two runs the same physics, so their means agree within the
+statistical error (per-seed variance; products carry their seed in the top
+id bits).
+
+Avalanche (Sec. VII.C): electrons at x = lambda/8 with p_y = 1000 in the
+standing wave E_y(t=0) = 1e-2 E_S sin(2 pi x/lambda), lambda = 1 um;
+dt = 0.17 t_rad against dt = 173 t_rad (8 field evaluations per cycle); the
+mean number of e+- per seed against time, with and without thinning
+(Sec. VI, global even redistribution).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1412_6426_gb300 import workloads
+from tests.util import box_scale, compare, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_1412_6426_gb300 import build
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    build.build()
+
+
+def standing_wave_case(n=1000, nsteps=60, seed=11):
+    """Electrons spread over one wavelength of the avalanche's standing wave,
+    random directions, |p| 1000..4000, dt = 0.17 t_rad."""
+    w = workloads.avalanche_cascade(n_seeds=1, substeps=1018, seed=seed)
+    rng = np.random.default_rng(seed)
+    lam = w.meta["lambda"]
+    x = np.column_stack([rng.uniform(0, lam, n), rng.uniform(0, lam, n), rng.uniform(0, lam, n)])
+    dirs = rng.standard_normal((n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    p = dirs * rng.uniform(1000, 4000, n)[:, None]
+    w.particles = {0: (x, p, np.ones(n), np.arange(n, dtype=np.uint64))}
+    w.nsteps = nsteps
+    return w
+
+
+def test_fp64_standing_wave_parity():
+    w = standing_wave_case()
+    ora, od, _, _ = run_oracle(w)
+    assert od["overflow"] == 0
+    gpu, gd = run_gpu(w, precision=64)
+    assert gd["status"] == 0, gd
+    rep = compare(gpu, ora, rtol_p=1e-12, xtol=1e-12 * box_scale(w))
+    assert rep["ok"], rep
+    for k in ("emissions", "pairs", "substeps_lepton", "substeps_photon"):
+        assert gd[k] == od[k], (k, gd[k], od[k])
+    assert gd["emissions"] > 50 and gd["pairs"] > 0
+
+
+def test_fp32_standing_wave_statistics():
+    w = standing_wave_case(n=3000, seed=12)
+    ora, od, _, _ = run_oracle(w)
+    gpu, gd = run_gpu(w, precision=32)
+    assert gd["status"] == 0
+    assert abs(gd["emissions"] - od["emissions"]) <= 3 * math.sqrt(od["emissions"]) and od["emissions"] > 500
+    xg, pg, _, ig = gpu[0]
+    xo, po, _, io = ora[0]
+    common, a, b = np.intersect1d(ig, io, return_indices=True)
+    assert len(common) >= 0.99 * len(io)
+    rel = np.linalg.norm(pg[a] - po[b], axis=1) / np.linalg.norm(po[b], axis=1)
+    assert np.median(rel) < 1e-5 and np.quantile(rel, 0.95) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# per-seed counts, computed on the device from the library's particle read
+
+def seed_counts(sim, species, eps_cut, ens_bits, n_seeds):
+    """Weighted number of particles of the given species with energy above
+    eps_cut, per seed (top ens_bits id bits), as a float64 numpy array."""
+    import torch
+    from paper_1412_6426_gb300 import qed
+    out = np.zeros(n_seeds)
+    for sp in species:
+        cap = max(sim.caps[sp], 1)
+        x = torch.empty((cap, 3), dtype=torch.float64, device="cuda")
+        p = torch.empty((cap, 3), dtype=torch.float64, device="cuda")
+        wt = torch.empty(cap, dtype=torch.float64, device="cuda")
+        ids = torch.empty(cap, dtype=torch.int64, device="cuda")
+        n = qed.qed_particles_get(sim.ctx, sp, x.data_ptr(), p.data_ptr(), wt.data_ptr(), ids.data_ptr(), cap,
+                                  sim.stream.cuda_stream)
+        if n == 0:
+            continue
+        m2 = 0.0 if sp == workloads.PHOTON else 1.0
+        eps = torch.sqrt(m2 + (p[:n] ** 2).sum(1))
+        seed = (ids[:n] >> (64 - ens_bits)) & ((1 << ens_bits) - 1)
+        sel = eps > eps_cut
+        c = torch.bincount(seed[sel], weights=wt[:n][sel], minlength=n_seeds)[:n_seeds]
+        out += c.cpu().numpy()
+    return out
+
+
+def tagged(w, ens_bits):
+    """Put seed i's index in the top ens_bits bits of its id."""
+    x, p, wt, ids = w.particles[workloads.ELECTRON]
+    tag = (np.arange(len(ids), dtype=np.uint64) << np.uint64(64 - ens_bits))
+    w.particles = {workloads.ELECTRON: (x, p, wt, tag)}
+    w.ens_bits = ens_bits
+    return w
+
+
+def run_series(w, chunk, samples, species, eps_cut, ens_bits, precision=32, caps=None, **opts):
+    """Run w for samples x chunk steps, recording per-seed counts after each
+    chunk; returns (array[samples, n_seeds], diagnostics)."""
+    from paper_1412_6426_gb300.sim import Simulation
+    n_seeds = len(w.particles[workloads.ELECTRON][3])
+    rows = []
+    with Simulation(w, precision=precision, capacity=caps, **opts) as sim:
+        sim.set_all()
+        for _ in range(samples):
+            sim.step(chunk)
+            d = sim.diag(check=False)
+            assert d["status"] == 0, d
+            rows.append(seed_counts(sim, species, eps_cut, ens_bits, n_seeds))
+    return np.array(rows), d
+
+
+def mean_and_error(rows):
+    n = rows.shape[1]
+    return rows.mean(1), rows.std(1, ddof=1) / math.sqrt(n)
+
+
+def test_shower_small_vs_large_dt():
+    bits, S = 8, 256
+    small = tagged(workloads.shower_cascade(n_seeds=S, dt_per_trad=1e-3, seed=21), bits)
+    large = tagged(workloads.shower_cascade(n_seeds=S, dt_per_trad=0.5, seed=22), bits)
+    cut = small.meta["eps_cut"]
+    # the soft photons dominate the memory: ~3e5 per seed by 2 t_rad, and a
+    # large step creates most of its photons within one step
+    caps = (4_000_000, 4_000_000, 150_000_000, 0)
+    species = (workloads.ELECTRON, workloads.POSITRON, workloads.PHOTON)
+    rs, ds = run_series(small, 500, 4, species, cut, bits, caps=caps)
+    rl, dl = run_series(large, 1, 4, species, cut, bits, caps=caps, nsub_max=100_000,
+                        pending_capacity=100_000_000)
+    assert ds["capped"] == 0 and dl["capped"] == 0
+    lep_s = ds["species_steps"][0] + ds["species_steps"][1]
+    lep_l = dl["species_steps"][0] + dl["species_steps"][1]
+    print("shower sub-intervals per lepton step: small", ds["substeps_lepton"] / lep_s,
+          "large", dl["substeps_lepton"] / lep_l)
+    # at 1e-3 t_rad only leptons below gamma ~ 130 are subdivided (few
+    # sub-intervals each); at 0.5 t_rad every lepton is, the softest into
+    # over a thousand sub-intervals
+    assert ds["substeps_lepton"] < 3.0 * lep_s
+    assert dl["substeps_lepton"] > 100 * lep_l
+    ms, es = mean_and_error(rs)
+    ml, el = mean_and_error(rl)
+    z = (ms - ml) / np.sqrt(es ** 2 + el ** 2)
+    print("shower per-seed counts above 1e-3 eps0 at t/t_rad = 0.5, 1, 1.5, 2: small", ms, "large", ml, "z", z)
+    assert ms[0] > 2.0 and ms[-1] > 5 * ms[0]      # the shower develops
+    assert np.all(np.abs(z) < 4.0), (ms, ml, z)
+
+
+def avalanche_series(substeps, S, bits, thin=None, periods=1.5, seed=31):
+    w = tagged(workloads.avalanche_cascade(n_seeds=S, substeps=substeps, periods=periods, seed=seed), bits)
+    opts = {"nsub_max": 100_000}
+    if thin is not None:
+        opts.update(thin_interval=1, thin_limit=thin)
+    caps = (8_000_000, 8_000_000, 40_000_000, 0)
+    rows, d = run_series(w, substeps, w.meta["n_large"], (workloads.ELECTRON, workloads.POSITRON), 0.0, bits,
+                         caps=caps, **opts)
+    return rows, d, w
+
+
+def test_avalanche_small_vs_large_dt_and_thinning():
+    bits, S = 8, 256
+    rs, ds, _ = avalanche_series(1018, S, bits, seed=32)     # dt = 0.17 t_rad
+    rl, dl, _ = avalanche_series(1, S, bits)                 # dt = 173 t_rad, 8 steps a cycle
+    r8, d8, _ = avalanche_series(8, S, bits, seed=33)        # dt = 21.6 t_rad
+    rt, dt_, _ = avalanche_series(1, S, bits, thin=(100 * S, 100 * S, 200 * S, 0))
+    ms, es = mean_and_error(rs)
+    ml, el = mean_and_error(rl)
+    m8, e8 = mean_and_error(r8)
+    mt, et = mean_and_error(rt)
+    print("avalanche e+- per seed every 173 t_rad:\n small", ms, "\n large", ml, "\n dt/8 ", m8,
+          "\n thinned", mt)
+    lep = lambda d: d["species_steps"][0] + d["species_steps"][1]
+    assert ds["substeps_lepton"] < 1.05 * lep(ds)           # 0.17 t_rad: no subdivision
+    assert dl["substeps_lepton"] > 100 * lep(dl)            # 173 t_rad: subdivided throughout
+    assert ds["capped"] == dl["capped"] == 0
+    # the avalanche grows by three orders of magnitude in 1.5 cycles
+    assert ms[-1] > 1000.0 and ml[-1] > 1000.0
+    # 8 field evaluations a cycle slow the growth a little (the push, not the
+    # event generator: the error shrinks with the step) -- final counts within
+    # a factor 1.5, and within 10% at an 8 times smaller step
+    assert 1 / 1.5 < ml[-1] / ms[-1] < 1.5, (ms, ml)
+    assert abs(m8[-1] / ms[-1] - 1.0) < 0.10 + 4 * math.hypot(e8[-1] / m8[-1], es[-1] / ms[-1]), (ms, m8)
+    assert abs(m8[-1] / ms[-1] - 1.0) < abs(ml[-1] / ms[-1] - 1.0)
+    # thinning (global even redistribution, every step) keeps the weighted
+    # count: identical until the first thinning, then within 4 sigma
+    assert dt_["thinned"] > 0
+    first = np.argmax(rt.sum(1) != rl.sum(1))
+    assert first > 0 and np.array_equal(rt[:first], rl[:first])
+    zt = (mt[first:] - ml[first:]) / np.sqrt(et[first:] ** 2 + el[first:] ** 2)
+    assert np.all(np.abs(zt) < 4.0), (ml, mt, zt)
