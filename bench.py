@@ -23,6 +23,10 @@ per-ensemble thinning, 500 steps of dt = T_laser/100 in FP32.  The first
 steps run under the autotuner; the rest are replays of a CUDA graph that
 holds a whole number of thinning intervals and an even number of
 compactions.  Its working set (GBs) is far larger than L2.
+
+--workload cascade times the self-consistent 256^3 cascade (2000 steps) and
+--workload cascade512 a window (steps 40..60 by default) of the large 512^3
+cascade with its hydrogen slab target, FP32 and FP64.
 """
 from __future__ import annotations
 
@@ -688,6 +692,222 @@ def main_cascade(args, world, rank, local):
         tdist.destroy_process_group()
 
 
+LARGE_NAME = ("large self-consistent 3D QED cascade: 512^3 periodic Yee mesh, dx = lambda/32 (lambda = 0.8 um), "
+              "dt = T_L/64, four CP plane-wave pulses at 2e24 W/cm^2 (two along x, two along y; sin^2 envelope "
+              "of half the box), hydrogen slab 1e22 cm^-3, 0.5 um thick, 8 ppc e- and p+ (4.2e7 each), "
+              "Esirkepov deposit + FDTD, emission + Breit-Wheeler pairs, thinning every 8 steps")
+LARGE_WARMUP, LARGE_STEPS = 40, 20
+
+
+def large_setup(precision: int, n: int = 512):
+    import torch
+    from paper_1412_6426_gb300 import workloads
+    w, fx, fy = workloads.large_cascade(n=n)
+    dt_ = torch.float32 if precision == 32 else torch.float64
+    F = workloads.expand_profiles(fx, fy, n, xp=torch, dtype=dt_, device="cuda")
+    J = [torch.zeros(n ** 3, dtype=dt_, device="cuda") for _ in range(3)]
+    opts = dict(precision=precision, capacity=w.meta["capacity%d" % precision], deposit_on=1,
+                compact_interval=8, thin_interval=w.meta["thin_interval"], thin_limit=w.meta["thin_limit"],
+                pending_capacity=50_000_000)
+    return w, F, J, opts
+
+
+def large_device(precision: int, K: int, W: int, dist_barrier) -> dict:
+    """W untimed steps of the 512^3 cascade, then K steps each bracketed by
+    CUDA events on the stream (the mesh alone, 4.8 GB in FP32, exceeds L2)."""
+    import torch
+    from paper_1412_6426_gb300.sim import Simulation
+    w, F, J, opts = large_setup(precision)
+    stream = torch.cuda.current_stream()
+    with Simulation(w, **opts) as sim:
+        sim.set_grid_fields(F[:3], F[3:], J)
+        sim.set_all()
+        sim.step(W)
+        d0 = sim.diag()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        dist_barrier()
+        sampler = ClockSampler(int(os.environ.get("BENCH_GPU_INDEX", torch.cuda.current_device())))
+        for k in range(K):
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        dist_barrier()
+        d1 = sim.diag()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    psteps = d1["particle_steps"] - d0["particle_steps"]
+    appended = (d1["photons_created"] - d0["photons_created"]) + 2 * (d1["pairs_created"] - d0["pairs_created"])
+    ncell = w.n[0] * w.n[1] * w.n[2]
+    r = 4 if precision == 32 else 8
+    # particles (68 / 120 B per particle-step, 40 / 68 B per append) and the mesh
+    # (FDTD: 9 reads + 6 writes a cell-step; J zeroed and accumulated: 3 + 3)
+    algo = (BYTES_PER_STEP[precision] * psteps + BYTES_PER_APPEND[precision] * appended
+            + 21 * r * ncell * K)
+    return {"particle_steps": psteps, "seconds": sum(step_ms) / 1e3, "ms_per_step": sum(step_ms) / K,
+            "steps": K, "warmup": W, "appended": appended, "algo_bytes": algo, "clocks": clocks,
+            "launches": d1["kernel_launches"] - d0["kernel_launches"], "live_end": d1["count"],
+            "emissions": d1["emissions"] - d0["emissions"], "pairs": d1["pairs"] - d0["pairs"],
+            "thinned": d1["thinned"] - d0["thinned"], "precision": precision}
+
+
+def large_e2e(at: int = 1) -> dict:
+    """One step through the C ABI with page-locked host buffers: every
+    species' records copied in before the step and read back after it."""
+    import torch
+    from paper_1412_6426_gb300 import qed
+    from paper_1412_6426_gb300.sim import Simulation
+    w, F, J, opts = large_setup(32)
+    stream = torch.cuda.current_stream()
+    with Simulation(w, **opts) as sim:
+        sim.set_grid_fields(F[:3], F[3:], J)
+        sim.set_all()
+        sim.step(at)
+        live = sim.diag()["count"]
+        host, n = {}, {}
+        for sp in range(4):
+            # early in the run the photons grow by millions a step
+            cap = int(live[sp] * 1.3) + (30_000_000 if sp == 2 else 1_000_000)
+            host[sp] = tuple(torch.empty(sh, dtype=dt_, pin_memory=True) for sh, dt_ in
+                             (((cap, 3), torch.float64), ((cap, 3), torch.float64), ((cap,), torch.float64),
+                              ((cap,), torch.int64)))
+
+        def get_all():
+            for sp in range(4):
+                x, p, wt, i = host[sp]
+                n[sp] = qed.qed_particles_get(sim.ctx, sp, x.data_ptr(), p.data_ptr(), wt.data_ptr(),
+                                              i.data_ptr(), len(wt), stream.cuda_stream)
+        get_all()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h2d = ps = 0
+        for sp in range(4):
+            x, p, wt, i = host[sp]
+            qed.qed_particles_set(sim.ctx, sp, x.data_ptr(), p.data_ptr(), wt.data_ptr(), i.data_ptr(),
+                                  n[sp], stream.cuda_stream)
+            h2d += 64 * n[sp]
+            ps += n[sp]
+        sim.step(1)
+        get_all()
+        d2h = 64 * sum(n.values())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    return {"value": ps / secs, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": 1, "at_step": at}
+
+
+def large_oracle_sample(nsteps: int = 1) -> dict:
+    """The oracle on a 64^3 sub-box of the same recipe (box 2 lambda, the same
+    density, ppc, intensity and thinning), one core, over its first steps."""
+    import numpy as np
+    from oracle import drive
+    from paper_1412_6426_gb300 import workloads
+    w, fx, fy = workloads.large_cascade(n=64)
+    fo = [np.array(a, dtype=np.float64) for a in workloads.expand_profiles(fx, fy, 64)]
+    Jo = [np.zeros_like(fo[0]) for _ in range(3)]
+    t0 = time.perf_counter()
+    _, diag, _, _ = drive.run(w.n, w.d, w.x0, w.periodic, w.field_mode, w.fp, w.dt, nsteps, w.particles,
+                              kappa=w.kappa, seed=w.seed, caps=w.meta["capacity64"], fields=fo, J=Jo,
+                              deposit_on=1, yee=True, thin_interval=w.meta["thin_interval"],
+                              thin_limit=w.meta["thin_limit"])
+    secs = time.perf_counter() - t0
+    return {"value": diag["particle_steps"] / secs, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": (f"steps 0..{nsteps - 1} of the same recipe on a 64^3 sub-box (2 lambda; 6.6e5 e- and "
+                       f"6.6e5 p+), FP64 oracle with deposit and field update, one process (the particles "
+                       f"share the mesh)")}
+
+
+def large_profile_window(start: int, count: int) -> None:
+    """For profiling captures: run the 512^3 cascade (FP32) to step `start`,
+    then `count` steps inside a CUDA profiler range (ncu --profile-from-start
+    off)."""
+    import torch
+    from paper_1412_6426_gb300.sim import Simulation
+    w, F, J, opts = large_setup(32)
+    with Simulation(w, **opts) as sim:
+        sim.set_grid_fields(F[:3], F[3:], J)
+        sim.set_all()
+        sim.step(start)
+        torch.cuda.synchronize()
+        live0 = sim.diag()["count"]
+        torch.cuda.profiler.start()
+        sim.step(count)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        d = sim.diag()
+    print(json.dumps({"profile_window": [start, count], "live_before": live0, "live_after": d["count"],
+                      "status": d["status"]}))
+
+
+def main_large(args, world, rank, local):
+    import torch
+    import torch.distributed as tdist
+    from paper_1412_6426_gb300 import build
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    build.build()
+    if args.profile_window:
+        a, b = (int(v) for v in args.profile_window.split(":"))
+        large_profile_window(a, b)
+        return
+    K = LARGE_STEPS if args.steps == RUN_STEPS - 3 else args.steps
+    W = LARGE_WARMUP if args.warmup == 3 else args.warmup
+    r = large_device(32, K, W, barrier)
+    r64 = None if args.no_fp64 else large_device(64, max(2, K // 4), W, barrier)
+    e2e = None if args.no_e2e else large_e2e()
+    tot, mx = float(r["particle_steps"]), r["seconds"]
+    if world > 1:
+        t = torch.tensor([tot, mx], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t[:1], op=tdist.ReduceOp.SUM)
+        tdist.all_reduce(t[1:], op=tdist.ReduceOp.MAX)
+        tot, mx = float(t[0]), float(t[1])
+    if rank != 0:
+        if world > 1:
+            tdist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+
+    def roof(rr):
+        ach = rr["algo_bytes"] / rr["seconds"] / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "peak_source": peak_kind,
+                "kernel": "whole step (all kernels: particles, deposit, FDTD, thinning, sort)",
+                "algorithmic_bytes_per_step": rr["algo_bytes"] / rr["steps"]}
+
+    line = {"metric": METRIC, "value": tot / mx, "unit": "particle-steps/s", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": LARGE_NAME, "precision": "fp32 fields, particles, push/rates; fp64 tables",
+                       "parallelism": f"independent boxes x{world}",
+                       "l2": "the mesh alone, 4.8 GB, is larger than L2 (no flush)",
+                       "compact_and_sort_interval": 8, "window": [W, W + K]},
+            "roofline": roof(r), "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "events": {"emissions": r["emissions"], "pairs": r["pairs"], "thinned": r["thinned"],
+                       "live_at_end": r["live_end"]}}
+    if r64 is not None:
+        v64 = r64["particle_steps"] / r64["seconds"]
+        line["fp64"] = {"value": v64, "ms_per_step": r64["ms_per_step"], "steps": r64["steps"],
+                        "window": [W, W + r64["steps"]], "roofline": roof(r64),
+                        "speedup_fp32_over_fp64": line["value"] / v64, "live_at_end": r64["live_end"]}
+    if e2e is not None:
+        line["e2e"] = e2e
+    if not args.no_cpu:
+        cb = large_oracle_sample(1)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line))
+    if world > 1:
+        tdist.destroy_process_group()
+
+
 def main_batched(args, world, rank, local):
     import torch
     import torch.distributed as tdist
@@ -780,15 +1000,17 @@ def main():
                     help="collision: emission generator (0 modified, 1 alternative, 2 standard)")
     ap.add_argument("--tuning", default="",
                     help="collision: qed_tuning fields, e.g. concurrent=1,photon_blocks_per_sm=2")
-    ap.add_argument("--workload", choices=("collision", "batched", "cascade"), default="collision",
+    ap.add_argument("--workload", choices=("collision", "batched", "cascade", "cascade512"), default="collision",
                     help="collision: the beam-laser collision (the headline line); batched: 512 ensembles; "
-                         "cascade: the self-consistent 256^3 cascade")
+                         "cascade: the self-consistent 256^3 cascade; cascade512: the large 512^3 cascade "
+                         "(a window of its run)")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="batched: electron counts x this (smaller sets are for profiling captures)")
     ap.add_argument("--batch-steps", type=int, default=BATCH_STEPS, help="batched: steps of the run")
     ap.add_argument("--no-autotune", action="store_true", help="batched: keep the default tuning")
     ap.add_argument("--profile-window", default="",
-                    help="cascade: START:COUNT, run to START and profile COUNT steps (for ncu captures)")
+                    help="cascade, cascade512: START:COUNT, run to START and profile COUNT steps "
+                         "(for ncu captures)")
     ap.add_argument("--cascade-caps", default="", help="cascade: e-,e+,photon capacities (profiling)")
     args = ap.parse_args()
     if args.electrons != N_ELECTRONS:
@@ -818,6 +1040,20 @@ def main():
                                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
             return
         main_cascade(args, world, rank, local)
+        return
+    if args.workload == "cascade512":
+        if args.impl == "reference":
+            if rank == 0:
+                cb = large_oracle_sample(1)
+                print(json.dumps({"metric": METRIC, "value": cb["value"], "unit": "particle-steps/s",
+                                  "n_gpus": args.gpus, "steps": 1, "warmup": 0, "higher_is_better": True,
+                                  "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                                  "impl": "reference", "config": {"workload": LARGE_NAME, "sample": cb["sample"]},
+                                  "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                                  "e2e": {"value": cb["value"], "unit": "particle-steps/s",
+                                          "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+            return
+        main_large(args, world, rank, local)
         return
     if args.workload == "batched":
         BATCH_SCALE, BATCH_STEPS, BATCH_AUTOTUNE = args.batch_scale, args.batch_steps, not args.no_autotune

@@ -277,6 +277,115 @@ def self_consistent_cascade(n: int = 256, seed: int = 1, nsteps: int = 2000, wav
     return w, f
 
 
+def large_cascade(n: int = 512, seed: int = 1, nsteps: int = 3000, wavelength_m: float = 0.8e-6,
+                  cells_per_lambda: int = 32, steps_per_period: int = 64, intensity_w_cm2: float = 2e24,
+                  density_cm3: float = 1e22, thickness_m: float = 0.5e-6, ppc: int = 8):
+    """The large self-consistent cascade: an n^3 periodic Yee mesh (dx =
+    lambda/32, box 16 lambda at n = 512) with four circularly polarised
+    plane-wave pulses at the given intensity each, two along +-x and two
+    along +-y, meeting at the box centre, and a cold hydrogen slab target
+    (electrons and protons at the same points, so rho = 0 at t = 0) of
+    density n_e and the given thickness along x at the centre, spanning the
+    transverse box, with ppc macro-particles per cell and species.
+
+    Each pulse has a sin^2 envelope of full width half the box (8 lambda at
+    n = 512; intensity FWHM 4 lambda), the longest that lets two
+    counter-propagating pulses start side by side in the periodic box; at
+    t = 0 their centres are a quarter box from the centre, so they meet there
+    at step 4 steps_per_period (n = 512).  Every field component is the sum
+    of an x-profile and a y-profile:
+        F_c[k, j, i] = fx[c][i] + fy[c][j]
+    on the Yee staggering.  Returns (workload, fx, fy) with fx, fy lists of
+    six 1-D numpy arrays (Ex, Ey, Ez, Bx, By, Bz); expand with
+    expand_profiles."""
+    rng = np.random.default_rng(seed)
+    lam = length(wavelength_m)
+    d = lam / cells_per_lambda
+    omega = laser_omega(wavelength_m)
+    t_laser = 2 * math.pi / omega
+    dt = t_laser / steps_per_period
+    a0 = a0_from_intensity(intensity_w_cm2, wavelength_m, circular=True)
+    E0 = a0_to_field(a0, wavelength_m)
+    L = n * d
+    c0 = 0.5 * L
+    W = 0.5 * L                                 # full width of the sin^2 envelope
+    off = 0.25 * L                              # pulse centres at c0 -+ off
+
+    def envelope(u):
+        e = np.sin(math.pi * (u / W + 0.5)) ** 2
+        return np.where(np.abs(u) < 0.5 * W, e, 0.0)
+
+    def wrap(u):
+        return (u + 0.5 * L) % L - 0.5 * L
+
+    def pair(s):
+        # the +s pulse starts at c0 - off and the -s pulse at c0 + off:
+        # (amplitude, phase) of each at coordinate s
+        ua, ub = wrap(s - (c0 - off)), wrap(s - (c0 + off))
+        return E0 * envelope(ua), omega * ua, E0 * envelope(ub), omega * ub
+
+    node = np.arange(n) * d
+    half = (np.arange(n) + 0.5) * d
+    fx = [np.zeros(n) for _ in range(6)]
+    fy = [np.zeros(n) for _ in range(6)]
+    # along x: E in the y-z plane; B = +x x E for the +x pulse, -x x E for the other
+    fa, pa, fb, pb = pair(node)                 # Ey, Ez sit at x = i d
+    fx[1] = fa * np.cos(pa) + fb * np.cos(pb)
+    fx[2] = fa * np.sin(pa) + fb * np.sin(pb)
+    fa, pa, fb, pb = pair(half)                 # By, Bz sit at x = (i + 1/2) d
+    fx[4] = -fa * np.sin(pa) + fb * np.sin(pb)
+    fx[5] = fa * np.cos(pa) - fb * np.cos(pb)
+    # along y: E in the z-x plane (E = f (cos p z + sin p x)); B = +y x E, -y x E
+    fa, pa, fb, pb = pair(node)                 # Ex, Ez sit at y = j d
+    fy[0] = fa * np.sin(pa) + fb * np.sin(pb)
+    fy[2] = fa * np.cos(pa) + fb * np.cos(pb)
+    fa, pa, fb, pb = pair(half)                 # Bx, Bz sit at y = (j + 1/2) d
+    fy[3] = fa * np.cos(pa) - fb * np.cos(pb)
+    fy[5] = -fa * np.sin(pa) + fb * np.sin(pb)
+    # target: n_e per Compton volume, weight = real particles per macro-particle
+    ne = density_cm3 * 1e6 * LAMBDA_C_BAR ** 3
+    cells_x = int(round(length(thickness_m) / d))
+    i0 = n // 2 - cells_x // 2
+    count = cells_x * n * n * ppc
+    x = np.empty((count, 3))
+    x[:, 0] = (i0 + rng.uniform(0.0, cells_x, count)) * d
+    x[:, 1] = rng.uniform(0.0, n, count) * d
+    x[:, 2] = rng.uniform(0.0, n, count) * d
+    wt = np.full(count, ne * d ** 3 / ppc)
+    p = np.zeros((count, 3))
+    ids = np.arange(count, dtype=np.uint64)
+    parts = {ELECTRON: (x, p, wt, ids), ION: (x, p, wt, ids + np.uint64(count))}
+    scale = count / (20 * 512 * 512 * 8)
+    w = Workload(name=f"large_cascade_{n}cubed_{intensity_w_cm2:g}Wcm2_x4", n=(n, n, n), d=(d, d, d),
+                 x0=(0.0, 0.0, 0.0), periodic=(1, 1, 1), field_mode=FIELD_GRID, fp=(), dt=dt, nsteps=nsteps,
+                 particles=parts, seed=seed,
+                 meta={"a0": a0, "E0": E0, "omega": omega, "lambda": lam, "n_e": ne, "weight": wt[0],
+                       "target_cells": (i0, i0 + cells_x), "meet_step": int(round(off / dt)),
+                       # the cascade would pass 1e9 particles within ~200 steps: thinning (Sec. VI)
+                       # every 8 steps holds e-, e+ and photons to these counts (at n = 512;
+                       # smaller boxes scale them with the target)
+                       "thin_interval": 8,
+                       "thin_limit": tuple(int(v * scale) for v in (2.0e8, 1.6e8, 6.0e8)) + (0,),
+                       # FP32 stores: 80 B a slot (two buffers); FP64: 144 B, 1.05e9 slots in 164 GB
+                       # plus 9.7 GB of FP64 mesh, within 180 GB
+                       "capacity32": tuple(int(v * scale) for v in (2.5e8, 2.0e8, 7.5e8)) + (count,),
+                       "capacity64": tuple(int(v * scale) for v in (2.0e8, 2.0e8, 6.0e8)) + (count,)})
+    return w, fx, fy
+
+
+def expand_profiles(fx, fy, n, xp=np, **kw):
+    """F_c[k, j, i] = fx[c][i] + fy[c][j] as flat arrays (x fastest), with
+    numpy or any array module of the same broadcasting rules (xp.asarray
+    takes the keyword arguments, e.g. dtype and device)."""
+    out = []
+    for a, b in zip(fx, fy):
+        ax = xp.asarray(a, **kw).reshape(1, 1, n)
+        by = xp.asarray(b, **kw).reshape(1, n, 1)
+        out.append((ax + by).expand(n, n, n).reshape(-1) if hasattr(ax, "expand")
+                   else np.broadcast_to(ax + by, (n, n, n)).reshape(-1))
+    return out
+
+
 def shower_t_rad(gamma0: float, H0: float) -> float:
     """Radiation time of the shower benchmark (Sec. VII.A):
     t_rad = 3.85 gamma0^(1/3) (E_S/H0)^(2/3) hbar^2/(m c e^2), and
