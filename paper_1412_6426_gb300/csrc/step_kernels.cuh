@@ -391,68 +391,106 @@ __device__ void gather_grid(const StepArgs<R> &a, const Pt<R> &q, V3<R> &E, V3<R
 }
 
 // ----- Esirkepov deposit (linear shape) ------------------------------------
+// The particle moves from offset os in cell cs to q (less than one cell per
+// axis).  Along each axis the shapes before and after cover three nodes at
+// most: nodes cs + lo + t, t = 0, 1, 2, with lo = min(0, end cell - cs).  In
+// the frame of node cs - 1 (where the weights are formed) node t is lo + 1 +
+// t.  The current along an axis is the running sum of that axis' weights
+// over its first two edges (the sum over all three is zero: the charge is
+// conserved), so a particle touches 2 x 3 x 3 nodes per component.
+template <typename R> struct EsirTerms {
+  int lo[3];
+  R S0[3][3], dS[3][3];
+  R pref[3];
+};
+
 template <typename R>
-__device__ __noinline__ void deposit(const StepArgs<R> &a, const int *cs, const R *os, const Pt<R> &q, R qw) {
-  R S0[3][4], dS[3][4];
-  int base[3];
+__device__ __forceinline__ bool esir_terms(const StepArgs<R> &a, const int *cs, const R *os, const Pt<R> &q, R qw,
+                                           EsirTerms<R> &t) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    base[c] = cs[c] - 1;
-    R ua = R(1) + os[c];
-    R ub = R(q.ci[c] - cs[c] + 1) + q.off[c];
-    if (!(fabs_r(ub - ua) < R(1))) { atomicOr(a.status, kStCourant); return; }
+    const int dc = q.ci[c] - cs[c];
+    const R ua = R(1) + os[c];
+    const R ub = R(dc + 1) + q.off[c];
+    if (!(fabs_r(ub - ua) < R(1))) return false;
+    t.lo[c] = dc < 0 ? dc : 0;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      R s0 = R(1) - fabs_r(ua - R(m));
-      R s1 = R(1) - fabs_r(ub - R(m));
+    for (int m = 0; m < 3; ++m) {
+      const R node = R(t.lo[c] + 1 + m);
+      R s0 = R(1) - fabs_r(ua - node);
+      R s1 = R(1) - fabs_r(ub - node);
       s0 = s0 > R(0) ? s0 : R(0);
       s1 = s1 > R(0) ? s1 : R(0);
-      S0[c][m] = s0;
-      dS[c][m] = s1 - s0;
+      t.S0[c][m] = s0;
+      t.dS[c][m] = s1 - s0;
     }
   }
   const R inv_vol = a.inv_d[0] * a.inv_d[1] * a.inv_d[2];
-  const R pref[3] = {-qw * a.d[0] / a.dt * inv_vol, -qw * a.d[1] / a.dt * inv_vol,
-                     -qw * a.d[2] / a.dt * inv_vol};
-  long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
-  int I[4], Jj[4], K[4];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    I[m] = wrapi(base[0] + m, a.n[0]);
-    Jj[m] = wrapi(base[1] + m, a.n[1]);
-    K[m] = wrapi(base[2] + m, a.n[2]);
-  }
+  for (int c = 0; c < 3; ++c) t.pref[c] = -qw * a.d[c] / a.dt * inv_vol;
+  return true;
+}
+
+// add(component, node offsets (di, dj, dk) from cs + lo, value) for every
+// non-zero current term of the Esirkepov scheme (Appendix C).
+template <typename R, typename Add>
+__device__ __forceinline__ void esir_apply(const EsirTerms<R> &t, Add add) {
   const R third = R(1.0 / 3.0);
-  for (int k = 0; k < 4; ++k)
-    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const R w = t.S0[1][j] * t.S0[2][k] + R(0.5) * t.dS[1][j] * t.S0[2][k] +
+                  R(0.5) * t.S0[1][j] * t.dS[2][k] + third * t.dS[1][j] * t.dS[2][k];
       R acc = R(0);
-      R wyz = S0[1][j] * S0[2][k] + R(0.5) * dS[1][j] * S0[2][k] + R(0.5) * S0[1][j] * dS[2][k] +
-              third * dS[1][j] * dS[2][k];
-      for (int i = 0; i < 4; ++i) {
-        acc += pref[0] * dS[0][i] * wyz;
-        if (acc != R(0)) atomicAdd(a.J[0] + K[k] * nxy + Jj[j] * nx + I[i], acc);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        acc += t.pref[0] * t.dS[0][i] * w;
+        if (acc != R(0)) add(0, i, j, k, acc);
       }
     }
-  for (int k = 0; k < 4; ++k)
-    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const R w = t.S0[0][i] * t.S0[2][k] + R(0.5) * t.dS[0][i] * t.S0[2][k] +
+                  R(0.5) * t.S0[0][i] * t.dS[2][k] + third * t.dS[0][i] * t.dS[2][k];
       R acc = R(0);
-      R wxz = S0[0][i] * S0[2][k] + R(0.5) * dS[0][i] * S0[2][k] + R(0.5) * S0[0][i] * dS[2][k] +
-              third * dS[0][i] * dS[2][k];
-      for (int j = 0; j < 4; ++j) {
-        acc += pref[1] * dS[1][j] * wxz;
-        if (acc != R(0)) atomicAdd(a.J[1] + K[k] * nxy + Jj[j] * nx + I[i], acc);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        acc += t.pref[1] * t.dS[1][j] * w;
+        if (acc != R(0)) add(1, i, j, k, acc);
       }
     }
-  for (int j = 0; j < 4; ++j)
-    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const R w = t.S0[0][i] * t.S0[1][j] + R(0.5) * t.dS[0][i] * t.S0[1][j] +
+                  R(0.5) * t.S0[0][i] * t.dS[1][j] + third * t.dS[0][i] * t.dS[1][j];
       R acc = R(0);
-      R wxy = S0[0][i] * S0[1][j] + R(0.5) * dS[0][i] * S0[1][j] + R(0.5) * S0[0][i] * dS[1][j] +
-              third * dS[0][i] * dS[1][j];
-      for (int k = 0; k < 4; ++k) {
-        acc += pref[2] * dS[2][k] * wxy;
-        if (acc != R(0)) atomicAdd(a.J[2] + K[k] * nxy + Jj[j] * nx + I[i], acc);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        acc += t.pref[2] * t.dS[2][k] * w;
+        if (acc != R(0)) add(2, i, j, k, acc);
       }
     }
+}
+
+// Esirkepov deposit into the global current (atomics).
+template <typename R>
+__device__ __noinline__ void deposit(const StepArgs<R> &a, const int *cs, const R *os, const Pt<R> &q, R qw) {
+  EsirTerms<R> t;
+  if (!esir_terms(a, cs, os, q, qw, t)) { atomicOr(a.status, kStCourant); return; }
+  const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+  int I[3], Jj[3], K[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    I[m] = wrapi(cs[0] + t.lo[0] + m, a.n[0]);
+    Jj[m] = wrapi(cs[1] + t.lo[1] + m, a.n[1]);
+    K[m] = wrapi(cs[2] + t.lo[2] + m, a.n[2]);
+  }
+  esir_apply(t, [&](int c, int i, int j, int k, R v) { atomicAdd(a.J[c] + K[k] * nxy + Jj[j] * nx + I[i], v); });
 }
 
 // Esirkepov deposit into the shared-memory current tile of a cell block
@@ -466,60 +504,15 @@ __device__ bool deposit_tile(const StepArgs<R> &a, R *jt, const int *torg, const
   int base[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
+    // nodes cs - 1 .. cs + 2 cover every stencil of a move below one cell
     base[c] = cs[c] - 1 - torg[c];
     if (base[c] < 0 || base[c] + 3 >= kTileNodes) return false;
   }
-  R S0[3][4], dS[3][4];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    R ua = R(1) + os[c];
-    R ub = R(q.ci[c] - cs[c] + 1) + q.off[c];
-    if (!(fabs_r(ub - ua) < R(1))) { atomicOr(a.status, kStCourant); return true; }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      R s0 = R(1) - fabs_r(ua - R(m));
-      R s1 = R(1) - fabs_r(ub - R(m));
-      s0 = s0 > R(0) ? s0 : R(0);
-      s1 = s1 > R(0) ? s1 : R(0);
-      S0[c][m] = s0;
-      dS[c][m] = s1 - s0;
-    }
-  }
-  const R inv_vol = a.inv_d[0] * a.inv_d[1] * a.inv_d[2];
-  const R pref[3] = {-qw * a.d[0] / a.dt * inv_vol, -qw * a.d[1] / a.dt * inv_vol,
-                     -qw * a.d[2] / a.dt * inv_vol};
+  EsirTerms<R> t;
+  if (!esir_terms(a, cs, os, q, qw, t)) { atomicOr(a.status, kStCourant); return true; }
   constexpr int T = kTileNodes, TT = kTileNodes * kTileNodes, TTT = TT * kTileNodes;
-  const R third = R(1.0 / 3.0);
-  for (int k = 0; k < 4; ++k)
-    for (int j = 0; j < 4; ++j) {
-      R acc = R(0);
-      R wyz = S0[1][j] * S0[2][k] + R(0.5) * dS[1][j] * S0[2][k] + R(0.5) * S0[1][j] * dS[2][k] +
-              third * dS[1][j] * dS[2][k];
-      for (int i = 0; i < 4; ++i) {
-        acc += pref[0] * dS[0][i] * wyz;
-        if (acc != R(0)) atomicAdd(jt + 0 * TTT + (base[2] + k) * TT + (base[1] + j) * T + base[0] + i, acc);
-      }
-    }
-  for (int k = 0; k < 4; ++k)
-    for (int i = 0; i < 4; ++i) {
-      R acc = R(0);
-      R wxz = S0[0][i] * S0[2][k] + R(0.5) * dS[0][i] * S0[2][k] + R(0.5) * S0[0][i] * dS[2][k] +
-              third * dS[0][i] * dS[2][k];
-      for (int j = 0; j < 4; ++j) {
-        acc += pref[1] * dS[1][j] * wxz;
-        if (acc != R(0)) atomicAdd(jt + 1 * TTT + (base[2] + k) * TT + (base[1] + j) * T + base[0] + i, acc);
-      }
-    }
-  for (int j = 0; j < 4; ++j)
-    for (int i = 0; i < 4; ++i) {
-      R acc = R(0);
-      R wxy = S0[0][i] * S0[1][j] + R(0.5) * dS[0][i] * S0[1][j] + R(0.5) * S0[0][i] * dS[1][j] +
-              third * dS[0][i] * dS[1][j];
-      for (int k = 0; k < 4; ++k) {
-        acc += pref[2] * dS[2][k] * wxy;
-        if (acc != R(0)) atomicAdd(jt + 2 * TTT + (base[2] + k) * TT + (base[1] + j) * T + base[0] + i, acc);
-      }
-    }
+  R *o = jt + (base[2] + 1 + t.lo[2]) * TT + (base[1] + 1 + t.lo[1]) * T + base[0] + 1 + t.lo[0];
+  esir_apply(t, [&](int c, int i, int j, int k, R v) { atomicAdd(o + c * TTT + k * TT + j * T + i, v); });
   return true;
 }
 
