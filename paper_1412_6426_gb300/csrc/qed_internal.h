@@ -172,6 +172,7 @@ struct qed_ctx {
   int blocks_massive = 0;
   int blocks_products = 0;
   int blocks_cells = 0;
+  int blocks_deposit = 0;
   int64_t step = 0;                   // host mirror of the clock (steps issued)
   int latched = 0;                    // a device error was observed
   int64_t steps_since_compact = 0;

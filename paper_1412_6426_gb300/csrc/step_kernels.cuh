@@ -1416,12 +1416,16 @@ __global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
 // cell block deposits into a shared tile of that block (the block plus the
 // stencil's reach), flushed with one global atomic per non-zero node; a
 // sparse item (several blocks) deposits straight into J.
+template <typename R> struct DepositOcc { static constexpr int blocks = sizeof(R) == 4 ? 3 : 2; };
+
 template <typename R>
-__global__ void __launch_bounds__(256, 2) k_deposit_blocks(const StepArgs<R> a) {
+__global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(const StepArgs<R> a) {
   constexpr int TTT = kTileNodes * kTileNodes * kTileNodes;
   __shared__ R jt[3 * TTT];
   __shared__ int blk;
   __shared__ long long ns[4];
+  // wrapped global offsets of the tile's node rows: x index, y x nx, z x nx ny
+  __shared__ long long gofs[3][kTileNodes];
   if (threadIdx.x < 4) ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
   __syncthreads();
   const BlockItems bi = block_items(a, ns);
@@ -1453,6 +1457,11 @@ __global__ void __launch_bounds__(256, 2) k_deposit_blocks(const StepArgs<R> a) 
       const int bc[3] = {bl % a.nb[0], (bl / a.nb[0]) % a.nb[1], bl / (a.nb[0] * a.nb[1])};
       for (int c = 0; c < 3; ++c) torg[c] = bc[c] * kBlockCells - 1;
       for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) jt[t] = R(0);
+      if (threadIdx.x < 3 * kTileNodes) {
+        const int c = threadIdx.x / kTileNodes, m = threadIdx.x % kTileNodes;
+        const long long stride = c == 0 ? 1 : (c == 1 ? nx : nxy);
+        gofs[c][m] = (long long)wrapi(torg[c] + m, a.n[c]) * stride;
+      }
     }
     __syncthreads();
     if (qc != R(0))
@@ -1481,11 +1490,10 @@ __global__ void __launch_bounds__(256, 2) k_deposit_blocks(const StepArgs<R> a) 
       for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) {
         const R v = jt[t];
         if (v == R(0)) continue;
-        const int c = t / TTT, r = t % TTT;
-        const int ti = r % kTileNodes, tj = (r / kTileNodes) % kTileNodes, tk = r / (kTileNodes * kTileNodes);
-        const int gi = wrapi(torg[0] + ti, a.n[0]), gj = wrapi(torg[1] + tj, a.n[1]),
-                  gk = wrapi(torg[2] + tk, a.n[2]);
-        atomicAdd(a.J[c] + gk * nxy + gj * nx + gi, v);
+        const int c = t / TTT, r = t - c * TTT;
+        const int tk = r / (kTileNodes * kTileNodes), r2 = r - tk * (kTileNodes * kTileNodes);
+        const int tj = r2 / kTileNodes, ti = r2 - tj * kTileNodes;
+        atomicAdd(a.J[c] + gofs[2][tk] + gofs[1][tj] + gofs[0][ti], v);
       }
     }
     __syncthreads();   // the tile and blk are reused by the next item
@@ -1669,7 +1677,7 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     e = cudaLaunchKernel((const void *)k_blocks<R, EXT>, dim3(c->blocks_cells), dim3(256), args, 0, s);
     if (e == cudaSuccess && a.deposit) {
       c->launches += 1;
-      e = cudaLaunchKernel((const void *)k_deposit_blocks<R>, dim3(c->blocks_cells), dim3(256), args, 0, s);
+      e = cudaLaunchKernel((const void *)k_deposit_blocks<R>, dim3(c->blocks_deposit), dim3(256), args, 0, s);
     }
   }
   if (e == cudaSuccess && conc) e = cudaStreamWaitEvent(s, c->ev_join, 0);
@@ -1695,6 +1703,9 @@ int step_blocks(qed_ctx *c) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k_blocks<R, EXT>, 256, 0) != cudaSuccess || g < 1)
     return QED_ERR_CUDA;
   c->blocks_cells = g * c->num_sms;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k_deposit_blocks<R>, 256, 0) != cudaSuccess || g < 1)
+    return QED_ERR_CUDA;
+  c->blocks_deposit = g * c->num_sms;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_photons<R, EXT>, qed::kPhotonThreads, 0) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pass0<R, false, EXT>, 256, 0) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k_products<R, EXT>, 256, 0) != cudaSuccess ||
