@@ -820,13 +820,16 @@ def large_oracle_sample(nsteps: int = 1) -> dict:
                        f"share the mesh)")}
 
 
-def large_profile_window(start: int, count: int) -> None:
-    """For profiling captures: run the 512^3 cascade (FP32) to step `start`,
-    then `count` steps inside a CUDA profiler range (ncu --profile-from-start
-    off)."""
+def large_profile_window(start: int, count: int, n: int = 512, caps=None) -> None:
+    """For profiling captures: run the large cascade (FP32; n^3 mesh, the
+    same recipe) to step `start`, then `count` steps inside a CUDA profiler
+    range (ncu --profile-from-start off)."""
     import torch
     from paper_1412_6426_gb300.sim import Simulation
-    w, F, J, opts = large_setup(32)
+    w, F, J, opts = large_setup(32, n)
+    if caps is not None:
+        opts["capacity"] = caps
+        opts["pending_capacity"] = 0
     with Simulation(w, **opts) as sim:
         sim.set_grid_fields(F[:3], F[3:], J)
         sim.set_all()
@@ -840,6 +843,12 @@ def large_profile_window(start: int, count: int) -> None:
         d = sim.diag()
     print(json.dumps({"profile_window": [start, count], "live_before": live0, "live_after": d["count"],
                       "status": d["status"]}))
+
+
+def workloads_target(n: int) -> int:
+    """Protons of the large cascade's target on an n^3 mesh."""
+    from paper_1412_6426_gb300 import workloads
+    return len(workloads.large_cascade(n=n)[0].particles[workloads.ION][3])
 
 
 def main_large(args, world, rank, local):
@@ -857,7 +866,11 @@ def main_large(args, world, rank, local):
     build.build()
     if args.profile_window:
         a, b = (int(v) for v in args.profile_window.split(":"))
-        large_profile_window(a, b)
+        caps = None
+        if args.cascade_caps:
+            caps = tuple(int(float(v)) for v in args.cascade_caps.split(","))
+            caps = caps + (workloads_target(args.box),)
+        large_profile_window(a, b, args.box, caps)
         return
     K = LARGE_STEPS if args.steps == RUN_STEPS - 3 else args.steps
     W = LARGE_WARMUP if args.warmup == 3 else args.warmup
@@ -1011,7 +1024,9 @@ def main():
     ap.add_argument("--profile-window", default="",
                     help="cascade, cascade512: START:COUNT, run to START and profile COUNT steps "
                          "(for ncu captures)")
-    ap.add_argument("--cascade-caps", default="", help="cascade: e-,e+,photon capacities (profiling)")
+    ap.add_argument("--cascade-caps", default="", help="cascade, cascade512: e-,e+,photon capacities (profiling)")
+    ap.add_argument("--box", type=int, default=512,
+                    help="cascade512 --profile-window: mesh edge of the same recipe (small profiling cases)")
     args = ap.parse_args()
     if args.electrons != N_ELECTRONS:
         scale_workload(args.electrons)
