@@ -558,6 +558,20 @@ __device__ __noinline__ void spectrum_add(const StepArgs<R> &a, R delta, R eps, 
   if (v >= R(0) && v < R(a.nbins)) atomicAdd(a.spectrum_energy + (int)v, (double)w);
 }
 
+// Upper bound of P_m(r1) over r1 for one sub-interval (Eq. (25)):
+// with delta = r1^3, z = 2 delta / (3 chi (1 - delta)) and F1(z) <= g1(0)
+// z^(1/3) (g1 = F1 z^(-1/3) decreases from g1(0) = 2.14953), the F1 term of
+// P_m is at most 3 g1(0) (2/(3 chi))^(1/3) and the F2 term 3 max F2 =
+// 3 x 0.60705, so
+//   P_m <= alpha h sqrt3/(2 pi gamma) (5.6336 chi^(2/3) + 1.8212 chi)
+// (the two bounds behind the time-step requirement of Sec. IV.H).  A factor
+// 1.02 covers the tables' and this evaluation's rounding.
+template <typename R>
+__device__ __forceinline__ R emit_bound(R chi, R gamma, R h) {
+  const R c13 = cbrt_r(chi);
+  return R(1.02 * kAlpha * kSqrt3Over2Pi) * h / gamma * (R(5.6336) * c13 * c13 + R(1.8212) * chi);
+}
+
 // Upper bound of P_p(de) over de for one sub-interval (Eq. (30)):
 // P_p <= alpha h sqrt3/(2pi) (chi/eps) F2(z_p), and z_p >= z_min = 8/(3 chi)
 // at de = 1/2, where F2 decreases beyond its maximum 0.60705 at z = 0.4169.
@@ -783,6 +797,9 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
       }
       continue;
     }
+    // P_m(r1) <= emit_bound <= r2: no emission, whatever r1 (and the bound
+    // is below 1, so P_m is too); the generator factors reuse (r1, r2)
+    if (!(EXT && (a.emit_ng > 1 || a.emit_keep < R(1))) && r2 >= emit_bound(chi, g, h)) continue;
     R pm = prob_emit(a.tab, r1, chi, g, h);
     if (pm > R(1)) {
       count_rare(a, kCntPmGt1, 1u);
@@ -844,10 +861,16 @@ __device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, P
   // No draw can make a pair when P_p is below the smallest uniform: below
   // chi_star (uncapped) by the bound of photon_chi_star, else by pair_bound.
   bool may_pair = a.pairs_on;
+  R bound = R(0);
   if (may_pair) {
     if (!capped && chig < chi_star) may_pair = false;
-    else may_pair = pair_bound(a.tab, chig, eps, h) >= r2_floor(h);
+    else {
+      bound = pair_bound(a.tab, chig, eps, h);
+      may_pair = bound >= r2_floor(h);
+    }
   }
+  // the generator factors draw further samples from the same (r1, r2)
+  const bool plain = !(EXT && (a.pair_ng > 1 || a.pair_keep < R(1)));
   if (may_pair && idp) q.id = __ldg(idp);
   for (int s = 0; s < n; ++s) {
     move(a, q, dir, h);
@@ -856,6 +879,8 @@ __device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, P
     if (!may_pair) continue;
     R r1, r2;
     draw2(q.id, step, (unsigned)s, kPair, a.seed, r1, r2);
+    // P_p(r1) <= bound <= r2: no pair, whatever r1 (and bound < 1, so P_p < 1)
+    if (plain && r2 >= bound) continue;
     R pp = prob_pair(a.tab, r1, chig, eps, h);
     if (pp > R(1)) {
       count_rare(a, kCntPpGt1, 1u);
