@@ -88,6 +88,24 @@ def test_thinning_without_ensembles_fp64_parity():
     assert rep["ok"], rep
 
 
+def test_lineage_bits_and_thinning_fp64_parity():
+    # seeds tagged in the top 4 id bits, products inheriting them, thinning
+    # of whole species (no ensemble field mode)
+    w = workloads.test_particles_static_b(n_particles=400, nsteps=8)
+    x, p, wt, ids = w.particles[0]
+    w.particles = {0: (x, p, wt, ids | (np.uint64(7) << np.uint64(60)))}
+    w.ens_bits = 4
+    opts = dict(thin_interval=2, thin_limit=(0, 0, 300, 0))
+    caps = (20_000, 20_000, 100_000, 1)
+    ora, od, _, _ = run_oracle(w, caps=caps, **opts)
+    assert od["thinned"] > 100
+    gpu, gd = run_gpu(w, precision=64, caps=caps, **opts)
+    assert gd["status"] == 0 and gd["thinned"] == od["thinned"]
+    rep = compare(gpu, ora, rtol_p=1e-12, xtol=1e-12 * box_scale(w), rtol_w=1e-12)
+    assert rep["ok"], rep
+    assert all(((i >> np.uint64(60)) == 7).all() for sp in range(3) for i in [gpu[sp][3]] if len(i))
+
+
 def _run32(w, nsteps, tuning=None, autotune=None):
     from paper_1412_6426_gb300.sim import Simulation
     with Simulation(w, precision=32, capacity=caps_for(w), compact_interval=4, **thin_opts(w)) as s:

@@ -249,6 +249,22 @@ def test_thinning_without_ensembles_is_one_group_per_species():
             assert abs(na - L) < 5 * math.sqrt(L)
 
 
+def test_lineage_bits_outside_ensembles_keep_one_group():
+    """Outside the ensemble field mode the top id bits only record a seed's
+    lineage: thinning still treats each species as one group, so the result
+    equals the run without the bits (same survivors, same weight factor)."""
+    rng = np.random.default_rng(2)
+    n = 2000
+    seeds = rng.integers(0, 16, n).astype(np.uint64)
+    ids = (seeds << np.uint64(60)) | np.arange(n, dtype=np.uint64)
+    parts = {0: (rng.normal(size=(n, 3)), rng.normal(size=(n, 3)), rng.uniform(1, 2, n), ids)}
+    _, plain, _ = _thin_once(parts, (500, 0, 0, 0))
+    _, tagged, d = _thin_once(parts, (500, 0, 0, 0), bits=4)
+    assert d["thinned"] > 0
+    assert np.array_equal(plain[0][3], tagged[0][3]) and np.array_equal(plain[0][2], tagged[0][2])
+    assert abs(len(tagged[0][3]) - 500) < 5 * math.sqrt(500)
+
+
 def test_thinned_shower_keeps_weighted_yields():
     # a chi = 1 shower, photons thinned to 300 every 2 steps vs not thinned:
     # the weighted photon number and energy agree within the thinning noise

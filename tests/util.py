@@ -17,6 +17,7 @@ def run_oracle(w, nsteps=None, *, caps=None, nbins=0, step0=0, t0=0.0, **opts):
     caps = default_caps(w) if caps is None else caps
     if getattr(w, "ens", None) is not None:
         opts.setdefault("ens", w.ens)
+    if getattr(w, "ens_bits", 0):
         opts.setdefault("ens_bits", w.ens_bits)
     return drive.run(w.n, w.d, w.x0, w.periodic, w.field_mode, w.fp, w.dt,
                      w.nsteps if nsteps is None else nsteps, w.particles, kappa=opts.pop("kappa", w.kappa),
