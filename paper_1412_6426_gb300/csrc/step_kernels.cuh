@@ -350,44 +350,56 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 }
 
 // CIC gather of one staggered component (stagger sx, sy, sz in {0, 1/2}).
+// wrapi for an index that is almost always in range already (one compare).
+__device__ __forceinline__ int wrap_fast(int i, int n) { return (unsigned)i < (unsigned)n ? i : wrapi(i, n); }
+
+// CIC weights along one axis for a component at stagger 0 or 1/2: the lower
+// node (wrapped), the upper node (wrapped) and the fraction towards it.
+template <typename R> struct Axis {
+  int i0, i1;
+  R fr;
+};
+
 template <typename R>
-__device__ __forceinline__ R cic(const R *__restrict__ f, const StepArgs<R> &a, const int *ci,
-                                 const R *off, int sx, int sy, int sz) {
-  int b[3];
-  R fr[3];
-  const int sg[3] = {sx, sy, sz};
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    R v = sg[c] ? off[c] - R(0.5) : off[c];
-    int bb = ci[c];
-    if (v < R(0)) { v += R(1); bb -= 1; }
-    b[c] = bb;
-    fr[c] = v;
-  }
-  int i0 = wrapi(b[0], a.n[0]), i1 = wrapi(b[0] + 1, a.n[0]);
-  int j0 = wrapi(b[1], a.n[1]), j1 = wrapi(b[1] + 1, a.n[1]);
-  int k0 = wrapi(b[2], a.n[2]), k1 = wrapi(b[2] + 1, a.n[2]);
-  long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
-  R acc = R(0);
-  acc += (R(1) - fr[0]) * (R(1) - fr[1]) * (R(1) - fr[2]) * __ldg(f + k0 * nxy + j0 * nx + i0);
-  acc += fr[0] * (R(1) - fr[1]) * (R(1) - fr[2]) * __ldg(f + k0 * nxy + j0 * nx + i1);
-  acc += (R(1) - fr[0]) * fr[1] * (R(1) - fr[2]) * __ldg(f + k0 * nxy + j1 * nx + i0);
-  acc += fr[0] * fr[1] * (R(1) - fr[2]) * __ldg(f + k0 * nxy + j1 * nx + i1);
-  acc += (R(1) - fr[0]) * (R(1) - fr[1]) * fr[2] * __ldg(f + k1 * nxy + j0 * nx + i0);
-  acc += fr[0] * (R(1) - fr[1]) * fr[2] * __ldg(f + k1 * nxy + j0 * nx + i1);
-  acc += (R(1) - fr[0]) * fr[1] * fr[2] * __ldg(f + k1 * nxy + j1 * nx + i0);
-  acc += fr[0] * fr[1] * fr[2] * __ldg(f + k1 * nxy + j1 * nx + i1);
-  return acc;
+__device__ __forceinline__ Axis<R> cic_axis(int ci, R off, bool half, int n) {
+  R v = half ? off - R(0.5) : off;
+  int b = ci;
+  if (v < R(0)) { v += R(1); b -= 1; }
+  return {wrap_fast(b, n), wrap_fast(b + 1, n), v};
 }
 
 template <typename R>
+__device__ __forceinline__ R cic(const R *__restrict__ f, const Axis<R> &x, const Axis<R> &y, const Axis<R> &z,
+                                 long long nx, long long nxy) {
+  const R fr[3] = {x.fr, y.fr, z.fr};
+  const long long r00 = z.i0 * nxy + y.i0 * nx, r01 = z.i0 * nxy + y.i1 * nx;
+  const long long r10 = z.i1 * nxy + y.i0 * nx, r11 = z.i1 * nxy + y.i1 * nx;
+  R acc = R(0);
+  acc += (R(1) - fr[0]) * (R(1) - fr[1]) * (R(1) - fr[2]) * __ldg(f + r00 + x.i0);
+  acc += fr[0] * (R(1) - fr[1]) * (R(1) - fr[2]) * __ldg(f + r00 + x.i1);
+  acc += (R(1) - fr[0]) * fr[1] * (R(1) - fr[2]) * __ldg(f + r01 + x.i0);
+  acc += fr[0] * fr[1] * (R(1) - fr[2]) * __ldg(f + r01 + x.i1);
+  acc += (R(1) - fr[0]) * (R(1) - fr[1]) * fr[2] * __ldg(f + r10 + x.i0);
+  acc += fr[0] * (R(1) - fr[1]) * fr[2] * __ldg(f + r10 + x.i1);
+  acc += (R(1) - fr[0]) * fr[1] * fr[2] * __ldg(f + r11 + x.i0);
+  acc += fr[0] * fr[1] * fr[2] * __ldg(f + r11 + x.i1);
+  return acc;
+}
+
+// CIC gather of the six staggered components (Yee positions in qed.h); the
+// per-axis nodes and fractions of both staggers are formed once.
+template <typename R>
 __device__ void gather_grid(const StepArgs<R> &a, const Pt<R> &q, V3<R> &E, V3<R> &B) {
-  E.x = cic(a.E[0], a, q.ci, q.off, 1, 0, 0);
-  E.y = cic(a.E[1], a, q.ci, q.off, 0, 1, 0);
-  E.z = cic(a.E[2], a, q.ci, q.off, 0, 0, 1);
-  B.x = cic(a.B[0], a, q.ci, q.off, 0, 1, 1);
-  B.y = cic(a.B[1], a, q.ci, q.off, 1, 0, 1);
-  B.z = cic(a.B[2], a, q.ci, q.off, 1, 1, 0);
+  const Axis<R> x0 = cic_axis(q.ci[0], q.off[0], false, a.n[0]), xh = cic_axis(q.ci[0], q.off[0], true, a.n[0]);
+  const Axis<R> y0 = cic_axis(q.ci[1], q.off[1], false, a.n[1]), yh = cic_axis(q.ci[1], q.off[1], true, a.n[1]);
+  const Axis<R> z0 = cic_axis(q.ci[2], q.off[2], false, a.n[2]), zh = cic_axis(q.ci[2], q.off[2], true, a.n[2]);
+  const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+  E.x = cic(a.E[0], xh, y0, z0, nx, nxy);
+  E.y = cic(a.E[1], x0, yh, z0, nx, nxy);
+  E.z = cic(a.E[2], x0, y0, zh, nx, nxy);
+  B.x = cic(a.B[0], x0, yh, zh, nx, nxy);
+  B.y = cic(a.B[1], xh, y0, zh, nx, nxy);
+  B.z = cic(a.B[2], xh, yh, z0, nx, nxy);
 }
 
 // ----- Esirkepov deposit (linear shape) ------------------------------------
@@ -486,9 +498,9 @@ __device__ __noinline__ void deposit(const StepArgs<R> &a, const int *cs, const 
   int I[3], Jj[3], K[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    I[m] = wrapi(cs[0] + t.lo[0] + m, a.n[0]);
-    Jj[m] = wrapi(cs[1] + t.lo[1] + m, a.n[1]);
-    K[m] = wrapi(cs[2] + t.lo[2] + m, a.n[2]);
+    I[m] = wrap_fast(cs[0] + t.lo[0] + m, a.n[0]);
+    Jj[m] = wrap_fast(cs[1] + t.lo[1] + m, a.n[1]);
+    K[m] = wrap_fast(cs[2] + t.lo[2] + m, a.n[2]);
   }
   esir_apply(t, [&](int c, int i, int j, int k, R v) { atomicAdd(a.J[c] + K[k] * nxy + Jj[j] * nx + I[i], v); });
 }
@@ -539,7 +551,7 @@ template <typename R>
 __device__ __forceinline__ int finish_cell(const StepArgs<R> &a, Pt<R> &q) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    if (a.periodic[c]) q.ci[c] = wrapi(q.ci[c], a.n[c]);
+    if (a.periodic[c]) q.ci[c] = wrap_fast(q.ci[c], a.n[c]);
     else if (q.ci[c] < 0 || q.ci[c] >= a.n[c]) return -1;
   }
   return (q.ci[2] * a.n[1] + q.ci[1]) * a.n[0] + q.ci[0];

@@ -503,6 +503,31 @@ __device__ __forceinline__ void thin_shared_flush(ThinShared &sh, int groups, un
   }
 }
 
+// A thread's running sums for the group of its last particles, added to the
+// block's shared sums when the group changes: a species without ensembles
+// (one group), or an ensemble stored contiguously, costs one shared atomic
+// per thread instead of one per particle.
+struct GroupRun {
+  int g = -1;
+  unsigned long long n = 0;
+  double w = 0.0;
+  __device__ __forceinline__ void flush(ThinShared &sh, bool count) {
+    if (g < 0) return;
+    if (count) atomicAdd(&sh.n[g], n);
+    atomicAdd(&sh.w[g], w);
+  }
+  __device__ __forceinline__ void add(ThinShared &sh, bool count, int gi, double wi) {
+    if (gi != g) {
+      flush(sh, count);
+      g = gi;
+      n = 0;
+      w = 0.0;
+    }
+    n += 1;
+    w += wi;
+  }
+};
+
 template <typename T>
 __global__ void k_thin_count(const T *pos, const T *mom, const uint64_t *id, const long long *count, int sp,
                              long long cap, ThinArgs t) {
@@ -511,6 +536,7 @@ __global__ void k_thin_count(const T *pos, const T *mom, const uint64_t *id, con
   if (priv) thin_shared_zero(sh, t.groups);
   const long long n = min(count[sp], cap);
   const long long stride = (long long)gridDim.x * blockDim.x;
+  GroupRun run;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
     const long long i = base + threadIdx.x;
     int g = -1;
@@ -520,15 +546,15 @@ __global__ void k_thin_count(const T *pos, const T *mom, const uint64_t *id, con
       w = weight_of(pos[i]);
     }
     if (priv) {
-      if (g >= 0) {
-        atomicAdd(&sh.n[g], 1ull);
-        atomicAdd(&sh.w[g], w);
-      }
+      if (g >= 0) run.add(sh, true, g, w);
     } else {
       group_add(g, g >= 0, w, t.n, t.w);
     }
   }
-  if (priv) thin_shared_flush(sh, t.groups, t.n, t.w);
+  if (priv) {
+    run.flush(sh, true);
+    thin_shared_flush(sh, t.groups, t.n, t.w);
+  }
 }
 
 template <typename T>
@@ -539,6 +565,7 @@ __global__ void k_thin_mark(const T *pos, const T *mom, const uint64_t *id, cons
   if (priv) thin_shared_zero(sh, t.groups);
   const long long n = min(count[sp], cap);
   const long long stride = (long long)gridDim.x * blockDim.x;
+  GroupRun run;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
     const long long i = base + threadIdx.x;
     int g = -1;
@@ -554,12 +581,15 @@ __global__ void k_thin_mark(const T *pos, const T *mom, const uint64_t *id, cons
       }
     }
     if (priv) {
-      if (g >= 0) atomicAdd(&sh.w[g], w);
+      if (g >= 0) run.add(sh, false, g, w);
     } else {
       group_add(g, g >= 0, w, nullptr, t.wsurv);
     }
   }
-  if (priv) thin_shared_flush(sh, t.groups, nullptr, t.wsurv);
+  if (priv) {
+    run.flush(sh, false);
+    thin_shared_flush(sh, t.groups, nullptr, t.wsurv);
+  }
 }
 
 template <typename T>
