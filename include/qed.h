@@ -72,7 +72,8 @@ typedef enum qed_species {
 } qed_species;
 
 typedef enum qed_field_mode {
-    /* E, B gathered by CIC from caller-owned Yee arrays (all axes periodic) */
+    /* E, B gathered by CIC from caller-owned Yee arrays (all axes periodic;
+     * n[2] <= 65535 and n[1] <= 524280, the FDTD launch shape) */
     QED_FIELD_GRID = 0,
     /* constant fields: fp = {Ex, Ey, Ez, Bx, By, Bz} */
     QED_FIELD_UNIFORM = 1,

@@ -167,9 +167,11 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
   if (ncell >= (1ll << 31)) return QED_ERR_ARG;
   if (g->field_mode < QED_FIELD_GRID || g->field_mode > QED_FIELD_STANDING_WAVE || g->reserved != 0)
     return QED_ERR_ARG;
-  if (g->field_mode == QED_FIELD_GRID)
+  if (g->field_mode == QED_FIELD_GRID) {
     for (int k = 0; k < 3; ++k)
       if (!g->periodic[k]) return QED_ERR_ARG;
+    if (g->n[2] > 65535 || (g->n[1] + 7) / 8 > 65535) return QED_ERR_ARG;   // the FDTD launch shape
+  }
   if (p->nsub_max < 1 || !(p->kappa > 0.0) || p->nbins < 0 || p->nbins > qed::kMaxBins)
     return QED_ERR_ARG;
   if (p->nbins > 0 && !(p->lg_hi > p->lg_lo)) return QED_ERR_ARG;

@@ -14,17 +14,28 @@ struct Mesh {
 __device__ __forceinline__ int wrap_up(int i, int n) { return i + 1 == n ? 0 : i + 1; }
 __device__ __forceinline__ int wrap_dn(int i, int n) { return i == 0 ? n - 1 : i - 1; }
 
+// One thread per cell; blocks of 32 x 8 cells in the x-y plane, blockIdx.z =
+// k, so the cell's indices come from the launch (no division) and each warp
+// reads 32 consecutive x.
+__device__ __forceinline__ bool cell_ijk(const Mesh &m, int &i, int &j, int &k) {
+  i = blockIdx.x * 32 + threadIdx.x;
+  j = blockIdx.y * 8 + threadIdx.y;
+  k = blockIdx.z;
+  return i < m.nx && j < m.ny;
+}
+
 // B -= h * curl E   (curl E at the B positions, forward differences)
 template <typename R>
-__global__ void k_yee_b(const R *__restrict__ Ex, const R *__restrict__ Ey, const R *__restrict__ Ez,
-                        R *Bx, R *By, R *Bz, Mesh m, R h_dx, R h_dy, R h_dz) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long nxy = (long long)m.nx * m.ny;
-  if (c >= nxy * m.nz) return;
-  int i = (int)(c % m.nx), j = (int)((c / m.nx) % m.ny), k = (int)(c / nxy);
-  long long ip = c - i + wrap_up(i, m.nx);
-  long long jp = c + (long long)(wrap_up(j, m.ny) - j) * m.nx;
-  long long kp = c + (long long)(wrap_up(k, m.nz) - k) * nxy;
+__global__ void __launch_bounds__(256) k_yee_b(const R *__restrict__ Ex, const R *__restrict__ Ey,
+                                               const R *__restrict__ Ez, R *Bx, R *By, R *Bz, Mesh m, R h_dx,
+                                               R h_dy, R h_dz) {
+  int i, j, k;
+  if (!cell_ijk(m, i, j, k)) return;
+  const long long nx = m.nx, nxy = (long long)m.nx * m.ny;
+  const long long c = k * nxy + j * nx + i;
+  const long long ip = c - i + wrap_up(i, m.nx);
+  const long long jp = c + (long long)(wrap_up(j, m.ny) - j) * nx;
+  const long long kp = c + (long long)(wrap_up(k, m.nz) - k) * nxy;
   R ex = Ex[c], ey = Ey[c], ez = Ez[c];
   Bx[c] -= h_dy * (Ez[jp] - ez) - h_dz * (Ey[kp] - ey);
   By[c] -= h_dz * (Ex[kp] - ex) - h_dx * (Ez[ip] - ez);
@@ -33,16 +44,18 @@ __global__ void k_yee_b(const R *__restrict__ Ex, const R *__restrict__ Ey, cons
 
 // E += dt * (curl B - 4 pi alpha J)   (curl B at the E positions, backward differences)
 template <typename R>
-__global__ void k_yee_e(R *Ex, R *Ey, R *Ez, const R *__restrict__ Bx, const R *__restrict__ By,
-                        const R *__restrict__ Bz, const R *__restrict__ Jx, const R *__restrict__ Jy,
-                        const R *__restrict__ Jz, Mesh m, R t_dx, R t_dy, R t_dz, R t_src) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long nxy = (long long)m.nx * m.ny;
-  if (c >= nxy * m.nz) return;
-  int i = (int)(c % m.nx), j = (int)((c / m.nx) % m.ny), k = (int)(c / nxy);
-  long long im = c - i + wrap_dn(i, m.nx);
-  long long jm = c + (long long)(wrap_dn(j, m.ny) - j) * m.nx;
-  long long km = c + (long long)(wrap_dn(k, m.nz) - k) * nxy;
+__global__ void __launch_bounds__(256) k_yee_e(R *Ex, R *Ey, R *Ez, const R *__restrict__ Bx,
+                                               const R *__restrict__ By, const R *__restrict__ Bz,
+                                               const R *__restrict__ Jx, const R *__restrict__ Jy,
+                                               const R *__restrict__ Jz, Mesh m, R t_dx, R t_dy, R t_dz,
+                                               R t_src) {
+  int i, j, k;
+  if (!cell_ijk(m, i, j, k)) return;
+  const long long nx = m.nx, nxy = (long long)m.nx * m.ny;
+  const long long c = k * nxy + j * nx + i;
+  const long long im = c - i + wrap_dn(i, m.nx);
+  const long long jm = c + (long long)(wrap_dn(j, m.ny) - j) * nx;
+  const long long km = c + (long long)(wrap_dn(k, m.nz) - k) * nxy;
   R bx = Bx[c], by = By[c], bz = Bz[c];
   Ex[c] += t_dy * (bz - Bz[jm]) - t_dz * (by - By[km]) - t_src * Jx[c];
   Ey[c] += t_dz * (bx - Bx[km]) - t_dx * (bz - Bz[im]) - t_src * Jy[c];
@@ -52,8 +65,8 @@ __global__ void k_yee_e(R *Ex, R *Ey, R *Ez, const R *__restrict__ Bx, const R *
 template <typename R>
 int yee(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   Mesh m{c->grid.n[0], c->grid.n[1], c->grid.n[2]};
-  long long nc = (long long)m.nx * m.ny * m.nz;
-  int blocks = (int)((nc + 255) / 256);
+  if (m.nz > 65535) return QED_ERR_ARG;
+  const dim3 blocks((m.nx + 31) / 32, (m.ny + 7) / 8, m.nz), threads(32, 8);
   const double *d = c->grid.d;
   R *E[3], *B[3], *J[3];
   for (int k = 0; k < 3; ++k) {
@@ -63,12 +76,12 @@ int yee(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   }
   const double h = 0.5 * dt;
   c->launches += 3;
-  k_yee_b<R><<<blocks, 256, 0, s>>>(E[0], E[1], E[2], B[0], B[1], B[2], m, (R)(h / d[0]), (R)(h / d[1]),
-                                     (R)(h / d[2]));
-  k_yee_e<R><<<blocks, 256, 0, s>>>(E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2], m, (R)(dt / d[0]),
+  k_yee_b<R><<<blocks, threads, 0, s>>>(E[0], E[1], E[2], B[0], B[1], B[2], m, (R)(h / d[0]), (R)(h / d[1]),
+                                         (R)(h / d[2]));
+  k_yee_e<R><<<blocks, threads, 0, s>>>(E[0], E[1], E[2], B[0], B[1], B[2], J[0], J[1], J[2], m, (R)(dt / d[0]),
                                      (R)(dt / d[1]), (R)(dt / d[2]), (R)(dt * 4.0 * 3.141592653589793 * kAlpha));
-  k_yee_b<R><<<blocks, 256, 0, s>>>(E[0], E[1], E[2], B[0], B[1], B[2], m, (R)(h / d[0]), (R)(h / d[1]),
-                                     (R)(h / d[2]));
+  k_yee_b<R><<<blocks, threads, 0, s>>>(E[0], E[1], E[2], B[0], B[1], B[2], m, (R)(h / d[0]), (R)(h / d[1]),
+                                         (R)(h / d[2]));
   return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 

@@ -1077,14 +1077,40 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
   return (unsigned long long)__double_as_longlong(fabs(v));
 }
 
+template <typename R> struct Vec16;
+template <> struct Vec16<float> { using T = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using T = double2; static constexpr int n = 2; };
+__device__ __forceinline__ unsigned long long abs_bits_max(const float4 &v) {
+  const unsigned long long a = max(abs_bits(v.x), abs_bits(v.y)), b = max(abs_bits(v.z), abs_bits(v.w));
+  return a > b ? a : b;
+}
+__device__ __forceinline__ unsigned long long abs_bits_max(const double2 &v) {
+  const unsigned long long a = abs_bits(v.x), b = abs_bits(v.y);
+  return a > b ? a : b;
+}
+
+// max |component| of each of the six mesh arrays (as ordered bit patterns of
+// non-negative values), 16-byte loads where the array allows.
 template <typename R>
 __global__ void __launch_bounds__(256) k_grid_max(const StepArgs<R> a) {
+  using V = typename Vec16<R>::T;
+  constexpr int kV = Vec16<R>::n;
   const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
   for (int c = 0; c < 6; ++c) {
     const R *f = c < 3 ? a.E[c] : a.B[c - 3];
     unsigned long long m = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncell;
-         i += (long long)gridDim.x * blockDim.x) {
+    long long head = 0;
+    if (((uintptr_t)f & 15) == 0) {
+      const V *fv = (const V *)f;
+      const long long nv = ncell / kV;
+      for (long long i = t0; i < nv; i += stride) {
+        const unsigned long long b = abs_bits_max(__ldg(fv + i));
+        m = b > m ? b : m;
+      }
+      head = nv * kV;
+    }
+    for (long long i = head + t0; i < ncell; i += stride) {
       const unsigned long long b = abs_bits(__ldg(f + i));
       m = b > m ? b : m;
     }
