@@ -751,15 +751,13 @@ __device__ __noinline__ SampleCounts pair_samples(const StepArgs<R> &a, int pass
 
 // Electron, positron or ion: the adaptive sub-interval loop (Sec. IV.H) of
 // Boris push and modified emission generator (Sec. IV.G); ions are pushed only.
-template <typename R, bool EXT>
-__device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, R t_span,
-                                                V3<R> E, V3<R> B, Cnt &cnt, const uint64_t *idp, unsigned step,
-                                                bool deposit_later = false) {
-  // start position (scalars: arrays handed to the deposit would live in
-  // local memory for the whole loop)
-  const int cs0 = q.ci[0], cs1 = q.ci[1], cs2 = q.ci[2];
-  const R os0 = q.off[0], os1 = q.off[1], os2 = q.off[2];
-  const R qc = a.charge[sp], m = a.mass[sp];
+// massive_begin returns the step's number of sub-intervals (Eq. (28)) and
+// loads the id when the generator will draw; massive_sub takes sub-interval
+// s of n, each of length h.
+template <typename R>
+__device__ __forceinline__ int massive_begin(const StepArgs<R> &a, int sp, Pt<R> &q, R t_span, V3<R> E, V3<R> B,
+                                             const uint64_t *idp) {
+  const R m = a.mass[sp];
   const bool qed = (sp != kIon) && a.emission_on;
   if (qed && idp) q.id = __ldg(idp);
   int n = 1, capped = 0;
@@ -768,80 +766,99 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
     n = nsub_lepton(t_span, g0, heff_lepton(q.p, g0, E, B), a.kappa, a.nsub_max, capped);
     count_rare(a, kCntCapped, (unsigned)capped);
   }
-  const R h = t_span / R(n);
-  for (int s = 0; s < n; ++s) {
-    boris(q.p, E, B, qc, m, h);
-    R g = sqrt_r(R(1) + dot(q.p, q.p) / (m * m));
-    R im = R(1) / (m * g);
-    move(a, q, V3<R>{q.p.x * im, q.p.y * im, q.p.z * im}, h);
-    if (!qed) continue;
-    cnt.sub_l++;
-    R chi = chi_lepton(q.p, g, E, B);
-    R r1, r2;
-    draw2(q.id, step, (unsigned)s, kEmit, a.seed, r1, r2);
-    if (EXT && a.generator != 0) {
-      // the unmodified generators of Sec. IV.F
-      R delta, pe;
-      bool fire;
-      if (a.generator == 1) {
-        delta = r1;                                   // r2 < P(r1)
-        pe = prob_alternative(a.tab, r1, chi, g, h);
-        fire = r2 < pe;
-      } else {
-        pe = std_total(a.std_lnw, chi, g, h);        // r1 < W(1), W(delta)/W(1) = r2
-        fire = r1 < pe;
-        delta = fire ? std_delta(a.tab, a.std_cdf, a.std_lnw, chi, r2) : R(0);
-      }
-      if (pe > R(1)) {
-        count_rare(a, kCntPmGt1, 1u);
-        if (a.pm_strict) atomicOr(a.status, kStPmGt1);
-      }
-      if (fire) {
-        Pt<R> ph = q;
-        ph.p = {delta * q.p.x, delta * q.p.y, delta * q.p.z};
-        ph.id = product_id(a, q.id, step, (unsigned)s, kPhoton);
-        const R omd = R(1) - delta;
-        q.p = {omd * q.p.x, omd * q.p.y, omd * q.p.z};
-        cnt.emis++;
-        cnt.made_ph++;
-        spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), q.w);
-        count_outcome(a, emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B));
-      }
-      continue;
+  return n;
+}
+
+template <typename R, bool EXT>
+__device__ __forceinline__ void massive_sub(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, const V3<R> &E,
+                                            const V3<R> &B, Cnt &cnt, unsigned step, int s, int n, R h) {
+  const R qc = a.charge[sp], m = a.mass[sp];
+  const bool qed = (sp != kIon) && a.emission_on;
+  boris(q.p, E, B, qc, m, h);
+  R g = sqrt_r(R(1) + dot(q.p, q.p) / (m * m));
+  R im = R(1) / (m * g);
+  move(a, q, V3<R>{q.p.x * im, q.p.y * im, q.p.z * im}, h);
+  if (!qed) return;
+  cnt.sub_l++;
+  R chi = chi_lepton(q.p, g, E, B);
+  R r1, r2;
+  draw2(q.id, step, (unsigned)s, kEmit, a.seed, r1, r2);
+  if (EXT && a.generator != 0) {
+    // the unmodified generators of Sec. IV.F
+    R delta, pe;
+    bool fire;
+    if (a.generator == 1) {
+      delta = r1;                                   // r2 < P(r1)
+      pe = prob_alternative(a.tab, r1, chi, g, h);
+      fire = r2 < pe;
+    } else {
+      pe = std_total(a.std_lnw, chi, g, h);        // r1 < W(1), W(delta)/W(1) = r2
+      fire = r1 < pe;
+      delta = fire ? std_delta(a.tab, a.std_cdf, a.std_lnw, chi, r2) : R(0);
     }
-    // P_m(r1) <= emit_bound <= r2: no emission, whatever r1 (and the bound
-    // is below 1, so P_m is too); the generator factors reuse (r1, r2)
-    if (!(EXT && (a.emit_ng > 1 || a.emit_keep < R(1))) && r2 >= emit_bound(chi, g, h)) continue;
-    R pm = prob_emit(a.tab, r1, chi, g, h);
-    if (pm > R(1)) {
+    if (pe > R(1)) {
       count_rare(a, kCntPmGt1, 1u);
       if (a.pm_strict) atomicOr(a.status, kStPmGt1);
     }
-    if (EXT && (a.emit_ng > 1 || a.emit_keep < R(1))) {
-      // generator factors: products from N_g samples, kept with 1/f_g
-      const SampleCounts sc = emit_samples(a, pass, q, r1, r2, pm, chi, g, h, s, n, step, E, B);
-      cnt.made_ph += sc.made;
-      count_rare(a, kCntPmGt1, sc.gt1);
-      count_outcome(a, sc.out);
-      if (r2 < pm) {
-        const R omd = R(1) - r1 * r1 * r1;
-        q.p = {omd * q.p.x, omd * q.p.y, omd * q.p.z};
-        cnt.emis++;
-      }
-    } else if (r2 < pm) {
-      // photon along p with delta of it; the parent keeps (1 - delta)
-      R delta = r1 * r1 * r1;
+    if (fire) {
       Pt<R> ph = q;
       ph.p = {delta * q.p.x, delta * q.p.y, delta * q.p.z};
       ph.id = product_id(a, q.id, step, (unsigned)s, kPhoton);
-      R omd = R(1) - delta;
+      const R omd = R(1) - delta;
       q.p = {omd * q.p.x, omd * q.p.y, omd * q.p.z};
       cnt.emis++;
       cnt.made_ph++;
       spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), q.w);
       count_outcome(a, emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B));
     }
+    return;
   }
+  // P_m(r1) <= emit_bound <= r2: no emission, whatever r1 (and the bound
+  // is below 1, so P_m is too); the generator factors reuse (r1, r2)
+  if (!(EXT && (a.emit_ng > 1 || a.emit_keep < R(1))) && r2 >= emit_bound(chi, g, h)) return;
+  R pm = prob_emit(a.tab, r1, chi, g, h);
+  if (pm > R(1)) {
+    count_rare(a, kCntPmGt1, 1u);
+    if (a.pm_strict) atomicOr(a.status, kStPmGt1);
+  }
+  if (EXT && (a.emit_ng > 1 || a.emit_keep < R(1))) {
+    // generator factors: products from N_g samples, kept with 1/f_g
+    const SampleCounts sc = emit_samples(a, pass, q, r1, r2, pm, chi, g, h, s, n, step, E, B);
+    cnt.made_ph += sc.made;
+    count_rare(a, kCntPmGt1, sc.gt1);
+    count_outcome(a, sc.out);
+    if (r2 < pm) {
+      const R omd = R(1) - r1 * r1 * r1;
+      q.p = {omd * q.p.x, omd * q.p.y, omd * q.p.z};
+      cnt.emis++;
+    }
+  } else if (r2 < pm) {
+    // photon along p with delta of it; the parent keeps (1 - delta)
+    R delta = r1 * r1 * r1;
+    Pt<R> ph = q;
+    ph.p = {delta * q.p.x, delta * q.p.y, delta * q.p.z};
+    ph.id = product_id(a, q.id, step, (unsigned)s, kPhoton);
+    R omd = R(1) - delta;
+    q.p = {omd * q.p.x, omd * q.p.y, omd * q.p.z};
+    cnt.emis++;
+    cnt.made_ph++;
+    spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), q.w);
+    count_outcome(a, emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B));
+  }
+}
+
+template <typename R, bool EXT>
+__device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, R t_span,
+                                                V3<R> E, V3<R> B, Cnt &cnt, const uint64_t *idp, unsigned step,
+                                                bool deposit_later = false) {
+  // start position (scalars: arrays handed to the deposit would live in
+  // local memory for the whole loop)
+  const int cs0 = q.ci[0], cs1 = q.ci[1], cs2 = q.ci[2];
+  const R os0 = q.off[0], os1 = q.off[1], os2 = q.off[2];
+  const R qc = a.charge[sp];
+  const int n = massive_begin(a, sp, q, t_span, E, B, idp);
+  const R h = t_span / R(n);
+  for (int s = 0; s < n; ++s) massive_sub<R, EXT>(a, pass, sp, q, E, B, cnt, step, s, n, h);
   if (a.deposit && qc != R(0) && !deposit_later) {
     const int cs[3] = {cs0, cs1, cs2};
     const R os[3] = {os0, os1, os2};
@@ -1160,6 +1177,93 @@ template <typename R, bool PHOTON> struct Pass0Occ;
 template <> struct Pass0Occ<float, false> { static constexpr int blocks = 3; };
 template <> struct Pass0Occ<double, false> { static constexpr int blocks = 1; };
 
+// Analytic fields (not ensembles): e-, e+ and ions with lanes refilled one
+// particle at a time.  A particle takes its own number of sub-intervals, so a lane that
+// has finished takes the next particle while the others are still in their
+// loops, instead of idling until the longest loop of the warp ends.  Warps
+// take indices 32 at a time from the pass's work counter; every lane runs
+// sub-interval after sub-interval of whichever particle it holds.
+template <typename R, bool EXT>
+__device__ __forceinline__ void massive_lanes(const StepArgs<R> &a, const StepConst &kc, Cnt &cnt,
+                                              const long long *ns, long long total) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  bool has = false;
+  int sp = kElectron, n = 1, s = 0, cell = 0;
+  long long i = 0;
+  Pt<R> q;
+  V3<R> E, B;
+  R h = R(0);
+  long long qb = 0, qe = 0;   // the warp's batch of indices [qb, qe), warp-uniform
+  bool dry = false;           // the work counter has run past the end
+  for (;;) {
+    for (;;) {
+      const unsigned need = __ballot_sync(0xffffffffu, !has);
+      if (!need || dry) break;
+      if (qb >= qe) {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(a.work_massive, 32ull);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        qb = (long long)b;
+        qe = min(qb + 32, total);
+        if (qb >= total) {
+          dry = true;
+          break;
+        }
+      }
+      const long long avail = qe - qb;
+      const int rank = __popc(need & below);
+      if (!has && rank < avail) {
+        long long it = qb + rank;
+        sp = kElectron;
+        if (it >= ns[kElectron]) {
+          it -= ns[kElectron];
+          sp = kPositron;
+          if (it >= ns[kPositron]) { it -= ns[kPositron]; sp = kIon; }
+        }
+        i = it;
+        load(a, sp, i, q, cell);
+        if (cell >= 0) {
+          cnt.psteps[sp]++;
+          const unsigned row = fast_div((unsigned)cell, a.div_m[0], a.div_l[0]);
+          const unsigned slab = fast_div((unsigned)cell, a.div_m[1], a.div_l[1]);
+          q.ci[0] = cell - (int)row * a.n[0];
+          q.ci[1] = (int)row - (int)slab * a.n[1];
+          q.ci[2] = (int)slab;
+          const uint64_t *idp = a.id[sp] + i;
+          if (EXT && a.field_mode == kFieldEnsemble) {
+            q.id = __ldg(idp);
+            idp = nullptr;
+            field_ensemble(a, q.id, E, B);
+          } else {
+            field_analytic(a, kc, q, E, B);
+          }
+          const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
+          if (!(probe == R(0))) {
+            count_rare(a, kCntNonfinite, 1u);
+            atomicOr(a.status, kStNonfinite);
+          }
+          n = massive_begin(a, sp, q, a.dt, E, B, idp);
+          h = a.dt / R(n);
+          s = 0;
+          has = true;
+        }
+      }
+      qb += min((long long)__popc(need), avail);
+    }
+    if (!__any_sync(0xffffffffu, has)) break;
+    if (has) {
+      massive_sub<R, EXT>(a, 0, sp, q, E, B, cnt, kc.step, s, n, h);
+      if (++s == n) {
+        const int nc = finish_cell(a, q);
+        if (nc < 0) count_rare(a, kCntAbsorbed, 1u);
+        store(a, sp, i, q, nc, false);
+        has = false;
+      }
+    }
+  }
+}
+
 template <typename R, bool PHOTON, bool EXT>
 __global__ void __launch_bounds__(256, (Pass0Occ<R, PHOTON>::blocks)) k_pass0(const StepArgs<R> a) {
   Cnt cnt;
@@ -1178,6 +1282,13 @@ __global__ void __launch_bounds__(256, (Pass0Occ<R, PHOTON>::blocks)) k_pass0(co
   }
   __syncthreads();
   const long long total = PHOTON ? ns[kPhoton] : ns[kElectron] + ns[kPositron] + ns[kIon];
+  // (ensembles order their leptons by estimated sub-interval count instead,
+  // and measured faster with whole-particle loops)
+  if (!PHOTON && a.field_mode != kFieldGrid && a.field_mode != kFieldEnsemble) {
+    massive_lanes<R, EXT>(a, kc, cnt, ns, total);
+    flush(cnt, a.counters);
+    return;
+  }
   auto body = [&](long long it) {
     int sp = kPhoton;
     long long i = it;
