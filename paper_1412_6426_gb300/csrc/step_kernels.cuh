@@ -152,11 +152,11 @@ __device__ __forceinline__ unsigned long long cycles_fixed(double cyc) {
 }
 
 // Largest chi_g for which no pair draw can succeed when the sub-interval is
-// not capped: there h <= dt_q = kappa 130 (2 pi)/H, so the bound of
-// pair_bound is at most 2 sqrt3/(2pi) alpha kappa 130 (2 pi) F2(z_min) =
-// 3.2862 kappa F2(z_min), z_min = 8/(3 chi_g).  z* solves
-// 3.2862 kappa F2(z*) = r2_floor / 2 on the decreasing branch of F2 (beyond
-// its maximum at 0.4169), by bisection on the table; chi* = 8/(3 z*).
+// not capped: there h <= dt_q = kappa 130 (2 pi)/H, so P_p is at most
+// sqrt3/(2pi) alpha kappa 130 (2 pi) F2(z_min) = 1.6431 kappa F2(z_min),
+// z_min = 8/(3 chi_g).  z* solves 3.2862 kappa F2(z*) = r2_floor / 2 on the
+// decreasing branch of F2 (beyond its maximum at 0.4169), by bisection on the
+// table (a factor 4 of margin); chi* = 8/(3 z*).
 template <typename R>
 __device__ double photon_chi_star(const R *tab, double kappa) {
   const double target = 0.5 * (double)r2_floor(R(0)) / (3.2862 * kappa);
@@ -587,18 +587,18 @@ __device__ __forceinline__ R emit_bound(R chi, R gamma, R h) {
 // Upper bound of P_p(de) over de for one sub-interval (Eq. (30)):
 // P_p <= alpha h sqrt3/(2pi) (chi/eps) F2(z_p), and z_p >= z_min = 8/(3 chi)
 // at de = 1/2, where F2 decreases beyond its maximum 0.60705 at z = 0.4169.
-// A factor 2 covers the table's rounding.
+// Beyond 0.42, F2(z) = z K_{2/3}(z) lies below the first two terms of the
+// asymptotic series of K_{2/3}, whose next term is negative:
+//   F2(z) <= sqrt(pi z / 2) e^(-z) (1 + 7/(72 z)),
+// which costs one exponential instead of a table evaluation.  A factor 1.02
+// covers this evaluation's rounding.
 template <typename R>
-__device__ __forceinline__ R pair_bound(const R *__restrict__ T, R chig, R eps, R h) {
+__device__ __forceinline__ R pair_bound(R chig, R eps, R h) {
   if (!(chig > R(0)) || !(eps > R(0))) return R(0);
-  R zmin = R(8.0 / 3.0) / chig;
+  const R zmin = R(8.0 / 3.0) / chig;
   R f2 = R(0.6071);
-  if (zmin > R(0.42)) {
-    R g1, g2;
-    syn_g(T, zmin, g1, g2);
-    f2 = cbrt_r(zmin) * g2;
-  }
-  return R(2) * R(kAlpha) * h * R(kSqrt3Over2Pi) * (chig / eps) * f2;
+  if (zmin > R(0.42)) f2 = sqrt_r(R(kPi / 2) * zmin) * exp_r(-zmin) * (R(1) + R(7.0 / 72.0) / zmin);
+  return R(1.02 * kAlpha * kSqrt3Over2Pi) * h * (chig / eps) * f2;
 }
 
 // Id of a product: child_id of the parent, keeping the parent's ensemble
@@ -894,7 +894,7 @@ __device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, P
   if (may_pair) {
     if (!capped && chig < chi_star) may_pair = false;
     else {
-      bound = pair_bound(a.tab, chig, eps, h);
+      bound = pair_bound(chig, eps, h);
       may_pair = bound >= r2_floor(h);
     }
   }

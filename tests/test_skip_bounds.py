@@ -8,7 +8,8 @@ unchanged only if the bound really holds:
       chi^(2/3) + 1.8212 chi), before the kernels' 2% rounding margin;
   pairs (Eq. (30)):    P_p(de) <= alpha h sqrt3/(2 pi) (chi/eps) F2(z_min),
       z_min = 8/(3 chi), F2 at most 0.60705 (at 0.4169) and decreasing
-      beyond, before the kernels' factor 2.
+      beyond, where F2(z) <= sqrt(pi z/2) e^(-z) (1 + 7/(72 z)) (the kernels
+      evaluate this form, with a 2% rounding margin).
 """
 import math
 
@@ -44,10 +45,14 @@ def test_pair_bound():
     assert f2.max() <= 0.60706 and abs(zs[f2.argmax()] - 0.4169) < 0.01
     beyond = zs > 0.4169
     assert np.all(np.diff(f2[beyond]) <= 0.0)
+    bound_f2 = lambda z: math.sqrt(math.pi * z / 2) * math.exp(-z) * (1 + 7 / (72 * z))
+    zz = np.concatenate([np.linspace(0.42, 5, 3000), np.logspace(math.log10(5), 2.5, 1000)])
+    ratio = np.array([o.F2(z) / bound_f2(z) for z in zz])
+    assert ratio.max() <= 1.0 and ratio.max() > 0.999       # tight at large z
     des = np.concatenate([np.linspace(1e-6, 1 - 1e-6, 1001), np.logspace(-9, -2, 50)])
     for chig in np.logspace(-2, 4, 31):
         eps, h = 100.0, 10.0
         zmin = 8.0 / (3.0 * chig)
-        f = o.F2(zmin) if zmin > 0.42 else 0.6071
+        f = bound_f2(zmin) if zmin > 0.42 else 0.6071
         b = ALPHA * h * K * (chig / eps) * f
         assert max(o.Pp(de, chig, eps, h) for de in des) <= b * (1 + 1e-12)
