@@ -995,28 +995,28 @@ __device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m, int l) {
 }
 
 // ----- the start records of the cell-block pass (second store buffer) ------
-__device__ __forceinline__ void copy_record(const StepArgs<float> &a, int sp, long long i) {
-  ((float4 *)a.pos_scratch[sp])[i] = ((const float4 *)a.pos[sp])[i];
-  ((float4 *)a.mom_scratch[sp])[i] = ((const float4 *)a.mom[sp])[i];
+// The start point of a record advanced by the cell-block pass (offsets and
+// cell: all the deposit needs of it), kept in the store's second buffer.
+__device__ __forceinline__ void keep_start(const StepArgs<float> &a, int sp, long long i, const Pt<float> &q,
+                                           int cell) {
+  ((float4 *)a.pos_scratch[sp])[i] = make_float4(q.off[0], q.off[1], q.off[2], __int_as_float(cell));
 }
-__device__ __forceinline__ void copy_record(const StepArgs<double> &a, int sp, long long i) {
-  const double2 *P = (const double2 *)a.pos[sp] + 2 * i, *M = (const double2 *)a.mom[sp] + 2 * i;
-  double2 *P2 = (double2 *)a.pos_scratch[sp] + 2 * i, *M2 = (double2 *)a.mom_scratch[sp] + 2 * i;
-  P2[0] = P[0]; P2[1] = P[1];
-  M2[0] = M[0]; M2[1] = M[1];
+__device__ __forceinline__ void keep_start(const StepArgs<double> &a, int sp, long long i, const Pt<double> &q,
+                                           int cell) {
+  double2 *P2 = (double2 *)a.pos_scratch[sp] + 2 * i;
+  P2[0] = make_double2(q.off[0], q.off[1]);
+  P2[1] = make_double2(q.off[2], (double)cell);
 }
-__device__ __forceinline__ void load_scratch(const StepArgs<float> &a, int sp, long long i, Pt<float> &q,
-                                             int &cell) {
-  unpack(__ldg((const float4 *)a.pos_scratch[sp] + i), __ldg((const float4 *)a.mom_scratch[sp] + i), q, cell);
+__device__ __forceinline__ void load_start(const StepArgs<float> &a, int sp, long long i, float *off, int &cell) {
+  const float4 v = __ldg((const float4 *)a.pos_scratch[sp] + i);
+  off[0] = v.x; off[1] = v.y; off[2] = v.z;
+  cell = __float_as_int(v.w);
 }
-__device__ __forceinline__ void load_scratch(const StepArgs<double> &a, int sp, long long i, Pt<double> &q,
-                                             int &cell) {
+__device__ __forceinline__ void load_start(const StepArgs<double> &a, int sp, long long i, double *off, int &cell) {
   const double2 *P = (const double2 *)a.pos_scratch[sp] + 2 * i;
-  const double2 *M = (const double2 *)a.mom_scratch[sp] + 2 * i;
-  double2 p0 = __ldg(P), p1 = __ldg(P + 1), m0 = __ldg(M), m1 = __ldg(M + 1);
-  q.off[0] = p0.x; q.off[1] = p0.y; q.off[2] = p1.x; q.w = p1.y;
-  q.p = {m0.x, m0.y, m1.x};
-  cell = (int)m1.y;
+  const double2 p0 = __ldg(P), p1 = __ldg(P + 1);
+  off[0] = p0.x; off[1] = p0.y; off[2] = p1.x;
+  cell = (int)p1.y;
 }
 template <typename R>
 __device__ __forceinline__ void decode_cell(const StepArgs<R> &a, int cell, int *ci) {
@@ -1561,7 +1561,7 @@ __global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
       int cell;
       load(a, sp, i, q, cell);
       if (cell < 0) continue;
-      if (a.deposit) copy_record(a, sp, i);
+      if (a.deposit) keep_start(a, sp, i, q, cell);
       cnt.psteps[sp]++;
       const unsigned row = fast_div((unsigned)cell, a.div_m[0], a.div_l[0]);
       const unsigned slab = fast_div((unsigned)cell, a.div_m[1], a.div_l[1]);
@@ -1616,10 +1616,10 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
     const R qc = a.charge[sp];
     const long long lo = (long long)item * kBlockChunk, hi = min(lo + kBlockChunk, bi.nsort[f]);
     // one cell block for the whole item (start positions)?
-    Pt<R> qa, qb;
+    R oa[3], ob[3];
     int ca, cb;
-    load_scratch(a, sp, lo, qa, ca);
-    load_scratch(a, sp, hi - 1, qb, cb);
+    load_start(a, sp, lo, oa, ca);
+    load_start(a, sp, hi - 1, ob, cb);
     int bl = -1;
     if (ca >= 0 && cb >= 0) {
       const int ba = block_of_cell(a, ca), bb = block_of_cell(a, cb);
@@ -1640,9 +1640,10 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
     __syncthreads();
     if (qc != R(0))
       for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        Pt<R> q0, q1;
+        Pt<R> q1;
+        R os[3];
         int c0, c1;
-        load_scratch(a, sp, i, q0, c0);
+        load_start(a, sp, i, os, c0);
         load(a, sp, i, q1, c1);
         if (c0 < 0 || c1 < 0) continue;
         int cs[3], ce[3];
@@ -1651,12 +1652,11 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
         // the end cell unwrapped next to the start (a step moves < 1 cell)
         for (int c = 0; c < 3; ++c) {
           int dc = ce[c] - cs[c];
-          const R disp = R(dc) + q1.off[c] - q0.off[c];
+          const R disp = R(dc) + q1.off[c] - os[c];
           if (disp >= R(1)) dc -= a.n[c];
           else if (disp <= R(-1)) dc += a.n[c];
           q1.ci[c] = cs[c] + dc;
         }
-        const R os[3] = {q0.off[0], q0.off[1], q0.off[2]};
         if (!tile || !deposit_tile(a, jt, torg, cs, os, q1, qc * q1.w)) deposit(a, cs, os, q1, qc * q1.w);
       }
     __syncthreads();
