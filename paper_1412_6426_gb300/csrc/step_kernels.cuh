@@ -578,10 +578,14 @@ __device__ __noinline__ void spectrum_add(const StepArgs<R> &a, R delta, R eps, 
 //   P_m <= alpha h sqrt3/(2 pi gamma) (5.6336 chi^(2/3) + 1.8212 chi)
 // (the two bounds behind the time-step requirement of Sec. IV.H).  A factor
 // 1.02 covers the tables' and this evaluation's rounding.
+// Both bounds are evaluated in FP32 in either precision: a bound only has to
+// lie above the probability, which the 2% margin keeps through FP32 rounding,
+// and where FP32 underflows to 0 the probability is far below the smallest
+// FP64 uniform as well.
 template <typename R>
 __device__ __forceinline__ R emit_bound(R chi, R gamma, R h) {
-  const R c13 = cbrt_r(chi);
-  return R(1.02 * kAlpha * kSqrt3Over2Pi) * h / gamma * (R(5.6336) * c13 * c13 + R(1.8212) * chi);
+  const float c = (float)chi, c13 = cbrtf(c);
+  return (R)(float(1.02 * kAlpha * kSqrt3Over2Pi) * (float)h / (float)gamma * (5.6336f * c13 * c13 + 1.8212f * c));
 }
 
 // Upper bound of P_p(de) over de for one sub-interval (Eq. (30)):
@@ -595,10 +599,10 @@ __device__ __forceinline__ R emit_bound(R chi, R gamma, R h) {
 template <typename R>
 __device__ __forceinline__ R pair_bound(R chig, R eps, R h) {
   if (!(chig > R(0)) || !(eps > R(0))) return R(0);
-  const R zmin = R(8.0 / 3.0) / chig;
-  R f2 = R(0.6071);
-  if (zmin > R(0.42)) f2 = sqrt_r(R(kPi / 2) * zmin) * exp_r(-zmin) * (R(1) + R(7.0 / 72.0) / zmin);
-  return R(1.02 * kAlpha * kSqrt3Over2Pi) * h * (chig / eps) * f2;
+  const float c = (float)chig, zmin = (8.0f / 3.0f) / c;
+  float f2 = 0.6071f;
+  if (zmin > 0.42f) f2 = sqrtf(float(kPi / 2) * zmin) * __expf(-zmin) * (1.0f + float(7.0 / 72.0) / zmin);
+  return (R)(float(1.02 * kAlpha * kSqrt3Over2Pi) * (float)h * (c / (float)eps) * f2);
 }
 
 // Id of a product: child_id of the parent, keeping the parent's ensemble
