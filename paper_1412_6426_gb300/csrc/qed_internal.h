@@ -42,12 +42,11 @@ struct Store {
 
 // Everything the step kernel reads, passed by value.
 template <typename R> struct StepArgs {
-  // stores (current buffers), and the second buffers (free between
-  // compactions: the cell-block pass keeps its start records there)
+  // stores (current buffers), and the second position buffers (free between
+  // compactions: the cell-block pass keeps its start points there)
   void *pos[4];
   void *mom[4];
   void *pos_scratch[4];
-  void *mom_scratch[4];
   uint64_t *id[4];
   long long *count;        // [4] store sizes (live + dead), appended atomically
   const long long *nstart; // [4] sizes at the start of the step

@@ -1726,7 +1726,6 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     a.pos[sp] = st.pos[st.cur];
     a.mom[sp] = st.mom[st.cur];
     a.pos_scratch[sp] = st.pos[st.cur ^ 1];
-    a.mom_scratch[sp] = st.mom[st.cur ^ 1];
     a.id[sp] = st.id[st.cur];
     a.cap[sp] = st.cap;
     a.charge[sp] = (R)c->species.charge[sp];
