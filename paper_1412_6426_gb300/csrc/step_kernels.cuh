@@ -998,7 +998,7 @@ __device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m, int l) {
   return (__umulhi(n, m) + n) >> l;   // exact for n < 2^31 (Granlund-Montgomery)
 }
 
-// ----- the start records of the cell-block pass (second store buffer) ------
+// ----- the start points of the cell-block pass (second store buffer) -------
 // The start point of a record advanced by the cell-block pass (offsets and
 // cell: all the deposit needs of it), kept in the store's second buffer.
 __device__ __forceinline__ void keep_start(const StepArgs<float> &a, int sp, long long i, const Pt<float> &q,
@@ -1525,7 +1525,7 @@ __device__ __forceinline__ BlockItems block_items(const StepArgs<R> &a, const lo
 // Grid mode: electrons, positrons and ions in cell-block order, advanced in
 // work items taken by work stealing; warps take 32 records at a time inside
 // an item, so fast warps take more.  The current is deposited afterwards by
-// k_deposit_blocks, from the start record each thread leaves in the store's
+// k_deposit_blocks, from the start point each thread leaves in the store's
 // second buffer (free between compactions): keeping the Esirkepov stencil
 // out of this kernel keeps its code within the instruction cache.
 template <typename R, bool EXT>
