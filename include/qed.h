@@ -209,7 +209,11 @@ typedef struct qed_tuning {
     int32_t work_chunk;            /* particles a block of the e-/e+/ion pass
                                       takes per grab of the shared work
                                       counter (multiple of 256); 0 = a static
-                                      grid-stride loop */
+                                      grid-stride loop.  Ensembles and the
+                                      mesh's unsorted records only: in the
+                                      other analytic modes warps take 32
+                                      particles per grab and refill each
+                                      lane as its particle finishes */
     int32_t compact_interval;      /* steps between removals of dead records
                                       (and re-sorts), >= 1 */
     int32_t sort_massive;          /* QED_FIELD_ENSEMBLE: at each compaction,
