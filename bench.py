@@ -133,6 +133,28 @@ def make_workload(seed: int):
     return workloads.beam_laser_collision(n_particles=N_ELECTRONS, seed=seed, nsteps=RUN_STEPS)
 
 
+def rank_seed(rank: int) -> int:
+    """Weak scaling: rank r runs its own workload, drawn with seed 1 + r."""
+    return 1 + rank
+
+
+def combine_ranks(items):
+    """[(value, "sum" | "max"), ...] -> the values summed or maximised over
+    the ranks of the current process group (one rank, or none: unchanged).
+    The only collective of a run: the data path has none."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return [float(v) for v, _ in items]
+    dev = "cuda" if tdist.get_backend() == "nccl" else "cpu"
+    out = []
+    for v, op in items:
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.SUM if op == "sum" else tdist.ReduceOp.MAX)
+        out.append(float(t.item()))
+    return out
+
+
 def scale_workload(n_electrons: int) -> None:
     """Shrink the beam (and capacities) for profiling captures."""
     global N_ELECTRONS, CAPS
@@ -651,13 +673,7 @@ def main_cascade(args, world, rank, local):
     W = args.warmup
     K = CASCADE_STEPS - W if args.steps == RUN_STEPS - 3 else args.steps
     r = cascade_run(K, W, barrier, e2e_steps=0 if args.no_e2e else 2)
-    tot = float(r["particle_steps"])
-    mx = r["seconds"]
-    if world > 1:
-        t = torch.tensor([tot, mx], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t[:1], op=tdist.ReduceOp.SUM)
-        tdist.all_reduce(t[1:], op=tdist.ReduceOp.MAX)
-        tot, mx = float(t[0]), float(t[1])
+    tot, mx = combine_ranks([(r["particle_steps"], "sum"), (r["seconds"], "max")])
     if rank != 0:
         if world > 1:
             tdist.destroy_process_group()
@@ -877,12 +893,7 @@ def main_large(args, world, rank, local):
     r = large_device(32, K, W, barrier)
     r64 = None if args.no_fp64 else large_device(64, max(2, K // 4), W, barrier)
     e2e = None if args.no_e2e else large_e2e()
-    tot, mx = float(r["particle_steps"]), r["seconds"]
-    if world > 1:
-        t = torch.tensor([tot, mx], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t[:1], op=tdist.ReduceOp.SUM)
-        tdist.all_reduce(t[1:], op=tdist.ReduceOp.MAX)
-        tot, mx = float(t[0]), float(t[1])
+    tot, mx = combine_ranks([(r["particle_steps"], "sum"), (r["seconds"], "max")])
     if rank != 0:
         if world > 1:
             tdist.destroy_process_group()
@@ -934,20 +945,12 @@ def main_batched(args, world, rank, local):
         if world > 1:
             tdist.barrier()
 
-    def reduce(x: float, op) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=op)
-        return float(t.item())
-
     build.build()
-    w = make_batched(seed=1 + rank)           # weak scaling: each rank its own 512 ensembles
+    w = make_batched(seed=rank_seed(rank))    # weak scaling: each rank its own 512 ensembles
     r = batched_device(w, 32, args.steps, args.warmup, barrier)
     r64 = None if args.no_fp64 else batched_device(w, 64, args.steps, args.warmup, barrier)
     e2e = None if args.no_e2e else batched_e2e(w, 32, 2)
-    tot = reduce(float(r["particle_steps"]), tdist.ReduceOp.SUM if world > 1 else None)
-    mx = reduce(r["seconds"], tdist.ReduceOp.MAX if world > 1 else None)
+    tot, mx = combine_ranks([(r["particle_steps"], "sum"), (r["seconds"], "max")])
     if rank != 0:
         if world > 1:
             tdist.destroy_process_group()
@@ -1112,32 +1115,22 @@ def main():
         if world > 1:
             tdist.barrier()
 
-    def reduce(x: float, op) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=op)
-        return float(t.item())
-
     from paper_1412_6426_gb300 import build
     build.build()
-    w = make_workload(seed=1 + rank)          # weak scaling: each rank its own beam
+    w = make_workload(seed=rank_seed(rank))   # weak scaling: each rank its own beam
     r32 = time_device(w, 32, K, W, barrier)
     r64 = None if args.no_fp64 else time_device(w, 64, K, W, barrier)
     e2e = None if args.no_e2e else time_e2e(w, 32, K, W)
 
-    tot_ps = reduce(float(r32["particle_steps"]), tdist.ReduceOp.SUM if world > 1 else None)
-    max_s = reduce(r32["seconds"], tdist.ReduceOp.MAX if world > 1 else None)
+    tot_ps, max_s = combine_ranks([(r32["particle_steps"], "sum"), (r32["seconds"], "max")])
     value = tot_ps / max_s
     out64 = None
     if r64 is not None:
-        tot64 = reduce(float(r64["particle_steps"]), tdist.ReduceOp.SUM if world > 1 else None)
-        max64 = reduce(r64["seconds"], tdist.ReduceOp.MAX if world > 1 else None)
+        tot64, max64 = combine_ranks([(r64["particle_steps"], "sum"), (r64["seconds"], "max")])
         out64 = {"value": tot64 / max64, "ms_per_step": r64["ms_per_step"]}
     e2e_val = None
     if e2e is not None:
-        tot_e = reduce(float(e2e["particle_steps"]), tdist.ReduceOp.SUM if world > 1 else None)
-        max_e = reduce(e2e["seconds"], tdist.ReduceOp.MAX if world > 1 else None)
+        tot_e, max_e = combine_ranks([(e2e["particle_steps"], "sum"), (e2e["seconds"], "max")])
         e2e_val = tot_e / max_e
     if rank != 0:
         if world > 1:
