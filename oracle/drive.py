@@ -18,7 +18,7 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
         ion_charge: float = 1.0, ion_mass: float = 1836.15267343, time_from: int = 0,
         ens_bits: int = 0, ens=None, emit_fg: float = 1.0, emit_ng: int = 1, pair_fg: float = 1.0,
         pair_ng: int = 1, thin_interval: int = 0, thin_limit=(0, 0, 0, 0), generator: int = 0,
-        schwinger_on: int = 0, schwinger_weight: float = 1.0):
+        schwinger_on: int = 0, schwinger_weight: float = 1.0, expect: bool = False):
     """Advance the given particles by nsteps steps of dt.
 
     particles: {species: (x[n,3], p[n,3], w[n], id[n])}.  Returns
@@ -29,7 +29,9 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
     "timed_particle_steps").  With thin_interval > 0 the stores are thinned
     after every step s with (s + 1) % thin_interval == 0 (Sec. VI).  With
     schwinger_on, pairs from the vacuum are created per cell after the
-    particles of each step, before the field update (Sec. V.B).
+    particles of each step, before the field update (Sec. V.B).  With expect
+    (and nbins), diag also holds "expected" and "expected_var": the photon
+    spectrum expected along the realised trajectories, and its variance.
     """
     import time
     P = o.make_params(n=n, d=d, x0=x0, periodic=periodic, field_mode=field_mode, fp=fp, kappa=kappa,
@@ -42,7 +44,7 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
     if caps is None:
         base = sum(len(v[3]) for v in particles.values())
         caps = (4 * base + 64,) * 4
-    run_ = o.Run(P, caps=caps, nbins=nbins)
+    run_ = o.Run(P, caps=caps, nbins=nbins, expect=expect)
     absorbed_at_set = 0
     for sp, (x, p, w, ids) in particles.items():
         # a particle placed outside an open lattice is removed before any step
@@ -86,4 +88,7 @@ def run(n, d, x0, periodic, field_mode, fp, dt, nsteps, particles: dict, *, kapp
     diag["particle_steps"] = psteps
     diag["timed_particle_steps"] = timed_ps
     diag["timed_seconds"] = t_end - t_start if nsteps > time_from else 0.0
+    if expect and nbins:
+        diag["expected"] = run_.expected[:nbins].copy()
+        diag["expected_var"] = run_.expected_var[:nbins].copy()
     return out, diag, spec, spec_e

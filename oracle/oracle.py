@@ -87,7 +87,9 @@ class Diag(ctypes.Structure):
         "thinned", "schwinger_pairs", "schwinger_gt1")] + [
         ("energy_defect", ctypes.c_double),
         ("spectrum", ctypes.POINTER(ctypes.c_double)),
-        ("spectrum_energy", ctypes.POINTER(ctypes.c_double))]
+        ("spectrum_energy", ctypes.POINTER(ctypes.c_double)),
+        ("expected", ctypes.POINTER(ctypes.c_double)),
+        ("expected_var", ctypes.POINTER(ctypes.c_double))]
 
 
 _lib = None
@@ -354,7 +356,7 @@ class Species:
 class Run:
     """One oracle simulation: four species stores, parameters, diagnostics."""
 
-    def __init__(self, params: Params, caps, nbins: int = 0):
+    def __init__(self, params: Params, caps, nbins: int = 0, expect: bool = False):
         self.P = params
         self.P.nbins = nbins
         self.sp = [Species(c) for c in caps]
@@ -363,6 +365,12 @@ class Run:
         self.D = Diag()
         self.D.spectrum = _dp(self.spectrum)
         self.D.spectrum_energy = _dp(self.spectrum_energy)
+        # the expected spectrum along the realised trajectories (and its variance)
+        self.expected = np.zeros(max(nbins, 1))
+        self.expected_var = np.zeros(max(nbins, 1))
+        if expect:
+            self.D.expected = _dp(self.expected)
+            self.D.expected_var = _dp(self.expected_var)
         self.fields = None
         self.J = None
 

@@ -673,6 +673,12 @@ typedef struct {
     double energy_defect;    /* sum of w*(energy before - energy after) over events */
     double *spectrum;        /* nbins, weighted by w, over log10(delta) */
     double *spectrum_energy; /* nbins, weighted by w, over log10(photon energy) with the same range */
+    /* optional (test infrastructure): along the realised trajectories, the
+     * expected number of photons in each spectrum bin, sum over lepton
+     * sub-intervals of w * int_bin P(delta) d delta (Eq. (24)), and the sum of
+     * w^2 p (1 - p), its variance (modified generator, trivial factors) */
+    double *expected;
+    double *expected_var;
 } or_diag;
 
 typedef struct {
@@ -739,6 +745,34 @@ static int or_keep(const or_params *P, double fg, uint64_t id, uint32_t step, ui
 
 static double or_fg(double fg) { return fg > 1.0 ? fg : 1.0; }
 static int or_ng(int32_t ng) { return ng > 1 ? (int)ng : 1; }
+
+/* Probability that the sub-interval of length h emits a photon with delta in
+ * each spectrum bin: int_bin P(delta) d delta, by 6-point Gauss-Legendre in
+ * ln delta per bin (P = alpha h G / gamma, Eq. (24)); the modified generator
+ * emits with exactly this probability when P_m <= 1 (Sec. IV.G). */
+static void or_expect_add(or_ctx *C, double chi, double gamma, double h, double w)
+{
+    static const double x6[6] = {-0.9324695142031521, -0.6612093864662645, -0.2386191860831969,
+                                 0.2386191860831969, 0.6612093864662645, 0.9324695142031521};
+    static const double w6[6] = {0.1713244923791704, 0.3607615730481386, 0.4679139345726910,
+                                 0.4679139345726910, 0.3607615730481386, 0.1713244923791704};
+    const or_params *P = C->P;
+    const double span = (P->lg_hi - P->lg_lo) / P->nbins;
+    for (int b = 0; b < P->nbins; ++b) {
+        double ua = (P->lg_lo + b * span) * log(10.0), ub = (P->lg_lo + (b + 1) * span) * log(10.0);
+        if (ua >= 0.0) break;                       /* delta < 1 */
+        if (ub > 0.0) ub = 0.0;
+        double mid = 0.5 * (ua + ub), half = 0.5 * (ub - ua), sum = 0.0;
+        for (int k = 0; k < 6; ++k) {
+            double delta = exp(mid + half * x6[k]);
+            if (delta >= 1.0) continue;
+            sum += w6[k] * or_P(delta, chi, gamma, h) * delta;
+        }
+        double pb = sum * half;
+        C->D->expected[b] += w * pb;
+        C->D->expected_var[b] += w * w * pb * (1.0 - pb);
+    }
+}
 
 static void or_spectrum_add(or_ctx *C, double delta, double eps, double w)
 {
@@ -858,6 +892,7 @@ static void or_process(or_ctx *C, int sp, or_particle *q, double t_span,
                 }
                 continue;
             }
+            if (C->D->expected && C->D->expected_var && P->nbins > 0) or_expect_add(C, chi, g, h, q->w);
             double pm = or_Pm(r1, chi, g, h);
             if (pm > 1.0) C->D->pm_gt1++;
             /* Products (Sec. VI): N_g samples of the generator, sample 0 being
