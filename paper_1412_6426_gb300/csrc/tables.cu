@@ -173,7 +173,7 @@ int build_standard(qed_ctx *c, cudaStream_t s) {
   if (c->prec == 64) {
     tab64 = (const double *)c->d_tables;
   } else {
-    // an FP64 synchrotron table only for this build
+    // a temporary FP64 synchrotron table, used only to fill the standard generator's table
     if (cudaMallocAsync(&tmp, sizeof(double) * Tab<double>::kSize, s) != cudaSuccess) return QED_ERR_CUDA;
     int rc = build_into<double>(c, tmp, s);
     if (rc != QED_OK) {
