@@ -87,3 +87,18 @@ def test_self_consistent_cascade_pulses_are_vacuum_plane_waves():
     w, f = wl.self_consistent_cascade(n=n, n_seed=10, precision=64, cells_per_lambda=16, steps_per_period=32)
     lo, hi = _poynting_ratio(f, n, 0)
     assert abs(lo - 1) < 0.03 and abs(hi + 1) < 0.03, (lo, hi)
+
+
+def test_profile_expansion_same_with_torch_and_numpy():
+    # the bench and the full-size tests expand the mesh profiles with torch on
+    # the device; the layout (x fastest) must be numpy's
+    import torch
+    n = 16
+    w, fx, fy = wl.large_cascade(n=n)
+    a = wl.expand_profiles(fx, fy, n)
+    b = wl.expand_profiles(fx, fy, n, xp=torch, dtype=torch.float64)
+    for u, v in zip(a, b):
+        assert np.array_equal(np.asarray(u), v.numpy())
+    # F[k, j, i] = fx[i] + fy[j]
+    f = np.asarray(a[2]).reshape(n, n, n)
+    assert f[3, 5, 7] == fx[2][7] + fy[2][5]
