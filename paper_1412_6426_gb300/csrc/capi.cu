@@ -16,15 +16,6 @@ namespace {
 
 cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
 
-int fold_status(int bits) {
-  if (bits & qed::kStCapacity) return QED_ERR_CAPACITY;
-  if (bits & qed::kStNonfinite) return QED_ERR_NONFINITE;
-  if (bits & qed::kStTimeout) return QED_ERR_TIMEOUT;
-  if (bits & qed::kStPmGt1) return QED_ERR_PMGT1;
-  if (bits & qed::kStCourant) return QED_ERR_COURANT;
-  return QED_OK;
-}
-
 template <typename T> int dalloc(T **p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return QED_OK;
@@ -90,8 +81,7 @@ int check_tuning(const qed_ctx *c, const qed_tuning *t) {
   if (t->work_chunk < 0 || t->work_chunk % 256 != 0 || t->work_chunk > (1 << 24)) return QED_ERR_ARG;
   if (t->compact_interval < 1 || (t->sort_massive != 0 && t->sort_massive != 1)) return QED_ERR_ARG;
   if (t->concurrent != 0 && t->concurrent != 1) return QED_ERR_ARG;
-  for (int k = 0; k < 2; ++k)
-    if (t->reserved[k] != 0) return QED_ERR_ARG;
+  if (t->deposit_halo < 0 || t->deposit_halo > qed::kMaxDepositHalo || t->reserved != 0) return QED_ERR_ARG;
   return QED_OK;
 }
 
@@ -128,9 +118,7 @@ int read_status(qed_ctx *c, cudaStream_t s) {
   if (cudaMemcpyAsync(&bits, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return QED_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return QED_ERR_CUDA;
-  int st = fold_status(bits);
-  if (st != QED_OK) c->latched = st;
-  return st;
+  return qed_latch_status(c, bits);
 }
 
 }  // namespace
@@ -308,6 +296,8 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     c->tune.work_chunk = 0;
     c->tune.compact_interval = p->compact_interval > 0 ? p->compact_interval : 8;
     c->tune.sort_massive = c->key_ensembles;
+    // FP32: the widest tile (three blocks per SM still fit); FP64: halo 2
+    c->tune.deposit_halo = c->prec == 64 ? 2 : qed::kMaxDepositHalo;
   }
   if (rc == QED_OK && (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
                        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -421,6 +411,7 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
     int rc = qed_launch_step(c, f, dt, s);
     if (rc == QED_OK && grid && c->par.deposit_on) rc = qed_launch_yee(c, f, dt, s);
     if (rc != QED_OK) return rc;
+    qed_mark(c, QED_STAGE_FIELD, s);
     c->step += 1;
     if (c->par.thin_interval > 0 && c->step % c->par.thin_interval == 0)
       for (int sp = 0; sp < 4; ++sp)
@@ -436,6 +427,7 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
         if (rc != QED_OK) return rc;
       }
     }
+    qed_mark(c, QED_STAGE_END, s);
   }
   return QED_OK;
 }
@@ -586,6 +578,11 @@ int qed_autotune(qed_ctx *c, const qed_fields *f, double dt, int32_t steps_per_t
     const int so[2] = {1, 0};
     rc = tune_field(&qed_tuning::sort_massive, so, 2);
   }
+  if (rc == QED_OK && c->grid.field_mode == QED_FIELD_GRID && c->par.deposit_on) {
+    // the deposit's current tiles: halo 4 .. 1, or global atomics only
+    const int halos[5] = {4, 3, 2, 1, 0};
+    rc = tune_field(&qed_tuning::deposit_halo, halos, 5);
+  }
   if (rc == QED_OK) {
     // the two passes side by side: split the SM's blocks between them
     qed_tuning t = best;
@@ -635,6 +632,12 @@ int qed_profile_events(qed_ctx *c, void *start, void *photon_done, void *stop) {
   return QED_OK;
 }
 
+int qed_profile_stages(qed_ctx *c, void *const *events, int32_t n) {
+  if (!c || n < 0 || n > QED_NSTAGES || (n > 0 && !events)) return QED_ERR_ARG;
+  for (int k = 0; k < QED_NSTAGES; ++k) c->ev_stage[k] = k < n ? (cudaEvent_t)events[k] : nullptr;
+  return QED_OK;
+}
+
 int qed_diagnostics(qed_ctx *c, qed_diag *out, void *stream) {
   if (!c || !out) return QED_ERR_ARG;
   if (out->nbins != 0 && out->nbins != c->par.nbins) return QED_ERR_ARG;
@@ -679,6 +682,8 @@ int qed_diagnostics(qed_ctx *c, qed_diag *out, void *stream) {
   out->thinned = (int64_t)cnt[qed::kCntThinned];
   out->schwinger_pairs = (int64_t)cnt[qed::kCntSchwinger];
   out->schwinger_gt1 = (int64_t)cnt[qed::kCntSchwingerGt1];
+  out->block_steps = (int64_t)cnt[qed::kCntBlockSteps];
+  out->tile_deposits = (int64_t)cnt[qed::kCntTileDeposits];
   out->particle_steps = 0;
   for (int k = 0; k < 4; ++k) {
     out->species_steps[k] = (int64_t)cnt[qed::kCntSpeciesSteps + k];
@@ -687,9 +692,8 @@ int qed_diagnostics(qed_ctx *c, qed_diag *out, void *stream) {
   out->kernel_launches = launches;
   out->step = clk.step;
   out->time = clk.t;
-  int st = fold_status(bits);
+  const int st = qed_latch_status(c, bits);
   out->status = st;
-  if (st != QED_OK) c->latched = st;
   return st;
 }
 

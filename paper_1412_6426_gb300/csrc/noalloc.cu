@@ -2,15 +2,15 @@
 // caller buffers without allocating any memory.
 //
 // Some callers cannot call cudaMalloc at the point where they want results:
-// code running while a stream is being captured into a CUDA graph (where
-// allocation is not allowed), hosts that hand all device memory to their own
-// pool allocator up front, or real-time loops that forbid allocation after
-// start-up.  qed_particles_get may allocate a staging buffer (pageable host
-// output) and compacts the store through the library's tile buffer; this
-// variant keeps its tile counts and offsets in a fixed file-scope device
-// array instead, writes straight into the caller's device or page-locked
-// host buffers, and leaves the store as it is (dead records stay in place
-// until the next compaction).
+// hosts that hand all device memory to their own pool allocator up front (a
+// cudaMalloc behind the pool's back can fail or fragment it), and real-time
+// loops that forbid allocation after start-up (an allocation can block on
+// the driver for an unbounded time).  qed_particles_get may allocate a
+// staging buffer (pageable host output) and compacts the store through the
+// library's tile buffer; this variant keeps its tile counts and offsets in a
+// fixed file-scope device array instead, writes straight into the caller's
+// device or page-locked host buffers, and leaves the store as it is (dead
+// records stay in place until the next compaction).
 #include <mutex>
 
 #include "qed_internal.h"
@@ -30,20 +30,31 @@ constexpr long long kReadStaticMaxRecords = kReadStaticTiles * qed::kCompactTile
 static __device__ __align__(256) long long g_read_scratch[kReadStaticTiles + 2];
 
 // Host-side device address of g_read_scratch, looked up once per device.
+// In host code the name g_read_scratch is only a host-side stand-in, so the
+// kernels are always given the address returned by cudaGetSymbolAddress.
 constexpr int kMaxDevices = 64;
 long long *g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
-int scratch_address(long long **out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    return QED_ERR_CUDA;
-  }
+// The address of the scratch on device dev (the context's device), looked up
+// with that device current; the caller's current device is restored.
+int scratch_address(int dev, long long **out) {
+  if (dev < 0 || dev >= kMaxDevices) return QED_ERR_ARG;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_addr[dev]) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+      cudaGetLastError();
+      return QED_ERR_CUDA;
+    }
+    if (cur != dev && cudaSetDevice(dev) != cudaSuccess) {
+      cudaGetLastError();
+      return QED_ERR_CUDA;
+    }
     void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_read_scratch) != cudaSuccess || !p) {
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_read_scratch);
+    if (cur != dev) cudaSetDevice(cur);
+    if (e != cudaSuccess || !p) {
       cudaGetLastError();
       return QED_ERR_CUDA;
     }
@@ -202,24 +213,22 @@ int read_static(qed_ctx *c, int sp, long long n, long long *scr, double *x, doub
   return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
 
-int status_of(int bits) {
-  if (bits & qed::kStCapacity) return QED_ERR_CAPACITY;
-  if (bits & qed::kStNonfinite) return QED_ERR_NONFINITE;
-  if (bits & qed::kStTimeout) return QED_ERR_TIMEOUT;
-  if (bits & qed::kStPmGt1) return QED_ERR_PMGT1;
-  if (bits & qed::kStCourant) return QED_ERR_COURANT;
-  return QED_OK;
-}
-
 }  // namespace
 
 extern "C" int qed_particles_read_static(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t *id,
                                          int64_t max_n, int64_t *n_out, void *stream) {
   if (!c || sp < 0 || sp >= QED_NSPECIES || !n_out || max_n < 0) return QED_ERR_ARG;
   *n_out = 0;
+  // the stream, the store and the scratch all belong to the context's device
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return QED_ERR_CUDA;
+  }
+  if (cur != c->device) return QED_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   long long *scr = nullptr;
-  int rc = scratch_address(&scr);
+  int rc = scratch_address(c->device, &scr);
   if (rc != QED_OK) return rc;
   long long records = 0;
   if (cudaMemcpyAsync(&records, c->d_count + sp, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -246,6 +255,8 @@ extern "C" int qed_particles_read_static(qed_ctx *c, int sp, double *x, double *
       cudaStreamSynchronize(s) != cudaSuccess)
     return QED_ERR_CUDA;
   *n_out = live;
-  if (live > max_n) return QED_ERR_ARG;
-  return status_of(bits);
+  // a device failure latches the context, as in qed_particles_get
+  const int st = qed_latch_status(c, bits);
+  if (st != QED_OK) return st;
+  return live > max_n ? QED_ERR_ARG : QED_OK;
 }

@@ -11,11 +11,13 @@
 namespace qed {
 
 constexpr int kMaxPass = 64;        // nesting depth of products within one step
-constexpr int kNumCounters = 20;    // device diagnostic counters
+constexpr int kNumCounters = 22;    // device diagnostic counters
 enum Counter {
   kCntEmissions = 0, kCntPairs, kCntSubLepton, kCntSubPhoton, kCntPmGt1, kCntPpGt1, kCntCapped,
   kCntAbsorbed, kCntOverflow, kCntNonfinite, kCntSpeciesSteps /* 4 slots: live particles per species */,
-  kCntPhotonsMade = kCntSpeciesSteps + 4, kCntPairsMade, kCntThinned, kCntSchwinger, kCntSchwingerGt1
+  kCntPhotonsMade = kCntSpeciesSteps + 4, kCntPairsMade, kCntThinned, kCntSchwinger, kCntSchwingerGt1,
+  kCntBlockSteps,  // particle-steps advanced (and deposited) in cell-block order
+  kCntTileDeposits // of those, deposits through the shared-memory tile of their cell block
 };
 constexpr int kWorkSlot = kMaxPass + 3;   // d_pend_count slot: work counter of the e-/e+/ion pass
 constexpr int kEnsFieldStride = 8;        // per ensemble per step: E[3], B[3], |E|+|B|, pad
@@ -24,8 +26,14 @@ constexpr int kMaxBins = 4096;
 constexpr int kCompactTile = 2048;   // particles per tile of the compaction
 constexpr int kBlockCells = 8;       // cell block edge (grid mode): 8 x 8 x 8 cells
 constexpr int kBlockChunk = 1024;    // records per work item of the cell-block kernel
-constexpr int kTileNodes = kBlockCells + 3;   // current tile edge: the deposit stencil of a
-                                              // particle starting in the block stays inside
+// Current tile of a cell block (the deposit): the block plus a halo of H
+// cells each side, kBlockCells + 2H + 1 nodes per axis.  The stencil of a
+// move that starts in cell cs touches nodes cs - 1 .. cs + 2, so a tile of
+// halo H takes every particle that starts within H - 1 cells of its block
+// (H = 1: the block itself); H = 0 deposits without tiles (global atomics).
+constexpr int kMaxDepositHalo = 4;
+constexpr int kMaxTileNodes = kBlockCells + 2 * kMaxDepositHalo + 1;
+__host__ __device__ constexpr int tile_nodes(int halo) { return kBlockCells + 2 * halo + 1; }
 
 // One species store: a structure of arrays, double-buffered for compaction.
 //   pos: {offset_x, offset_y, offset_z, weight}   (R4 = float4 or 2 x double2)
@@ -93,6 +101,7 @@ template <typename R> struct StepArgs {
   const R *B[3];
   R *J[3];
   int deposit;
+  int deposit_halo;        // current tiles of the deposit: halo H (0 = global atomics only)
   // generator
   R dt, kappa;
   int nsub_max, emission_on, pairs_on, same_step, pm_strict;
@@ -171,7 +180,6 @@ struct qed_ctx {
   int blocks_massive = 0;
   int blocks_products = 0;
   int blocks_cells = 0;
-  int blocks_deposit = 0;
   int64_t step = 0;                   // host mirror of the clock (steps issued)
   int latched = 0;                    // a device error was observed
   int64_t steps_since_compact = 0;
@@ -180,10 +188,34 @@ struct qed_ctx {
   cudaEvent_t ev_start = nullptr;     // recorded around the step kernels
   cudaEvent_t ev_photon = nullptr;
   cudaEvent_t ev_stop = nullptr;
+  cudaEvent_t ev_stage[QED_NSTAGES] = {};   // qed_profile_stages: recorded at each stage
   cudaStream_t side = nullptr;        // the e-/e+/ion pass when it runs beside the photon pass
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int64_t launches = 0;               // kernels launched by this context
 };
+
+// A device status word folded into one qed_status (the most severe bit first).
+inline int qed_fold_status(int bits) {
+  if (bits & qed::kStCapacity) return QED_ERR_CAPACITY;
+  if (bits & qed::kStNonfinite) return QED_ERR_NONFINITE;
+  if (bits & qed::kStTimeout) return QED_ERR_TIMEOUT;
+  if (bits & qed::kStPmGt1) return QED_ERR_PMGT1;
+  if (bits & qed::kStCourant) return QED_ERR_COURANT;
+  return QED_OK;
+}
+
+// Fold a status word read from the device and latch a failure in the
+// context: qed_step refuses to run (QED_ERR_STATE) from then on.
+inline int qed_latch_status(qed_ctx *c, int bits) {
+  const int st = qed_fold_status(bits);
+  if (st != QED_OK) c->latched = st;
+  return st;
+}
+
+// Record the profiling event of one stage of the step, if the caller set one.
+inline void qed_mark(qed_ctx *c, int stage, cudaStream_t s) {
+  if (c->ev_stage[stage]) cudaEventRecord(c->ev_stage[stage], s);
+}
 
 // Internal launch interfaces (implemented in the .cu files).
 int qed_build_tables(qed_ctx *c, cudaStream_t s);
