@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define QED_ABI_VERSION 2
+#define QED_ABI_VERSION 3
 
 typedef enum qed_status {
     QED_OK = 0,
@@ -228,7 +228,16 @@ typedef struct qed_tuning {
                                       fills the photon pass's idle issue
                                       slots; give the two passes at most the
                                       SM's blocks between them */
-    int32_t reserved[2];           /* must be 0 */
+    int32_t deposit_halo;          /* QED_FIELD_GRID: the current of a cell
+                                      block's e-, e+, ions is summed in a
+                                      shared-memory tile covering the block
+                                      and H cells each side, 0 .. 4 (Appendix
+                                      C: the current reduced per block in
+                                      shared memory); a particle that has
+                                      drifted farther since the last sort, and
+                                      every particle with H = 0, adds its
+                                      current to J with global atomics */
+    int32_t reserved;              /* must be 0 */
 } qed_tuning;
 
 /* Caller-owned Yee arrays (device memory, context precision). */
@@ -267,6 +276,17 @@ typedef struct qed_diag {
                                    weighted counts of emitted photons over
                                    log10(delta) in [lg_lo, lg_hi) */
     double *spectrum_energy;    /* same over log10(photon energy / m c^2) */
+    int64_t block_steps;        /* QED_FIELD_GRID: the part of particle_steps
+                                   that the cell-block pass advanced and
+                                   deposited (e-, e+, ions in cell-block
+                                   order; the rest go through the other
+                                   passes) */
+    int64_t tile_deposits;      /* QED_FIELD_GRID: of block_steps, the
+                                   deposits made through the shared-memory
+                                   current tile of their cell block (the
+                                   others, which drifted out of the tile's
+                                   reach since the last sort, add to J
+                                   directly) */
 } qed_diag;
 
 typedef struct qed_ctx qed_ctx;
@@ -295,42 +315,63 @@ int qed_particles_set(qed_ctx *ctx, int species, const double *x, const double *
                       const double *w, const uint64_t *id, int64_t n, void *stream);
 
 /* Remove dead particles of one species and copy the live ones out (host or
- * device pointers; layout as in qed_particles_set, FP64).  *n_out receives
- * the live count; at most max_n are written (QED_ERR_ARG if more are live).
- * Synchronises the stream and returns the device status. */
+ * device pointers; layout as in qed_particles_set, FP64).  This is the
+ * particle ensemble of the module interface (Appendix A: the Ensemble
+ * object the Controller exposes, with its iterator over a domain's
+ * particles); the records hold what Sec. IV.F and V.A give a super-particle:
+ * position, momentum, statistical weight, plus the id that keys its random
+ * streams.  *n_out receives the live count; at most max_n are written
+ * (QED_ERR_ARG if more are live, and nothing is written then).
+ * Synchronises the stream and returns the device status (a failure latches
+ * the context). */
 int qed_particles_get(qed_ctx *ctx, int species, double *x, double *p, double *w,
                       uint64_t *id, int64_t max_n, int64_t *n_out, void *stream);
 
 /* Read the live particles of one species, like qed_particles_get, without
  * allocating any memory.  The paper has no counterpart; this call exists for
- * callers that cannot call cudaMalloc when they want the results: code that
- * runs while a stream is being captured into a CUDA graph, hosts whose
- * device memory all belongs to their own pool allocator, real-time loops
- * that forbid allocation after start-up.
+ * callers that cannot call cudaMalloc when they want the results: hosts
+ * whose device memory all belongs to their own pool allocator (an
+ * allocation behind the pool's back can fail or fragment it), and real-time
+ * loops that forbid allocation after start-up (an allocation can block on
+ * the driver for an unbounded time).
  *  x, p, w, id: device or page-locked host buffers (layout as in
  *    qed_particles_set); pageable host memory is refused with QED_ERR_ARG,
- *    since it would need a staging buffer.
+ *    since it would need a staging buffer.  With max_n == 0 they may be NULL.
+ *  The current device must be the context's (else QED_ERR_ARG).
  *  At most max_n particles are written, in store order (the order
  *  qed_particles_get would give); *n_out receives the live count, and
- *  QED_ERR_ARG is returned when it exceeds max_n.
+ *  QED_ERR_ARG is returned when it exceeds max_n (the first max_n are
+ *  written all the same).
  *  Unlike qed_particles_get the store is not compacted.
  *  Scratch: a fixed device array of 65536 tile counters inside the library
  *  (512 KiB, held by every GPU that loads the library until exit), enough
  *  for stores of up to 134,217,728 records (live plus not yet removed);
  *  larger stores are refused with QED_ERR_CAPACITY.  The first call on a
- *  device looks up the array's device address, so make that first call
- *  before any stream capture.  All calls share the array: calls that
- *  overlap on the GPU race and must be ordered by the caller.
- * Synchronises the stream and returns the device status. */
+ *  device looks up the array's device address (cudaGetSymbolAddress), so
+ *  make that first call before any stream capture.  All calls share the
+ *  array: calls that overlap on the GPU race and must be ordered by the
+ *  caller.
+ * Synchronises the stream and returns the device status; a failure latches
+ * the context as in qed_particles_get. */
 int qed_particles_read_static(qed_ctx *ctx, int species, double *x, double *p, double *w,
                               uint64_t *id, int64_t max_n, int64_t *n_out, void *stream);
 
-/* Advance all species by nsteps steps of dt.  fields: NULL unless
- * field_mode is QED_FIELD_GRID, where the E, B arrays are read (gather),
- * J is overwritten by the deposit and E, B are advanced by one symmetrised
- * FDTD step after the particles (deposit_on).  Asynchronous; allocates
- * nothing, so it may be captured in a CUDA graph.  QED_ERR_STATE after a
- * device error, QED_ERR_ARG for dt <= 0 or missing fields. */
+/* Advance all species by nsteps steps of dt: the module's run at the port
+ * points of one PIC iteration (Appendix A), fused into one launch sequence.
+ * Each step is, per particle, the field held fixed over the step (Sec. IV.H),
+ * the adaptive event generator (Sec. IV.H: N = ceil(dt/dt_q) sub-intervals,
+ * dt_q from Eq. (28) for e-/e+ and Eq. (33) for photons) around the Boris
+ * push (Appendix A) and the modified emission generator (Sec. IV.G,
+ * Eq. (25)) or the pair generator (Sec. V.A, Eq. (30)), creation of the
+ * products, and, in QED_FIELD_GRID, the Esirkepov deposit and the Yee FDTD
+ * update (Appendix C); then thinning (Sec. VI) and pairs from the vacuum
+ * (Sec. V.B) when enabled.
+ *  fields: NULL unless field_mode is QED_FIELD_GRID, where the E, B arrays
+ *    are read (gather), J is overwritten by the deposit and E, B are advanced
+ *    by one symmetrised FDTD step after the particles (deposit_on).
+ *  Asynchronous; allocates nothing, so it may be captured in a CUDA graph.
+ *  QED_ERR_STATE after a device error, QED_ERR_ARG for dt <= 0 or missing
+ *  fields. */
 int qed_step(qed_ctx *ctx, const qed_fields *fields, double dt, int32_t nsteps, void *stream);
 
 /* Set the field table of QED_FIELD_ENSEMBLE: n_ens rows of QED_ENS_STRIDE
@@ -359,7 +400,8 @@ int qed_set_tuning(qed_ctx *ctx, const qed_tuning *tuning);
  * Candidates: 1 .. 4 blocks per SM for each pass (up to the occupancy
  * limit), work chunks {0, 256, 1024, 4096, 16384}, compaction intervals
  * {c, c/2, c/4} below the current interval c (the capacities were sized
- * for c), and with ensembles sorting on or off.  The search stops before a
+ * for c), with ensembles sorting on or off, and on the Yee mesh the deposit's
+ * tile halo {4, 3, 2, 1} or global atomics only (0).  The search stops before a
  * trial that would take more than max_steps steps in all; the fields not
  * reached keep their values.  Applies the best tuning found, writes it to
  * *out (may be NULL) and the number of steps taken to *steps_taken (may be
@@ -379,8 +421,40 @@ int qed_set_clock(qed_ctx *ctx, int64_t step, double time);
  * are not owned by the library. */
 int qed_profile_events(qed_ctx *ctx, void *start, void *photon_done, void *stop);
 
+/* Points of a step at which qed_profile_stages records its events, in the
+ * order the step reaches them on its stream.  A stage a step does not run
+ * (no mesh, no vacuum pairs, ...) is recorded right after the previous one,
+ * so the time between two consecutive events is the time of the kernels in
+ * between (zero when there are none). */
+typedef enum qed_stage {
+    QED_STAGE_BEGIN = 0,     /* before the step's first kernel */
+    QED_STAGE_CONSTANTS,     /* after the mesh maxima and the step constants */
+    QED_STAGE_PHOTONS,       /* after the photon pass */
+    QED_STAGE_BLOCKS,        /* after the cell-block pass of e-, e+, ions (mesh) */
+    QED_STAGE_DEPOSIT,       /* after the cell-block current deposit (mesh) */
+    QED_STAGE_MASSIVE,       /* after the e-/e+/ion pass of the other records */
+    QED_STAGE_PRODUCTS,      /* after the in-step products */
+    QED_STAGE_SCHWINGER,     /* after the pairs from the vacuum */
+    QED_STAGE_FIELD,         /* after the Yee field update (mesh) */
+    QED_STAGE_END,           /* after thinning, compaction and sorting */
+    QED_NSTAGES
+} qed_stage;
+
+/* Profiling aid: record the caller's CUDA events (cudaEvent_t passed as
+ * void*, created on the context's device; n of them, n <= QED_NSTAGES,
+ * entry k for stage k, NULL entries skipped) at the stages of every
+ * following step, on the stream of that step.  Give a fresh array before
+ * each step to keep every step's times.  n == 0 stops recording.  The events
+ * are not owned by the library; the array itself is copied. */
+int qed_profile_stages(qed_ctx *ctx, void *const *events, int32_t n);
+
 /* Synchronise the stream and read counters, live counts, spectra and the
- * device status into *out (host struct).  Returns the device status. */
+ * device status into *out (host struct).  The quantities are the ones the
+ * paper's tests read off a run: the emitted-photon spectrum over log10(delta)
+ * that Sec. IV.G compares with Eq. (21), the particle numbers per species
+ * (the distribution functions of Sec. VII.B integrated over energy) and the
+ * event and sub-interval counts of the adaptive generator (Sec. IV.H).
+ * Returns the device status (a failure latches the context). */
 int qed_diagnostics(qed_ctx *ctx, qed_diag *out, void *stream);
 
 /* Free every resource of the context.  NULL is accepted. */

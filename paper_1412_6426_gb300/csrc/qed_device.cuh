@@ -342,6 +342,64 @@ __device__ __noinline__ R std_delta(const R *__restrict__ T, const R *__restrict
   return s * s * s * sc;
 }
 
+// The standard generator in FP64 at the particle's own chi, without tables
+// in chi: W(x) = int_0^{x^(1/3)} f(s) ds with f(s) = 3 s^2 G(s^3, chi) (the
+// modified generator's density; no cutoff is needed in s = delta^(1/3)),
+// summed over kStdPanels panels of equal width in s, each by 8-point
+// Gauss-Legendre (the roots of P_8 and their weights, to 20 digits).  The root of
+// W(delta) = u W(1) lies in the first panel where the running sum reaches
+// u W(1); inside it a safeguarded Newton iteration on the partial panel
+// integral converges to the last bit of s.
+constexpr int kStdPanels = 256;
+
+__device__ __forceinline__ double std_f(const double *__restrict__ T, double s, double chi) {
+  return prob_emit(T, s, chi, 1.0, 1.0 / kAlpha);
+}
+
+static __device__ __noinline__ double std_gl8(const double *__restrict__ T, double chi, double a, double b) {
+  const double x[4] = {0.18343464249564980494, 0.52553240991632898582, 0.79666647741362673959,
+                       0.96028985649753623168};
+  const double w[4] = {0.36268378337836198297, 0.31370664587788728734, 0.22238103445337447054,
+                       0.10122853629037625915};
+  const double m = 0.5 * (a + b), r = 0.5 * (b - a);
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 3; k >= 0; --k) acc += w[k] * (std_f(T, m - r * x[k], chi) + std_f(T, m + r * x[k], chi));
+  return r * acc;
+}
+
+// W(1) / (alpha h / gamma) at chi.
+static __device__ __noinline__ double std_total_exact(const double *__restrict__ T, double chi) {
+  double acc = 0.0;
+  for (int k = 0; k < kStdPanels; ++k)
+    acc += std_gl8(T, chi, (double)k / kStdPanels, (double)(k + 1) / kStdPanels);
+  return acc;
+}
+
+// delta with W(delta) = u W(1) at chi.
+static __device__ __noinline__ double std_delta_exact(const double *__restrict__ T, double chi, double u) {
+  const double target = u * std_total_exact(T, chi);
+  double below = 0.0;
+  int k = 0;
+  for (; k < kStdPanels - 1; ++k) {
+    const double pk = std_gl8(T, chi, (double)k / kStdPanels, (double)(k + 1) / kStdPanels);
+    if (!(below + pk < target)) break;
+    below += pk;
+  }
+  const double a = (double)k / kStdPanels;
+  double lo = a, hi = (double)(k + 1) / kStdPanels, s = 0.5 * (lo + hi);
+  for (int it = 0; it < 100; ++it) {
+    const double g = below + std_gl8(T, chi, a, s) - target;
+    if (g < 0.0) lo = s; else hi = s;
+    const double fs = std_f(T, s, chi);
+    double sn = fs > 0.0 ? s - g / fs : 0.5 * (lo + hi);
+    if (!(sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
+    if (sn == s || hi - lo <= 0x1p-53 * hi) { s = sn; break; }
+    s = sn;
+  }
+  return s * s * s;
+}
+
 // Pair generator, Eq. (30), with (3/2) chi_g z_p = 1/(de (1-de)):
 //   P_p = alpha h sqrt3/(2pi) (chi_g/eps) z^{1/3} [g2(z) - de(1-de) g1(z)].
 template <typename R>
@@ -355,7 +413,8 @@ __device__ __forceinline__ R prob_pair(const R *__restrict__ T, R de, R chig, R 
   return R(kAlpha) * h * R(kSqrt3Over2Pi) * (chig / eps) * cbrt_r(z) * (g2 - d * g1);
 }
 
-// Boris push (Appendix A): half E, rotation by B, half E.
+// Boris push (Appendix A): half E, rotation by B, half E.  FP32: the
+// compiler may contract products and sums into FMAs.
 template <typename R>
 __device__ __forceinline__ void boris(V3<R> &p, V3<R> E, V3<R> B, R q, R m, R h) {
   R a = R(0.5) * q * h;
@@ -369,6 +428,39 @@ __device__ __forceinline__ void boris(V3<R> &p, V3<R> E, V3<R> B, R q, R m, R h)
   V3<R> up = {um.x + c1.x, um.y + c1.y, um.z + c1.z};
   V3<R> c2 = cross(up, s);
   p = {um.x + c2.x + a * E.x, um.y + c2.y + a * E.y, um.z + c2.z + a * E.z};
+}
+
+// FP64: every product, sum and quotient rounded on its own (the _rn
+// intrinsics are never contracted into FMAs), in a fixed order -- sums left
+// to right, s = 2t / (1 + t^2) -- so that the push is a function of (p, E,
+// B, q, m, h) alone, exact to the last bit of IEEE binary64 arithmetic.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dot_rn(V3<double> a, V3<double> b) {
+  return add_rn(add_rn(mul_rn(a.x, b.x), mul_rn(a.y, b.y)), mul_rn(a.z, b.z));
+}
+__device__ __forceinline__ V3<double> cross_rn(V3<double> a, V3<double> b) {
+  return {sub_rn(mul_rn(a.y, b.z), mul_rn(a.z, b.y)), sub_rn(mul_rn(a.z, b.x), mul_rn(a.x, b.z)),
+          sub_rn(mul_rn(a.x, b.y), mul_rn(a.y, b.x))};
+}
+
+template <>
+__device__ __forceinline__ void boris<double>(V3<double> &p, V3<double> E, V3<double> B, double q, double m,
+                                              double h) {
+  const double a = mul_rn(mul_rn(0.5, q), h);
+  const V3<double> um = {add_rn(p.x, mul_rn(a, E.x)), add_rn(p.y, mul_rn(a, E.y)), add_rn(p.z, mul_rn(a, E.z))};
+  const double gm = __dsqrt_rn(add_rn(1.0, __ddiv_rn(dot_rn(um, um), mul_rn(m, m))));
+  const double f = __ddiv_rn(a, mul_rn(m, gm));
+  const V3<double> t = {mul_rn(f, B.x), mul_rn(f, B.y), mul_rn(f, B.z)};
+  const double den = add_rn(1.0, dot_rn(t, t));
+  const V3<double> sv = {__ddiv_rn(mul_rn(2.0, t.x), den), __ddiv_rn(mul_rn(2.0, t.y), den),
+                         __ddiv_rn(mul_rn(2.0, t.z), den)};
+  const V3<double> c1 = cross_rn(um, t);
+  const V3<double> up = {add_rn(um.x, c1.x), add_rn(um.y, c1.y), add_rn(um.z, c1.z)};
+  const V3<double> c2 = cross_rn(up, sv);
+  p = {add_rn(add_rn(um.x, c2.x), mul_rn(a, E.x)), add_rn(add_rn(um.y, c2.y), mul_rn(a, E.y)),
+       add_rn(add_rn(um.z, c2.z), mul_rn(a, E.z))};
 }
 
 }  // namespace qed

@@ -410,15 +410,22 @@ __device__ void gather_grid(const StepArgs<R> &a, const Pt<R> &q, V3<R> &E, V3<R
 // t.  The current along an axis is the running sum of that axis' weights
 // over its first two edges (the sum over all three is zero: the charge is
 // conserved), so a particle touches 2 x 3 x 3 nodes per component.
+//
+// With S0, S1 the shape weights before and after the move, dS = S1 - S0 and
+// A = (S0 + S1)/2, Esirkepov's transverse factor of the x current,
+//   S0y S0z + dSy S0z/2 + S0y dSz/2 + dSy dSz/3,
+// is A_y A_z + dSy dSz/12 (and likewise for y and z), so every term is one
+// fused multiply-add and one product.
 template <typename R> struct EsirTerms {
   int lo[3];
-  R S0[3][3], dS[3][3];
-  R pref[3];
+  R A[3][3], dS[3][3], dS12[3][3];
+  R P[3][2];   // per component: prefactor times the running sum over edges 0 and 1
 };
 
 template <typename R>
 __device__ __forceinline__ bool esir_terms(const StepArgs<R> &a, const int *cs, const R *os, const Pt<R> &q, R qw,
                                            EsirTerms<R> &t) {
+  const R inv_vol = a.inv_d[0] * a.inv_d[1] * a.inv_d[2];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int dc = q.ci[c] - cs[c];
@@ -433,13 +440,14 @@ __device__ __forceinline__ bool esir_terms(const StepArgs<R> &a, const int *cs, 
       R s1 = R(1) - fabs_r(ub - node);
       s0 = s0 > R(0) ? s0 : R(0);
       s1 = s1 > R(0) ? s1 : R(0);
-      t.S0[c][m] = s0;
+      t.A[c][m] = R(0.5) * (s0 + s1);
       t.dS[c][m] = s1 - s0;
+      t.dS12[c][m] = t.dS[c][m] * R(1.0 / 12.0);
     }
+    const R pref = -qw * a.d[c] / a.dt * inv_vol;
+    t.P[c][0] = pref * t.dS[c][0];
+    t.P[c][1] = pref * (t.dS[c][0] + t.dS[c][1]);
   }
-  const R inv_vol = a.inv_d[0] * a.inv_d[1] * a.inv_d[2];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) t.pref[c] = -qw * a.d[c] / a.dt * inv_vol;
   return true;
 }
 
@@ -447,44 +455,37 @@ __device__ __forceinline__ bool esir_terms(const StepArgs<R> &a, const int *cs, 
 // non-zero current term of the Esirkepov scheme (Appendix C).
 template <typename R, typename Add>
 __device__ __forceinline__ void esir_apply(const EsirTerms<R> &t, Add add) {
-  const R third = R(1.0 / 3.0);
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const R w = t.S0[1][j] * t.S0[2][k] + R(0.5) * t.dS[1][j] * t.S0[2][k] +
-                  R(0.5) * t.S0[1][j] * t.dS[2][k] + third * t.dS[1][j] * t.dS[2][k];
-      R acc = R(0);
+      const R w = fma_r(t.A[1][j], t.A[2][k], t.dS12[1][j] * t.dS[2][k]);
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
-        acc += t.pref[0] * t.dS[0][i] * w;
-        if (acc != R(0)) add(0, i, j, k, acc);
+        const R v = t.P[0][i] * w;
+        if (v != R(0)) add(0, i, j, k, v);
       }
     }
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const R w = t.S0[0][i] * t.S0[2][k] + R(0.5) * t.dS[0][i] * t.S0[2][k] +
-                  R(0.5) * t.S0[0][i] * t.dS[2][k] + third * t.dS[0][i] * t.dS[2][k];
-      R acc = R(0);
+      const R w = fma_r(t.A[0][i], t.A[2][k], t.dS12[0][i] * t.dS[2][k]);
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        acc += t.pref[1] * t.dS[1][j] * w;
-        if (acc != R(0)) add(1, i, j, k, acc);
+        const R v = t.P[1][j] * w;
+        if (v != R(0)) add(1, i, j, k, v);
       }
     }
 #pragma unroll
   for (int j = 0; j < 3; ++j)
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const R w = t.S0[0][i] * t.S0[1][j] + R(0.5) * t.dS[0][i] * t.S0[1][j] +
-                  R(0.5) * t.S0[0][i] * t.dS[1][j] + third * t.dS[0][i] * t.dS[1][j];
-      R acc = R(0);
+      const R w = fma_r(t.A[0][i], t.A[1][j], t.dS12[0][i] * t.dS[1][j]);
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        acc += t.pref[2] * t.dS[2][k] * w;
-        if (acc != R(0)) add(2, i, j, k, acc);
+        const R v = t.P[2][k] * w;
+        if (v != R(0)) add(2, i, j, k, v);
       }
     }
 }
@@ -503,29 +504,6 @@ __device__ __noinline__ void deposit(const StepArgs<R> &a, const int *cs, const 
     K[m] = wrap_fast(cs[2] + t.lo[2] + m, a.n[2]);
   }
   esir_apply(t, [&](int c, int i, int j, int k, R v) { atomicAdd(a.J[c] + K[k] * nxy + Jj[j] * nx + I[i], v); });
-}
-
-// Esirkepov deposit into the shared-memory current tile of a cell block
-// (tile node (0,0,0) = global node torg, kTileNodes per axis).  Returns false,
-// depositing nothing, when the particle's stencil leaves the tile (it has
-// drifted out of its block since the last sort); the caller then deposits to
-// global memory.
-template <typename R>
-__device__ bool deposit_tile(const StepArgs<R> &a, R *jt, const int *torg, const int *cs, const R *os,
-                             const Pt<R> &q, R qw) {
-  int base[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    // nodes cs - 1 .. cs + 2 cover every stencil of a move below one cell
-    base[c] = cs[c] - 1 - torg[c];
-    if (base[c] < 0 || base[c] + 3 >= kTileNodes) return false;
-  }
-  EsirTerms<R> t;
-  if (!esir_terms(a, cs, os, q, qw, t)) { atomicOr(a.status, kStCourant); return true; }
-  constexpr int T = kTileNodes, TT = kTileNodes * kTileNodes, TTT = TT * kTileNodes;
-  R *o = jt + (base[2] + 1 + t.lo[2]) * TT + (base[1] + 1 + t.lo[1]) * T + base[0] + 1 + t.lo[0];
-  esir_apply(t, [&](int c, int i, int j, int k, R v) { atomicAdd(o + c * TTT + k * TT + j * T + i, v); });
-  return true;
 }
 
 // ----- movement and boundaries ---------------------------------------------
@@ -797,8 +775,18 @@ __device__ __forceinline__ void massive_sub(const StepArgs<R> &a, int pass, int 
       fire = r2 < pe;
     } else {
       pe = std_total(a.std_lnw, chi, g, h);        // r1 < W(1), W(delta)/W(1) = r2
-      fire = r1 < pe;
-      delta = fire ? std_delta(a.tab, a.std_cdf, a.std_lnw, chi, r2) : R(0);
+      if (sizeof(R) == 8) {
+        // FP64: W(1) at the particle's chi where the interpolated table
+        // (good to better than 1e-6) could decide otherwise, and delta at
+        // the particle's chi from the panel quadrature
+        if (fabs_r(r1 - pe) <= R(1e-5) * pe)
+          pe = R(kAlpha) * h / g * (R)std_total_exact((const double *)a.tab, (double)chi);
+        fire = r1 < pe;
+        delta = fire ? (R)std_delta_exact((const double *)a.tab, (double)chi, (double)r2) : R(0);
+      } else {
+        fire = r1 < pe;
+        delta = fire ? std_delta(a.tab, a.std_cdf, a.std_lnw, chi, r2) : R(0);
+      }
     }
     if (pe > R(1)) {
       count_rare(a, kCntPmGt1, 1u);
@@ -1586,96 +1574,203 @@ __global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
     }
     __syncthreads();   // blk and next are reused by the next item
   }
+  // every live record this block advanced was counted in psteps
+  unsigned long long mine = cnt.psteps[kElectron] + cnt.psteps[kPositron] + cnt.psteps[kIon];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(a.counters + kCntBlockSteps, mine);
   flush(cnt, a.counters);
 }
 
 // The Esirkepov deposit of the records k_blocks advanced: start from the
-// second buffer, end from the store.  An item whose records all lie in one
-// cell block deposits into a shared tile of that block (the block plus the
-// stencil's reach), flushed with one global atomic per non-zero node; a
-// sparse item (several blocks) deposits straight into J.
+// second buffer, end from the store.  One work item is one cell block: the
+// e-, e+ and ion records of the sorted prefixes that belong to it deposit
+// into a shared-memory tile covering the block and a halo of H cells each
+// side (the current reduced per block in shared memory, as the paper's GPU
+// code does, Appendix C), which is flushed once, with one global atomic per
+// non-zero node.  A particle whose stencil leaves the tile (it has drifted
+// farther since the last sort), every particle of a cell block too sparse to
+// pay for zeroing and flushing a tile, and every particle with H = 0 add
+// their current straight to J.  Blocks claim kDepositGrab consecutive cell
+// blocks at a time and skip the empty ones.  A warp whose lanes all move
+// within their cells takes the short form of the stencil: along each axis
+// the shapes cover the cell's two nodes and the current crosses one edge,
+// so each component has 4 terms instead of 18.
 template <typename R> struct DepositOcc { static constexpr int blocks = sizeof(R) == 4 ? 3 : 2; };
+constexpr int kDepositGrab = 32;
+
+template <typename R>
+__device__ __forceinline__ void deposit_in_cell(const StepArgs<R> &a, R *o, int T, const R *os, const R *oe, R qw) {
+  const int TT = T * T, TTT = TT * T;
+  R A[3][2], D[3][2], pref[3];
+  const R inv_vol = a.inv_d[0] * a.inv_d[1] * a.inv_d[2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R m = R(0.5) * (os[c] + oe[c]);
+    A[c][0] = R(1) - m;
+    A[c][1] = m;
+    D[c][0] = os[c] - oe[c];
+    D[c][1] = oe[c] - os[c];
+    pref[c] = -qw * a.d[c] / a.dt * inv_vol * D[c][0];
+  }
+  const R r12 = R(1.0 / 12.0);
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      atomicAdd(o + k * TT + j * T, pref[0] * fma_r(A[1][j], A[2][k], r12 * D[1][j] * D[2][k]));
+      atomicAdd(o + TTT + k * TT + j, pref[1] * fma_r(A[0][j], A[2][k], r12 * D[0][j] * D[2][k]));
+      atomicAdd(o + 2 * TTT + k * T + j, pref[2] * fma_r(A[0][j], A[1][k], r12 * D[0][j] * D[1][k]));
+    }
+}
 
 template <typename R>
 __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(const StepArgs<R> a) {
-  constexpr int TTT = kTileNodes * kTileNodes * kTileNodes;
-  __shared__ R jt[3 * TTT];
-  __shared__ int blk;
+  extern __shared__ __align__(16) unsigned char dep_smem[];
+  R *jt = (R *)dep_smem;
+  const int halo = a.deposit_halo;
+  const int T = tile_nodes(halo), TT = T * T, TTT = TT * T;
+  __shared__ unsigned grab, nonempty;
   __shared__ long long ns[4];
+  __shared__ long long rlo[3], rn[3];       // per family: first record and count in the current cell block
   // wrapped global offsets of the tile's node rows: x index, y x nx, z x nx ny
-  __shared__ long long gofs[3][kTileNodes];
+  __shared__ long long gofs[3][kMaxTileNodes];
   if (threadIdx.x < 4) ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
   __syncthreads();
-  const BlockItems bi = block_items(a, ns);
   const int fam[3] = {kElectron, kPositron, kIon};
-  const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
-  for (;;) {
-    if (threadIdx.x == 0) blk = (int)atomicAdd(a.work + 1, 1u);
-    __syncthreads();
-    unsigned item = (unsigned)blk;
-    if (item >= bi.items) break;
-    int f = 0;
-    while (item >= bi.nitem[f]) { item -= (unsigned)bi.nitem[f]; ++f; }
+  long long nsort[3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
     const int sp = fam[f];
-    const R qc = a.charge[sp];
-    const long long lo = (long long)item * kBlockChunk, hi = min(lo + kBlockChunk, bi.nsort[f]);
-    // one cell block for the whole item (start positions)?
-    R oa[3], ob[3];
-    int ca, cb;
-    load_start(a, sp, lo, oa, ca);
-    load_start(a, sp, hi - 1, ob, cb);
-    int bl = -1;
-    if (ca >= 0 && cb >= 0) {
-      const int ba = block_of_cell(a, ca), bb = block_of_cell(a, cb);
-      if (ba == bb) bl = ba;
-    }
-    const bool tile = bl >= 0 && qc != R(0);
-    int torg[3] = {0, 0, 0};
-    if (tile) {
-      const int bc[3] = {bl % a.nb[0], (bl / a.nb[0]) % a.nb[1], bl / (a.nb[0] * a.nb[1])};
-      for (int c = 0; c < 3; ++c) torg[c] = bc[c] * kBlockCells - 1;
-      for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) jt[t] = R(0);
-      if (threadIdx.x < 3 * kTileNodes) {
-        const int c = threadIdx.x / kTileNodes, m = threadIdx.x % kTileNodes;
-        const long long stride = c == 0 ? 1 : (c == 1 ? nx : nxy);
-        gofs[c][m] = (long long)wrapi(torg[c] + m, a.n[c]) * stride;
-      }
+    nsort[f] = (a.blk_start[sp] && a.charge[sp] != R(0)) ? min((long long)a.blk_start[sp][a.nblk], ns[sp]) : 0;
+  }
+  const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+  // a tile pays for itself when the block holds a record per 64 of its values
+  const long long tile_min = halo > 0 ? (3ll * TTT) / 64 : (1ll << 62);
+  unsigned in_tile = 0;
+  for (;;) {
+    if (threadIdx.x == 0) grab = atomicAdd(a.work + 1, (unsigned)kDepositGrab);
+    __syncthreads();
+    const unsigned base = grab;
+    if (base >= (unsigned)a.nblk) break;
+    if (threadIdx.x < 32) {
+      const unsigned b = base + threadIdx.x;
+      bool any = false;
+      if (b < (unsigned)a.nblk)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          if (nsort[f] == 0) continue;
+          const unsigned *st = a.blk_start[fam[f]];
+          any |= min((long long)st[b + 1], nsort[f]) > min((long long)st[b], nsort[f]);
+        }
+      const unsigned m = __ballot_sync(0xffffffffu, any);
+      if (threadIdx.x == 0) nonempty = m;
     }
     __syncthreads();
-    if (qc != R(0))
-      for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    for (unsigned m = nonempty; m; m &= m - 1) {
+      const int bl = (int)base + __ffs(m) - 1;
+      const int bc[3] = {bl % a.nb[0], (bl / a.nb[0]) % a.nb[1], bl / (a.nb[0] * a.nb[1])};
+      int torg[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) torg[c] = bc[c] * kBlockCells - halo;
+      if (threadIdx.x < 3) {
+        const int f = threadIdx.x;
+        long long lo = 0, hi = 0;
+        if (nsort[f]) {
+          const unsigned *st = a.blk_start[fam[f]];
+          lo = min((long long)st[bl], nsort[f]);
+          hi = min((long long)st[bl + 1], nsort[f]);
+        }
+        rlo[f] = lo;
+        rn[f] = hi - lo;
+      }
+      __syncthreads();
+      const long long n0 = rn[0], n01 = rn[0] + rn[1], total = n01 + rn[2];
+      const bool tile = total >= tile_min;
+      if (tile) {
+        if (threadIdx.x < 3 * T) {
+          const int c = threadIdx.x / T, k = threadIdx.x % T;
+          const long long stride = c == 0 ? 1 : (c == 1 ? nx : nxy);
+          gofs[c][k] = (long long)wrapi(torg[c] + k, a.n[c]) * stride;
+        }
+        for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) jt[t] = R(0);
+        __syncthreads();
+      }
+      for (long long t = threadIdx.x; t < total; t += blockDim.x) {
+        const int f = t < n0 ? 0 : (t < n01 ? 1 : 2);
+        const int sp = fam[f];
+        const long long i = rlo[f] + (t - (f == 0 ? 0 : (f == 1 ? n0 : n01)));
         Pt<R> q1;
         R os[3];
         int c0, c1;
         load_start(a, sp, i, os, c0);
         load(a, sp, i, q1, c1);
-        if (c0 < 0 || c1 < 0) continue;
+        const bool live = c0 >= 0 && c1 >= 0;
         int cs[3], ce[3];
-        decode_cell(a, c0, cs);
-        decode_cell(a, c1, ce);
+        decode_cell(a, live ? c0 : 0, cs);
+        decode_cell(a, live ? c1 : 0, ce);
         // the end cell unwrapped next to the start (a step moves < 1 cell)
+        bool inside = tile, incell = true;
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
           int dc = ce[c] - cs[c];
           const R disp = R(dc) + q1.off[c] - os[c];
           if (disp >= R(1)) dc -= a.n[c];
           else if (disp <= R(-1)) dc += a.n[c];
           q1.ci[c] = cs[c] + dc;
+          incell &= dc == 0;
+          // nodes cs - 1 .. cs + 2 cover every stencil of a move below one cell
+          const int b0 = cs[c] - 1 - torg[c];
+          inside &= b0 >= 0 && b0 + 3 < T;
         }
-        if (!tile || !deposit_tile(a, jt, torg, cs, os, q1, qc * q1.w)) deposit(a, cs, os, q1, qc * q1.w);
+        const R qw = a.charge[sp] * q1.w;
+        const unsigned act = __activemask();
+        if (__all_sync(act, !live || (inside && incell))) {
+          if (live) {
+            deposit_in_cell(a, jt + (cs[2] - torg[2]) * TT + (cs[1] - torg[1]) * T + (cs[0] - torg[0]), T, os,
+                            q1.off, qw);
+            ++in_tile;
+          }
+          continue;
+        }
+        if (!live) continue;
+        if (!inside) {
+          deposit(a, cs, os, q1, qw);
+          continue;
+        }
+        EsirTerms<R> et;
+        if (!esir_terms(a, cs, os, q1, qw, et)) {
+          atomicOr(a.status, kStCourant);
+          continue;
+        }
+        R *o = jt + (cs[2] - torg[2] + et.lo[2]) * TT + (cs[1] - torg[1] + et.lo[1]) * T +
+               (cs[0] - torg[0] + et.lo[0]);
+        esir_apply(et, [&](int c, int i, int j, int k, R v) { atomicAdd(o + c * TTT + k * TT + j * T + i, v); });
+        ++in_tile;
       }
-    __syncthreads();
-    if (tile) {
-      for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) {
-        const R v = jt[t];
-        if (v == R(0)) continue;
-        const int c = t / TTT, r = t - c * TTT;
-        const int tk = r / (kTileNodes * kTileNodes), r2 = r - tk * (kTileNodes * kTileNodes);
-        const int tj = r2 / kTileNodes, ti = r2 - tj * kTileNodes;
-        atomicAdd(a.J[c] + gofs[2][tk] + gofs[1][tj] + gofs[0][ti], v);
+      __syncthreads();
+      if (tile) {
+        for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) {
+          const R v = jt[t];
+          if (v == R(0)) continue;
+          const int c = t / TTT, r = t - c * TTT;
+          const int tk = r / TT, r2 = r - tk * TT;
+          const int tj = r2 / T, ti = r2 - tj * T;
+          atomicAdd(a.J[c] + gofs[2][tk] + gofs[1][tj] + gofs[0][ti], v);
+        }
+        __syncthreads();   // the tile, rlo and rn are reused by the next cell block
       }
     }
-    __syncthreads();   // the tile and blk are reused by the next item
   }
+  unsigned long long v = in_tile;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.counters + kCntTileDeposits, v);
+}
+
+// Dynamic shared memory of the deposit kernel for a tile halo.
+template <typename R> size_t deposit_smem(int halo) {
+  return halo > 0 ? 3 * sizeof(R) * (size_t)tile_nodes(halo) * tile_nodes(halo) * tile_nodes(halo) : 0;
 }
 
 // Passes 1, 2, ...: products evolving for the rest of the step.  All blocks
@@ -1782,6 +1877,7 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     }
   }
   a.deposit = (a.field_mode == kFieldGrid) && c->par.deposit_on;
+  a.deposit_halo = c->tune.deposit_halo;
   a.dt = (R)dt;
   a.kappa = (R)c->par.kappa;
   a.nsub_max = c->par.nsub_max;
@@ -1808,6 +1904,8 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   a.status = c->d_status;
   a.barrier = c->d_barrier;
 
+  // the step starts with its resets (counts, J) on the stream
+  qed_mark(c, QED_STAGE_BEGIN, s);
   if (cudaMemcpyAsync(c->d_nstart, c->d_count, 4 * sizeof(long long), cudaMemcpyDeviceToDevice, s) !=
       cudaSuccess)
     return QED_ERR_CUDA;
@@ -1834,6 +1932,7 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   if (e == cudaSuccess)
     e = cudaLaunchKernel((const void *)k_step_constants<R>, dim3(1),
                        dim3(a.field_mode == kFieldEnsemble ? 256 : 32), args, 0, s);
+  qed_mark(c, QED_STAGE_CONSTANTS, s);
   // concurrent: the e-/e+/ion pass runs on the side stream beside the
   // photon pass (fork after the step constants, join before the products)
   const bool conc = c->tune.concurrent && c->side && !a.blk_start[kElectron];
@@ -1849,26 +1948,40 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     e = cudaLaunchKernel((const void *)k_photons<R, EXT>, dim3(c->num_sms * c->tune.photon_blocks_per_sm),
                          dim3(kPhotonThreads), args, 0, s);
   if (c->ev_photon) cudaEventRecord(c->ev_photon, s);
+  qed_mark(c, QED_STAGE_PHOTONS, s);
   if (e == cudaSuccess && a.blk_start[kElectron]) {
     c->launches += 1;
     e = cudaLaunchKernel((const void *)k_blocks<R, EXT>, dim3(c->blocks_cells), dim3(256), args, 0, s);
+    qed_mark(c, QED_STAGE_BLOCKS, s);
     if (e == cudaSuccess && a.deposit) {
       c->launches += 1;
-      e = cudaLaunchKernel((const void *)k_deposit_blocks<R>, dim3(c->blocks_deposit), dim3(256), args, 0, s);
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deposit_blocks<R>, 256,
+                                                        deposit_smem<R>(a.deposit_halo)) != cudaSuccess ||
+          per_sm < 1)
+        return QED_ERR_CUDA;
+      e = cudaLaunchKernel((const void *)k_deposit_blocks<R>, dim3(per_sm * c->num_sms), dim3(256), args,
+                           deposit_smem<R>(a.deposit_halo), s);
     }
+  } else {
+    qed_mark(c, QED_STAGE_BLOCKS, s);
   }
+  qed_mark(c, QED_STAGE_DEPOSIT, s);
   if (e == cudaSuccess && conc) e = cudaStreamWaitEvent(s, c->ev_join, 0);
   else if (e == cudaSuccess)
     e = cudaLaunchKernel((const void *)k_pass0<R, false, EXT>, dim3(c->num_sms * c->tune.massive_blocks_per_sm),
                          dim3(256), args, 0, s);
+  qed_mark(c, QED_STAGE_MASSIVE, s);
   if (e == cudaSuccess && a.same_step) {
     c->launches += 1;
     e = cudaLaunchCooperativeKernel((const void *)k_products<R, EXT>, dim3(c->blocks_products), dim3(256), args, 0, s);
   }
+  qed_mark(c, QED_STAGE_PRODUCTS, s);
   if (e == cudaSuccess && a.schwinger) {
     c->launches += 1;
     e = cudaLaunchKernel((const void *)k_schwinger<R>, dim3(c->num_sms * 8), dim3(256), args, 0, s);
   }
+  qed_mark(c, QED_STAGE_SCHWINGER, s);
   if (c->ev_stop) cudaEventRecord(c->ev_stop, s);
   return e == cudaSuccess ? QED_OK : QED_ERR_CUDA;
 }
@@ -1880,9 +1993,9 @@ int step_blocks(qed_ctx *c) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k_blocks<R, EXT>, 256, 0) != cudaSuccess || g < 1)
     return QED_ERR_CUDA;
   c->blocks_cells = g * c->num_sms;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k_deposit_blocks<R>, 256, 0) != cudaSuccess || g < 1)
+  if (cudaFuncSetAttribute(k_deposit_blocks<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)deposit_smem<R>(kMaxDepositHalo)) != cudaSuccess)
     return QED_ERR_CUDA;
-  c->blocks_deposit = g * c->num_sms;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_photons<R, EXT>, qed::kPhotonThreads, 0) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pass0<R, false, EXT>, 256, 0) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k_products<R, EXT>, 256, 0) != cudaSuccess ||

@@ -23,12 +23,15 @@ QED_FIELD_GRID, QED_FIELD_UNIFORM, QED_FIELD_GAUSSIAN_LP, QED_FIELD_ROTATING_E, 
 QED_ENS_STRIDE = 10
 QED_GEN_MODIFIED, QED_GEN_ALTERNATIVE, QED_GEN_STANDARD = 0, 1, 2
 QED_MAX_ENS_BITS = 16
+# qed_stage: the points of a step at which qed_profile_stages records events
+(QED_STAGE_BEGIN, QED_STAGE_CONSTANTS, QED_STAGE_PHOTONS, QED_STAGE_BLOCKS, QED_STAGE_DEPOSIT, QED_STAGE_MASSIVE,
+ QED_STAGE_PRODUCTS, QED_STAGE_SCHWINGER, QED_STAGE_FIELD, QED_STAGE_END, QED_NSTAGES) = range(11)
 
 # every entry point the header declares (checked by the CPU tests)
 EXPORTS = ("qed_init", "qed_tables_export", "qed_particles_set", "qed_particles_get", "qed_step",
            "qed_set_clock", "qed_profile_events", "qed_diagnostics", "qed_destroy", "qed_error_string",
            "qed_particles_read_static", "qed_ensembles_set", "qed_get_tuning", "qed_set_tuning",
-           "qed_autotune")
+           "qed_autotune", "qed_profile_stages")
 
 
 class QedGridDesc(ctypes.Structure):
@@ -64,10 +67,10 @@ class QedTuning(ctypes.Structure):
     _fields_ = [("photon_blocks_per_sm", ctypes.c_int32), ("massive_blocks_per_sm", ctypes.c_int32),
                 ("work_chunk", ctypes.c_int32), ("compact_interval", ctypes.c_int32),
                 ("sort_massive", ctypes.c_int32), ("concurrent", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("deposit_halo", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_[:6]}
+        return {k: getattr(self, k) for k, _ in self._fields_[:7]}
 
 
 class QedFields(ctypes.Structure):
@@ -82,7 +85,8 @@ class QedDiag(ctypes.Structure):
         "thinned", "schwinger_pairs", "schwinger_gt1", "kernel_launches", "step")] + [
         ("time", ctypes.c_double), ("status", ctypes.c_int32), ("nbins", ctypes.c_int32),
         ("spectrum", ctypes.POINTER(ctypes.c_double)),
-        ("spectrum_energy", ctypes.POINTER(ctypes.c_double))]
+        ("spectrum_energy", ctypes.POINTER(ctypes.c_double)), ("block_steps", ctypes.c_int64),
+        ("tile_deposits", ctypes.c_int64)]
 
 
 _lib = None
@@ -106,6 +110,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qed_particles_read_static.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp, i64, ctypes.POINTER(i64), vp]
     lib.qed_set_clock.argtypes = [vp, i64, ctypes.c_double]
     lib.qed_profile_events.argtypes = [vp, vp, vp, vp]
+    lib.qed_profile_stages.argtypes = [vp, ctypes.POINTER(vp), i32]
     lib.qed_diagnostics.argtypes = [vp, ctypes.POINTER(QedDiag), vp]
     lib.qed_destroy.argtypes = [vp]
     lib.qed_ensembles_set.argtypes = [vp, i32, dp, vp]
@@ -200,6 +205,12 @@ def qed_profile_events(ctx: int, start_event: int, photon_event: int, stop_event
                                                            ctypes.c_void_p(stop_event)))
 
 
+def qed_profile_stages(ctx: int, events) -> None:
+    """events: raw cudaEvent_t handles (ints or 0), entry k for stage k; [] stops recording."""
+    arr = (ctypes.c_void_p * max(len(events), 1))(*[ctypes.c_void_p(e or None) for e in events])
+    _check("qed_profile_stages", load().qed_profile_stages(ctypes.c_void_p(ctx), arr, len(events)))
+
+
 def qed_diagnostics(ctx: int, nbins: int = 0, stream: int = 0, check: bool = True) -> dict:
     d = QedDiag()
     spec = np.zeros(max(nbins, 1))
@@ -217,6 +228,8 @@ def qed_diagnostics(ctx: int, nbins: int = 0, stream: int = 0, check: bool = Tru
     out["species_steps"] = list(d.species_steps)
     out["time"] = d.time
     out["status"] = d.status
+    out["block_steps"] = d.block_steps
+    out["tile_deposits"] = d.tile_deposits
     if nbins:
         out["spectrum"] = spec[:nbins].copy()
         out["spectrum_energy"] = spec_e[:nbins].copy()

@@ -106,10 +106,17 @@ def test_header_constants_match_binding():
     consts = dict(re.findall(r"#define (QED_\w+)\s+(\d+)", text))
     assert int(consts["QED_ENS_STRIDE"]) == qed.QED_ENS_STRIDE == workloads.ENS_STRIDE
     assert int(consts["QED_MAX_ENS_BITS"]) == qed.QED_MAX_ENS_BITS
-    assert int(consts["QED_ABI_VERSION"]) == 2
+    assert int(consts["QED_ABI_VERSION"]) == 3
     modes = dict(re.findall(r"(QED_FIELD_\w+) = (\d+)", text))
     assert int(modes["QED_FIELD_ENSEMBLE"]) == qed.QED_FIELD_ENSEMBLE == workloads.FIELD_ENSEMBLE
     assert int(modes["QED_FIELD_STANDING_WAVE"]) == qed.QED_FIELD_STANDING_WAVE == workloads.FIELD_STANDING_WAVE
+    stages = re.findall(r"(QED_STAGE_\w+|QED_NSTAGES)\b", text[text.index("typedef enum qed_stage"):])
+    order = list(dict.fromkeys(stages))
+    assert order[:11] == ["QED_STAGE_BEGIN", "QED_STAGE_CONSTANTS", "QED_STAGE_PHOTONS", "QED_STAGE_BLOCKS",
+                          "QED_STAGE_DEPOSIT", "QED_STAGE_MASSIVE", "QED_STAGE_PRODUCTS", "QED_STAGE_SCHWINGER",
+                          "QED_STAGE_FIELD", "QED_STAGE_END", "QED_NSTAGES"]
+    for k, name in enumerate(order[:11]):
+        assert getattr(qed, name) == k
 
 
 def _descs():
@@ -201,3 +208,20 @@ def test_product_path_has_no_oracle_import():
             "try:\n q.load(q.LIB_PATH)\nexcept RuntimeError: print('raised')\n")
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT).stdout
     assert "raised" in out
+
+
+def test_device_gauss_legendre_constants():
+    # the 8-point Gauss-Legendre nodes and weights the FP64 standard generator
+    # integrates with (written into the device header) against the roots of
+    # P_8 and their weights 2 / ((1 - x^2) P_8'(x)^2), found to 30 digits
+    mpmath = pytest.importorskip("mpmath")
+    text = open(os.path.join(ROOT, "paper_1412_6426_gb300", "csrc", "qed_device.cuh")).read()
+    body = text[text.index("double std_gl8("):]
+    x = [float(v) for v in re.search(r"const double x\[4\] = \{([^}]*)\}", body).group(1).split(",")]
+    w = [float(v) for v in re.search(r"const double w\[4\] = \{([^}]*)\}", body).group(1).split(",")]
+    mpmath.mp.dps = 30
+    P8 = lambda t: mpmath.legendre(8, t)
+    for xi, wi in zip(x, w):
+        r = mpmath.findroot(P8, xi)
+        wt = 2 / ((1 - r ** 2) * mpmath.diff(P8, r) ** 2)
+        assert xi == float(r) and wi == float(wt)
