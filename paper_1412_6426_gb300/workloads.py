@@ -136,7 +136,7 @@ def beam_laser_collision(n_particles: int = 1_000_000, seed: int = 1, nsteps: in
         n=(nx, nr, nr), d=(cell, cell, cell), x0=(-half_x, -half_r, -half_r), periodic=(0, 0, 0),
         field_mode=FIELD_GAUSSIAN_LP, fp=fp, dt=dt, nsteps=nsteps,
         particles={ELECTRON: (x, p, np.ones(n_particles), np.arange(n_particles, dtype=np.uint64))},
-        seed=seed, meta={"gamma0": gamma0, "E0": E0, "omega": omega, "t_focus": t_focus,
+        seed=seed, meta={"gamma0": gamma0, "E0": E0, "omega": omega, "t_focus": t_focus, "a0": a0,
                          "chi_headon": 2 * gamma0 * E0})
 
 

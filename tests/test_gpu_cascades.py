@@ -81,8 +81,12 @@ def test_fp32_standing_wave_statistics():
     xo, po, _, io = ora[0]
     common, a, b = np.intersect1d(ig, io, return_indices=True)
     assert len(common) >= 0.99 * len(io)
-    rel = np.linalg.norm(pg[a] - po[b], axis=1) / np.linalg.norm(po[b], axis=1)
-    assert np.median(rel) < 1e-5 and np.quantile(rel, 0.95) < 1e-4
+    # every particle with a shared history within the FP32 bound
+    # (tests/test_gpu_parity.py); the field adds at most E0 dt = 3.2 to |p| a step
+    from tests.test_gpu_parity import fp32_momentum_bounds
+    p_max = 4000.0 + w.nsteps * w.fp[0] * w.dt
+    matched, worst = fp32_momentum_bounds(gpu, ora, p_max, n_ev=40)
+    assert worst <= 1.0, worst
 
 
 # ---------------------------------------------------------------------------

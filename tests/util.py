@@ -42,11 +42,14 @@ def box_scale(w):
 
 
 def compare(gpu: dict, ora: dict, *, rtol_p: float, xtol: float, species=(0, 1, 2, 3), subset_ids=None,
-            rtol_w: float = 0.0):
+            rtol_w: float = 0.0, p_floor: float = 0.0):
     """Match particles by id; returns a report dict.  With subset_ids the GPU
     side is restricted to those ids (sampled families at full size).  Weights
     must agree exactly unless rtol_w is given (thinning rescales them by
-    ratios of sums whose rounding depends on the summation order)."""
+    ratios of sums whose rounding depends on the summation order).  Momenta
+    agree to rtol_p relative to max(|p|, p_floor): p_floor is the momentum
+    scale of an external field for particles slower than it (0: plain
+    relative error)."""
     rep = {"missing": 0, "extra": 0, "matched": 0, "max_rel_p": 0.0, "max_dx": 0.0}
     for sp in species:
         xg, pg, wg, ig = gpu[sp]
@@ -61,7 +64,7 @@ def compare(gpu: dict, ora: dict, *, rtol_p: float, xtol: float, species=(0, 1, 
         if len(common) == 0:
             continue
         pa, pb = pg[a], po[b]
-        scale = np.maximum(np.linalg.norm(pb, axis=1), 1e-300)
+        scale = np.maximum(np.linalg.norm(pb, axis=1), max(p_floor, 1e-300))
         rel = np.linalg.norm(pa - pb, axis=1) / scale
         rep["max_rel_p"] = max(rep["max_rel_p"], float(rel.max()))
         rep["max_dx"] = max(rep["max_dx"], float(np.abs(xg[a] - xo[b]).max()))
