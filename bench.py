@@ -1,32 +1,39 @@
 """Throughput of the QED particle step: particle-steps/s with QED events.
 
-Workload (default): head-on collision of a 1 GeV electron beam (1e6
-electrons, 1% energy spread, 1 um rms radius, 3 um rms length) with a
-counter-propagating linearly polarised Gaussian pulse (lambda = 0.8 um,
-a0 = 200, 30 fs FWHM, 2 um waist), test particles in the analytic field,
-photon emission and Breit-Wheeler pairs on, dt = T_laser/100, 600 steps.
+Workload (default, --workload cascade512): the large self-consistent 3D
+cascade -- a 512^3 periodic Yee mesh (dx = lambda/32, lambda = 0.8 um,
+dt = T_L/64), four circularly polarised plane-wave pulses at 2e24 W/cm^2
+(two along x, two along y), a cold hydrogen slab of 1e22 cm^-3, 0.5 um
+thick, with 8 macro-electrons and 8 macro-protons per cell (4.2e7 each),
+photon emission and Breit-Wheeler pairs, Esirkepov deposit, FDTD update,
+thinning every 8 steps.  A window of K steps starting at step 40 is timed
+(W warm-up steps right before it), each step bracketed by CUDA events on its
+stream; the stages of every timed step (photon pass, cell-block pass,
+deposit, FDTD, ...) are recorded on the same stream (qed_profile_stages),
+and the roofline object is for the stage that takes the most time.  The
+FP64 form runs side by side over the same window.  The mesh alone (4.8 GB in
+FP32) is far larger than L2.
 
 One bench step = one qed_step (every live particle of every species advanced
-by dt).  W warm-up steps and K timed steps are taken from the 600-step run in
-a window centred on the collision (K + W = 600 covers the whole run, the
-default).  Between timed steps a 256 MiB buffer is written to flush L2; each
-step is bracketed by CUDA events on the stream it runs on, and the step
-kernel is bracketed separately (qed_profile_events) for the roofline.
+by dt, then the field update).  Prints one JSON line on rank 0.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload instead (a 32^3 box of the same recipe, one core).
 
-Prints one JSON line on rank 0.  --impl reference times the FP64 CPU oracle
-on a bounded sample of the same workload instead.
+--workload collision times the head-on collision of a 1 GeV electron beam
+(1e6 electrons, 1% energy spread, 1 um rms radius, 3 um rms length) with a
+counter-propagating linearly polarised Gaussian pulse (lambda = 0.8 um,
+a0 = 200, 30 fs FWHM, 2 um waist), test particles in the analytic field,
+dt = T_laser/100, 600 steps: W warm-up steps and K timed steps in a window
+centred on the collision, a 256 MiB buffer written between timed steps to
+flush L2.
 
---workload batched times the batched-ensemble workload instead: 512
-independent test-particle instances in uniform rotating E fields (chi
-log-uniform in [0.1, 100], electron counts log-uniform in [1e3, 1e6]), with
-per-ensemble thinning, 500 steps of dt = T_laser/100 in FP32.  The first
-steps run under the autotuner; the rest are replays of a CUDA graph that
-holds a whole number of thinning intervals and an even number of
-compactions.  Its working set (GBs) is far larger than L2.
+--workload batched times the batched-ensemble workload: 512 independent
+test-particle instances in uniform rotating E fields (chi log-uniform in
+[0.1, 100], electron counts log-uniform in [1e3, 1e6]), with per-ensemble
+thinning, 500 steps of dt = T_laser/100 in FP32; the first steps run under
+the autotuner, the rest are replays of a CUDA graph.
 
---workload cascade times the self-consistent 256^3 cascade (2000 steps) and
---workload cascade512 a window (steps 40..60 by default) of the large 512^3
-cascade with its hydrogen slab target, FP32 and FP64.
+--workload cascade times the self-consistent 256^3 cascade (2000 steps).
 """
 from __future__ import annotations
 
@@ -712,7 +719,28 @@ LARGE_NAME = ("large self-consistent 3D QED cascade: 512^3 periodic Yee mesh, dx
               "dt = T_L/64, four CP plane-wave pulses at 2e24 W/cm^2 (two along x, two along y; sin^2 envelope "
               "of half the box), hydrogen slab 1e22 cm^-3, 0.5 um thick, 8 ppc e- and p+ (4.2e7 each), "
               "Esirkepov deposit + FDTD, emission + Breit-Wheeler pairs, thinning every 8 steps")
-LARGE_WARMUP, LARGE_STEPS = 40, 20
+LARGE_START, LARGE_STEPS = 40, 20   # the timed window starts at step 40 (W warm-ups right before it)
+# The stages of a step (qed_profile_stages) and the kernels each one holds.
+STAGES = ("constants", "photons", "blocks", "deposit", "massive", "products", "schwinger", "field", "end")
+STAGE_KERNELS = {"constants": "J and count resets, k_grid_max, k_step_constants", "photons": "k_photons",
+                 "blocks": "k_blocks", "deposit": "k_deposit_blocks", "massive": "k_pass0",
+                 "products": "k_products", "schwinger": "k_schwinger", "field": "k_yee_b, k_yee_e",
+                 "end": "thinning, compaction and cell-block sort"}
+# Algorithmic bytes per unit of each stage, FP32 / FP64:
+#  photons, blocks, massive: the particle step, 68 / 120 B per particle-step
+#    (read cell, offsets, p, w, id; write cell, offsets, p);
+#  deposit: the start point and the end record of each particle the cell-block
+#    pass advanced, 16 + 32 = 48 / 96 B (the current tiles are flushed once);
+#  field: the Yee update, 9 reads + 6 writes a cell, 60 / 120 B per cell-step;
+#  constants: J zeroed (3 values) and the mesh maxima (6 reads), 36 / 72 B
+#    per cell-step.
+STAGE_BYTES = {"photons": (68, 120), "blocks": (68, 120), "massive": (68, 120), "deposit": (48, 96),
+               "field": (60, 120), "constants": (36, 72)}
+# DRAM bytes (read + write) per unit of a kernel from one ncu capture of that
+# kernel on the large-cascade recipe; the bench scales them by the units of
+# its own launches.  Remove an entry when the kernel changes until it is
+# measured again.
+LARGE_DRAM_BYTES_PER_UNIT: dict = {}
 
 
 def large_setup(precision: int, n: int = 512):
@@ -728,44 +756,88 @@ def large_setup(precision: int, n: int = 512):
     return w, F, J, opts
 
 
-def large_device(precision: int, K: int, W: int, dist_barrier) -> dict:
-    """W untimed steps of the 512^3 cascade, then K steps each bracketed by
-    CUDA events on the stream (the mesh alone, 4.8 GB in FP32, exceeds L2)."""
+def large_device(precision: int, K: int, W: int, dist_barrier, start: int = LARGE_START) -> dict:
+    """Advance the 512^3 cascade to step max(start, W) - W untimed, take W
+    warm-up steps, then K steps each bracketed by CUDA events on the stream
+    (the mesh alone, 4.8 GB in FP32, exceeds L2), with the stages of every
+    timed step recorded by qed_profile_stages on the same stream."""
     import torch
+    from paper_1412_6426_gb300 import qed
     from paper_1412_6426_gb300.sim import Simulation
     w, F, J, opts = large_setup(precision)
     stream = torch.cuda.current_stream()
+    s0 = max(start, W)
     with Simulation(w, **opts) as sim:
         sim.set_grid_fields(F[:3], F[3:], J)
         sim.set_all()
+        if s0 - W:
+            sim.step(s0 - W)
         sim.step(W)
         d0 = sim.diag()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        sev = [[torch.cuda.Event(enable_timing=True) for _ in range(qed.QED_NSTAGES)] for _ in range(K)]
+        for row in sev:                       # materialise the events before the library records them
+            for e_ in row:
+                e_.record(stream)
         torch.cuda.synchronize()
         dist_barrier()
         sampler = ClockSampler(int(os.environ.get("BENCH_GPU_INDEX", torch.cuda.current_device())))
         for k in range(K):
+            qed.qed_profile_stages(sim.ctx, [e_.cuda_event for e_ in sev[k]])
             ev[k][0].record(stream)
             sim.step(1)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         clocks = sampler.stop()
         dist_barrier()
+        qed.qed_profile_stages(sim.ctx, [])
         d1 = sim.diag()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    stage_ms = {name: sum(sev[k][j].elapsed_time(sev[k][j + 1]) for k in range(K)) / K
+                for j, name in enumerate(STAGES)}
     psteps = d1["particle_steps"] - d0["particle_steps"]
+    sp = [d1["species_steps"][i] - d0["species_steps"][i] for i in range(4)]
+    blk = d1["block_steps"] - d0["block_steps"]
     appended = (d1["photons_created"] - d0["photons_created"]) + 2 * (d1["pairs_created"] - d0["pairs_created"])
     ncell = w.n[0] * w.n[1] * w.n[2]
+    units = {"photons": sp[2], "blocks": blk, "deposit": blk, "massive": sp[0] + sp[1] + sp[3] - blk,
+             "field": ncell * K, "constants": ncell * K}
+    pi = 0 if precision == 32 else 1
     r = 4 if precision == 32 else 8
     # particles (68 / 120 B per particle-step, 40 / 68 B per append) and the mesh
     # (FDTD: 9 reads + 6 writes a cell-step; J zeroed and accumulated: 3 + 3)
     algo = (BYTES_PER_STEP[precision] * psteps + BYTES_PER_APPEND[precision] * appended
             + 21 * r * ncell * K)
     return {"particle_steps": psteps, "seconds": sum(step_ms) / 1e3, "ms_per_step": sum(step_ms) / K,
-            "steps": K, "warmup": W, "appended": appended, "algo_bytes": algo, "clocks": clocks,
+            "steps": K, "warmup": W, "window": [s0, s0 + K], "appended": appended, "algo_bytes": algo,
+            "clocks": clocks, "stage_ms": stage_ms, "stage_units": units,
+            "stage_bytes": {k: STAGE_BYTES[k][pi] for k in STAGE_BYTES},
             "launches": d1["kernel_launches"] - d0["kernel_launches"], "live_end": d1["count"],
             "emissions": d1["emissions"] - d0["emissions"], "pairs": d1["pairs"] - d0["pairs"],
-            "thinned": d1["thinned"] - d0["thinned"], "precision": precision}
+            "thinned": d1["thinned"] - d0["thinned"], "precision": precision,
+            "tile_fraction": (d1["tile_deposits"] - d0["tile_deposits"]) / blk if blk else None}
+
+
+def dominant_roofline(rr: dict, peak: float, peak_kind: str) -> dict:
+    """The roofline of the kernel that takes the most time per step (among the
+    stages with a byte model): algorithmic bytes per launch over its own
+    launch time, measured by the stage events on its stream."""
+    K = rr["steps"]
+    name = max(STAGE_BYTES, key=lambda k: rr["stage_ms"][k])
+    ms = rr["stage_ms"][name]
+    units = rr["stage_units"][name] / K
+    per = rr["stage_bytes"][name]
+    ach = per * units / (ms * 1e-3) / 1e9
+    dram = LARGE_DRAM_BYTES_PER_UNIT.get((name, rr["precision"]))
+    traffic = dram * units if dram else None
+    out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+           "traffic": traffic, "peak_source": peak_kind, "kernel": STAGE_KERNELS[name],
+           "kernel_ms_per_launch": ms, "algorithmic_bytes_per_launch": per * units, "units_per_launch": units,
+           "bytes_per_unit": per,
+           "share_of_step": ms / rr["ms_per_step"]}
+    if traffic:
+        out["frac_traffic"] = traffic / (ms * 1e-3) / 1e9 / peak
+    return out
 
 
 def large_e2e(at: int = 1) -> dict:
@@ -815,25 +887,27 @@ def large_e2e(at: int = 1) -> dict:
             "steps": 1, "at_step": at}
 
 
-def large_oracle_sample(nsteps: int = 1) -> dict:
-    """The oracle on a 64^3 sub-box of the same recipe (box 2 lambda, the same
-    density, ppc, intensity and thinning), one core, over its first steps."""
+def large_oracle_sample(nsteps: int = 1, n: int = 64, time_from: int = 0) -> dict:
+    """The oracle on an n^3 box of the same recipe (box n/32 lambda, the same
+    density, ppc, intensity and thinning), one core, over its first nsteps
+    steps (those from index time_from on timed)."""
     import numpy as np
     from oracle import drive
     from paper_1412_6426_gb300 import workloads
-    w, fx, fy = workloads.large_cascade(n=64)
-    fo = [np.array(a, dtype=np.float64) for a in workloads.expand_profiles(fx, fy, 64)]
+    w, fx, fy = workloads.large_cascade(n=n)
+    fo = [np.array(a, dtype=np.float64) for a in workloads.expand_profiles(fx, fy, n)]
     Jo = [np.zeros_like(fo[0]) for _ in range(3)]
-    t0 = time.perf_counter()
     _, diag, _, _ = drive.run(w.n, w.d, w.x0, w.periodic, w.field_mode, w.fp, w.dt, nsteps, w.particles,
                               kappa=w.kappa, seed=w.seed, caps=w.meta["capacity64"], fields=fo, J=Jo,
                               deposit_on=1, yee=True, thin_interval=w.meta["thin_interval"],
-                              thin_limit=w.meta["thin_limit"])
-    secs = time.perf_counter() - t0
-    return {"value": diag["particle_steps"] / secs, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": (f"steps 0..{nsteps - 1} of the same recipe on a 64^3 sub-box (2 lambda; 6.6e5 e- and "
-                       f"6.6e5 p+), FP64 oracle with deposit and field update, one process (the particles "
-                       f"share the mesh)")}
+                              thin_limit=w.meta["thin_limit"], time_from=time_from)
+    secs = diag["timed_seconds"]
+    ne = len(w.particles[workloads.ELECTRON][3])
+    return {"value": diag["timed_particle_steps"] / secs, "unit": "particle-steps/s", "cores": 1,
+            "kind": "oracle", "seconds": secs, "steps": nsteps - time_from,
+            "sample": (f"steps {time_from}..{nsteps - 1} of the same recipe on a {n}^3 box ({n / 32:g} lambda; "
+                       f"{ne:.2g} e- and as many p+ at the start), FP64 oracle with deposit and field update, "
+                       f"one process (the particles share the mesh)")}
 
 
 def large_profile_window(start: int, count: int, n: int = 512, caps=None) -> None:
@@ -888,8 +962,7 @@ def main_large(args, world, rank, local):
             caps = caps + (workloads_target(args.box),)
         large_profile_window(a, b, args.box, caps)
         return
-    K = LARGE_STEPS if args.steps == RUN_STEPS - 3 else args.steps
-    W = LARGE_WARMUP if args.warmup == 3 else args.warmup
+    K, W = args.steps, args.warmup
     r = large_device(32, K, W, barrier)
     r64 = None if args.no_fp64 else large_device(64, max(2, K // 4), W, barrier)
     e2e = None if args.no_e2e else large_e2e()
@@ -900,12 +973,15 @@ def main_large(args, world, rank, local):
         return
     peak, peak_kind = peaks()
 
-    def roof(rr):
+    def roof_step(rr):
         ach = rr["algo_bytes"] / rr["seconds"] / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "peak_source": peak_kind,
+                "peak_source": peak_kind,
                 "kernel": "whole step (all kernels: particles, deposit, FDTD, thinning, sort)",
                 "algorithmic_bytes_per_step": rr["algo_bytes"] / rr["steps"]}
+
+    def stages(rr):
+        return {k: round(v, 4) for k, v in rr["stage_ms"].items()}
 
     line = {"metric": METRIC, "value": tot / mx, "unit": "particle-steps/s", "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -913,15 +989,18 @@ def main_large(args, world, rank, local):
             "config": {"workload": LARGE_NAME, "precision": "fp32 fields, particles, push/rates; fp64 tables",
                        "parallelism": f"independent boxes x{world}",
                        "l2": "the mesh alone, 4.8 GB, is larger than L2 (no flush)",
-                       "compact_and_sort_interval": 8, "window": [W, W + K]},
-            "roofline": roof(r), "gpu_launches": r["launches"], "clocks": r["clocks"],
+                       "compact_and_sort_interval": 8, "window": r["window"]},
+            "roofline": dominant_roofline(r, peak, peak_kind), "roofline_step": roof_step(r),
+            "stages_ms_per_step": stages(r), "gpu_launches": r["launches"], "clocks": r["clocks"],
             "events": {"emissions": r["emissions"], "pairs": r["pairs"], "thinned": r["thinned"],
-                       "live_at_end": r["live_end"]}}
+                       "live_at_end": r["live_end"], "deposits_through_tiles": r["tile_fraction"]}}
     if r64 is not None:
         v64 = r64["particle_steps"] / r64["seconds"]
         line["fp64"] = {"value": v64, "ms_per_step": r64["ms_per_step"], "steps": r64["steps"],
-                        "window": [W, W + r64["steps"]], "roofline": roof(r64),
-                        "speedup_fp32_over_fp64": line["value"] / v64, "live_at_end": r64["live_end"]}
+                        "window": r64["window"], "roofline": dominant_roofline(r64, peak, peak_kind),
+                        "roofline_step": roof_step(r64), "stages_ms_per_step": stages(r64),
+                        "speedup_fp32_over_fp64": line["value"] / v64, "live_at_end": r64["live_end"],
+                        "clocks": r64["clocks"]}
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu:
@@ -1001,7 +1080,8 @@ def main():
     global COMPACT_INTERVAL, BATCH_SCALE, BATCH_STEPS, BATCH_AUTOTUNE, GENERATOR
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=RUN_STEPS - 3)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 20 for cascade512, 597 for collision)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 side-by-side run")
@@ -1016,10 +1096,10 @@ def main():
                     help="collision: emission generator (0 modified, 1 alternative, 2 standard)")
     ap.add_argument("--tuning", default="",
                     help="collision: qed_tuning fields, e.g. concurrent=1,photon_blocks_per_sm=2")
-    ap.add_argument("--workload", choices=("collision", "batched", "cascade", "cascade512"), default="collision",
-                    help="collision: the beam-laser collision (the headline line); batched: 512 ensembles; "
-                         "cascade: the self-consistent 256^3 cascade; cascade512: the large 512^3 cascade "
-                         "(a window of its run)")
+    ap.add_argument("--workload", choices=("collision", "batched", "cascade", "cascade512"), default="cascade512",
+                    help="cascade512: the large 512^3 cascade with its slab target, a window of its run (the "
+                         "headline line); collision: the beam-laser collision; batched: 512 ensembles; "
+                         "cascade: the self-consistent 256^3 cascade")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="batched: electron counts x this (smaller sets are for profiling captures)")
     ap.add_argument("--batch-steps", type=int, default=BATCH_STEPS, help="batched: steps of the run")
@@ -1038,9 +1118,11 @@ def main():
     for kv in filter(None, args.tuning.split(",")):
         k, v = kv.split("=")
         TUNING[k.strip()] = int(v)
+    if args.steps is None:
+        args.steps = LARGE_STEPS if args.workload == "cascade512" else RUN_STEPS - 3
     K, W = args.steps, args.warmup
-    if K < 1 or W < 0 or K + W > RUN_STEPS:
-        ap.error(f"need 1 <= steps and steps + warmup <= {RUN_STEPS}")
+    if K < 1 or W < 0 or (args.workload == "collision" and K + W > RUN_STEPS):
+        ap.error(f"need 1 <= steps, 0 <= warmup and (collision) steps + warmup <= {RUN_STEPS}")
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -1062,9 +1144,12 @@ def main():
     if args.workload == "cascade512":
         if args.impl == "reference":
             if rank == 0:
-                cb = large_oracle_sample(1)
+                # the oracle as it stands on a 32^3 box of the same recipe: W
+                # untimed steps, then K timed steps (about 6 s each on one core)
+                cb = large_oracle_sample(W + K, n=32, time_from=W)
                 print(json.dumps({"metric": METRIC, "value": cb["value"], "unit": "particle-steps/s",
-                                  "n_gpus": args.gpus, "steps": 1, "warmup": 0, "higher_is_better": True,
+                                  "n_gpus": args.gpus, "steps": K, "warmup": W,
+                                  "ms_per_step": cb["seconds"] * 1e3 / K, "higher_is_better": True,
                                   "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                                   "impl": "reference", "config": {"workload": LARGE_NAME, "sample": cb["sample"]},
                                   "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
