@@ -221,7 +221,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
   if (rc == QED_OK) rc = dalloc(&c->d_count, 8 * sizeof(long long));   // [4 + 4]: sort totals
   if (rc == QED_OK) rc = dalloc(&c->d_nstart, 4 * sizeof(long long));
   // product counts per pass, then the work counters of the cell-block kernel
-  if (rc == QED_OK) rc = dalloc(&c->d_pend_count, sizeof(unsigned long long) * (qed::kMaxPass + 4));
+  if (rc == QED_OK) rc = dalloc(&c->d_pend_count, sizeof(unsigned long long) * (qed::kMaxPass + 5));
   if (g->field_mode == QED_FIELD_GRID) {
     long long nblk = 1;
     for (int k = 0; k < 3; ++k) {

@@ -114,7 +114,8 @@ template <typename R> struct StepArgs {
   int nb[3];
   int nblk;
   const unsigned *blk_start[4];
-  unsigned *work;          // work-stealing counter of the cell-block kernel (zeroed per step)
+  unsigned *work;          // work-stealing counters of the cell-block kernels (zeroed per step):
+                           // [0] e-/e+ items, [1] deposit, [4] ion items ([2..3]: kWorkSlot)
   void *step_const;        // per-step field constants (written by k_step_constants)
   void *clock;             // device clock {t, step}: read and advanced once per step
   double dt_d;             // the step in FP64 (advances the clock)
@@ -179,7 +180,8 @@ struct qed_ctx {
   int blocks_photon = 0;              // grid sizes of the step kernels
   int blocks_massive = 0;
   int blocks_products = 0;
-  int blocks_cells = 0;
+  int blocks_cells = 0;               // the cell-block pass: e-/e+, and ions alone
+  int blocks_cells_ions = 0;
   int64_t step = 0;                   // host mirror of the clock (steps issued)
   int latched = 0;                    // a device error was observed
   int64_t steps_since_compact = 0;

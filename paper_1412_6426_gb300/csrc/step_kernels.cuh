@@ -1496,28 +1496,35 @@ struct BlockItems {
   unsigned items;
 };
 
+// The families of the cell-block pass: electrons and positrons (LEPTONS),
+// or ions alone, whose step has no event generator and is compiled without
+// it, so that it runs with fewer registers and more warps (FP32).
 template <typename R>
-__device__ __forceinline__ BlockItems block_items(const StepArgs<R> &a, const long long *ns) {
+__device__ __forceinline__ BlockItems block_items(const StepArgs<R> &a, const long long *ns, bool ions) {
   BlockItems b;
   const int fam[3] = {kElectron, kPositron, kIon};
   b.items = 0;
   for (int f = 0; f < 3; ++f) {
     const int sp = fam[f];
-    b.nsort[f] = a.blk_start[sp] ? min((long long)a.blk_start[sp][a.nblk], ns[sp]) : 0;
+    const bool mine = ions ? sp == kIon : sp != kIon;
+    b.nsort[f] = (mine && a.blk_start[sp]) ? min((long long)a.blk_start[sp][a.nblk], ns[sp]) : 0;
     b.nitem[f] = (b.nsort[f] + kBlockChunk - 1) / kBlockChunk;
     b.items += (unsigned)b.nitem[f];
   }
   return b;
 }
 
-// Grid mode: electrons, positrons and ions in cell-block order, advanced in
-// work items taken by work stealing; warps take 32 records at a time inside
-// an item, so fast warps take more.  The current is deposited afterwards by
-// k_deposit_blocks, from the start point each thread leaves in the store's
-// second buffer (free between compactions): keeping the Esirkepov stencil
-// out of this kernel keeps its code within the instruction cache.
-template <typename R, bool EXT>
-__global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
+template <typename R, bool IONS> struct BlocksOcc { static constexpr int blocks = IONS && sizeof(R) == 4 ? 3 : 2; };
+
+// Grid mode: electrons, positrons (IONS = false) or ions (IONS = true) in
+// cell-block order, advanced in work items taken by work stealing; warps
+// take 32 records at a time inside an item, so fast warps take more.  The
+// current is deposited afterwards by k_deposit_blocks, from the start point
+// each thread leaves in the store's second buffer (free between
+// compactions): keeping the Esirkepov stencil out of this kernel keeps its
+// code within the instruction cache.
+template <typename R, bool EXT, bool IONS>
+__global__ void __launch_bounds__(256, (BlocksOcc<R, IONS>::blocks)) k_blocks(const StepArgs<R> a) {
   __shared__ int blk;
   __shared__ int next;
   __shared__ long long ns[4];
@@ -1525,12 +1532,13 @@ __global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
   const unsigned step = ((const StepConst *)a.step_const)->step;
   if (threadIdx.x < 4) ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
   __syncthreads();
-  const BlockItems bi = block_items(a, ns);
+  const BlockItems bi = block_items(a, ns, IONS);
   const int fam[3] = {kElectron, kPositron, kIon};
   const int lane = threadIdx.x & 31;
+  unsigned *work = IONS ? a.work + 4 : a.work;
   for (;;) {
     if (threadIdx.x == 0) {
-      blk = (int)atomicAdd(a.work, 1u);
+      blk = (int)atomicAdd(work, 1u);
       next = 0;
     }
     __syncthreads();
@@ -1538,7 +1546,7 @@ __global__ void __launch_bounds__(256, 2) k_blocks(const StepArgs<R> a) {
     if (item >= bi.items) break;
     int f = 0;
     while (item >= bi.nitem[f]) { item -= (unsigned)bi.nitem[f]; ++f; }
-    const int sp = fam[f];
+    const int sp = IONS ? (int)kIon : fam[f];
     const long long lo = (long long)item * kBlockChunk, hi = min(lo + kBlockChunk, bi.nsort[f]);
     const int total = (int)(hi - lo);
     for (;;) {
@@ -1909,7 +1917,7 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   if (cudaMemcpyAsync(c->d_nstart, c->d_count, 4 * sizeof(long long), cudaMemcpyDeviceToDevice, s) !=
       cudaSuccess)
     return QED_ERR_CUDA;
-  if (cudaMemsetAsync(c->d_pend_count, 0, sizeof(unsigned long long) * (kMaxPass + 4), s) !=
+  if (cudaMemsetAsync(c->d_pend_count, 0, sizeof(unsigned long long) * (kMaxPass + 5), s) !=
       cudaSuccess)
     return QED_ERR_CUDA;
   if (a.deposit) {
@@ -1951,7 +1959,11 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   qed_mark(c, QED_STAGE_PHOTONS, s);
   if (e == cudaSuccess && a.blk_start[kElectron]) {
     c->launches += 1;
-    e = cudaLaunchKernel((const void *)k_blocks<R, EXT>, dim3(c->blocks_cells), dim3(256), args, 0, s);
+    e = cudaLaunchKernel((const void *)k_blocks<R, EXT, false>, dim3(c->blocks_cells), dim3(256), args, 0, s);
+    if (e == cudaSuccess && a.blk_start[kIon]) {
+      c->launches += 1;
+      e = cudaLaunchKernel((const void *)k_blocks<R, EXT, true>, dim3(c->blocks_cells_ions), dim3(256), args, 0, s);
+    }
     qed_mark(c, QED_STAGE_BLOCKS, s);
     if (e == cudaSuccess && a.deposit) {
       c->launches += 1;
@@ -1990,9 +2002,12 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
 template <typename R, bool EXT>
 int step_blocks(qed_ctx *c) {
   int a = 0, b = 0, p = 0, g = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k_blocks<R, EXT>, 256, 0) != cudaSuccess || g < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k_blocks<R, EXT, false>, 256, 0) != cudaSuccess || g < 1)
     return QED_ERR_CUDA;
   c->blocks_cells = g * c->num_sms;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k_blocks<R, EXT, true>, 256, 0) != cudaSuccess || g < 1)
+    return QED_ERR_CUDA;
+  c->blocks_cells_ions = g * c->num_sms;
   if (cudaFuncSetAttribute(k_deposit_blocks<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)deposit_smem<R>(kMaxDepositHalo)) != cudaSuccess)
     return QED_ERR_CUDA;
