@@ -770,6 +770,9 @@ def large_device(precision: int, K: int, W: int, dist_barrier, start: int = LARG
     with Simulation(w, **opts) as sim:
         sim.set_grid_fields(F[:3], F[3:], J)
         sim.set_all()
+        if TUNING:
+            sim.set_tuning(**TUNING)
+        tuning = sim.tuning()
         if s0 - W:
             sim.step(s0 - W)
         sim.step(W)
@@ -814,7 +817,8 @@ def large_device(precision: int, K: int, W: int, dist_barrier, start: int = LARG
             "stage_bytes": {k: STAGE_BYTES[k][pi] for k in STAGE_BYTES},
             "launches": d1["kernel_launches"] - d0["kernel_launches"], "live_end": d1["count"],
             "emissions": d1["emissions"] - d0["emissions"], "pairs": d1["pairs"] - d0["pairs"],
-            "thinned": d1["thinned"] - d0["thinned"], "precision": precision,
+            "substeps_lepton": d1["substeps_lepton"] - d0["substeps_lepton"],
+            "thinned": d1["thinned"] - d0["thinned"], "precision": precision, "tuning": tuning,
             "tile_fraction": (d1["tile_deposits"] - d0["tile_deposits"]) / blk if blk else None}
 
 
@@ -989,11 +993,12 @@ def main_large(args, world, rank, local):
             "config": {"workload": LARGE_NAME, "precision": "fp32 fields, particles, push/rates; fp64 tables",
                        "parallelism": f"independent boxes x{world}",
                        "l2": "the mesh alone, 4.8 GB, is larger than L2 (no flush)",
-                       "compact_and_sort_interval": 8, "window": r["window"]},
+                       "compact_and_sort_interval": 8, "window": r["window"], "tuning": r["tuning"]},
             "roofline": dominant_roofline(r, peak, peak_kind), "roofline_step": roof_step(r),
             "stages_ms_per_step": stages(r), "gpu_launches": r["launches"], "clocks": r["clocks"],
             "events": {"emissions": r["emissions"], "pairs": r["pairs"], "thinned": r["thinned"],
-                       "live_at_end": r["live_end"], "deposits_through_tiles": r["tile_fraction"]}}
+                       "live_at_end": r["live_end"], "deposits_through_tiles": r["tile_fraction"],
+                       "lepton_substeps_per_step": r["substeps_lepton"] / K}}
     if r64 is not None:
         v64 = r64["particle_steps"] / r64["seconds"]
         line["fp64"] = {"value": v64, "ms_per_step": r64["ms_per_step"], "steps": r64["steps"],
@@ -1095,7 +1100,7 @@ def main():
     ap.add_argument("--generator", type=int, default=0, choices=(0, 1, 2),
                     help="collision: emission generator (0 modified, 1 alternative, 2 standard)")
     ap.add_argument("--tuning", default="",
-                    help="collision: qed_tuning fields, e.g. concurrent=1,photon_blocks_per_sm=2")
+                    help="collision, cascade512: qed_tuning fields, e.g. deposit_halo=3,refill_lanes=16")
     ap.add_argument("--workload", choices=("collision", "batched", "cascade", "cascade512"), default="cascade512",
                     help="cascade512: the large 512^3 cascade with its slab target, a window of its run (the "
                          "headline line); collision: the beam-laser collision; batched: 512 ensembles; "

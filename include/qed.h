@@ -237,7 +237,14 @@ typedef struct qed_tuning {
                                       drifted farther since the last sort, and
                                       every particle with H = 0, adds its
                                       current to J with global atomics */
-    int32_t reserved;              /* must be 0 */
+    int32_t refill_lanes;          /* QED_FIELD_GRID, e-/e+ in cell-block
+                                      order: a warp takes new particles for
+                                      its idle lanes together once at least
+                                      this many lanes have finished their
+                                      sub-interval loops (Sec. IV.H: the
+                                      loops differ in length), 1 .. 32; 0 =
+                                      whole batches of 32, taken when every
+                                      lane has finished */
 } qed_tuning;
 
 /* Caller-owned Yee arrays (device memory, context precision). */
@@ -401,7 +408,8 @@ int qed_set_tuning(qed_ctx *ctx, const qed_tuning *tuning);
  * limit), work chunks {0, 256, 1024, 4096, 16384}, compaction intervals
  * {c, c/2, c/4} below the current interval c (the capacities were sized
  * for c), with ensembles sorting on or off, and on the Yee mesh the deposit's
- * tile halo {4, 3, 2, 1} or global atomics only (0).  The search stops before a
+ * tile halo {4, 3, 2, 1} or global atomics only (0) and the lane refill of
+ * the cell-block pass {0, 24, 16}.  The search stops before a
  * trial that would take more than max_steps steps in all; the fields not
  * reached keep their values.  Applies the best tuning found, writes it to
  * *out (may be NULL) and the number of steps taken to *steps_taken (may be

@@ -81,7 +81,8 @@ int check_tuning(const qed_ctx *c, const qed_tuning *t) {
   if (t->work_chunk < 0 || t->work_chunk % 256 != 0 || t->work_chunk > (1 << 24)) return QED_ERR_ARG;
   if (t->compact_interval < 1 || (t->sort_massive != 0 && t->sort_massive != 1)) return QED_ERR_ARG;
   if (t->concurrent != 0 && t->concurrent != 1) return QED_ERR_ARG;
-  if (t->deposit_halo < 0 || t->deposit_halo > qed::kMaxDepositHalo || t->reserved != 0) return QED_ERR_ARG;
+  if (t->deposit_halo < 0 || t->deposit_halo > qed::kMaxDepositHalo) return QED_ERR_ARG;
+  if (t->refill_lanes < 0 || t->refill_lanes > 32) return QED_ERR_ARG;
   return QED_OK;
 }
 
@@ -582,6 +583,11 @@ int qed_autotune(qed_ctx *c, const qed_fields *f, double dt, int32_t steps_per_t
     // the deposit's current tiles: halo 4 .. 1, or global atomics only
     const int halos[5] = {4, 3, 2, 1, 0};
     rc = tune_field(&qed_tuning::deposit_halo, halos, 5);
+  }
+  if (rc == QED_OK && c->grid.field_mode == QED_FIELD_GRID) {
+    // e-/e+ of the cell-block pass: whole batches, or lanes refilled in groups
+    const int refill[3] = {0, 24, 16};
+    rc = tune_field(&qed_tuning::refill_lanes, refill, 3);
   }
   if (rc == QED_OK) {
     // the two passes side by side: split the SM's blocks between them

@@ -413,8 +413,23 @@ __device__ __forceinline__ R prob_pair(const R *__restrict__ T, R de, R chig, R 
   return R(kAlpha) * h * R(kSqrt3Over2Pi) * (chig / eps) * cbrt_r(z) * (g2 - d * g1);
 }
 
-// Boris push (Appendix A): half E, rotation by B, half E.  FP32: the
-// compiler may contract products and sums into FMAs.
+// gamma = sqrt(1 + p^2/m^2) and 1/(m gamma) of a momentum p (units m_e c) of
+// a particle of mass m (units m_e), from 1/m^2 and 1/m.  FP32: one
+// reciprocal square root (a few ulp; the FP32 path is held to 1e-5 between
+// events); FP64: correctly rounded square root and division.
+__device__ __forceinline__ void lorentz(const V3<float> &p, float inv_m, float inv_m2, float &g, float &ig_m) {
+  const float x = 1.0f + (p.x * p.x + p.y * p.y + p.z * p.z) * inv_m2;
+  const float r = rsqrtf(x);
+  g = x * r;
+  ig_m = inv_m * r;
+}
+__device__ __forceinline__ void lorentz(const V3<double> &p, double inv_m, double inv_m2, double &g, double &ig_m) {
+  g = sqrt(1.0 + (p.x * p.x + p.y * p.y + p.z * p.z) * inv_m2);
+  ig_m = inv_m / g;
+}
+
+// Boris push (Appendix A): half E, rotation by B, half E.  The generic form;
+// FP32 and FP64 use the specialisations below.
 template <typename R>
 __device__ __forceinline__ void boris(V3<R> &p, V3<R> E, V3<R> B, R q, R m, R h) {
   R a = R(0.5) * q * h;
@@ -427,6 +442,24 @@ __device__ __forceinline__ void boris(V3<R> &p, V3<R> E, V3<R> B, R q, R m, R h)
   V3<R> c1 = cross(um, t);
   V3<R> up = {um.x + c1.x, um.y + c1.y, um.z + c1.z};
   V3<R> c2 = cross(up, s);
+  p = {um.x + c2.x + a * E.x, um.y + c2.y + a * E.y, um.z + c2.z + a * E.z};
+}
+
+// FP32: 1/gamma from one reciprocal square root and the rotation factor
+// 2/(1 + t^2) from a fast division (a few ulp each: the rotation then keeps
+// |p| to ~1e-7 per push, with random sign), no other division.
+template <>
+__device__ __forceinline__ void boris<float>(V3<float> &p, V3<float> E, V3<float> B, float q, float m, float h) {
+  const float a = 0.5f * q * h;
+  const V3<float> um = {p.x + a * E.x, p.y + a * E.y, p.z + a * E.z};
+  const float im = __frcp_rn(m);
+  const float f = a * im * rsqrtf(1.0f + dot(um, um) * im * im);
+  const V3<float> t = {f * B.x, f * B.y, f * B.z};
+  const float k = __fdividef(2.0f, 1.0f + dot(t, t));
+  const V3<float> sv = {k * t.x, k * t.y, k * t.z};
+  const V3<float> c1 = cross(um, t);
+  const V3<float> up = {um.x + c1.x, um.y + c1.y, um.z + c1.z};
+  const V3<float> c2 = cross(up, sv);
   p = {um.x + c2.x + a * E.x, um.y + c2.y + a * E.y, um.z + c2.z + a * E.z};
 }
 

@@ -102,11 +102,12 @@ template <typename R> struct StepArgs {
   R *J[3];
   int deposit;
   int deposit_halo;        // current tiles of the deposit: halo H (0 = global atomics only)
+  int refill_lanes;        // cell-block pass, e-/e+: refill a warp's idle lanes at this many (0: batches)
   // generator
   R dt, kappa;
   int nsub_max, emission_on, pairs_on, same_step, pm_strict;
   unsigned seed;
-  R charge[4], mass[4];
+  R charge[4], mass[4], inv_mass[4];
   const R *tab;
   const double *chi_star;  // photons below this chi_g cannot pair (per context)
   // grid mode, cell-block sort: blocks per axis, and per species the first

@@ -562,8 +562,10 @@ __device__ __noinline__ void spectrum_add(const StepArgs<R> &a, R delta, R eps, 
 // FP64 uniform as well.
 template <typename R>
 __device__ __forceinline__ R emit_bound(R chi, R gamma, R h) {
-  const float c = (float)chi, c13 = cbrtf(c);
-  return (R)(float(1.02 * kAlpha * kSqrt3Over2Pi) * (float)h / (float)gamma * (5.6336f * c13 * c13 + 1.8212f * c));
+  // chi^(2/3) by the hardware base-2 logarithm and exponential (a few parts
+  // in 1e7, far inside the 2% margin; chi = 0 gives 0, as it should)
+  const float c = (float)chi, c23 = exp2f(0.6666667f * __log2f(c));
+  return (R)(float(1.02 * kAlpha * kSqrt3Over2Pi) * (float)h / (float)gamma * (5.6336f * c23 + 1.8212f * c));
 }
 
 // Upper bound of P_p(de) over de for one sub-interval (Eq. (30)):
@@ -757,8 +759,8 @@ __device__ __forceinline__ void massive_sub(const StepArgs<R> &a, int pass, int 
   const R qc = a.charge[sp], m = a.mass[sp];
   const bool qed = (sp != kIon) && a.emission_on;
   boris(q.p, E, B, qc, m, h);
-  R g = sqrt_r(R(1) + dot(q.p, q.p) / (m * m));
-  R im = R(1) / (m * g);
+  R g, im;
+  lorentz(q.p, a.inv_mass[sp], a.inv_mass[sp] * a.inv_mass[sp], g, im);
   move(a, q, V3<R>{q.p.x * im, q.p.y * im, q.p.z * im}, h);
   if (!qed) return;
   cnt.sub_l++;
@@ -1514,6 +1516,68 @@ __device__ __forceinline__ BlockItems block_items(const StepArgs<R> &a, const lo
   return b;
 }
 
+// Electrons and positrons of one work item with lanes refilled in groups: a
+// lane holds one particle through its sub-interval loop (Sec. IV.H); once at
+// least k lanes of the warp have finished, the warp takes that many new
+// records from the item at once, so that their loads and field gathers are
+// issued together, and every lane then takes its next sub-interval.
+template <typename R, bool EXT>
+__device__ __forceinline__ void blocks_refill(const StepArgs<R> &a, int sp, long long lo, int total, int *next,
+                                              Cnt &cnt, unsigned step, int k) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  bool has = false, dry = false;
+  Pt<R> q;
+  V3<R> E, B;
+  int n = 1, s = 0;
+  R h = R(0);
+  long long i = 0;
+  for (;;) {
+    const unsigned idle = __ballot_sync(0xffffffffu, !has);
+    if (!dry && (__popc(idle) >= k || idle == 0xffffffffu)) {
+      const int want = __popc(idle);
+      int base = 0;
+      if (lane == 0) base = atomicAdd(next, want);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base + want >= total) dry = true;
+      const int rank = __popc(idle & below);
+      if (!has && base + rank < total) {
+        i = lo + base + rank;
+        int cell;
+        load(a, sp, i, q, cell);
+        if (cell >= 0) {
+          if (a.deposit) keep_start(a, sp, i, q, cell);
+          cnt.psteps[sp]++;
+          decode_cell(a, cell, q.ci);
+          gather_grid(a, q, E, B);
+          const R probe = (E.x + E.y + E.z + B.x + B.y + B.z) * R(0) + (q.p.x + q.p.y + q.p.z) * R(0);
+          if (!(probe == R(0))) {
+            count_rare(a, kCntNonfinite, 1u);
+            atomicOr(a.status, kStNonfinite);
+          }
+          n = massive_begin(a, sp, q, a.dt, E, B, a.id[sp] + i);
+          h = a.dt / R(n);
+          s = 0;
+          has = true;
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, has)) {
+      if (dry) break;
+      continue;
+    }
+    if (has) {
+      massive_sub<R, EXT>(a, 0, sp, q, E, B, cnt, step, s, n, h);
+      if (++s == n) {
+        const int nc = finish_cell(a, q);
+        if (nc < 0) count_rare(a, kCntAbsorbed, 1u);
+        store(a, sp, i, q, nc, false);
+        has = false;
+      }
+    }
+  }
+}
+
 template <typename R, bool IONS> struct BlocksOcc { static constexpr int blocks = IONS && sizeof(R) == 4 ? 3 : 2; };
 
 // Grid mode: electrons, positrons (IONS = false) or ions (IONS = true) in
@@ -1549,6 +1613,11 @@ __global__ void __launch_bounds__(256, (BlocksOcc<R, IONS>::blocks)) k_blocks(co
     const int sp = IONS ? (int)kIon : fam[f];
     const long long lo = (long long)item * kBlockChunk, hi = min(lo + kBlockChunk, bi.nsort[f]);
     const int total = (int)(hi - lo);
+    if (!IONS && a.refill_lanes > 0) {
+      blocks_refill<R, EXT>(a, sp, lo, total, &next, cnt, step, a.refill_lanes);
+      __syncthreads();   // blk and next are reused by the next item
+      continue;
+    }
     for (;;) {
       int base = 0;
       if (lane == 0) base = atomicAdd(&next, 32);
@@ -1833,6 +1902,7 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     a.cap[sp] = st.cap;
     a.charge[sp] = (R)c->species.charge[sp];
     a.mass[sp] = (R)c->species.mass[sp];
+    a.inv_mass[sp] = c->species.mass[sp] > 0.0 ? (R)(1.0 / c->species.mass[sp]) : R(0);
   }
   a.count = c->d_count;
   a.nstart = c->d_nstart;
@@ -1886,6 +1956,7 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   }
   a.deposit = (a.field_mode == kFieldGrid) && c->par.deposit_on;
   a.deposit_halo = c->tune.deposit_halo;
+  a.refill_lanes = c->tune.refill_lanes;
   a.dt = (R)dt;
   a.kappa = (R)c->par.kappa;
   a.nsub_max = c->par.nsub_max;

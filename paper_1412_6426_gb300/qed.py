@@ -67,10 +67,10 @@ class QedTuning(ctypes.Structure):
     _fields_ = [("photon_blocks_per_sm", ctypes.c_int32), ("massive_blocks_per_sm", ctypes.c_int32),
                 ("work_chunk", ctypes.c_int32), ("compact_interval", ctypes.c_int32),
                 ("sort_massive", ctypes.c_int32), ("concurrent", ctypes.c_int32),
-                ("deposit_halo", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("deposit_halo", ctypes.c_int32), ("refill_lanes", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_[:7]}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class QedFields(ctypes.Structure):
