@@ -72,7 +72,9 @@ int main(void) {
   P(qed_params, schwinger_weight); P(qed_diag, schwinger_pairs); P(qed_diag, schwinger_gt1);
   P(qed_diag, photons_created); P(qed_diag, pairs_created); P(qed_diag, thinned);
   P(qed_diag, kernel_launches);
-  P(qed_tuning, work_chunk); P(qed_tuning, sort_massive); P(qed_tuning, concurrent); P(qed_tuning, reserved);
+  P(qed_tuning, work_chunk); P(qed_tuning, sort_massive); P(qed_tuning, concurrent);
+  P(qed_tuning, deposit_halo); P(qed_tuning, refill_lanes);
+  P(qed_diag, block_steps); P(qed_diag, tile_deposits);
   P(qed_diag, particle_steps); P(qed_diag, species_steps); P(qed_diag, emissions);
   P(qed_diag, time); P(qed_diag, status); P(qed_diag, spectrum);
   P(qed_species_desc, charge); P(qed_fields, J);
