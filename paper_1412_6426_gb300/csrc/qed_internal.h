@@ -102,6 +102,7 @@ template <typename R> struct StepArgs {
   R *J[3];
   int deposit;
   int deposit_halo;        // current tiles of the deposit: halo H (0 = global atomics only)
+  int deposit_grab;        // cell blocks a deposit block claims at a time (1 .. 32)
   int refill_lanes;        // cell-block pass, e-/e+: refill a warp's idle lanes at this many (0: batches)
   // generator
   R dt, kappa;

@@ -1668,17 +1668,26 @@ __global__ void __launch_bounds__(256, (BlocksOcc<R, IONS>::blocks)) k_blocks(co
 // non-zero node.  A particle whose stencil leaves the tile (it has drifted
 // farther since the last sort), every particle of a cell block too sparse to
 // pay for zeroing and flushing a tile, and every particle with H = 0 add
-// their current straight to J.  Blocks claim kDepositGrab consecutive cell
-// blocks at a time and skip the empty ones.  A warp whose lanes all move
+// their current straight to J.  Blocks claim a.deposit_grab (1 .. 32)
+// consecutive cell blocks at a time, so that every resident block gets
+// several claims, and skip the empty ones.  A warp whose lanes all move
 // within their cells takes the short form of the stencil: along each axis
 // the shapes cover the cell's two nodes and the current crosses one edge,
 // so each component has 4 terms instead of 18.
 template <typename R> struct DepositOcc { static constexpr int blocks = sizeof(R) == 4 ? 3 : 2; };
-constexpr int kDepositGrab = 32;
 
-template <typename R>
-__device__ __forceinline__ void deposit_in_cell(const StepArgs<R> &a, R *o, int T, const R *os, const R *oe, R qw) {
-  const int TT = T * T, TTT = TT * T;
+// Add to a shared-memory value without reading the sum back (a reduction:
+// no register waits on the result).
+__device__ __forceinline__ void red_shared(float *p, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_shared(double *p, double v) {
+  asm volatile("red.shared.add.f64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "d"(v) : "memory");
+}
+
+template <typename R, int T>
+__device__ __forceinline__ void deposit_in_cell(const StepArgs<R> &a, R *o, const R *os, const R *oe, R qw) {
+  constexpr int TT = T * T, TTT = TT * T;
   R A[3][2], D[3][2], pref[3];
   const R inv_vol = a.inv_d[0] * a.inv_d[1] * a.inv_d[2];
 #pragma unroll
@@ -1695,18 +1704,18 @@ __device__ __forceinline__ void deposit_in_cell(const StepArgs<R> &a, R *o, int 
   for (int k = 0; k < 2; ++k)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      atomicAdd(o + k * TT + j * T, pref[0] * fma_r(A[1][j], A[2][k], r12 * D[1][j] * D[2][k]));
-      atomicAdd(o + TTT + k * TT + j, pref[1] * fma_r(A[0][j], A[2][k], r12 * D[0][j] * D[2][k]));
-      atomicAdd(o + 2 * TTT + k * T + j, pref[2] * fma_r(A[0][j], A[1][k], r12 * D[0][j] * D[1][k]));
+      red_shared(o + k * TT + j * T, pref[0] * fma_r(A[1][j], A[2][k], r12 * D[1][j] * D[2][k]));
+      red_shared(o + TTT + k * TT + j, pref[1] * fma_r(A[0][j], A[2][k], r12 * D[0][j] * D[2][k]));
+      red_shared(o + 2 * TTT + k * T + j, pref[2] * fma_r(A[0][j], A[1][k], r12 * D[0][j] * D[1][k]));
     }
 }
 
-template <typename R>
+template <typename R, int HALO>
 __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(const StepArgs<R> a) {
   extern __shared__ __align__(16) unsigned char dep_smem[];
   R *jt = (R *)dep_smem;
-  const int halo = a.deposit_halo;
-  const int T = tile_nodes(halo), TT = T * T, TTT = TT * T;
+  constexpr int halo = HALO;
+  constexpr int T = tile_nodes(HALO), TT = T * T, TTT = TT * T;
   __shared__ unsigned grab, nonempty;
   __shared__ long long ns[4];
   __shared__ long long rlo[3], rn[3];       // per family: first record and count in the current cell block
@@ -1726,14 +1735,14 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
   const long long tile_min = halo > 0 ? (3ll * TTT) / 64 : (1ll << 62);
   unsigned in_tile = 0;
   for (;;) {
-    if (threadIdx.x == 0) grab = atomicAdd(a.work + 1, (unsigned)kDepositGrab);
+    if (threadIdx.x == 0) grab = atomicAdd(a.work + 1, (unsigned)a.deposit_grab);
     __syncthreads();
     const unsigned base = grab;
     if (base >= (unsigned)a.nblk) break;
     if (threadIdx.x < 32) {
       const unsigned b = base + threadIdx.x;
       bool any = false;
-      if (b < (unsigned)a.nblk)
+      if ((int)threadIdx.x < a.deposit_grab && b < (unsigned)a.nblk)
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
           if (nsort[f] == 0) continue;
@@ -1770,7 +1779,10 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
           const long long stride = c == 0 ? 1 : (c == 1 ? nx : nxy);
           gofs[c][k] = (long long)wrapi(torg[c] + k, a.n[c]) * stride;
         }
-        for (int t = threadIdx.x; t < 3 * TTT; t += blockDim.x) jt[t] = R(0);
+        using V = typename Vec16<R>::T;
+        constexpr int kV = Vec16<R>::n, nv = (3 * TTT) / kV;
+        for (int t = threadIdx.x; t < nv; t += blockDim.x) ((V *)jt)[t] = V{};
+        for (int t = nv * kV + threadIdx.x; t < 3 * TTT; t += blockDim.x) jt[t] = R(0);
         __syncthreads();
       }
       for (long long t = threadIdx.x; t < total; t += blockDim.x) {
@@ -1804,8 +1816,8 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
         const unsigned act = __activemask();
         if (__all_sync(act, !live || (inside && incell))) {
           if (live) {
-            deposit_in_cell(a, jt + (cs[2] - torg[2]) * TT + (cs[1] - torg[1]) * T + (cs[0] - torg[0]), T, os,
-                            q1.off, qw);
+            deposit_in_cell<R, T>(a, jt + (cs[2] - torg[2]) * TT + (cs[1] - torg[1]) * T + (cs[0] - torg[0]), os,
+                                  q1.off, qw);
             ++in_tile;
           }
           continue;
@@ -1822,7 +1834,7 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
         }
         R *o = jt + (cs[2] - torg[2] + et.lo[2]) * TT + (cs[1] - torg[1] + et.lo[1]) * T +
                (cs[0] - torg[0] + et.lo[0]);
-        esir_apply(et, [&](int c, int i, int j, int k, R v) { atomicAdd(o + c * TTT + k * TT + j * T + i, v); });
+        esir_apply(et, [&](int c, int i, int j, int k, R v) { red_shared(o + c * TTT + k * TT + j * T + i, v); });
         ++in_tile;
       }
       __syncthreads();
@@ -1848,6 +1860,17 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
 // Dynamic shared memory of the deposit kernel for a tile halo.
 template <typename R> size_t deposit_smem(int halo) {
   return halo > 0 ? 3 * sizeof(R) * (size_t)tile_nodes(halo) * tile_nodes(halo) * tile_nodes(halo) : 0;
+}
+
+// The deposit kernel of a tile halo (the tile edge is a compile-time constant).
+template <typename R> const void *deposit_kernel(int halo) {
+  switch (halo) {
+    case 0: return (const void *)k_deposit_blocks<R, 0>;
+    case 1: return (const void *)k_deposit_blocks<R, 1>;
+    case 2: return (const void *)k_deposit_blocks<R, 2>;
+    case 3: return (const void *)k_deposit_blocks<R, 3>;
+    default: return (const void *)k_deposit_blocks<R, 4>;
+  }
 }
 
 // Passes 1, 2, ...: products evolving for the rest of the step.  All blocks
@@ -2038,13 +2061,16 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     qed_mark(c, QED_STAGE_BLOCKS, s);
     if (e == cudaSuccess && a.deposit) {
       c->launches += 1;
+      const void *kern = deposit_kernel<R>(a.deposit_halo);
       int per_sm = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deposit_blocks<R>, 256,
-                                                        deposit_smem<R>(a.deposit_halo)) != cudaSuccess ||
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, deposit_smem<R>(a.deposit_halo)) !=
+              cudaSuccess ||
           per_sm < 1)
         return QED_ERR_CUDA;
-      e = cudaLaunchKernel((const void *)k_deposit_blocks<R>, dim3(per_sm * c->num_sms), dim3(256), args,
-                           deposit_smem<R>(a.deposit_halo), s);
+      // claims of 1 .. 32 cell blocks: eight or more per resident block
+      const long long per = (long long)c->nblk / (8ll * per_sm * c->num_sms);
+      a.deposit_grab = (int)(per < 1 ? 1 : (per > 32 ? 32 : per));
+      e = cudaLaunchKernel(kern, dim3(per_sm * c->num_sms), dim3(256), args, deposit_smem<R>(a.deposit_halo), s);
     }
   } else {
     qed_mark(c, QED_STAGE_BLOCKS, s);
@@ -2079,9 +2105,10 @@ int step_blocks(qed_ctx *c) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g, k_blocks<R, EXT, true>, 256, 0) != cudaSuccess || g < 1)
     return QED_ERR_CUDA;
   c->blocks_cells_ions = g * c->num_sms;
-  if (cudaFuncSetAttribute(k_deposit_blocks<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)deposit_smem<R>(kMaxDepositHalo)) != cudaSuccess)
-    return QED_ERR_CUDA;
+  for (int h = 1; h <= kMaxDepositHalo; ++h)
+    if (cudaFuncSetAttribute(deposit_kernel<R>(h), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)deposit_smem<R>(h)) != cudaSuccess)
+      return QED_ERR_CUDA;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_photons<R, EXT>, qed::kPhotonThreads, 0) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pass0<R, false, EXT>, 256, 0) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k_products<R, EXT>, 256, 0) != cudaSuccess ||
