@@ -20,7 +20,9 @@ template <typename R> struct Pt {
   uint64_t id;
 };
 
-// A product waiting to evolve for the rest of the step.
+// A product waiting to evolve for the rest of the step.  Its id is formed
+// by the pass that takes it (product_id of the parent's id, the sub-interval
+// of its birth and its kind), out of the parent's sub-interval loop.
 template <typename R> struct Pend {
   R off[3];
   R w;
@@ -29,7 +31,8 @@ template <typename R> struct Pend {
   V3<R> E, B;
   int ci[3];
   int sp;
-  uint64_t id;
+  uint64_t parent;
+  unsigned sub, kind;
 };
 
 // Per-thread counts of the frequent events, summed per warp at the end of a
@@ -629,8 +632,12 @@ __device__ __noinline__ unsigned append(const StepArgs<R> &a, int sp, Pt<R> &q) 
 }
 
 // Queue a product for the rest of the step (same_step), or append it now.
+// q.id is the parent's id on entry; the product's own id is product_id(q.id,
+// step, sub, kind), formed here for an append and by the product pass for a
+// queued product.
 template <typename R>
-__device__ __noinline__ unsigned emit(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, R trem, V3<R> E, V3<R> B) {
+__device__ __noinline__ unsigned emit(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, unsigned step, unsigned sub,
+                                      unsigned kind, R trem, V3<R> E, V3<R> B) {
   if (a.same_step && trem > R(0)) {
     // lanes queueing products in this pass share one atomic
     const unsigned mask = __activemask();
@@ -647,9 +654,10 @@ __device__ __noinline__ unsigned emit(const StepArgs<R> &a, int pass, int sp, Pt
     r->off[0] = q.off[0]; r->off[1] = q.off[1]; r->off[2] = q.off[2];
     r->w = q.w; r->p = q.p; r->trem = trem; r->E = E; r->B = B;
     r->ci[0] = q.ci[0]; r->ci[1] = q.ci[1]; r->ci[2] = q.ci[2];
-    r->sp = sp; r->id = q.id;
+    r->sp = sp; r->parent = q.id; r->sub = sub; r->kind = kind;
     return 0;
   }
+  q.id = product_id(a, q.id, step, sub, kind);
   return append(a, sp, q);
 }
 
@@ -686,10 +694,9 @@ __device__ __noinline__ SampleCounts emit_samples(const StepArgs<R> &a, int pass
     Pt<R> ph = q;
     ph.p = {delta * q.p.x, delta * q.p.y, delta * q.p.z};
     ph.w = q.w * a.emit_wf;
-    ph.id = product_id(a, q.id, step, (unsigned)s, kPhoton | ((unsigned)j << 8));
     c.made++;
-    spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), ph.w);
-    c.out |= emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B);
+    if (a.nbins > 0) spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), ph.w);
+    c.out |= emit(a, pass, kPhoton, ph, step, (unsigned)s, kPhoton | ((unsigned)j << 8), R(n - 1 - s) * h, E, B);
   }
   return c;
 }
@@ -724,11 +731,9 @@ __device__ __noinline__ SampleCounts pair_samples(const StepArgs<R> &a, int pass
     const R c1 = R(1) - a1;
     po.p = {c1 * q.p.x, c1 * q.p.y, c1 * q.p.z};
     el.w = po.w = q.w * a.pair_wf;
-    el.id = product_id(a, q.id, step, (unsigned)s, kElectron | ((unsigned)j << 8));
-    po.id = product_id(a, q.id, step, (unsigned)s, kPositron | ((unsigned)j << 8));
     c.made++;
-    c.out |= emit(a, pass, kElectron, el, trem, E, B);
-    c.out |= emit(a, pass, kPositron, po, trem, E, B);
+    c.out |= emit(a, pass, kElectron, el, step, (unsigned)s, kElectron | ((unsigned)j << 8), trem, E, B);
+    c.out |= emit(a, pass, kPositron, po, step, (unsigned)s, kPositron | ((unsigned)j << 8), trem, E, B);
   }
   return c;
 }
@@ -797,13 +802,12 @@ __device__ __forceinline__ void massive_sub(const StepArgs<R> &a, int pass, int 
     if (fire) {
       Pt<R> ph = q;
       ph.p = {delta * q.p.x, delta * q.p.y, delta * q.p.z};
-      ph.id = product_id(a, q.id, step, (unsigned)s, kPhoton);
       const R omd = R(1) - delta;
       q.p = {omd * q.p.x, omd * q.p.y, omd * q.p.z};
       cnt.emis++;
       cnt.made_ph++;
-      spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), q.w);
-      count_outcome(a, emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B));
+      if (a.nbins > 0) spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), q.w);
+      count_outcome(a, emit(a, pass, kPhoton, ph, step, (unsigned)s, kPhoton, R(n - 1 - s) * h, E, B));
     }
     return;
   }
@@ -831,13 +835,12 @@ __device__ __forceinline__ void massive_sub(const StepArgs<R> &a, int pass, int 
     R delta = r1 * r1 * r1;
     Pt<R> ph = q;
     ph.p = {delta * q.p.x, delta * q.p.y, delta * q.p.z};
-    ph.id = product_id(a, q.id, step, (unsigned)s, kPhoton);
     R omd = R(1) - delta;
     q.p = {omd * q.p.x, omd * q.p.y, omd * q.p.z};
     cnt.emis++;
     cnt.made_ph++;
-    spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), q.w);
-    count_outcome(a, emit(a, pass, kPhoton, ph, R(n - 1 - s) * h, E, B));
+    if (a.nbins > 0) spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), q.w);
+    count_outcome(a, emit(a, pass, kPhoton, ph, step, (unsigned)s, kPhoton, R(n - 1 - s) * h, E, B));
   }
 }
 
@@ -925,12 +928,11 @@ __device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, P
       el.p = {r1 * q.p.x, r1 * q.p.y, r1 * q.p.z};
       R r1c = R(1) - r1;
       po.p = {r1c * q.p.x, r1c * q.p.y, r1c * q.p.z};
-      el.id = product_id(a, q.id, step, (unsigned)s, kElectron);
-      po.id = product_id(a, q.id, step, (unsigned)s, kPositron);
       cnt.pairs++;
       cnt.made_pair++;
       R trem = R(n - 1 - s) * h;
-      count_outcome(a, emit(a, pass, kElectron, el, trem, E, B) | emit(a, pass, kPositron, po, trem, E, B));
+      count_outcome(a, emit(a, pass, kElectron, el, step, (unsigned)s, kElectron, trem, E, B) |
+                           emit(a, pass, kPositron, po, step, (unsigned)s, kPositron, trem, E, B));
       return false;
     }
   }
@@ -1894,7 +1896,8 @@ __global__ void __launch_bounds__(256, 2) k_products(const StepArgs<R> a) {
       Pt<R> q;
       q.off[0] = r.off[0]; q.off[1] = r.off[1]; q.off[2] = r.off[2];
       q.ci[0] = r.ci[0]; q.ci[1] = r.ci[1]; q.ci[2] = r.ci[2];
-      q.p = r.p; q.w = r.w; q.id = r.id;
+      q.p = r.p; q.w = r.w;
+      q.id = product_id(a, r.parent, step, r.sub, r.kind);
       bool alive = true;
       if (r.sp == kPhoton) alive = advance_photon<R, EXT>(a, pass, q, r.trem, r.E, r.B, cnt, nullptr, chi_star, step);
       else advance_massive<R, EXT>(a, pass, r.sp, q, r.trem, r.E, r.B, cnt, nullptr, step);
