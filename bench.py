@@ -723,7 +723,7 @@ LARGE_START, LARGE_STEPS = 40, 20   # the timed window starts at step 40 (W warm
 # The stages of a step (qed_profile_stages) and the kernels each one holds.
 STAGES = ("constants", "photons", "blocks", "deposit", "massive", "products", "schwinger", "field", "end")
 STAGE_KERNELS = {"constants": "J and count resets, k_grid_max, k_step_constants", "photons": "k_photons",
-                 "blocks": "k_blocks", "deposit": "k_deposit_blocks", "massive": "k_pass0",
+                 "blocks": "k_blocks (e-/e+, then ions)", "deposit": "k_deposit_blocks", "massive": "k_pass0",
                  "products": "k_products", "schwinger": "k_schwinger", "field": "k_yee_b, k_yee_e",
                  "end": "thinning, compaction and cell-block sort"}
 # Algorithmic bytes per unit of each stage, FP32 / FP64:
@@ -740,7 +740,9 @@ STAGE_BYTES = {"photons": (68, 120), "blocks": (68, 120), "massive": (68, 120), 
 # kernel on the large-cascade recipe; the bench scales them by the units of
 # its own launches.  Remove an entry when the kernel changes until it is
 # measured again.
-LARGE_DRAM_BYTES_PER_UNIT: dict = {}
+# "blocks" (k_blocks, e-/e+ and ions): 451.3 MB read + written over 5.289e6
+# particle-steps at step 40 of the same recipe on a 128^3 mesh.
+LARGE_DRAM_BYTES_PER_UNIT: dict = {("blocks", 32): 451.28e6 / 5.289e6}
 
 
 def large_setup(precision: int, n: int = 512):
@@ -835,7 +837,7 @@ def dominant_roofline(rr: dict, peak: float, peak_kind: str) -> dict:
     dram = LARGE_DRAM_BYTES_PER_UNIT.get((name, rr["precision"]))
     traffic = dram * units if dram else None
     out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-           "traffic": traffic, "peak_source": peak_kind, "kernel": STAGE_KERNELS[name],
+           "traffic": traffic, "peak_source": peak_kind, "kernel": STAGE_KERNELS[name], "stage": name,
            "kernel_ms_per_launch": ms, "algorithmic_bytes_per_launch": per * units, "units_per_launch": units,
            "bytes_per_unit": per,
            "share_of_step": ms / rr["ms_per_step"]}

@@ -456,6 +456,17 @@ typedef enum qed_stage {
  * are not owned by the library; the array itself is copied. */
 int qed_profile_stages(qed_ctx *ctx, void *const *events, int32_t n);
 
+/* Self-test of the failure detection of the bounded device waits: the grid
+ * barrier between the passes of the in-step products, in a cooperative
+ * launch of one block per SM of which block absent_block (-1: none) never
+ * arrives.  The others give up after spin_limit polls of about 64 ns each
+ * (the step itself allows 2^24, about a second).  Returns QED_ERR_TIMEOUT
+ * when the wait ran out, QED_OK when every block got through; uses spare
+ * device words of the context and leaves its status as it was.  The paper
+ * has no counterpart; the call exists to test that a wait that cannot end
+ * ends with an error instead of a hang.  Synchronises the stream. */
+int qed_selftest_barrier(qed_ctx *ctx, int32_t absent_block, int64_t spin_limit, void *stream);
+
 /* Synchronise the stream and read counters, live counts, spectra and the
  * device status into *out (host struct).  The quantities are the ones the
  * paper's tests read off a run: the emitted-photon spectrum over log10(delta)

@@ -36,7 +36,42 @@ __global__ void k_chi_star(const R *tab, double kappa, int mode, qed_grid_desc g
   *eps = hmax > 0.0 ? 0.999 * cs / hmax : 0.0;
 }
 
+// Self-test of the bounded grid barrier of the product passes: every block
+// of a cooperative launch but `absent` meets at the barrier; `passed` counts
+// the blocks that got through it.
+__global__ void k_barrier_check(unsigned *bar, int *status, int absent, long long limit, int *passed) {
+  if ((int)blockIdx.x == absent) return;
+  const bool ok = qed::grid_barrier(bar, status, limit);
+  if (threadIdx.x == 0 && ok) atomicAdd(passed, 1);
+}
+
 }  // namespace
+
+extern "C" int qed_selftest_barrier(qed_ctx *c, int32_t absent_block, int64_t spin_limit, void *stream) {
+  if (!c || spin_limit < 1 || absent_block >= c->num_sms) return QED_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // spare words of the context: barrier [2..3], status [1], pass count [2]
+  unsigned *bar = c->d_barrier + 2;
+  int *status = c->d_status + 1, *passed = c->d_status + 2;
+  if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemsetAsync(status, 0, 2 * sizeof(int), s) != cudaSuccess)
+    return QED_ERR_CUDA;
+  int absent = absent_block < 0 ? -1 : absent_block;
+  long long limit = spin_limit;
+  void *args[] = {(void *)&bar, (void *)&status, (void *)&absent, (void *)&limit, (void *)&passed};
+  c->launches += 1;
+  // one block of one warp per SM: every block is co-resident
+  if (cudaLaunchCooperativeKernel((const void *)k_barrier_check, dim3(c->num_sms), dim3(32), args, 0, s) !=
+      cudaSuccess)
+    return QED_ERR_CUDA;
+  int out[2] = {0, 0};
+  if (cudaMemcpyAsync(out, status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return QED_ERR_CUDA;
+  const int expect = absent < 0 ? c->num_sms : 0;
+  if (out[0] & qed::kStTimeout) return out[1] == 0 ? QED_ERR_TIMEOUT : QED_ERR_CUDA;
+  return out[1] == expect ? QED_OK : QED_ERR_CUDA;
+}
 
 int qed_step_kernel_blocks(qed_ctx *c) {
   if (c->ext) return qed_step_kernel_blocks_ext(c);

@@ -940,8 +940,11 @@ __device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, P
 }
 
 // Bounded grid barrier (all blocks are co-resident: cooperative launch).
-// Gives up after ~1 s, sets the timeout status and returns false.
-__device__ bool grid_barrier(unsigned *bar, int *status) {
+// Gives up after `limit` polls of ~64 ns (the default: ~1 s), sets the
+// timeout status and returns false.
+constexpr long long kBarrierPolls = 1ll << 24;
+
+__device__ bool grid_barrier(unsigned *bar, int *status, long long limit = kBarrierPolls) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -958,7 +961,7 @@ __device__ bool grid_barrier(unsigned *bar, int *status) {
       long long it = 0;
       while (*gen == g) {
         __nanosleep(64);
-        if (++it > (1ll << 24)) {
+        if (++it > limit) {
           atomicOr(status, kStTimeout);
           ok = 0;
           break;

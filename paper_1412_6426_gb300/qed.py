@@ -31,7 +31,7 @@ QED_MAX_ENS_BITS = 16
 EXPORTS = ("qed_init", "qed_tables_export", "qed_particles_set", "qed_particles_get", "qed_step",
            "qed_set_clock", "qed_profile_events", "qed_diagnostics", "qed_destroy", "qed_error_string",
            "qed_particles_read_static", "qed_ensembles_set", "qed_get_tuning", "qed_set_tuning",
-           "qed_autotune", "qed_profile_stages")
+           "qed_autotune", "qed_profile_stages", "qed_selftest_barrier")
 
 
 class QedGridDesc(ctypes.Structure):
@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qed_set_clock.argtypes = [vp, i64, ctypes.c_double]
     lib.qed_profile_events.argtypes = [vp, vp, vp, vp]
     lib.qed_profile_stages.argtypes = [vp, ctypes.POINTER(vp), i32]
+    lib.qed_selftest_barrier.argtypes = [vp, i32, i64, vp]
     lib.qed_diagnostics.argtypes = [vp, ctypes.POINTER(QedDiag), vp]
     lib.qed_destroy.argtypes = [vp]
     lib.qed_ensembles_set.argtypes = [vp, i32, dp, vp]
@@ -209,6 +210,12 @@ def qed_profile_stages(ctx: int, events) -> None:
     """events: raw cudaEvent_t handles (ints or 0), entry k for stage k; [] stops recording."""
     arr = (ctypes.c_void_p * max(len(events), 1))(*[ctypes.c_void_p(e or None) for e in events])
     _check("qed_profile_stages", load().qed_profile_stages(ctypes.c_void_p(ctx), arr, len(events)))
+
+
+def qed_selftest_barrier(ctx: int, absent_block: int, spin_limit: int, stream: int = 0) -> int:
+    """Run the bounded grid barrier with block absent_block (-1: none) never
+    arriving; returns the status (QED_OK or QED_ERR_TIMEOUT) without raising."""
+    return load().qed_selftest_barrier(ctypes.c_void_p(ctx), int(absent_block), int(spin_limit), ctypes.c_void_p(stream))
 
 
 def qed_diagnostics(ctx: int, nbins: int = 0, stream: int = 0, check: bool = True) -> dict:

@@ -198,6 +198,9 @@ def test_null_arguments(lib):
     assert lib.qed_autotune(None, None, 1.0, 1, 10, None, None, None) == qed.QED_ERR_ARG
     assert lib.qed_destroy(None) == qed.QED_OK
     assert lib.qed_diagnostics(None, None, None) == qed.QED_ERR_ARG
+    assert lib.qed_selftest_barrier(None, -1, 1, None) == qed.QED_ERR_ARG
+    assert lib.qed_profile_stages(None, None, 0) == qed.QED_ERR_ARG
+    assert lib.qed_particles_read_static(None, 0, None, None, None, None, 0, None, None) == qed.QED_ERR_ARG
 
 
 def test_product_path_has_no_oracle_import():

@@ -194,3 +194,23 @@ def test_fp64_rotating_field_parity():
     rep = compare(gpu, ora, rtol_p=1e-12, xtol=1e-12 * box_scale(w))
     assert rep["ok"], rep
     assert gd["emissions"] == od["emissions"] > 100
+
+
+def test_bounded_barrier_gives_up():
+    # The grid barrier between the passes of the in-step products, with one
+    # block that never arrives: the other blocks give up after the poll limit
+    # (2^14 polls of ~64 ns) with QED_ERR_TIMEOUT instead of waiting forever,
+    # and the context stays usable.  With every block present the barrier
+    # lets them all through.
+    import time
+    from paper_1412_6426_gb300.sim import Simulation
+    w = workloads.test_particles_static_b(n_particles=100, nsteps=2)
+    with Simulation(w, precision=32, capacity=(2000, 100, 5000, 0)) as sim:
+        sim.set_all()
+        assert qed.qed_selftest_barrier(sim.ctx, -1, 1 << 20, sim.stream.cuda_stream) == qed.QED_OK
+        t0 = time.perf_counter()
+        assert qed.qed_selftest_barrier(sim.ctx, 3, 1 << 14, sim.stream.cuda_stream) == qed.QED_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 5.0
+        sim.step(2)
+        d = sim.diag()
+        assert d["status"] == 0 and d["emissions"] > 0
