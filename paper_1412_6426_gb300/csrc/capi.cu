@@ -231,7 +231,8 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     }
     c->nblk = (int)nblk;
     if (rc == QED_OK) rc = dalloc(&c->d_blk_start, sizeof(unsigned) * 4 * (nblk + 1));
-    if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (nblk + 2));
+    // cursors (nblk + 2), then the block sums of the scan (one per 1024 keys)
+    if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (nblk + 2 + (nblk + 1024) / 1024 + 1));
     if (rc == QED_OK) rc = dalloc(&c->d_phot_start, sizeof(unsigned) * (nblk + 2));
     if (rc == QED_OK) rc = dalloc(&c->d_grid_max, sizeof(unsigned long long) * 6);
   }
@@ -247,7 +248,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
       c->key_ensembles = 1;
       c->nblk = qed::kNsubKeys;
       if (rc == QED_OK) rc = dalloc(&c->d_blk_start, sizeof(unsigned) * 4 * (c->nblk + 1));
-      if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (c->nblk + 1));
+      if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (c->nblk + 2 + (c->nblk + 1024) / 1024 + 1));
     }
   }
   if (thinning) {

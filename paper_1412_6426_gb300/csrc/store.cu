@@ -322,33 +322,74 @@ __global__ void k_blk_hist(const T *mom, const uint64_t *id, const long long *co
   }
 }
 
-__global__ void k_blk_scan(unsigned *hist, int nblk, unsigned *start, long long *count, int sp) {
-  __shared__ unsigned part[1024];
-  __shared__ unsigned carry;
-  if (threadIdx.x == 0) carry = 0;
+// Exclusive scan of the per-block histogram in three launches of 1024-thread
+// blocks: the sum of each 1024 keys, an exclusive scan of those sums, then
+// each 1024 keys scanned again with its offset.  Writes start[i] (the first
+// record of block i), the scatter cursor hist[i] = start[i], start[n] and
+// the total (count[sp]).
+constexpr int kScanBlock = 1024;
+
+// Exclusive scan of one value per thread over a 1024-thread block; *total
+// receives the block's sum.
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned *warp_tot, unsigned *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
   __syncthreads();
-  for (int base = 0; base < nblk; base += 1024) {
+  if (warp == 0) {
+    unsigned t = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_tot[lane] = t;   // inclusive over the warps
+  }
+  __syncthreads();
+  *total = warp_tot[31];
+  const unsigned excl = x - v + (warp > 0 ? warp_tot[warp - 1] : 0u);
+  __syncthreads();   // warp_tot is reused by the caller's next scan
+  return excl;
+}
+
+__global__ void k_blk_sums(const unsigned *hist, int n, unsigned *part) {
+  __shared__ unsigned wt[32];
+  const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
+  unsigned total;
+  block_exclusive_scan(i < n ? hist[i] : 0u, wt, &total);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void k_blk_scan_parts(unsigned *part, int nparts, unsigned *start, int n, long long *count, int sp) {
+  __shared__ unsigned wt[32];
+  unsigned carry = 0;
+  for (int base = 0; base < nparts; base += kScanBlock) {
     const int i = base + threadIdx.x;
-    const unsigned v = i < nblk ? hist[i] : 0u;
-    part[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-      const unsigned add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-      __syncthreads();
-      part[threadIdx.x] += add;
-      __syncthreads();
-    }
-    if (i < nblk) {
-      start[i] = carry + part[threadIdx.x] - v;
-      hist[i] = start[i];                // becomes the scatter cursor
-    }
-    __syncthreads();
-    if (threadIdx.x == 1023) carry += part[1023];
-    __syncthreads();
+    const unsigned v = i < nparts ? part[i] : 0u;
+    unsigned total;
+    const unsigned e = block_exclusive_scan(v, wt, &total);
+    if (i < nparts) part[i] = carry + e;
+    carry += total;
   }
   if (threadIdx.x == 0) {
-    start[nblk] = carry;
+    start[n] = carry;
     count[sp] = carry;
+  }
+}
+
+__global__ void k_blk_scan_out(unsigned *hist, int n, const unsigned *part, unsigned *start) {
+  __shared__ unsigned wt[32];
+  const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
+  unsigned total;
+  const unsigned e = block_exclusive_scan(i < n ? hist[i] : 0u, wt, &total) + part[blockIdx.x];
+  if (i < n) {
+    start[i] = e;
+    hist[i] = e;   // becomes the scatter cursor
   }
 }
 
@@ -405,7 +446,13 @@ int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
   k_blk_hist<T><<<grid, 256, 0, s>>>((const T *)st.mom[cur], st.id[cur], c->d_count, sp, (long long)st.cap, g,
                                      c->d_blk_cursor);
   // the record count to scatter is read on the device: the histogram keeps it
-  k_blk_scan<<<1, 1024, 0, s>>>(c->d_blk_cursor, g.nkeys, start, c->d_count + 4, sp);   // total -> [4 + sp]
+  // total -> [4 + sp]; the block sums go to the spare words after the cursors
+  const int nparts = (g.nkeys + kScanBlock - 1) / kScanBlock;
+  unsigned *part = c->d_blk_cursor + (c->nblk + 2);
+  c->launches += 2;
+  k_blk_sums<<<nparts, kScanBlock, 0, s>>>(c->d_blk_cursor, g.nkeys, part);
+  k_blk_scan_parts<<<1, kScanBlock, 0, s>>>(part, nparts, start, g.nkeys, c->d_count + 4, sp);
+  k_blk_scan_out<<<nparts, kScanBlock, 0, s>>>(c->d_blk_cursor, g.nkeys, part, start);
   k_blk_scatter<T><<<grid, 256, 0, s>>>((const T *)st.pos[cur], (const T *)st.mom[cur], st.id[cur],
                                         (T *)st.pos[nxt], (T *)st.mom[nxt], st.id[nxt], c->d_count, sp,
                                         (long long)st.cap, g, c->d_blk_cursor);
@@ -542,7 +589,7 @@ __global__ void k_thin_count(const T *pos, const T *mom, const uint64_t *id, con
     int g = -1;
     double w = 0.0;
     if (i < n && cell_of(mom[i]) >= 0) {
-      g = group_of(id[i], t);
+      g = t.ens_shift >= 64 ? 0 : group_of(id[i], t);   // one group: the id is not needed
       w = weight_of(pos[i]);
     }
     if (priv) {
@@ -557,9 +604,15 @@ __global__ void k_thin_count(const T *pos, const T *mom, const uint64_t *id, con
   }
 }
 
+// One group at or below its limit: nothing to mark or apply.
+__device__ __forceinline__ bool thin_nothing(const ThinArgs &t) {
+  return t.groups == 1 && (long long)t.n[0] <= group_limit(0, t);
+}
+
 template <typename T>
 __global__ void k_thin_mark(const T *pos, const T *mom, const uint64_t *id, const long long *count, int sp,
                             long long cap, ThinArgs t) {
+  if (thin_nothing(t)) return;
   __shared__ ThinShared sh;
   const bool priv = t.groups <= kThinShared;
   if (priv) thin_shared_zero(sh, t.groups);
@@ -595,6 +648,7 @@ __global__ void k_thin_mark(const T *pos, const T *mom, const uint64_t *id, cons
 template <typename T>
 __global__ void k_thin_apply(T *pos, T *mom, const uint64_t *id, const long long *count, int sp, long long cap,
                              ThinArgs t) {
+  if (thin_nothing(t)) return;
   const long long n = min(count[sp], cap);
   unsigned long long removed = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
