@@ -230,9 +230,14 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
       nblk *= c->nb[k];
     }
     c->nblk = (int)nblk;
+    // records are sorted by cell, cell blocks in order and the cells of a
+    // block in order, where the keys fit an int; else by cell block alone
+    c->blk_keys = nblk * qed::kBlockVolume + 1 < (1ll << 31) ? qed::kBlockVolume : 1;
+    const long long nkeys = nblk * c->blk_keys + 1;   // + 1: the photons that cannot pair
     if (rc == QED_OK) rc = dalloc(&c->d_blk_start, sizeof(unsigned) * 4 * (nblk + 1));
-    // cursors (nblk + 2), then the block sums of the scan (one per 1024 keys)
-    if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (nblk + 2 + (nblk + 1024) / 1024 + 1));
+    // cursors (nkeys + 2), then the sums of the scan (one per 16384 keys; at
+    // most one per 1024 allocated)
+    if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (nkeys + 2 + (nkeys + 1024) / 1024 + 1));
     if (rc == QED_OK) rc = dalloc(&c->d_phot_start, sizeof(unsigned) * (nblk + 2));
     if (rc == QED_OK) rc = dalloc(&c->d_grid_max, sizeof(unsigned long long) * 6);
   }

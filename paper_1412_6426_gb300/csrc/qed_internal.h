@@ -25,6 +25,7 @@ constexpr int kNsubKeys = 64;             // sort keys of the sub-interval estim
 constexpr int kMaxBins = 4096;
 constexpr int kCompactTile = 2048;   // particles per tile of the compaction
 constexpr int kBlockCells = 8;       // cell block edge (grid mode): 8 x 8 x 8 cells
+constexpr int kBlockVolume = kBlockCells * kBlockCells * kBlockCells;
 constexpr int kBlockChunk = 1024;    // records per work item of the cell-block kernel
 // Current tile of a cell block (the deposit): the block plus a halo of H
 // cells each side, kBlockCells + 2H + 1 nodes per axis.  The stencil of a
@@ -168,10 +169,11 @@ struct qed_ctx {
   int thin_groups = 0;
   qed_tuning tune{};
   unsigned *d_blk_start = nullptr;    // [4][nblk + 1] first record of each cell block
-  unsigned *d_blk_cursor = nullptr;   // [nblk + 1] histogram / scatter cursors of the sort
+  unsigned *d_blk_cursor = nullptr;   // histogram / scatter cursors of the sort, one per key
   unsigned *d_phot_start = nullptr;   // [nblk + 2] photon sort starts (grid mode)
   int nb[3] = {0, 0, 0};
   int nblk = 0;
+  int blk_keys = 1;                   // sort keys per cell block: its cells (grid mode), else 1
   int sorted = 0;                     // the stores are in cell-block order (up to the tail)
   void *d_clock = nullptr;            // {double t; long long step}: kernels advance it, so
                                       // captured CUDA graphs replay correctly

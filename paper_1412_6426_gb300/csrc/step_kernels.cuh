@@ -1792,16 +1792,23 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
         for (int t = nv * kV + threadIdx.x; t < 3 * TTT; t += blockDim.x) jt[t] = R(0);
         __syncthreads();
       }
-      for (long long t = threadIdx.x; t < total; t += blockDim.x) {
-        const int f = t < n0 ? 0 : (t < n01 ? 1 : 2);
+      // the block's records are in cell order: lane l of a warp takes record
+      // l x rows + k, so that the lanes' stencils lie in cells far apart and
+      // their shared-memory additions seldom meet on one node
+      const long long rows = (total + 31) / 32;
+      for (long long t = threadIdx.x; t < 32 * rows; t += blockDim.x) {
+        const long long u = (t & 31) * rows + (t >> 5);
+        const bool have = u < total;
+        const long long uu = have ? u : 0;
+        const int f = uu < n0 ? 0 : (uu < n01 ? 1 : 2);
         const int sp = fam[f];
-        const long long i = rlo[f] + (t - (f == 0 ? 0 : (f == 1 ? n0 : n01)));
+        const long long i = rlo[f] + (uu - (f == 0 ? 0 : (f == 1 ? n0 : n01)));
         Pt<R> q1;
         R os[3];
         int c0, c1;
         load_start(a, sp, i, os, c0);
         load(a, sp, i, q1, c1);
-        const bool live = c0 >= 0 && c1 >= 0;
+        const bool live = have && c0 >= 0 && c1 >= 0;
         int cs[3], ce[3];
         decode_cell(a, live ? c0 : 0, cs);
         decode_cell(a, live ? c1 : 0, ce);

@@ -250,6 +250,7 @@ __global__ void k_count_live(const T *mom, const long long *count, int sp, long 
 struct BlockGeom {
   int n[3], nb[3];
   int nkeys;
+  int per_block;           // keys per cell block: 1, or one per cell (kBlockVolume)
   int nsub_key;            // 1: key = estimated sub-intervals (ensembles)
   int ens_shift;           // ensemble = id >> ens_shift (64: ensemble 0)
   int n_ens;
@@ -262,9 +263,14 @@ struct BlockGeom {
   const double *eps_star;
 };
 
+// The key of a cell: its cell block, and with one key per cell its place in
+// the block (x fastest), so that the records of a block are in cell order
+// and a warp's 32 consecutive records sit in a few neighbouring cells.
 __device__ __forceinline__ int block_of(int cell, const BlockGeom &g) {
   const int i = cell % g.n[0], j = (cell / g.n[0]) % g.n[1], k = cell / (g.n[0] * g.n[1]);
-  return (i / kBlockCells) + g.nb[0] * ((j / kBlockCells) + g.nb[1] * (k / kBlockCells));
+  const int b = (i / kBlockCells) + g.nb[0] * ((j / kBlockCells) + g.nb[1] * (k / kBlockCells));
+  if (g.per_block == 1) return b;
+  return b * kBlockVolume + (i % kBlockCells) + kBlockCells * ((j % kBlockCells) + kBlockCells * (k % kBlockCells));
 }
 
 // Sub-intervals of Eq. (28) with the ensemble's bound |E0| + |Eu| + |Bu| in
@@ -322,12 +328,28 @@ __global__ void k_blk_hist(const T *mom, const uint64_t *id, const long long *co
   }
 }
 
-// Exclusive scan of the per-block histogram in three launches of 1024-thread
-// blocks: the sum of each 1024 keys, an exclusive scan of those sums, then
-// each 1024 keys scanned again with its offset.  Writes start[i] (the first
-// record of block i), the scatter cursor hist[i] = start[i], start[n] and
-// the total (count[sp]).
-constexpr int kScanBlock = 1024;
+// Exclusive scan of the histogram in three launches of 1024-thread blocks,
+// each thread taking kScanRun consecutive keys: the sum of each part of
+// kScanPart keys, an exclusive scan of those sums, then each part scanned
+// again with its offset.  Writes the scatter cursor of every key, the first
+// record of every cell block, the end of the last and the total
+// (count[sp]).
+constexpr int kScanBlock = 1024, kScanRun = 16, kScanPart = kScanBlock * kScanRun;
+
+// The kScanRun keys of this thread (zero past n), by 16-byte loads where
+// they lie inside the histogram.
+__device__ __forceinline__ void load_run(const unsigned *h, long long first, int n, unsigned *v) {
+  if (first + kScanRun <= n) {
+#pragma unroll
+    for (int q = 0; q < kScanRun / 4; ++q) {
+      const uint4 u = ((const uint4 *)(h + first))[q];
+      v[4 * q] = u.x; v[4 * q + 1] = u.y; v[4 * q + 2] = u.z; v[4 * q + 3] = u.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < kScanRun; ++q) v[q] = first + q < n ? h[first + q] : 0u;
+  }
+}
 
 // Exclusive scan of one value per thread over a 1024-thread block; *total
 // receives the block's sum.
@@ -359,37 +381,68 @@ __device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned *w
 
 __global__ void k_blk_sums(const unsigned *hist, int n, unsigned *part) {
   __shared__ unsigned wt[32];
-  const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
+  unsigned v[kScanRun], sum = 0;
+  load_run(hist, (long long)blockIdx.x * kScanPart + (long long)threadIdx.x * kScanRun, n, v);
+#pragma unroll
+  for (int q = 0; q < kScanRun; ++q) sum += v[q];
   unsigned total;
-  block_exclusive_scan(i < n ? hist[i] : 0u, wt, &total);
+  block_exclusive_scan(sum, wt, &total);
   if (threadIdx.x == 0) part[blockIdx.x] = total;
 }
 
-__global__ void k_blk_scan_parts(unsigned *part, int nparts, unsigned *start, int n, long long *count, int sp) {
+// Each thread scans a run of consecutive sums in turn (their total first,
+// then the runs' exclusive scan across the block, then the run itself).
+__global__ void k_blk_scan_parts(unsigned *part, int nparts, unsigned *start, int nstart, long long *count, int sp) {
   __shared__ unsigned wt[32];
-  unsigned carry = 0;
-  for (int base = 0; base < nparts; base += kScanBlock) {
-    const int i = base + threadIdx.x;
-    const unsigned v = i < nparts ? part[i] : 0u;
-    unsigned total;
-    const unsigned e = block_exclusive_scan(v, wt, &total);
-    if (i < nparts) part[i] = carry + e;
-    carry += total;
+  const int run = (nparts + kScanBlock - 1) / kScanBlock;
+  const int lo = min(nparts, (int)threadIdx.x * run), hi = min(nparts, lo + run);
+  unsigned sum = 0;
+  for (int i = lo; i < hi; ++i) sum += part[i];
+  unsigned total;
+  unsigned e = block_exclusive_scan(sum, wt, &total);
+  for (int i = lo; i < hi; ++i) {
+    const unsigned v = part[i];
+    part[i] = e;
+    e += v;
   }
   if (threadIdx.x == 0) {
-    start[n] = carry;
-    count[sp] = carry;
+    start[nstart] = total;
+    count[sp] = total;
   }
 }
 
-__global__ void k_blk_scan_out(unsigned *hist, int n, const unsigned *part, unsigned *start) {
+// The scatter cursor of every key, and the first record of every cell block
+// (the first key of the block; keys past nblk x per_block each start an
+// entry of their own).
+__global__ void k_blk_scan_out(unsigned *hist, int n, const unsigned *part, unsigned *start, int per_block,
+                               int nmain, int nblk) {
   __shared__ unsigned wt[32];
-  const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
+  const long long first = (long long)blockIdx.x * kScanPart + (long long)threadIdx.x * kScanRun;
+  unsigned v[kScanRun], sum = 0;
+  load_run(hist, first, n, v);
+#pragma unroll
+  for (int q = 0; q < kScanRun; ++q) sum += v[q];
   unsigned total;
-  const unsigned e = block_exclusive_scan(i < n ? hist[i] : 0u, wt, &total) + part[blockIdx.x];
-  if (i < n) {
-    start[i] = e;
-    hist[i] = e;   // becomes the scatter cursor
+  unsigned e = block_exclusive_scan(sum, wt, &total) + part[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kScanRun; ++q) {
+    const long long i = first + q;
+    if (i < n) {
+      if (i >= nmain) start[nblk + (i - nmain)] = e;
+      else if (i % per_block == 0) start[i / per_block] = e;
+    }
+    const unsigned x = v[q];
+    v[q] = e;   // becomes the scatter cursor
+    e += x;
+  }
+  if (first + kScanRun <= n) {
+#pragma unroll
+    for (int q = 0; q < kScanRun / 4; ++q)
+      ((uint4 *)(hist + first))[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < kScanRun; ++q)
+      if (first + q < n) hist[first + q] = v[q];
   }
 }
 
@@ -427,7 +480,9 @@ int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
     g.n[k] = c->grid.n[k];
     g.nb[k] = c->nb[k];
   }
-  g.nkeys = c->nblk;
+  g.per_block = c->key_ensembles ? 1 : c->blk_keys;
+  const int nmain = c->nblk * g.per_block;
+  g.nkeys = nmain;
   g.nsub_key = c->key_ensembles;
   g.ens_shift = c->par.ens_bits > 0 ? 64 - c->par.ens_bits : 64;
   g.n_ens = c->n_ens;
@@ -437,7 +492,7 @@ int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
   g.mass = (sp == kIon || !c->par.emission_on) ? 0.f : (float)c->species.mass[sp];
   g.photon_split = sp == kPhoton && !c->key_ensembles;
   g.eps_star = c->d_eps_star;
-  if (g.photon_split) g.nkeys = c->nblk + 1;
+  if (g.photon_split) g.nkeys = nmain + 1;
   const int cur = st.cur, nxt = cur ^ 1;
   unsigned *start = g.photon_split ? c->d_phot_start : c->d_blk_start + (size_t)sp * (c->nblk + 1);
   if (cudaMemsetAsync(c->d_blk_cursor, 0, sizeof(unsigned) * (g.nkeys + 1), s) != cudaSuccess) return QED_ERR_CUDA;
@@ -447,12 +502,13 @@ int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
                                      c->d_blk_cursor);
   // the record count to scatter is read on the device: the histogram keeps it
   // total -> [4 + sp]; the block sums go to the spare words after the cursors
-  const int nparts = (g.nkeys + kScanBlock - 1) / kScanBlock;
-  unsigned *part = c->d_blk_cursor + (c->nblk + 2);
+  const int nparts = (g.nkeys + kScanPart - 1) / kScanPart;
+  unsigned *part = c->d_blk_cursor + (g.nkeys + 2);
+  const int nstart = c->nblk + (g.nkeys - nmain);
   c->launches += 2;
   k_blk_sums<<<nparts, kScanBlock, 0, s>>>(c->d_blk_cursor, g.nkeys, part);
-  k_blk_scan_parts<<<1, kScanBlock, 0, s>>>(part, nparts, start, g.nkeys, c->d_count + 4, sp);
-  k_blk_scan_out<<<nparts, kScanBlock, 0, s>>>(c->d_blk_cursor, g.nkeys, part, start);
+  k_blk_scan_parts<<<1, kScanBlock, 0, s>>>(part, nparts, start, nstart, c->d_count + 4, sp);
+  k_blk_scan_out<<<nparts, kScanBlock, 0, s>>>(c->d_blk_cursor, g.nkeys, part, start, g.per_block, nmain, c->nblk);
   k_blk_scatter<T><<<grid, 256, 0, s>>>((const T *)st.pos[cur], (const T *)st.mom[cur], st.id[cur],
                                         (T *)st.pos[nxt], (T *)st.mom[nxt], st.id[nxt], c->d_count, sp,
                                         (long long)st.cap, g, c->d_blk_cursor);
