@@ -114,6 +114,17 @@ def test_fp64_grid_parity():
     assert gd["emissions"] == od["emissions"] > 10
 
 
+@pytest.mark.parametrize("n", [(12, 10, 7), (9, 13, 3), (8, 8, 2)])
+def test_fp64_grid_parity_mesh_shapes(n):
+    # ragged meshes for the field update's launch tiles (32 x 8 cells in x-y,
+    # one z plane each) and the cell blocks (8^3): x below a warp, y not a
+    # multiple of 8, odd plane counts, and two planes, where the periodic
+    # wrap in z meets the neighbour plane from both sides
+    w, f = grid_case(seed=17, npart=200, n=n)
+    gd, od = fp64_grid_parity(w, f, 4)
+    assert gd["emissions"] == od["emissions"]
+
+
 @pytest.mark.parametrize("halo", [1, 4, 0])
 def test_fp64_grid_parity_dense_cell_block(halo):
     # 2 x 2500 leptons and 830 ions inside one 8^3 cell block of a 16^3 mesh
