@@ -661,6 +661,53 @@ __device__ __noinline__ unsigned emit(const StepArgs<R> &a, int pass, int sp, Pt
   return append(a, sp, q);
 }
 
+// Photons emitted by the lanes of one warp, held in shared memory until the
+// warp is converged again: emitting lanes are few and seldom together, so
+// queueing each product (a record written to shared memory) and emitting the
+// queue at once lets the lanes share the atomic of emit / append instead of
+// each paying its round trip while the rest of the warp waits.
+constexpr unsigned kWarpQueue = 16;
+template <typename R> struct WarpQueue {
+  unsigned count;
+  Pend<R> rec[kWarpQueue];
+};
+
+template <typename R>
+__device__ __forceinline__ unsigned queue_emit(const StepArgs<R> &a, WarpQueue<R> *wq, int sp, const Pt<R> &q,
+                                               unsigned step, unsigned sub, unsigned kind, R trem, V3<R> E,
+                                               V3<R> B) {
+  const unsigned slot = atomicAdd(&wq->count, 1u);
+  if (slot >= kWarpQueue) {
+    Pt<R> d = q;
+    return emit(a, 0, sp, d, step, sub, kind, trem, E, B);   // full: emit now
+  }
+  Pend<R> *r = wq->rec + slot;
+  r->off[0] = q.off[0]; r->off[1] = q.off[1]; r->off[2] = q.off[2];
+  r->w = q.w; r->p = q.p; r->trem = trem; r->E = E; r->B = B;
+  r->ci[0] = q.ci[0]; r->ci[1] = q.ci[1]; r->ci[2] = q.ci[2];
+  r->sp = sp; r->parent = q.id; r->sub = sub; r->kind = kind;
+  return 0;
+}
+
+// Emit a warp's queued products; every lane of the warp calls this.
+template <typename R>
+__device__ __noinline__ void flush_queue(const StepArgs<R> &a, WarpQueue<R> *wq, unsigned step) {
+  __syncwarp();
+  const unsigned n = min(wq->count, kWarpQueue);
+  const unsigned lane = threadIdx.x & 31;
+  if (lane < n) {
+    const Pend<R> r = wq->rec[lane];
+    Pt<R> q;
+    q.off[0] = r.off[0]; q.off[1] = r.off[1]; q.off[2] = r.off[2];
+    q.ci[0] = r.ci[0]; q.ci[1] = r.ci[1]; q.ci[2] = r.ci[2];
+    q.p = r.p; q.w = r.w; q.id = r.parent;
+    count_outcome(a, emit(a, 0, r.sp, q, step, r.sub, r.kind, r.trem, r.E, r.B));
+  }
+  __syncwarp();
+  if (lane == 0) wq->count = 0;
+  __syncwarp();
+}
+
 // Generator factors (Sec. VI) for the emission: N_g samples of the modified
 // generator in sub-interval s (sample 0 is the parent's own draw r1, r2);
 // each accepted sample makes a photon carrying delta = r1^3 of the parent's
@@ -760,7 +807,8 @@ __device__ __forceinline__ int massive_begin(const StepArgs<R> &a, int sp, Pt<R>
 
 template <typename R, bool EXT>
 __device__ __forceinline__ void massive_sub(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, const V3<R> &E,
-                                            const V3<R> &B, Cnt &cnt, unsigned step, int s, int n, R h) {
+                                            const V3<R> &B, Cnt &cnt, unsigned step, int s, int n, R h,
+                                            WarpQueue<R> *wq = nullptr) {
   const R qc = a.charge[sp], m = a.mass[sp];
   const bool qed = (sp != kIon) && a.emission_on;
   boris(q.p, E, B, qc, m, h);
@@ -840,14 +888,15 @@ __device__ __forceinline__ void massive_sub(const StepArgs<R> &a, int pass, int 
     cnt.emis++;
     cnt.made_ph++;
     if (a.nbins > 0) spectrum_add(a, delta, sqrt_r(dot(ph.p, ph.p)), q.w);
-    count_outcome(a, emit(a, pass, kPhoton, ph, step, (unsigned)s, kPhoton, R(n - 1 - s) * h, E, B));
+    if (wq) count_outcome(a, queue_emit(a, wq, kPhoton, ph, step, (unsigned)s, kPhoton, R(n - 1 - s) * h, E, B));
+    else count_outcome(a, emit(a, pass, kPhoton, ph, step, (unsigned)s, kPhoton, R(n - 1 - s) * h, E, B));
   }
 }
 
 template <typename R, bool EXT>
 __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, int sp, Pt<R> &q, R t_span,
                                                 V3<R> E, V3<R> B, Cnt &cnt, const uint64_t *idp, unsigned step,
-                                                bool deposit_later = false) {
+                                                bool deposit_later = false, WarpQueue<R> *wq = nullptr) {
   // start position (scalars: arrays handed to the deposit would live in
   // local memory for the whole loop)
   const int cs0 = q.ci[0], cs1 = q.ci[1], cs2 = q.ci[2];
@@ -855,7 +904,7 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
   const R qc = a.charge[sp];
   const int n = massive_begin(a, sp, q, t_span, E, B, idp);
   const R h = t_span / R(n);
-  for (int s = 0; s < n; ++s) massive_sub<R, EXT>(a, pass, sp, q, E, B, cnt, step, s, n, h);
+  for (int s = 0; s < n; ++s) massive_sub<R, EXT>(a, pass, sp, q, E, B, cnt, step, s, n, h, wq);
   if (a.deposit && qc != R(0) && !deposit_later) {
     const int cs[3] = {cs0, cs1, cs2};
     const R os[3] = {os0, os1, os2};
@@ -1599,6 +1648,10 @@ __global__ void __launch_bounds__(256, (BlocksOcc<R, IONS>::blocks)) k_blocks(co
   __shared__ int blk;
   __shared__ int next;
   __shared__ long long ns[4];
+  // e-/e+: each warp's queue of emitted photons (ions emit nothing)
+  __shared__ WarpQueue<R> queues[IONS ? 1 : 8];
+  WarpQueue<R> *wq = IONS ? nullptr : queues + (threadIdx.x >> 5);
+  if (wq && (threadIdx.x & 31) == 0) wq->count = 0;
   Cnt cnt;
   const unsigned step = ((const StepConst *)a.step_const)->step;
   if (threadIdx.x < 4) ns[threadIdx.x] = min(a.nstart[threadIdx.x], a.cap[threadIdx.x]);
@@ -1629,6 +1682,10 @@ __global__ void __launch_bounds__(256, (BlocksOcc<R, IONS>::blocks)) k_blocks(co
       int base = 0;
       if (lane == 0) base = atomicAdd(&next, 32);
       base = __shfl_sync(0xffffffffu, base, 0);
+      if (wq) {
+        __syncwarp();   // every lane's queued records are visible
+        if (base >= total || wq->count >= kWarpQueue / 2) flush_queue(a, wq, step);
+      }
       if (base >= total) break;
       const int pos = base + lane;
       if (pos >= total) continue;
@@ -1651,7 +1708,7 @@ __global__ void __launch_bounds__(256, (BlocksOcc<R, IONS>::blocks)) k_blocks(co
         count_rare(a, kCntNonfinite, 1u);
         atomicOr(a.status, kStNonfinite);
       }
-      advance_massive<R, EXT>(a, 0, sp, q, a.dt, E, B, cnt, a.id[sp] + i, step, true);
+      advance_massive<R, EXT>(a, 0, sp, q, a.dt, E, B, cnt, a.id[sp] + i, step, true, wq);
       const int nc = finish_cell(a, q);
       if (nc < 0) count_rare(a, kCntAbsorbed, 1u);
       store(a, sp, i, q, nc, false);
