@@ -666,7 +666,7 @@ __device__ __noinline__ unsigned emit(const StepArgs<R> &a, int pass, int sp, Pt
 // queueing each product (a record written to shared memory) and emitting the
 // queue at once lets the lanes share the atomic of emit / append instead of
 // each paying its round trip while the rest of the warp waits.
-constexpr unsigned kWarpQueue = 16;
+constexpr unsigned kWarpQueue = 32;
 template <typename R> struct WarpQueue {
   unsigned count;
   Pend<R> rec[kWarpQueue];
@@ -1684,7 +1684,7 @@ __global__ void __launch_bounds__(256, (BlocksOcc<R, IONS>::blocks)) k_blocks(co
       base = __shfl_sync(0xffffffffu, base, 0);
       if (wq) {
         __syncwarp();   // every lane's queued records are visible
-        if (base >= total || wq->count >= kWarpQueue / 2) flush_queue(a, wq, step);
+        if (wq->count >= kWarpQueue - 8) flush_queue(a, wq, step);
       }
       if (base >= total) break;
       const int pos = base + lane;
@@ -1715,6 +1715,7 @@ __global__ void __launch_bounds__(256, (BlocksOcc<R, IONS>::blocks)) k_blocks(co
     }
     __syncthreads();   // blk and next are reused by the next item
   }
+  if (wq) flush_queue(a, wq, step);   // the queue outlives the work items
   // every live record this block advanced was counted in psteps
   unsigned long long mine = cnt.psteps[kElectron] + cnt.psteps[kPositron] + cnt.psteps[kIon];
 #pragma unroll
