@@ -694,15 +694,15 @@ template <typename R>
 __device__ __noinline__ void flush_queue(const StepArgs<R> &a, WarpQueue<R> *wq, unsigned step) {
   __syncwarp();
   const unsigned n = min(wq->count, kWarpQueue);
-  const unsigned lane = threadIdx.x & 31;
-  if (lane < n) {
-    const Pend<R> r = wq->rec[lane];
+  for (unsigned k = threadIdx.x & 31; k < n; k += 32) {
+    const Pend<R> r = wq->rec[k];
     Pt<R> q;
     q.off[0] = r.off[0]; q.off[1] = r.off[1]; q.off[2] = r.off[2];
     q.ci[0] = r.ci[0]; q.ci[1] = r.ci[1]; q.ci[2] = r.ci[2];
     q.p = r.p; q.w = r.w; q.id = r.parent;
     count_outcome(a, emit(a, 0, r.sp, q, step, r.sub, r.kind, r.trem, r.E, r.B));
   }
+  const unsigned lane = threadIdx.x & 31;
   __syncwarp();
   if (lane == 0) wq->count = 0;
   __syncwarp();
