@@ -1836,7 +1836,7 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
         rn[f] = hi - lo;
       }
       __syncthreads();
-      const long long n0 = rn[0], n01 = rn[0] + rn[1], total = n01 + rn[2];
+      const long long total = rn[0] + rn[1] + rn[2];
       const bool tile = total >= tile_min;
       if (tile) {
         if (threadIdx.x < 3 * T) {
@@ -1850,17 +1850,21 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
         for (int t = nv * kV + threadIdx.x; t < 3 * TTT; t += blockDim.x) jt[t] = R(0);
         __syncthreads();
       }
-      // the block's records are in cell order: lane l of a warp takes record
-      // l x rows + k, so that the lanes' stencils lie in cells far apart and
-      // their shared-memory additions seldom meet on one node
-      const long long rows = (total + 31) / 32;
-      for (long long t = threadIdx.x; t < 32 * rows; t += blockDim.x) {
-        const long long u = (t & 31) * rows + (t >> 5);
-        const bool have = u < total;
-        const long long uu = have ? u : 0;
-        const int f = uu < n0 ? 0 : (uu < n01 ? 1 : 2);
+      // the block's records of each family are in cell order: lane l of a
+      // warp takes record l x rows + k of one family, so that the lanes'
+      // stencils lie in cells far apart and their shared-memory additions
+      // seldom meet on one node, and a warp holds one family (ions, which
+      // seldom leave their cells, then take the short form together)
+      const long long rows0 = (rn[0] + 31) / 32, rows1 = (rn[1] + 31) / 32, rows2 = (rn[2] + 31) / 32;
+      const long long rows01 = rows0 + rows1;
+      for (long long t = threadIdx.x; t < 32 * (rows01 + rows2); t += blockDim.x) {
+        const long long w = t >> 5;
+        const int f = w < rows0 ? 0 : (w < rows01 ? 1 : 2);
+        const long long rows_f = f == 0 ? rows0 : (f == 1 ? rows1 : rows2);
+        const long long u = (t & 31) * rows_f + (w - (f == 0 ? 0 : (f == 1 ? rows0 : rows01)));
+        const bool have = u < rn[f];
         const int sp = fam[f];
-        const long long i = rlo[f] + (uu - (f == 0 ? 0 : (f == 1 ? n0 : n01)));
+        const long long i = rlo[f] + (have ? u : 0);
         Pt<R> q1;
         R os[3];
         int c0, c1;
