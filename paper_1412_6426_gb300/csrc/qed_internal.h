@@ -70,6 +70,7 @@ template <typename R> struct StepArgs {
   int n[3];
   int periodic[3];
   R d[3], inv_d[3];
+  R jscale[3];             // d / (dt dx dy dz) per axis: current density of a unit charge moved one cell
   double dd[3], x0[3];
   // fields
   int field_mode;

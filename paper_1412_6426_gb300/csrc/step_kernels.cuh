@@ -428,7 +428,6 @@ template <typename R> struct EsirTerms {
 template <typename R>
 __device__ __forceinline__ bool esir_terms(const StepArgs<R> &a, const int *cs, const R *os, const Pt<R> &q, R qw,
                                            EsirTerms<R> &t) {
-  const R inv_vol = a.inv_d[0] * a.inv_d[1] * a.inv_d[2];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int dc = q.ci[c] - cs[c];
@@ -447,7 +446,7 @@ __device__ __forceinline__ bool esir_terms(const StepArgs<R> &a, const int *cs, 
       t.dS[c][m] = s1 - s0;
       t.dS12[c][m] = t.dS[c][m] * R(1.0 / 12.0);
     }
-    const R pref = -qw * a.d[c] / a.dt * inv_vol;
+    const R pref = -qw * a.jscale[c];
     t.P[c][0] = pref * t.dS[c][0];
     t.P[c][1] = pref * (t.dS[c][0] + t.dS[c][1]);
   }
@@ -455,7 +454,8 @@ __device__ __forceinline__ bool esir_terms(const StepArgs<R> &a, const int *cs, 
 }
 
 // add(component, node offsets (di, dj, dk) from cs + lo, value) for every
-// non-zero current term of the Esirkepov scheme (Appendix C).
+// current term of the Esirkepov scheme (Appendix C); the terms of nodes
+// outside the move's support are zero, and add() skips them.
 template <typename R, typename Add>
 __device__ __forceinline__ void esir_apply(const EsirTerms<R> &t, Add add) {
 #pragma unroll
@@ -466,7 +466,7 @@ __device__ __forceinline__ void esir_apply(const EsirTerms<R> &t, Add add) {
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         const R v = t.P[0][i] * w;
-        if (v != R(0)) add(0, i, j, k, v);
+        add(0, i, j, k, v);
       }
     }
 #pragma unroll
@@ -477,7 +477,7 @@ __device__ __forceinline__ void esir_apply(const EsirTerms<R> &t, Add add) {
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const R v = t.P[1][j] * w;
-        if (v != R(0)) add(1, i, j, k, v);
+        add(1, i, j, k, v);
       }
     }
 #pragma unroll
@@ -488,7 +488,7 @@ __device__ __forceinline__ void esir_apply(const EsirTerms<R> &t, Add add) {
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const R v = t.P[2][k] * w;
-        if (v != R(0)) add(2, i, j, k, v);
+        add(2, i, j, k, v);
       }
     }
 }
@@ -506,7 +506,9 @@ __device__ __noinline__ void deposit(const StepArgs<R> &a, const int *cs, const 
     Jj[m] = wrap_fast(cs[1] + t.lo[1] + m, a.n[1]);
     K[m] = wrap_fast(cs[2] + t.lo[2] + m, a.n[2]);
   }
-  esir_apply(t, [&](int c, int i, int j, int k, R v) { atomicAdd(a.J[c] + K[k] * nxy + Jj[j] * nx + I[i], v); });
+  esir_apply(t, [&](int c, int i, int j, int k, R v) {
+    if (v != R(0)) atomicAdd(a.J[c] + K[k] * nxy + Jj[j] * nx + I[i], v);
+  });
 }
 
 // ----- movement and boundaries ---------------------------------------------
@@ -1750,11 +1752,21 @@ __device__ __forceinline__ void red_shared(double *p, double v) {
   asm volatile("red.shared.add.f64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "d"(v) : "memory");
 }
 
+// The same, predicated on v != 0 (no branch: the zero terms of a move's
+// support just do not add).
+__device__ __forceinline__ void red_shared_nz(float *p, float v) {
+  asm volatile("{\n .reg .pred nz;\n setp.ne.f32 nz, %1, 0f00000000;\n @nz red.shared.add.f32 [%0], %1;\n}"
+               ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_shared_nz(double *p, double v) {
+  asm volatile("{\n .reg .pred nz;\n setp.ne.f64 nz, %1, 0d0000000000000000;\n @nz red.shared.add.f64 [%0], %1;\n}"
+               ::"r"((unsigned)__cvta_generic_to_shared(p)), "d"(v) : "memory");
+}
+
 template <typename R, int T>
 __device__ __forceinline__ void deposit_in_cell(const StepArgs<R> &a, R *o, const R *os, const R *oe, R qw) {
   constexpr int TT = T * T, TTT = TT * T;
   R A[3][2], D[3][2], pref[3];
-  const R inv_vol = a.inv_d[0] * a.inv_d[1] * a.inv_d[2];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const R m = R(0.5) * (os[c] + oe[c]);
@@ -1762,7 +1774,7 @@ __device__ __forceinline__ void deposit_in_cell(const StepArgs<R> &a, R *o, cons
     A[c][1] = m;
     D[c][0] = os[c] - oe[c];
     D[c][1] = oe[c] - os[c];
-    pref[c] = -qw * a.d[c] / a.dt * inv_vol * D[c][0];
+    pref[c] = -qw * a.jscale[c] * D[c][0];
   }
   const R r12 = R(1.0 / 12.0);
 #pragma unroll
@@ -1910,7 +1922,7 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
         }
         R *o = jt + (cs[2] - torg[2] + et.lo[2]) * TT + (cs[1] - torg[1] + et.lo[1]) * T +
                (cs[0] - torg[0] + et.lo[0]);
-        esir_apply(et, [&](int c, int i, int j, int k, R v) { red_shared(o + c * TTT + k * TT + j * T + i, v); });
+        esir_apply(et, [&](int c, int i, int j, int k, R v) { red_shared_nz(o + c * TTT + k * TT + j * T + i, v); });
         ++in_tile;
       }
       __syncthreads();
@@ -2058,6 +2070,10 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
   a.deposit_halo = c->tune.deposit_halo;
   a.refill_lanes = c->tune.refill_lanes;
   a.dt = (R)dt;
+  {
+    const double vol = c->grid.d[0] * c->grid.d[1] * c->grid.d[2];
+    for (int k = 0; k < 3; ++k) a.jscale[k] = (R)(c->grid.d[k] / dt / vol);
+  }
   a.kappa = (R)c->par.kappa;
   a.nsub_max = c->par.nsub_max;
   a.emission_on = c->par.emission_on;
