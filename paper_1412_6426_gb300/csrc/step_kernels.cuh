@@ -1744,27 +1744,29 @@ __global__ void __launch_bounds__(256, (BlocksOcc<R, IONS>::blocks)) k_blocks(co
 template <typename R> struct DepositOcc { static constexpr int blocks = sizeof(R) == 4 ? 4 : 2; };
 
 // Add to a shared-memory value without reading the sum back (a reduction:
-// no register waits on the result).
-__device__ __forceinline__ void red_shared(float *p, float v) {
-  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v) : "memory");
+// no register waits on the result).  The address is a shared-window byte
+// address: the tile's is formed once, and each term adds a constant to it.
+__device__ __forceinline__ void red_shared(unsigned addr, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
-__device__ __forceinline__ void red_shared(double *p, double v) {
-  asm volatile("red.shared.add.f64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "d"(v) : "memory");
+__device__ __forceinline__ void red_shared(unsigned addr, double v) {
+  asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
 
 // The same, predicated on v != 0 (no branch: the zero terms of a move's
 // support just do not add).
-__device__ __forceinline__ void red_shared_nz(float *p, float v) {
+__device__ __forceinline__ void red_shared_nz(unsigned addr, float v) {
   asm volatile("{\n .reg .pred nz;\n setp.ne.f32 nz, %1, 0f00000000;\n @nz red.shared.add.f32 [%0], %1;\n}"
-               ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v) : "memory");
+               ::"r"(addr), "f"(v) : "memory");
 }
-__device__ __forceinline__ void red_shared_nz(double *p, double v) {
+__device__ __forceinline__ void red_shared_nz(unsigned addr, double v) {
   asm volatile("{\n .reg .pred nz;\n setp.ne.f64 nz, %1, 0d0000000000000000;\n @nz red.shared.add.f64 [%0], %1;\n}"
-               ::"r"((unsigned)__cvta_generic_to_shared(p)), "d"(v) : "memory");
+               ::"r"(addr), "d"(v) : "memory");
 }
 
+// o: shared byte address of the tile node (cs) of the first component.
 template <typename R, int T>
-__device__ __forceinline__ void deposit_in_cell(const StepArgs<R> &a, R *o, const R *os, const R *oe, R qw) {
+__device__ __forceinline__ void deposit_in_cell(const StepArgs<R> &a, unsigned o, const R *os, const R *oe, R qw) {
   constexpr int TT = T * T, TTT = TT * T;
   R A[3][2], D[3][2], pref[3];
 #pragma unroll
@@ -1781,9 +1783,9 @@ __device__ __forceinline__ void deposit_in_cell(const StepArgs<R> &a, R *o, cons
   for (int k = 0; k < 2; ++k)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      red_shared(o + k * TT + j * T, pref[0] * fma_r(A[1][j], A[2][k], r12 * D[1][j] * D[2][k]));
-      red_shared(o + TTT + k * TT + j, pref[1] * fma_r(A[0][j], A[2][k], r12 * D[0][j] * D[2][k]));
-      red_shared(o + 2 * TTT + k * T + j, pref[2] * fma_r(A[0][j], A[1][k], r12 * D[0][j] * D[1][k]));
+      red_shared(o + sizeof(R) * (k * TT + j * T), pref[0] * fma_r(A[1][j], A[2][k], r12 * D[1][j] * D[2][k]));
+      red_shared(o + sizeof(R) * (TTT + k * TT + j), pref[1] * fma_r(A[0][j], A[2][k], r12 * D[0][j] * D[2][k]));
+      red_shared(o + sizeof(R) * (2 * TTT + k * T + j), pref[2] * fma_r(A[0][j], A[1][k], r12 * D[0][j] * D[1][k]));
     }
 }
 
@@ -1791,6 +1793,7 @@ template <typename R, int HALO>
 __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(const StepArgs<R> a) {
   extern __shared__ __align__(16) unsigned char dep_smem[];
   R *jt = (R *)dep_smem;
+  const unsigned jt_s = (unsigned)__cvta_generic_to_shared(jt);
   constexpr int halo = HALO;
   constexpr int T = tile_nodes(HALO), TT = T * T, TTT = TT * T;
   __shared__ unsigned grab, nonempty;
@@ -1904,8 +1907,9 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
         const unsigned act = __activemask();
         if (__all_sync(act, !live || (inside && incell))) {
           if (live) {
-            deposit_in_cell<R, T>(a, jt + (cs[2] - torg[2]) * TT + (cs[1] - torg[1]) * T + (cs[0] - torg[0]), os,
-                                  q1.off, qw);
+            deposit_in_cell<R, T>(a, jt_s + (unsigned)sizeof(R) * ((cs[2] - torg[2]) * TT + (cs[1] - torg[1]) * T +
+                                                                   (cs[0] - torg[0])),
+                                  os, q1.off, qw);
             ++in_tile;
           }
           continue;
@@ -1920,9 +1924,11 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
           atomicOr(a.status, kStCourant);
           continue;
         }
-        R *o = jt + (cs[2] - torg[2] + et.lo[2]) * TT + (cs[1] - torg[1] + et.lo[1]) * T +
-               (cs[0] - torg[0] + et.lo[0]);
-        esir_apply(et, [&](int c, int i, int j, int k, R v) { red_shared_nz(o + c * TTT + k * TT + j * T + i, v); });
+        const unsigned o = jt_s + (unsigned)sizeof(R) * ((cs[2] - torg[2] + et.lo[2]) * TT +
+                                                         (cs[1] - torg[1] + et.lo[1]) * T + (cs[0] - torg[0] + et.lo[0]));
+        esir_apply(et, [&](int c, int i, int j, int k, R v) {
+          red_shared_nz(o + (unsigned)sizeof(R) * (c * TTT + k * TT + j * T + i), v);
+        });
         ++in_tile;
       }
       __syncthreads();
