@@ -328,7 +328,9 @@ int qed_particles_set(qed_ctx *ctx, int species, const double *x, const double *
  * particles); the records hold what Sec. IV.F and V.A give a super-particle:
  * position, momentum, statistical weight, plus the id that keys its random
  * streams.  *n_out receives the live count; at most max_n are written
- * (QED_ERR_ARG if more are live, and nothing is written then).
+ * (QED_ERR_ARG if more are live, and nothing is written then).  Host
+ * buffers are filled by copies from a device staging buffer of 64 B per
+ * particle, allocated on first use and kept by the context.
  * Synchronises the stream and returns the device status (a failure latches
  * the context). */
 int qed_particles_get(qed_ctx *ctx, int species, double *x, double *p, double *w,

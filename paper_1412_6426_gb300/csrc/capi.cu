@@ -104,6 +104,17 @@ const void *device_alias(const void *p) {
   return nullptr;
 }
 
+// p itself when it is device (or managed) memory, else NULL.
+const void *device_memory(const void *p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? p : nullptr;
+}
+
 int ensure_stage(qed_ctx *c, size_t bytes) {
   if (c->stage_bytes >= bytes) return QED_OK;
   cudaFree(c->stage);
@@ -369,8 +380,11 @@ int qed_particles_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint6
   if (n > max_n) return QED_ERR_ARG;
   if (n > 0) {
     if (!x || !p || !w || !id) return QED_ERR_ARG;
-    void *dx = (void *)device_alias(x), *dp = (void *)device_alias(p), *dw = (void *)device_alias(w),
-         *di = (void *)device_alias(id);
+    // host buffers, page-locked or not, are filled from a device staging
+    // buffer by the copy engines: kernel stores to host memory ran at a
+    // third of their rate
+    void *dx = (void *)device_memory(x), *dp = (void *)device_memory(p), *dw = (void *)device_memory(w),
+         *di = (void *)device_memory(id);
     const size_t nn = (size_t)n;
     bool staged = !dx || !dp || !dw || !di;
     if (staged) {
