@@ -371,21 +371,23 @@ __device__ __forceinline__ Axis<R> cic_axis(int ci, R off, bool half, int n) {
   return {wrap_fast(b, n), wrap_fast(b + 1, n), v};
 }
 
+// Node indices in 32 bits (the mesh holds fewer than 2^31 cells): one
+// multiply-add forms each load's address.
 template <typename R>
 __device__ __forceinline__ R cic(const R *__restrict__ f, const Axis<R> &x, const Axis<R> &y, const Axis<R> &z,
-                                 long long nx, long long nxy) {
+                                 unsigned nx, unsigned nxy) {
   const R fr[3] = {x.fr, y.fr, z.fr};
-  const long long r00 = z.i0 * nxy + y.i0 * nx, r01 = z.i0 * nxy + y.i1 * nx;
-  const long long r10 = z.i1 * nxy + y.i0 * nx, r11 = z.i1 * nxy + y.i1 * nx;
+  const unsigned r00 = z.i0 * nxy + y.i0 * nx, r01 = z.i0 * nxy + y.i1 * nx;
+  const unsigned r10 = z.i1 * nxy + y.i0 * nx, r11 = z.i1 * nxy + y.i1 * nx;
   R acc = R(0);
-  acc += (R(1) - fr[0]) * (R(1) - fr[1]) * (R(1) - fr[2]) * __ldg(f + r00 + x.i0);
-  acc += fr[0] * (R(1) - fr[1]) * (R(1) - fr[2]) * __ldg(f + r00 + x.i1);
-  acc += (R(1) - fr[0]) * fr[1] * (R(1) - fr[2]) * __ldg(f + r01 + x.i0);
-  acc += fr[0] * fr[1] * (R(1) - fr[2]) * __ldg(f + r01 + x.i1);
-  acc += (R(1) - fr[0]) * (R(1) - fr[1]) * fr[2] * __ldg(f + r10 + x.i0);
-  acc += fr[0] * (R(1) - fr[1]) * fr[2] * __ldg(f + r10 + x.i1);
-  acc += (R(1) - fr[0]) * fr[1] * fr[2] * __ldg(f + r11 + x.i0);
-  acc += fr[0] * fr[1] * fr[2] * __ldg(f + r11 + x.i1);
+  acc += (R(1) - fr[0]) * (R(1) - fr[1]) * (R(1) - fr[2]) * __ldg(f + (r00 + (unsigned)x.i0));
+  acc += fr[0] * (R(1) - fr[1]) * (R(1) - fr[2]) * __ldg(f + (r00 + (unsigned)x.i1));
+  acc += (R(1) - fr[0]) * fr[1] * (R(1) - fr[2]) * __ldg(f + (r01 + (unsigned)x.i0));
+  acc += fr[0] * fr[1] * (R(1) - fr[2]) * __ldg(f + (r01 + (unsigned)x.i1));
+  acc += (R(1) - fr[0]) * (R(1) - fr[1]) * fr[2] * __ldg(f + (r10 + (unsigned)x.i0));
+  acc += fr[0] * (R(1) - fr[1]) * fr[2] * __ldg(f + (r10 + (unsigned)x.i1));
+  acc += (R(1) - fr[0]) * fr[1] * fr[2] * __ldg(f + (r11 + (unsigned)x.i0));
+  acc += fr[0] * fr[1] * fr[2] * __ldg(f + (r11 + (unsigned)x.i1));
   return acc;
 }
 
@@ -396,7 +398,7 @@ __device__ void gather_grid(const StepArgs<R> &a, const Pt<R> &q, V3<R> &E, V3<R
   const Axis<R> x0 = cic_axis(q.ci[0], q.off[0], false, a.n[0]), xh = cic_axis(q.ci[0], q.off[0], true, a.n[0]);
   const Axis<R> y0 = cic_axis(q.ci[1], q.off[1], false, a.n[1]), yh = cic_axis(q.ci[1], q.off[1], true, a.n[1]);
   const Axis<R> z0 = cic_axis(q.ci[2], q.off[2], false, a.n[2]), zh = cic_axis(q.ci[2], q.off[2], true, a.n[2]);
-  const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+  const unsigned nx = a.n[0], nxy = (unsigned)a.n[0] * a.n[1];
   E.x = cic(a.E[0], xh, y0, z0, nx, nxy);
   E.y = cic(a.E[1], x0, yh, z0, nx, nxy);
   E.z = cic(a.E[2], x0, y0, zh, nx, nxy);

@@ -480,7 +480,9 @@ int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
     g.n[k] = c->grid.n[k];
     g.nb[k] = c->nb[k];
   }
-  g.per_block = c->key_ensembles ? 1 : c->blk_keys;
+  // photons by cell block only: most fly straight without a gather, and the
+  // finer order did not pay for its larger histogram
+  g.per_block = (c->key_ensembles || sp == kPhoton) ? 1 : c->blk_keys;
   const int nmain = c->nblk * g.per_block;
   g.nkeys = nmain;
   g.nsub_key = c->key_ensembles;
