@@ -722,7 +722,7 @@ LARGE_NAME = ("large self-consistent 3D QED cascade: 512^3 periodic Yee mesh, dx
 LARGE_START, LARGE_STEPS = 40, 20   # the timed window starts at step 40 (W warm-ups right before it)
 # The stages of a step (qed_profile_stages) and the kernels each one holds.
 STAGES = ("constants", "photons", "blocks", "deposit", "massive", "products", "schwinger", "field", "end")
-STAGE_KERNELS = {"constants": "J and count resets, k_grid_max, k_step_constants", "photons": "k_photons",
+STAGE_KERNELS = {"constants": "J and count resets, k_grid_max (first step of a call), k_step_constants", "photons": "k_photons",
                  "blocks": "k_blocks (e-/e+, then ions)", "deposit": "k_deposit_blocks", "massive": "k_pass0",
                  "products": "k_products", "schwinger": "k_schwinger", "field": "k_yee_b, k_yee_e",
                  "end": "thinning, compaction and cell-block sort"}
@@ -732,10 +732,11 @@ STAGE_KERNELS = {"constants": "J and count resets, k_grid_max, k_step_constants"
 #  deposit: the start point and the end record of each particle the cell-block
 #    pass advanced, 16 + 32 = 48 / 96 B (the current tiles are flushed once);
 #  field: the Yee update, 9 reads + 6 writes a cell, 60 / 120 B per cell-step;
-#  constants: J zeroed (3 values) and the mesh maxima (6 reads), 36 / 72 B
-#    per cell-step.
+#  constants: J zeroed (3 values), 12 / 24 B per cell-step (the mesh maxima
+#    are read off the fields at the first step of a qed_step call only; the
+#    field update forms them for the steps after it).
 STAGE_BYTES = {"photons": (68, 120), "blocks": (68, 120), "massive": (68, 120), "deposit": (48, 96),
-               "field": (60, 120), "constants": (36, 72)}
+               "field": (60, 120), "constants": (12, 24)}
 # DRAM bytes (read + write) per unit of a kernel from one ncu capture of that
 # kernel on the large-cascade recipe; the bench scales them by the units of
 # its own launches.  Remove an entry when the kernel changes until it is
@@ -761,9 +762,10 @@ def large_setup(precision: int, n: int = 512):
 
 def large_device(precision: int, K: int, W: int, dist_barrier, start: int = LARGE_START) -> dict:
     """Advance the 512^3 cascade to step max(start, W) - W untimed, take W
-    warm-up steps, then K steps each bracketed by CUDA events on the stream
-    (the mesh alone, 4.8 GB in FP32, exceeds L2), with the stages of every
-    timed step recorded by qed_profile_stages on the same stream."""
+    warm-up steps, then K steps in one qed_step call bracketed by CUDA events
+    on the stream (the mesh alone, 4.8 GB in FP32, exceeds L2), with the
+    stages of every timed step recorded by qed_profile_stages on the same
+    stream (one block of events per step of the call)."""
     import torch
     from paper_1412_6426_gb300 import qed
     from paper_1412_6426_gb300.sim import Simulation
@@ -780,25 +782,26 @@ def large_device(precision: int, K: int, W: int, dist_barrier, start: int = LARG
             sim.step(s0 - W)
         sim.step(W)
         d0 = sim.diag()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
         sev = [[torch.cuda.Event(enable_timing=True) for _ in range(qed.QED_NSTAGES)] for _ in range(K)]
         for row in sev:                       # materialise the events before the library records them
             for e_ in row:
                 e_.record(stream)
+        qed.qed_profile_stages(sim.ctx, [e_.cuda_event for row in sev for e_ in row] if K > 1
+                               else [e_.cuda_event for e_ in sev[0]])
         torch.cuda.synchronize()
         dist_barrier()
         sampler = ClockSampler(int(os.environ.get("BENCH_GPU_INDEX", torch.cuda.current_device())))
-        for k in range(K):
-            qed.qed_profile_stages(sim.ctx, [e_.cuda_event for e_ in sev[k]])
-            ev[k][0].record(stream)
-            sim.step(1)
-            ev[k][1].record(stream)
+        ev[0].record(stream)
+        sim.step(K)
+        ev[1].record(stream)
         torch.cuda.synchronize()
         clocks = sampler.stop()
         dist_barrier()
         qed.qed_profile_stages(sim.ctx, [])
         d1 = sim.diag()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = ev[0].elapsed_time(ev[1])
+    step_ms = [sev[k][0].elapsed_time(sev[k][-1]) for k in range(K)]
     stage_ms = {name: sum(sev[k][j].elapsed_time(sev[k][j + 1]) for k in range(K)) / K
                 for j, name in enumerate(STAGES)}
     psteps = d1["particle_steps"] - d0["particle_steps"]
@@ -814,7 +817,8 @@ def large_device(precision: int, K: int, W: int, dist_barrier, start: int = LARG
     # (FDTD: 9 reads + 6 writes a cell-step; J zeroed and accumulated: 3 + 3)
     algo = (BYTES_PER_STEP[precision] * psteps + BYTES_PER_APPEND[precision] * appended
             + 21 * r * ncell * K)
-    return {"particle_steps": psteps, "seconds": sum(step_ms) / 1e3, "ms_per_step": sum(step_ms) / K,
+    return {"particle_steps": psteps, "seconds": total_ms / 1e3, "ms_per_step": total_ms / K,
+            "step_ms_min_max": [min(step_ms), max(step_ms)],
             "steps": K, "warmup": W, "window": [s0, s0 + K], "appended": appended, "algo_bytes": algo,
             "clocks": clocks, "stage_ms": stage_ms, "stage_units": units,
             "stage_bytes": {k: STAGE_BYTES[k][pi] for k in STAGE_BYTES},

@@ -377,7 +377,11 @@ int qed_particles_read_static(qed_ctx *ctx, int species, double *x, double *p, d
  * (Sec. V.B) when enabled.
  *  fields: NULL unless field_mode is QED_FIELD_GRID, where the E, B arrays
  *    are read (gather), J is overwritten by the deposit and E, B are advanced
- *    by one symmetrised FDTD step after the particles (deposit_on).
+ *    by one symmetrised FDTD step after the particles (deposit_on).  The
+ *    first step of a call reads the largest |E|, |B| components off the
+ *    arrays (the bound behind the photons' early exit); later steps of the
+ *    same call take them from the field update before, so the caller
+ *    changes the arrays only between calls.
  *  Asynchronous; allocates nothing, so it may be captured in a CUDA graph.
  *  QED_ERR_STATE after a device error, QED_ERR_ARG for dt <= 0 or missing
  *  fields. */
@@ -438,7 +442,9 @@ int qed_profile_events(qed_ctx *ctx, void *start, void *photon_done, void *stop)
  * between (zero when there are none). */
 typedef enum qed_stage {
     QED_STAGE_BEGIN = 0,     /* before the step's first kernel */
-    QED_STAGE_CONSTANTS,     /* after the mesh maxima and the step constants */
+    QED_STAGE_CONSTANTS,     /* after the mesh maxima (read off the fields at the
+                                first step of a qed_step call; later steps take
+                                them from the field update) and the step constants */
     QED_STAGE_PHOTONS,       /* after the photon pass */
     QED_STAGE_BLOCKS,        /* after the cell-block pass of e-, e+, ions (mesh) */
     QED_STAGE_DEPOSIT,       /* after the cell-block current deposit (mesh) */
@@ -451,11 +457,15 @@ typedef enum qed_stage {
 } qed_stage;
 
 /* Profiling aid: record the caller's CUDA events (cudaEvent_t passed as
- * void*, created on the context's device; n of them, n <= QED_NSTAGES,
- * entry k for stage k, NULL entries skipped) at the stages of every
- * following step, on the stream of that step.  Give a fresh array before
- * each step to keep every step's times.  n == 0 stops recording.  The events
- * are not owned by the library; the array itself is copied. */
+ * void*, created on the context's device) at the stages of the following
+ * steps, on the stream of each step.  n <= QED_NSTAGES: entry k for stage
+ * k, recorded by every step (give a fresh array before each step to keep
+ * every step's times).  n = m QED_NSTAGES with m > 1: entries j QED_NSTAGES
+ * + k for stage k of step j of every following qed_step call (steps from m
+ * on record nothing), so one call of m steps keeps every step's times.
+ * NULL entries are skipped; n == 0 stops recording.  QED_ERR_ARG for any
+ * other n.  The events are not owned by the library; the array itself is
+ * copied. */
 int qed_profile_stages(qed_ctx *ctx, void *const *events, int32_t n);
 
 /* Self-test of the failure detection of the bounded device waits: the grid

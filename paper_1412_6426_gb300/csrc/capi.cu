@@ -56,6 +56,7 @@ void release(qed_ctx *c) {
   cudaFree(c->d_ens_h);
   cudaFree(c->d_std_cdf);
   cudaFree(c->d_grid_max);
+  cudaFree(c->d_grid_max_next);
   cudaFree(c->d_phot_start);
   cudaFree(c->d_std_lnw);
   if (c->side) cudaStreamDestroy(c->side);
@@ -251,6 +252,7 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (nkeys + 2 + (nkeys + 1024) / 1024 + 1));
     if (rc == QED_OK) rc = dalloc(&c->d_phot_start, sizeof(unsigned) * (nblk + 2));
     if (rc == QED_OK) rc = dalloc(&c->d_grid_max, sizeof(unsigned long long) * 6);
+    if (rc == QED_OK) rc = dalloc(&c->d_grid_max_next, sizeof(unsigned long long) * 6 * qed::kMaxStripes);
   }
   if (g->field_mode == QED_FIELD_ENSEMBLE) {
     c->ens_cap = 1 << p->ens_bits;
@@ -419,7 +421,14 @@ int qed_step(qed_ctx *c, const qed_fields *f, double dt, int32_t nsteps, void *s
   if (c->grid.field_mode == QED_FIELD_ENSEMBLE && c->n_ens < 1) return QED_ERR_ARG;
   cudaStream_t s = as_stream(stream);
   c->last_dt = dt;
+  // the caller may have changed the fields since the last call
+  c->grid_max_ready = 0;
   for (int n = 0; n < nsteps; ++n) {
+    if (!c->ev_steps.empty()) {
+      const size_t k = c->ev_steps.size() / QED_NSTAGES;
+      for (int st = 0; st < QED_NSTAGES; ++st)
+        c->ev_stage[st] = (size_t)n < k ? c->ev_steps[(size_t)n * QED_NSTAGES + st] : nullptr;
+    }
     if (grid && c->nblk > 0 && !c->sorted) {
       // records in cell-block order let electrons, positrons and ions deposit
       // through shared-memory tiles
@@ -660,7 +669,12 @@ int qed_profile_events(qed_ctx *c, void *start, void *photon_done, void *stop) {
 }
 
 int qed_profile_stages(qed_ctx *c, void *const *events, int32_t n) {
-  if (!c || n < 0 || n > QED_NSTAGES || (n > 0 && !events)) return QED_ERR_ARG;
+  if (!c || n < 0 || (n > QED_NSTAGES && n % QED_NSTAGES) || (n > 0 && !events)) return QED_ERR_ARG;
+  c->ev_steps.clear();
+  if (n > QED_NSTAGES) {
+    c->ev_steps.assign((cudaEvent_t *)events, (cudaEvent_t *)events + n);
+    n = 0;   // set per step by qed_step
+  }
   for (int k = 0; k < QED_NSTAGES; ++k) c->ev_stage[k] = k < n ? (cudaEvent_t)events[k] : nullptr;
   return QED_OK;
 }

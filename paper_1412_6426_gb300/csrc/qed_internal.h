@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/qed.h"
@@ -26,6 +28,7 @@ constexpr int kMaxBins = 4096;
 constexpr int kCompactTile = 2048;   // particles per tile of the compaction
 constexpr int kBlockCells = 8;       // cell block edge (grid mode): 8 x 8 x 8 cells
 constexpr int kBlockVolume = kBlockCells * kBlockCells * kBlockCells;
+constexpr int kMaxStripes = 64;      // field update: stripes of the next step's mesh maxima
 constexpr int kBlockChunk = 1024;    // records per work item of the cell-block kernel
 // Current tile of a cell block (the deposit): the block plus a halo of H
 // cells each side, kBlockCells + 2H + 1 nodes per axis.  The stencil of a
@@ -165,6 +168,8 @@ struct qed_ctx {
   int ext = 0;                        // ensembles or generator factors: EXT kernels
   void *d_thin = nullptr;             // thinning: per group count, weight, survivors' weight
   unsigned long long *d_grid_max = nullptr;   // Yee mesh: |E|, |B| component maxima per step
+  unsigned long long *d_grid_max_next = nullptr;  // [kMaxStripes][6]: the same, of the fields the last update wrote
+  int grid_max_ready = 0;             // d_grid_max_next holds the maxima of the current fields
   void *d_std_cdf = nullptr;          // standard generator: kStdRows x kStdCols cumulative W
   void *d_std_lnw = nullptr;          // and ln W(1) per row (context precision)
   int thin_groups = 0;
@@ -196,6 +201,7 @@ struct qed_ctx {
   cudaEvent_t ev_photon = nullptr;
   cudaEvent_t ev_stop = nullptr;
   cudaEvent_t ev_stage[QED_NSTAGES] = {};   // qed_profile_stages: recorded at each stage
+  std::vector<cudaEvent_t> ev_steps;  // qed_profile_stages with one block of events per step of a call
   cudaStream_t side = nullptr;        // the e-/e+/ion pass when it runs beside the photon pass
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int64_t launches = 0;               // kernels launched by this context
@@ -228,6 +234,9 @@ inline void qed_mark(qed_ctx *c, int stage, cudaStream_t s) {
 int qed_build_tables(qed_ctx *c, cudaStream_t s);
 int qed_launch_step(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s);
 int qed_launch_yee(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s);
+namespace qed {
+int fold_grid_max(qed_ctx *c, cudaStream_t s);   // d_grid_max_next's stripes -> d_grid_max
+}
 int qed_launch_set(qed_ctx *c, int sp, const double *x, const double *p, const double *w,
                    const uint64_t *id, int64_t n, cudaStream_t s);
 int qed_launch_get(qed_ctx *c, int sp, double *x, double *p, double *w, uint64_t *id, int64_t n,

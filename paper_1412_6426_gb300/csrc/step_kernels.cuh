@@ -2120,14 +2120,19 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     for (int k = 0; k < 3; ++k)
       if (cudaMemsetAsync(a.J[k], 0, nc * sizeof(R), s) != cudaSuccess) return QED_ERR_CUDA;
   }
+  // the mesh maxima: from the field update of the step before, within one
+  // qed_step call, else read off the fields
+  const bool have_max = a.field_mode == kFieldGrid && c->grid_max_ready;
+  c->grid_max_ready = 0;
+  if (have_max && fold_grid_max(c, s) != QED_OK) return QED_ERR_CUDA;
   a.grid_max = a.field_mode == kFieldGrid ? c->d_grid_max : nullptr;
   a.eps_star_out = a.field_mode == kFieldGrid ? c->d_eps_star : nullptr;
-  if (a.grid_max && cudaMemsetAsync(c->d_grid_max, 0, sizeof(unsigned long long) * 6, s) != cudaSuccess)
+  if (a.grid_max && !have_max && cudaMemsetAsync(c->d_grid_max, 0, sizeof(unsigned long long) * 6, s) != cudaSuccess)
     return QED_ERR_CUDA;
   void *args[] = {(void *)&a};
   cudaError_t e = cudaSuccess;
   if (c->ev_start) cudaEventRecord(c->ev_start, s);
-  if (a.grid_max) {
+  if (a.grid_max && !have_max) {
     c->launches += 1;
     e = cudaLaunchKernel((const void *)k_grid_max<R>, dim3(c->num_sms * 4), dim3(256), args, 0, s);
   }

@@ -207,7 +207,9 @@ def qed_profile_events(ctx: int, start_event: int, photon_event: int, stop_event
 
 
 def qed_profile_stages(ctx: int, events) -> None:
-    """events: raw cudaEvent_t handles (ints or 0), entry k for stage k; [] stops recording."""
+    """events: raw cudaEvent_t handles (ints or 0), entry k for stage k, or
+    m blocks of QED_NSTAGES for steps 0..m-1 of each following call; []
+    stops recording."""
     arr = (ctypes.c_void_p * max(len(events), 1))(*[ctypes.c_void_p(e or None) for e in events])
     _check("qed_profile_stages", load().qed_profile_stages(ctypes.c_void_p(ctx), arr, len(events)))
 
