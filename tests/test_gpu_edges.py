@@ -214,3 +214,43 @@ def test_bounded_barrier_gives_up():
         sim.step(2)
         d = sim.diag()
         assert d["status"] == 0 and d["emissions"] > 0
+
+
+def test_stage_events_per_step_of_a_call():
+    # One block of stage events per step of a qed_step call: the first two
+    # steps of a three-step call record theirs, in order on the stream, the
+    # third records none; a count that is not a multiple of the stages (above
+    # one block) is refused.  On the mesh the later steps of the call take
+    # the field maxima from the field update before them.
+    import torch
+    from tests.test_gpu_grid import grid_case
+    from paper_1412_6426_gb300.sim import Simulation
+    w, f = grid_case(seed=21, npart=300)
+    n = qed.QED_NSTAGES
+    with Simulation(w, precision=32, capacity=(4000, 4000, 8000, 400), deposit_on=1) as sim:
+        dt_ = torch.float32
+        E = [torch.tensor(a, dtype=dt_, device="cuda") for a in f[:3]]
+        B = [torch.tensor(a, dtype=dt_, device="cuda") for a in f[3:]]
+        J = [torch.zeros(len(f[0]), dtype=dt_, device="cuda") for _ in range(3)]
+        sim.set_grid_fields(E, B, J)
+        sim.set_all()
+        stream = sim.stream
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * n)]
+        for e_ in ev:
+            e_.record(stream)
+        torch.cuda.synchronize()
+        with pytest.raises(qed.QedError) as e:
+            qed.qed_profile_stages(sim.ctx, [x.cuda_event for x in ev[: n + 1]])
+        assert e.value.status == qed.QED_ERR_ARG
+        mark = torch.cuda.Event(enable_timing=True)
+        mark.record(stream)
+        qed.qed_profile_stages(sim.ctx, [x.cuda_event for x in ev[: 2 * n]])
+        sim.step(3)
+        qed.qed_profile_stages(sim.ctx, [])
+        torch.cuda.synchronize()
+        # steps 0 and 1 recorded after the mark, in order; the third block untouched (before the mark)
+        seq = [mark] + ev[: 2 * n]
+        for a_, b_ in zip(seq, seq[1:]):
+            assert a_.elapsed_time(b_) >= 0.0
+        assert mark.elapsed_time(ev[2 * n]) < 0.0
+        assert sim.diag()["status"] == 0
