@@ -192,6 +192,30 @@ __device__ __forceinline__ R heff_lepton(V3<R> p, R gamma, V3<R> E, V3<R> B) {
   return s > R(0) ? sqrt_r(s) : R(0);
 }
 
+// FP32 forms of chi, H_eff and the sub-interval count, with the hardware
+// reciprocal square root, fast division and base-2 logarithm/exponential (a
+// few ulp; the FP32 path is held to statistics and to 1e-5 between events):
+// they decide sub-interval counts and probabilities, not the push itself.
+// FP64 keeps the correctly rounded forms above.
+__device__ __forceinline__ float sqrt_fast(float s) { return s > 0.f ? s * rsqrtf(s) : 0.f; }
+template <>
+__device__ __forceinline__ float chi_lepton<float>(V3<float> p, float gamma, V3<float> E, V3<float> B) {
+  V3<float> c = cross(p, B);
+  float ax = gamma * E.x + c.x, ay = gamma * E.y + c.y, az = gamma * E.z + c.z;
+  float pe = dot(p, E);
+  return sqrt_fast(ax * ax + ay * ay + az * az - pe * pe);
+}
+template <>
+__device__ __forceinline__ float heff_lepton<float>(V3<float> p, float gamma, V3<float> E, V3<float> B) {
+  const float ig = __fdividef(1.f, gamma);
+  V3<float> v = {p.x * ig, p.y * ig, p.z * ig};
+  V3<float> c = cross(v, B);
+  float ax = E.x + c.x, ay = E.y + c.y, az = E.z + c.z;
+  const float pp = dot(p, p);
+  float pe = pp > 0.f ? dot(p, E) * rsqrtf(pp) : 0.f;
+  return sqrt_fast(ax * ax + ay * ay + az * az - pe * pe);
+}
+
 // H^gamma_eff of Eq. (32) for unit direction n.
 template <typename R>
 __device__ __forceinline__ R heff_photon(V3<R> n, V3<R> E, V3<R> B) {
@@ -218,6 +242,23 @@ __device__ __forceinline__ int nsub_lepton(R t_span, R gamma, R heff, R kappa, i
   if (!(ratio > R(1))) return 1;
   R n = ceil_r(ratio);
   if (n > R(nmax)) { capped = 1; return nmax; }
+  return (int)n;
+}
+
+// FP32: (gamma / H^2)^(1/3) from one base-2 logarithm pair and exponential.
+template <>
+__device__ __forceinline__ int nsub_lepton<float>(float t_span, float gamma, float heff, float kappa, int nmax,
+                                                  int &capped) {
+  capped = 0;
+  if (!(heff > 0.f)) return 1;
+  const float ih = __fdividef(1.f, heff);
+  const float a = 0.67f * exp2f((__log2f(gamma) - 2.f * __log2f(heff)) * (1.f / 3.f));
+  const float b = 2.f * ih;
+  const float dtq = kappa * 137.f * (a < b ? a : b);
+  const float ratio = __fdividef(t_span, dtq);
+  if (!(ratio > 1.f)) return 1;
+  const float n = ceilf(ratio);
+  if (n > (float)nmax) { capped = 1; return nmax; }
   return (int)n;
 }
 

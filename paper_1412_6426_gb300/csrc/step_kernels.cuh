@@ -802,7 +802,13 @@ __device__ __forceinline__ int massive_begin(const StepArgs<R> &a, int sp, Pt<R>
   if (qed && idp) q.id = __ldg(idp);
   int n = 1, capped = 0;
   if (qed) {
-    R g0 = sqrt_r(R(1) + dot(q.p, q.p) / (m * m));
+    R g0;
+    if constexpr (sizeof(R) == 4) {
+      R igm;
+      lorentz(q.p, a.inv_mass[sp], a.inv_mass[sp] * a.inv_mass[sp], g0, igm);
+    } else {
+      g0 = sqrt_r(R(1) + dot(q.p, q.p) / (m * m));
+    }
     n = nsub_lepton(t_span, g0, heff_lepton(q.p, g0, E, B), a.kappa, a.nsub_max, capped);
     count_rare(a, kCntCapped, (unsigned)capped);
   }
