@@ -216,6 +216,18 @@ __device__ __forceinline__ float heff_lepton<float>(V3<float> p, float gamma, V3
   return sqrt_fast(ax * ax + ay * ay + az * az - pe * pe);
 }
 
+// A photon's energy |p| and 1/|p| (0 for p = 0).  FP32: one reciprocal
+// square root; FP64: correctly rounded square root and division.
+__device__ __forceinline__ void photon_norm(const V3<float> &p, float &eps, float &ie) {
+  const float pp = dot(p, p);
+  ie = pp > 0.f ? rsqrtf(pp) : 0.f;
+  eps = pp * ie;
+}
+__device__ __forceinline__ void photon_norm(const V3<double> &p, double &eps, double &ie) {
+  eps = sqrt(dot(p, p));
+  ie = eps > 0.0 ? 1.0 / eps : 0.0;
+}
+
 // H^gamma_eff of Eq. (32) for unit direction n.
 template <typename R>
 __device__ __forceinline__ R heff_photon(V3<R> n, V3<R> E, V3<R> B) {
@@ -243,6 +255,14 @@ __device__ __forceinline__ int nsub_lepton(R t_span, R gamma, R heff, R kappa, i
   R n = ceil_r(ratio);
   if (n > R(nmax)) { capped = 1; return nmax; }
   return (int)n;
+}
+
+template <>
+__device__ __forceinline__ float heff_photon<float>(V3<float> n, V3<float> E, V3<float> B) {
+  V3<float> c = cross(n, B);
+  float ax = E.x + c.x, ay = E.y + c.y, az = E.z + c.z;
+  float ne = dot(n, E);
+  return sqrt_fast(ax * ax + ay * ay + az * az - ne * ne);
 }
 
 // FP32: (gamma / H^2)^(1/3) from one base-2 logarithm pair and exponential.

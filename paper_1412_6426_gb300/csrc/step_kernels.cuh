@@ -929,12 +929,9 @@ __device__ __forceinline__ void advance_massive(const StepArgs<R> &a, int pass, 
 template <typename R, bool EXT>
 __device__ __forceinline__ bool advance_photon(const StepArgs<R> &a, int pass, Pt<R> &q, R t_span, V3<R> E,
                                                V3<R> B, Cnt &cnt, const uint64_t *idp, R chi_star, unsigned step) {
-  const R eps = sqrt_r(dot(q.p, q.p));
-  V3<R> dir = {R(0), R(0), R(0)};
-  if (eps > R(0)) {
-    const R ie = R(1) / eps;
-    dir = {q.p.x * ie, q.p.y * ie, q.p.z * ie};
-  }
+  R eps, ie;
+  photon_norm(q.p, eps, ie);
+  const V3<R> dir = {q.p.x * ie, q.p.y * ie, q.p.z * ie};
   const R hg = heff_photon(dir, E, B);
   const R chig = eps * hg;
   int n = 1, capped = 0;
@@ -1496,7 +1493,8 @@ __global__ void __launch_bounds__(kPhotonThreads, PhotonOcc<R>::blocks) k_photon
     q.ci[1] = (int)row - (int)slab * a.n[1];
     q.ci[2] = (int)slab;
     bool alive = true;
-    const R eps = sqrt_r(dot(q.p, q.p));
+    R eps, ie;
+    photon_norm(q.p, eps, ie);
     R hmax = sizeof(R) == 4 ? (R)kc.hmax_f : (R)kc.hmax;
     bool one = kc.one_interval;
     if (EXT && a.field_mode == kFieldEnsemble) {
@@ -1514,12 +1512,7 @@ __global__ void __launch_bounds__(kPhotonThreads, PhotonOcc<R>::blocks) k_photon
         count_rare(a, kCntNonfinite, 1u);
         atomicOr(a.status, kStNonfinite);
       }
-      V3<R> dir = {R(0), R(0), R(0)};
-      if (eps > R(0)) {
-        const R ie = R(1) / eps;
-        dir = {q.p.x * ie, q.p.y * ie, q.p.z * ie};
-      }
-      move(a, q, dir, a.dt);
+      move(a, q, V3<R>{q.p.x * ie, q.p.y * ie, q.p.z * ie}, a.dt);
       if (a.pairs_on) cnt.sub_g++;
     } else {
       V3<R> E, B;
