@@ -56,6 +56,7 @@ void release(qed_ctx *c) {
   cudaFree(c->d_ens_h);
   cudaFree(c->d_std_cdf);
   cudaFree(c->d_grid_max);
+  cudaFree(c->d_drift);
   cudaFree(c->d_grid_max_next);
   cudaFree(c->d_phot_start);
   cudaFree(c->d_std_lnw);
@@ -252,6 +253,13 @@ int qed_init(qed_ctx **out, const qed_grid_desc *g, const qed_species_desc *sp, 
     if (rc == QED_OK) rc = dalloc(&c->d_blk_cursor, sizeof(unsigned) * (nkeys + 2 + (nkeys + 1024) / 1024 + 1));
     if (rc == QED_OK) rc = dalloc(&c->d_phot_start, sizeof(unsigned) * (nblk + 2));
     if (rc == QED_OK) rc = dalloc(&c->d_grid_max, sizeof(unsigned long long) * 6);
+    if (c->par.deposit_on) {
+      // the records that drift out of their block's current tile between
+      // sorts: an eighth of the charged stores' capacity (more deposit directly)
+      const long long charged = (long long)c->st[QED_ELECTRON].cap + c->st[QED_POSITRON].cap + c->st[QED_ION].cap;
+      c->drift_cap = charged / 8 > (1ll << 20) ? charged / 8 : (1ll << 20);
+      if (rc == QED_OK) rc = dalloc(&c->d_drift, sizeof(unsigned long long) * c->drift_cap);
+    }
     if (rc == QED_OK) rc = dalloc(&c->d_grid_max_next, sizeof(unsigned long long) * 6 * qed::kMaxStripes);
   }
   if (g->field_mode == QED_FIELD_ENSEMBLE) {

@@ -122,7 +122,10 @@ template <typename R> struct StepArgs {
   int nblk;
   const unsigned *blk_start[4];
   unsigned *work;          // work-stealing counters of the cell-block kernels (zeroed per step):
-                           // [0] e-/e+ items, [1] deposit, [4] ion items ([2..3]: kWorkSlot)
+                           // [0] e-/e+ items, [1] deposit, [4] ion items, [5] drifted records
+                           // ([2..3]: kWorkSlot)
+  unsigned long long *drift;   // records whose stencil left their block's tile: species << 62 | index
+  long long drift_cap;
   void *step_const;        // per-step field constants (written by k_step_constants)
   void *clock;             // device clock {t, step}: read and advanced once per step
   double dt_d;             // the step in FP64 (advances the clock)
@@ -168,6 +171,8 @@ struct qed_ctx {
   int ext = 0;                        // ensembles or generator factors: EXT kernels
   void *d_thin = nullptr;             // thinning: per group count, weight, survivors' weight
   unsigned long long *d_grid_max = nullptr;   // Yee mesh: |E|, |B| component maxima per step
+  unsigned long long *d_drift = nullptr;      // deposit: the records that left their block's tile
+  long long drift_cap = 0;
   unsigned long long *d_grid_max_next = nullptr;  // [kMaxStripes][6]: the same, of the fields the last update wrote
   int grid_max_ready = 0;             // d_grid_max_next holds the maxima of the current fields
   void *d_std_cdf = nullptr;          // standard generator: kStdRows x kStdCols cumulative W

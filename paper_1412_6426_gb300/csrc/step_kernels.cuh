@@ -1917,6 +1917,16 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
         }
         if (!live) continue;
         if (!inside) {
+          // drifted out of the tile since the sort: listed, and deposited
+          // after this kernel by full warps (k_deposit_drift); a sparse
+          // block without a tile deposits its records here
+          if (tile && a.drift) {
+            const unsigned slot = atomicAdd(a.work + 5, 1u);
+            if ((long long)slot < a.drift_cap) {
+              a.drift[slot] = ((unsigned long long)sp << 62) | (unsigned long long)i;
+              continue;
+            }
+          }
           deposit(a, cs, os, q1, qw);
           continue;
         }
@@ -1950,6 +1960,36 @@ __global__ void __launch_bounds__(256, DepositOcc<R>::blocks) k_deposit_blocks(c
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(a.counters + kCntTileDeposits, v);
+}
+
+// The listed records that drifted out of their block's tile: the
+// Esirkepov current of each straight into J, by full warps.
+template <typename R>
+__global__ void __launch_bounds__(256) k_deposit_drift(const StepArgs<R> a) {
+  const long long n = min((long long)a.work[5], a.drift_cap);
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long d = a.drift[k];
+    const int sp = (int)(d >> 62);
+    const long long i = (long long)(d & ((1ull << 62) - 1));
+    Pt<R> q1;
+    R os[3];
+    int c0, c1;
+    load_start(a, sp, i, os, c0);
+    load(a, sp, i, q1, c1);
+    int cs[3], ce[3];
+    decode_cell(a, c0, cs);
+    decode_cell(a, c1, ce);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      int dc = ce[c] - cs[c];
+      const R disp = R(dc) + q1.off[c] - os[c];
+      if (disp >= R(1)) dc -= a.n[c];
+      else if (disp <= R(-1)) dc += a.n[c];
+      q1.ci[c] = cs[c] + dc;
+    }
+    deposit(a, cs, os, q1, a.charge[sp] * q1.w);
+  }
 }
 
 // Dynamic shared memory of the deposit kernel for a tile halo.
@@ -2096,6 +2136,8 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
     a.blk_start[sp] = (c->sorted && c->nblk > 0 && !c->key_ensembles && sp != kPhoton && c->st[sp].cap > 0)
                           ? c->d_blk_start + (size_t)sp * (c->nblk + 1) : nullptr;
   a.work = (unsigned *)(c->d_pend_count + kMaxPass + 2);
+  a.drift = c->d_drift;
+  a.drift_cap = c->drift_cap;
   a.step_const = c->d_step_const;
   a.counters = c->d_counters;
   a.spectrum = c->d_spec;
@@ -2176,6 +2218,10 @@ int launch(qed_ctx *c, const qed_fields *f, double dt, cudaStream_t s) {
       const long long per = (long long)c->nblk / (8ll * per_sm * c->num_sms);
       a.deposit_grab = (int)(per < 1 ? 1 : (per > 32 ? 32 : per));
       e = cudaLaunchKernel(kern, dim3(per_sm * c->num_sms), dim3(256), args, deposit_smem<R>(a.deposit_halo), s);
+      if (e == cudaSuccess && a.drift) {
+        c->launches += 1;
+        e = cudaLaunchKernel((const void *)k_deposit_drift<R>, dim3(c->num_sms * 4), dim3(256), args, 0, s);
+      }
     }
   } else {
     qed_mark(c, QED_STAGE_BLOCKS, s);
