@@ -372,23 +372,24 @@ __device__ __forceinline__ Axis<R> cic_axis(int ci, R off, bool half, int n) {
 }
 
 // Node indices in 32 bits (the mesh holds fewer than 2^31 cells): one
-// multiply-add forms each load's address.
+// multiply-add forms each load's address.  The trilinear weights are
+// applied as nested linear interpolations (four along x, two along y, one
+// along z: a + f (b - a) each), 14 operations instead of the 8 weight
+// products and 8 multiply-adds.
 template <typename R>
 __device__ __forceinline__ R cic(const R *__restrict__ f, const Axis<R> &x, const Axis<R> &y, const Axis<R> &z,
                                  unsigned nx, unsigned nxy) {
-  const R fr[3] = {x.fr, y.fr, z.fr};
   const unsigned r00 = z.i0 * nxy + y.i0 * nx, r01 = z.i0 * nxy + y.i1 * nx;
   const unsigned r10 = z.i1 * nxy + y.i0 * nx, r11 = z.i1 * nxy + y.i1 * nx;
-  R acc = R(0);
-  acc += (R(1) - fr[0]) * (R(1) - fr[1]) * (R(1) - fr[2]) * __ldg(f + (r00 + (unsigned)x.i0));
-  acc += fr[0] * (R(1) - fr[1]) * (R(1) - fr[2]) * __ldg(f + (r00 + (unsigned)x.i1));
-  acc += (R(1) - fr[0]) * fr[1] * (R(1) - fr[2]) * __ldg(f + (r01 + (unsigned)x.i0));
-  acc += fr[0] * fr[1] * (R(1) - fr[2]) * __ldg(f + (r01 + (unsigned)x.i1));
-  acc += (R(1) - fr[0]) * (R(1) - fr[1]) * fr[2] * __ldg(f + (r10 + (unsigned)x.i0));
-  acc += fr[0] * (R(1) - fr[1]) * fr[2] * __ldg(f + (r10 + (unsigned)x.i1));
-  acc += (R(1) - fr[0]) * fr[1] * fr[2] * __ldg(f + (r11 + (unsigned)x.i0));
-  acc += fr[0] * fr[1] * fr[2] * __ldg(f + (r11 + (unsigned)x.i1));
-  return acc;
+  const unsigned x0 = (unsigned)x.i0, x1 = (unsigned)x.i1;
+  const R f000 = __ldg(f + (r00 + x0)), f100 = __ldg(f + (r00 + x1));
+  const R f010 = __ldg(f + (r01 + x0)), f110 = __ldg(f + (r01 + x1));
+  const R f001 = __ldg(f + (r10 + x0)), f101 = __ldg(f + (r10 + x1));
+  const R f011 = __ldg(f + (r11 + x0)), f111 = __ldg(f + (r11 + x1));
+  const R a0 = fma_r(x.fr, f100 - f000, f000), a1 = fma_r(x.fr, f110 - f010, f010);
+  const R a2 = fma_r(x.fr, f101 - f001, f001), a3 = fma_r(x.fr, f111 - f011, f011);
+  const R b0 = fma_r(y.fr, a1 - a0, a0), b1 = fma_r(y.fr, a3 - a2, a2);
+  return fma_r(z.fr, b1 - b0, b0);
 }
 
 // CIC gather of the six staggered components (Yee positions in qed.h); the
