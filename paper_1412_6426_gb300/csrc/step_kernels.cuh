@@ -365,7 +365,8 @@ template <typename R> struct Axis {
 
 template <typename R>
 __device__ __forceinline__ Axis<R> cic_axis(int ci, R off, bool half, int n) {
-  R v = half ? off - R(0.5) : off;
+  if (!half) return {ci, ci + 1 == n ? 0 : ci + 1, off};   // off in [0, 1): nodes ci, ci + 1
+  R v = off - R(0.5);
   int b = ci;
   if (v < R(0)) { v += R(1); b -= 1; }
   return {wrap_fast(b, n), wrap_fast(b + 1, n), v};

@@ -379,8 +379,22 @@ __device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned *w
   return excl;
 }
 
-__global__ void k_blk_sums(const unsigned *hist, int n, unsigned *part) {
+// A species with no records skips the histogram's zeroing and scan (its
+// starts are all zero): the histogram then holds another species' cursors.
+__global__ void k_zero_hist(unsigned *hist, long long n, const long long *count, int sp) {
+  if (count[sp] <= 0) return;
+  const long long nv = n / 4, stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride)
+    ((uint4 *)hist)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (long long i = 4 * nv + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) hist[i] = 0u;
+}
+
+__global__ void k_blk_sums(const unsigned *hist, int n, unsigned *part, const long long *count, int sp) {
   __shared__ unsigned wt[32];
+  if (count[sp] <= 0) {
+    if (threadIdx.x == 0) part[blockIdx.x] = 0u;
+    return;
+  }
   unsigned v[kScanRun], sum = 0;
   load_run(hist, (long long)blockIdx.x * kScanPart + (long long)threadIdx.x * kScanRun, n, v);
 #pragma unroll
@@ -415,9 +429,19 @@ __global__ void k_blk_scan_parts(unsigned *part, int nparts, unsigned *start, in
 // (the first key of the block; keys past nblk x per_block each start an
 // entry of their own).
 __global__ void k_blk_scan_out(unsigned *hist, int n, const unsigned *part, unsigned *start, int per_block,
-                               int nmain, int nblk) {
+                               int nmain, int nblk, const long long *count, int sp) {
   __shared__ unsigned wt[32];
   const long long first = (long long)blockIdx.x * kScanPart + (long long)threadIdx.x * kScanRun;
+  if (count[sp] <= 0) {
+    for (int q = 0; q < kScanRun; ++q) {
+      const long long i = first + q;
+      if (i < n) {
+        if (i >= nmain) start[nblk + (i - nmain)] = 0u;
+        else if (i % per_block == 0) start[i / per_block] = 0u;
+      }
+    }
+    return;
+  }
   unsigned v[kScanRun], sum = 0;
   load_run(hist, first, n, v);
 #pragma unroll
@@ -497,9 +521,9 @@ int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
   if (g.photon_split) g.nkeys = nmain + 1;
   const int cur = st.cur, nxt = cur ^ 1;
   unsigned *start = g.photon_split ? c->d_phot_start : c->d_blk_start + (size_t)sp * (c->nblk + 1);
-  if (cudaMemsetAsync(c->d_blk_cursor, 0, sizeof(unsigned) * (g.nkeys + 1), s) != cudaSuccess) return QED_ERR_CUDA;
+  k_zero_hist<<<c->num_sms * 4, 256, 0, s>>>(c->d_blk_cursor, (long long)g.nkeys + 1, c->d_count, sp);
   const int grid = c->num_sms * 8;
-  c->launches += 3;
+  c->launches += 4;
   k_blk_hist<T><<<grid, 256, 0, s>>>((const T *)st.mom[cur], st.id[cur], c->d_count, sp, (long long)st.cap, g,
                                      c->d_blk_cursor);
   // the record count to scatter is read on the device: the histogram keeps it
@@ -508,9 +532,10 @@ int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
   unsigned *part = c->d_blk_cursor + (g.nkeys + 2);
   const int nstart = c->nblk + (g.nkeys - nmain);
   c->launches += 2;
-  k_blk_sums<<<nparts, kScanBlock, 0, s>>>(c->d_blk_cursor, g.nkeys, part);
+  k_blk_sums<<<nparts, kScanBlock, 0, s>>>(c->d_blk_cursor, g.nkeys, part, c->d_count, sp);
   k_blk_scan_parts<<<1, kScanBlock, 0, s>>>(part, nparts, start, nstart, c->d_count + 4, sp);
-  k_blk_scan_out<<<nparts, kScanBlock, 0, s>>>(c->d_blk_cursor, g.nkeys, part, start, g.per_block, nmain, c->nblk);
+  k_blk_scan_out<<<nparts, kScanBlock, 0, s>>>(c->d_blk_cursor, g.nkeys, part, start, g.per_block, nmain, c->nblk,
+                                              c->d_count, sp);
   k_blk_scatter<T><<<grid, 256, 0, s>>>((const T *)st.pos[cur], (const T *)st.mom[cur], st.id[cur],
                                         (T *)st.pos[nxt], (T *)st.mom[nxt], st.id[nxt], c->d_count, sp,
                                         (long long)st.cap, g, c->d_blk_cursor);
