@@ -28,6 +28,15 @@ constexpr int kMaxBins = 4096;
 constexpr int kCompactTile = 2048;   // particles per tile of the compaction
 constexpr int kBlockCells = 8;       // cell block edge (grid mode): 8 x 8 x 8 cells
 constexpr int kBlockVolume = kBlockCells * kBlockCells * kBlockCells;
+
+// n / d for n < 2^31 by a multiply-high and a shift (Granlund-Montgomery):
+// fast_div_magic forms (m, l) for d on the host.
+__device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m, int l) { return (__umulhi(n, m) + n) >> l; }
+inline void fast_div_magic(unsigned d, unsigned &m, int &l) {
+  l = 0;
+  while ((1ull << l) < d) ++l;
+  m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+}
 constexpr int kMaxStripes = 64;      // field update: stripes of the next step's mesh maxima
 constexpr int kBlockChunk = 1024;    // records per work item of the cell-block kernel
 // Current tile of a cell block (the deposit): the block plus a halo of H

@@ -1047,10 +1047,6 @@ __device__ __forceinline__ void flush(const Cnt &c, unsigned long long *g) {
   }
 }
 
-__device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m, int l) {
-  return (__umulhi(n, m) + n) >> l;   // exact for n < 2^31 (Granlund-Montgomery)
-}
-
 // ----- the start points of the cell-block pass (second store buffer) -------
 // The start point of a record advanced by the cell-block pass (offsets and
 // cell: all the deposit needs of it), kept in the store's second buffer.
@@ -2043,12 +2039,6 @@ __global__ void __launch_bounds__(256, 2) k_products(const StepArgs<R> a) {
     }
   }
   flush(cnt, a.counters);
-}
-
-void fast_div_magic(unsigned d, unsigned &m, int &l) {
-  l = 0;
-  while ((1ull << l) < d) ++l;
-  m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
 }
 
 template <typename R, bool EXT>

@@ -249,6 +249,8 @@ __global__ void k_count_live(const T *mom, const long long *count, int sp, long 
 // key share one atomic.
 struct BlockGeom {
   int n[3], nb[3];
+  unsigned div_m[2];       // cell / n0 and cell / (n0 n1) by multiply-shift
+  int div_l[2];
   int nkeys;
   int per_block;           // keys per cell block: 1, or one per cell (kBlockVolume)
   int nsub_key;            // 1: key = estimated sub-intervals (ensembles)
@@ -267,7 +269,9 @@ struct BlockGeom {
 // the block (x fastest), so that the records of a block are in cell order
 // and a warp's 32 consecutive records sit in a few neighbouring cells.
 __device__ __forceinline__ int block_of(int cell, const BlockGeom &g) {
-  const int i = cell % g.n[0], j = (cell / g.n[0]) % g.n[1], k = cell / (g.n[0] * g.n[1]);
+  const unsigned row = fast_div((unsigned)cell, g.div_m[0], g.div_l[0]);
+  const unsigned slab = fast_div((unsigned)cell, g.div_m[1], g.div_l[1]);
+  const int i = cell - (int)row * g.n[0], j = (int)row - (int)slab * g.n[1], k = (int)slab;
   const int b = (i / kBlockCells) + g.nb[0] * ((j / kBlockCells) + g.nb[1] * (k / kBlockCells));
   if (g.per_block == 1) return b;
   return b * kBlockVolume + (i % kBlockCells) + kBlockCells * ((j % kBlockCells) + kBlockCells * (k % kBlockCells));
@@ -504,6 +508,8 @@ int sort_blocks(qed_ctx *c, int sp, cudaStream_t s) {
     g.n[k] = c->grid.n[k];
     g.nb[k] = c->nb[k];
   }
+  fast_div_magic((unsigned)g.n[0], g.div_m[0], g.div_l[0]);
+  fast_div_magic((unsigned)(g.n[0] * g.n[1]), g.div_m[1], g.div_l[1]);
   // photons by cell block only: most fly straight without a gather, and the
   // finer order did not pay for its larger histogram
   g.per_block = (c->key_ensembles || sp == kPhoton) ? 1 : c->blk_keys;
