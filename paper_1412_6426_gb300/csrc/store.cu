@@ -301,6 +301,28 @@ __device__ __forceinline__ int key_of(int cell, uint64_t id, const T &m, const B
   return block_of(cell, g);
 }
 
+// Two of block_atomic_add at once: both atomics are issued before either
+// result is read.
+__device__ __forceinline__ void block_atomic_add2(unsigned *ctr, const int *key, const bool *on, unsigned *out) {
+  const int lane = threadIdx.x & 31;
+  unsigned peers[2] = {0u, 0u}, base[2] = {0u, 0u};
+  int leader[2] = {0, 0};
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const unsigned mask = __ballot_sync(0xffffffffu, on[r]);
+    if (on[r]) {
+      peers[r] = __match_any_sync(mask, key[r]);
+      leader[r] = __ffs(peers[r]) - 1;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+    if (on[r] && lane == leader[r]) base[r] = atomicAdd(ctr + key[r], (unsigned)__popc(peers[r]));
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+    if (on[r]) out[r] = __shfl_sync(peers[r], base[r], leader[r]) + __popc(peers[r] & ((1u << lane) - 1u));
+}
+
 __device__ __forceinline__ unsigned block_atomic_add(unsigned *ctr, int key, bool on) {
   const unsigned mask = __ballot_sync(0xffffffffu, on);
   if (!on) return 0;
@@ -312,23 +334,31 @@ __device__ __forceinline__ unsigned block_atomic_add(unsigned *ctr, int key, boo
   return base + __popc(peers & ((1u << lane) - 1u));
 }
 
+// Two records per thread and iteration (i and i + stride), their loads and
+// atomics issued together, so that their latencies overlap.
 template <typename T>
 __global__ void k_blk_hist(const T *mom, const uint64_t *id, const long long *count, int sp, long long cap,
                            BlockGeom g, unsigned *hist) {
   const long long n = min(count[sp], cap);
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const long long i = base + threadIdx.x;
-    int cell = -1;
-    uint64_t pid = 0;
-    T M;
-    if (i < n) {
-      M = mom[i];
-      cell = cell_of(M);
-      if (g.nsub_key) pid = id[i];
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += 2 * stride) {
+    int cell[2] = {-1, -1};
+    uint64_t pid[2] = {0, 0};
+    T M[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const long long i = base + r * stride + threadIdx.x;
+      if (i < n) {
+        M[r] = mom[i];
+        cell[r] = cell_of(M[r]);
+        if (g.nsub_key) pid[r] = id[i];
+      }
     }
-    const bool live = cell >= 0;
-    block_atomic_add(hist, live ? key_of(cell, pid, M, g) : 0, live);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const bool live = cell[r] >= 0;
+      block_atomic_add(hist, live ? key_of(cell[r], pid[r], M[r], g) : 0, live);
+    }
   }
 }
 
@@ -479,22 +509,37 @@ __global__ void k_blk_scatter(const T *pos, const T *mom, const uint64_t *id, T 
                               const long long *count, int sp, long long cap, BlockGeom g, unsigned *cursor) {
   const long long n = min(count[sp], cap);   // records before the sort (the total goes elsewhere)
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const long long i = base + threadIdx.x;
-    int cell = -1;
-    T M;
-    if (i < n) {
-      M = mom[i];
-      cell = cell_of(M);
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += 2 * stride) {
+    // two records per thread (i and i + stride): all their loads first,
+    // then both cursor atomics, then the stores
+    int cell[2] = {-1, -1}, key[2] = {0, 0};
+    bool live[2];
+    T M[2], P[2];
+    uint64_t pid[2] = {0, 0};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const long long i = base + r * stride + threadIdx.x;
+      if (i < n) {
+        M[r] = mom[i];
+        P[r] = pos[i];
+        pid[r] = id[i];
+        cell[r] = cell_of(M[r]);
+      }
     }
-    const bool live = cell >= 0;
-    const uint64_t pid = live ? id[i] : 0;
-    const unsigned o = block_atomic_add(cursor, live ? key_of(cell, pid, M, g) : 0, live);
-    if (live) {
-      pos2[o] = pos[i];
-      mom2[o] = M;
-      id2[o] = pid;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      live[r] = cell[r] >= 0;
+      if (live[r]) key[r] = key_of(cell[r], pid[r], M[r], g);
     }
+    unsigned o[2] = {0u, 0u};
+    block_atomic_add2(cursor, key, live, o);
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      if (live[r]) {
+        pos2[o[r]] = P[r];
+        mom2[o[r]] = M[r];
+        id2[o[r]] = pid[r];
+      }
   }
 }
 
