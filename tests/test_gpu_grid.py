@@ -125,6 +125,18 @@ def test_fp64_grid_parity_mesh_shapes(n):
     assert gd["emissions"] == od["emissions"]
 
 
+def test_fp64_grid_parity_drifted_out_of_the_tile():
+    # the dense block with a tile of one halo cell over 12 steps without a
+    # re-sort: particles near the block's faces move more than a cell out of
+    # its tile, are listed and deposited by the drift kernel, and J (like
+    # E, B and the particles) still matches the oracle's to 1e-12
+    w, f = grid_case(seed=11, npart=2500, n=(16, 16, 16), region=((2, 2, 2), (6, 6, 6)))
+    gd, od = fp64_grid_parity(w, f, 12, caps=(20_000, 20_000, 40_000, 2_000), tuning={"deposit_halo": 1})
+    assert gd["emissions"] == od["emissions"] > 10
+    assert 0.5 * gd["block_steps"] < gd["tile_deposits"] < 0.995 * gd["block_steps"], \
+        (gd["tile_deposits"], gd["block_steps"])
+
+
 @pytest.mark.parametrize("halo", [1, 4, 0])
 def test_fp64_grid_parity_dense_cell_block(halo):
     # 2 x 2500 leptons and 830 ions inside one 8^3 cell block of a 16^3 mesh
