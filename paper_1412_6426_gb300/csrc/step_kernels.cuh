@@ -1555,9 +1555,11 @@ struct BlockItems {
 
 // The families of the cell-block pass: electrons and positrons (LEPTONS),
 // or ions alone, whose step has no event generator and is compiled without
-// it.  FP32 runs three blocks per SM (80 registers): measured on the 512^3
-// cascade, the pass took 8.43 ms per step at three blocks (the e-/e+ kernel
-// spilling 204 B), 9.10 at two and 8.70 at four.
+// it.  FP32 runs four blocks per SM (64 registers): measured on the 512^3
+// cascade, the pass took 4.38 ms per step at four blocks (the e-/e+ kernel
+// spilling 68 B) and 4.80 at three (80 registers); before the gather took
+// its interpolating form, three blocks had been best (8.43 ms, against 9.10
+// at two and 8.70 at four).
 template <typename R>
 __device__ __forceinline__ BlockItems block_items(const StepArgs<R> &a, const long long *ns, bool ions) {
   BlockItems b;
@@ -1635,7 +1637,7 @@ __device__ __forceinline__ void blocks_refill(const StepArgs<R> &a, int sp, long
   }
 }
 
-template <typename R, bool IONS> struct BlocksOcc { static constexpr int blocks = sizeof(R) == 4 ? 3 : 2; };
+template <typename R, bool IONS> struct BlocksOcc { static constexpr int blocks = sizeof(R) == 4 ? 4 : 2; };
 
 // Grid mode: electrons, positrons (IONS = false) or ions (IONS = true) in
 // cell-block order, advanced in work items taken by work stealing; warps
