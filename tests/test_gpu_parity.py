@@ -92,8 +92,8 @@ def fp32_momentum_bounds(gpu, ora, p_max, n_ev):
     """The FP32 path against the FP64 oracle, particle by particle, for every
     particle whose event history the FP32 run shares (same id).
 
-    Between events the push keeps within 1e-5 relative (north_star's bound;
-    tested alone by test_fp32_push_between_events).  An event moves a
+    Between events the push keeps within 1e-5 relative (the FP32 path's
+    bound; tested alone by test_fp32_push_between_events).  An event moves a
     momentum by a drawn fraction of its parent's: the parent keeps 1 - delta,
     the photon takes delta = r1^3, a pair splits r1 : 1 - r1.  The FP32 path
     takes r1 from the top 23 bits of the Philox word whose top 52 bits the
@@ -118,8 +118,8 @@ def fp32_momentum_bounds(gpu, ora, p_max, n_ev):
 
 
 def test_fp32_push_between_events():
-    # North_star's bound for the FP32 path, "momentum relative error <= 1e-5
-    # between events", on its own: emission and pairs off, so that every step
+    # The FP32 path's bound, momentum relative error <= 1e-5 between events,
+    # on its own: emission and pairs off, so that every step
     # is the push between events, over far more steps than an event takes
     # (at chi = 1 an electron emits about every 2 steps): every particle
     # within 1e-5 of the FP64 oracle's momentum.  Measured on a GB300: 2.2e-6
