@@ -1,0 +1,138 @@
+"""The oracle against the numbers the paper prints.
+
+tests/golden/paper_printed_values.txt lists each printed number with the
+passage that prints it and one unit in its last printed digit.  Each row
+names a quantity evaluated here with the oracle (the last rows with the
+workload recipes that both the oracle and the CUDA path read).  It must lie
+within that unit of the printed value.  A mistake that changes a constant, a
+Bessel order, a power of chi or a unit conversion moves at least one of
+these quantities by more than that.
+"""
+import math
+from pathlib import Path
+
+import pytest
+from scipy.integrate import quad
+from scipy.optimize import minimize_scalar
+
+from oracle import oracle as o
+from paper_1412_6426_gb300 import workloads as wl
+
+ALPHA = 7.2973525693e-3        # CODATA 2018
+GOLDEN = Path(__file__).parent / "golden" / "paper_printed_values.txt"
+
+
+def rows():
+    out = []
+    for line in GOLDEN.read_text().splitlines():
+        if not line.strip() or line.lstrip().startswith("#"):
+            continue
+        name, printed, unit, where, what = (s.strip() for s in line.split("|"))
+        out.append((name, float(printed), float(unit), where))
+    return out
+
+
+def maximise(f, lo, hi):
+    r = minimize_scalar(lambda u: -f(u), bounds=(lo, hi), method="bounded", options={"xatol": 1e-10})
+    return -r.fun
+
+
+def F1_small_x():
+    x = 1e-12
+    return o.F1(x) / x ** (1 / 3)
+
+
+def F2_max():
+    return maximise(o.F2, 0.01, 3.0)
+
+
+def P_small_delta():
+    # P carries [dt alpha / tau_C] / gamma; dt = 2 Compton times, gamma = 100
+    d, chi, gam, h = 1e-24, 1.0, 100.0, 2.0
+    return o.P(d, chi, gam, h) * gam / (ALPHA * h) / (chi ** (2 / 3) * d ** (-2 / 3))
+
+
+def I_q_large_chi():
+    # radiated power / (alpha m c^2 / tau_C) = int delta G(delta, chi) d delta
+    chi = 1e4
+    f = lambda d: d * o.G(d, chi)
+    low = quad(lambda u: f(math.exp(u)) * math.exp(u), math.log(1e-20), math.log(0.5),
+               limit=400, epsabs=0, epsrel=1e-11)[0]
+    high = quad(f, 0.5, 1 - 1e-12, limit=400, points=[0.9, 0.99, 0.999, 0.9999, 1 - 1e-5, 1 - 1e-6])[0]
+    return (low + high) / chi ** (2 / 3)
+
+
+def Pm_first_term_max():
+    # the F1 term is largest at r1 -> 0, where the F2 term vanishes
+    chi, gam, h = 1.0, 1000.0, 50.0
+    return o.Pm(1e-15, chi, gam, h) * gam / (ALPHA * h) / chi ** (2 / 3)
+
+
+def Pm_second_term_max():
+    # at chi = 1e6 the chi-linear F2 term dominates near r1 -> 1; u = log10(1 - r1)
+    chi, gam, h = 1e6, 1000.0, 50.0
+    return maximise(lambda u: o.Pm(1 - 10 ** u, chi, gam, h) * gam / (ALPHA * h) / chi, -14.0, -0.5)
+
+
+def dtq_simplified():
+    # Compton units: lambda_C / c = 2 pi tau_C; H in units of E_s
+    H = 1e-3
+    return o.dtq_lepton(1.0, H, 1.0) / (2 * math.pi * (1 / H) ** (2 / 3))
+
+
+def dtq_second_branch():
+    H = 1e-3
+    return o.dtq_lepton(1e12, H, 1.0) / (137 / (2 * math.pi) * 2 * math.pi / H)
+
+
+def dtp_pairs():
+    # P_p(delta_e, chi_g, eps, dt) with eps = 1, dt = 1: H / E_s = chi_g, so
+    # P_p / chi_g is the probability per Compton time per unit H; its supremum
+    # (chi_g -> infinity, delta_e -> 0) sets dt_p in units of lambda_C / c
+    chi = 1e6
+    s = maximise(lambda u: o.Pp(10 ** u, chi, 1.0, 1.0) / chi, -14.0, math.log10(0.5))
+    return 1 / (2 * math.pi * s)
+
+
+def E_S():
+    return wl.E_S
+
+
+def avalanche_updates():
+    t_rad = wl.avalanche_t_rad(1e-2)
+    period = 2 * math.pi / wl.laser_omega(1e-6)
+    return period / (173 * t_rad)
+
+
+def avalanche_no_subdiv():
+    t_rad = wl.avalanche_t_rad(1e-2)
+    n, capped = o.nsub(0.17 * t_rad, o.dtq_lepton(1000.0, 1e-2, 0.1), 1 << 20)
+    assert not capped
+    return n
+
+
+EVALUATE = {f.__name__: f for f in (F1_small_x, F2_max, P_small_delta, I_q_large_chi, Pm_first_term_max,
+                                    Pm_second_term_max, dtq_simplified, dtq_second_branch, dtp_pairs, E_S,
+                                    avalanche_updates, avalanche_no_subdiv)}
+
+
+def test_every_row_has_an_evaluation():
+    names = [r[0] for r in rows()]
+    assert sorted(names) == sorted(EVALUATE)
+
+
+@pytest.mark.parametrize("name,printed,unit,where", rows(), ids=[r[0] for r in rows()])
+def test_printed_value(name, printed, unit, where):
+    got = EVALUATE[name]()
+    assert abs(got - printed) <= unit, f"{name} ({where}): oracle {got!r}, printed {printed!r}"
+
+
+def test_the_paper_rounds_not_the_oracle():
+    # the printed coefficients are two- or three-digit forms of closed values
+    # the oracle reaches to many more digits: 2^(2/3) Gamma(2/3) for F1's
+    # slope, and three times the small-delta coefficient for P_m at r1 -> 0
+    g23 = math.gamma(2 / 3)
+    assert F1_small_x() == pytest.approx(2 ** (2 / 3) * g23, rel=1e-7)     # next term: O(x^(2/3))
+    c = math.sqrt(3) / (2 * math.pi) * 2 ** (2 / 3) * g23 * (2 / 3) ** (1 / 3)
+    assert P_small_delta() == pytest.approx(c, rel=1e-6)
+    assert Pm_first_term_max() == pytest.approx(3 * c, rel=1e-6)
