@@ -67,8 +67,10 @@ BYTES_PER_APPEND = {32: 40, 64: 68}
 # beam: (dram__bytes_read.sum + dram__bytes_write.sum) / live photons.  The
 # kernel's traffic is proportional to the records it touches, so the bench
 # scales it by the photons of its own launches.  Remove an entry when the
-# kernel changes until it is measured again.
-PHOTON_DRAM_BYTES_PER_STEP = {32: 247.68e6 / 5.567e6}
+# kernel changes until it is measured again.  (Empty: the FP32 photon kernel
+# changed, photon norms by the reciprocal square root, after its last
+# capture, 247.68e6 / 5.567e6 = 44.5 B per photon-step.)
+PHOTON_DRAM_BYTES_PER_STEP: dict = {}
 METRIC = "particle-steps/s with QED events, FP32 vs FP64 GPU path; % of HBM roofline"
 WORKLOAD_NAME = ("beam-laser head-on collision: 1e6 e- at 1 GeV (1% spread, 1 um x 3 um rms), "
                  "LP Gaussian pulse lambda=0.8 um a0=200 30 fs FWHM w0=2 um, analytic field, "
