@@ -26,12 +26,16 @@ ENS_STRIDE = 10  # per ensemble: E0, omega, phase, Eu[3], Bu[3], thin_scale
 GEN_MODIFIED, GEN_ALTERNATIVE, GEN_STANDARD = 0, 1, 2
 
 
+def compile_library(src: str, out: str) -> None:
+    """Compile one copy of the oracle's C source into a shared library."""
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-o", out, src, "-lm"])
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into a shared library next to its source."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               "-o", LIB + ".tmp", SRC, "-lm"]
-        subprocess.check_call(cmd)
+        compile_library(SRC, LIB + ".tmp")
         os.replace(LIB + ".tmp", LIB)
     return LIB
 
@@ -96,9 +100,11 @@ _lib = None
 
 
 def lib():
+    """The loaded oracle library.  QED_ORACLE_LIB names another build of the
+    same source to load instead (the planted-mistake tests use it)."""
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        _lib = ctypes.CDLL(os.environ.get("QED_ORACLE_LIB") or build())
         d, i64, u32, u64, i32 = (ctypes.c_double, ctypes.c_int64, ctypes.c_uint32,
                                  ctypes.c_uint64, ctypes.c_int32)
         pd = ctypes.POINTER(d)

@@ -136,3 +136,21 @@ def test_the_paper_rounds_not_the_oracle():
     c = math.sqrt(3) / (2 * math.pi) * 2 ** (2 / 3) * g23 * (2 / 3) ** (1 / 3)
     assert P_small_delta() == pytest.approx(c, rel=1e-6)
     assert Pm_first_term_max() == pytest.approx(3 * c, rel=1e-6)
+
+
+def test_time_step_bounds_match_the_rates():
+    # the printed coefficients come from the rates: at dt = dt_q (no margin,
+    # kappa = 1) the largest P_m of a lepton and the largest P_p of a photon
+    # are about 1.  Lepton, chi-linear branch (gamma large): max_r P_m =
+    # 0.502 chi/gamma [alpha dt], against the printed 0.5; photon: sup P_p
+    # = dt H / 130.33 in lambda_C/c, against the printed 130
+    gam, H = 1e12, 1e-3
+    dtq = o.dtq_lepton(gam, H, 1.0)
+    chi = gam * H
+    worst = maximise(lambda u: o.Pm(1 - 10 ** u, chi, gam, dtq), -14.0, -0.5)
+    assert abs(worst - 1.0) < 0.02, worst
+    H = 1e-2
+    dtp = o.dtq_photon(H, 1.0)
+    chig, eps = 1e6, 1e6 / H                      # chi_gamma = eps H
+    s = maximise(lambda u: o.Pp(10 ** u, chig, eps, dtp), -14.0, math.log10(0.5))
+    assert abs(s - 1.0) < 0.01, s

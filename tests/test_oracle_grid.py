@@ -5,6 +5,9 @@ Yee: a vacuum plane wave obeys the discrete dispersion relation
 rounding level.  CIC reproduces linear fields exactly.  Esirkepov: the
 deposited current satisfies the discrete continuity equation
 (rho^{n+1} - rho^n)/dt + div J = 0 cell by cell, and sum J dV = q w dx/dt.
+Together (Gauss's law in Compton units, div E = 4 pi alpha rho): one FDTD step
+with that current changes the discrete div E by exactly 4 pi alpha times the
+change of the charge density at every node, whatever the fields.
 """
 import math
 
@@ -124,3 +127,38 @@ def test_esirkepov_continuity():
     dV = np.prod(d)
     for c in range(3):
         assert abs(J[c].sum() * dV - (qw * dx[:, c]).sum() / dt) < 1e-11
+
+
+def div_nodes(n, d, F):
+    """Discrete divergence at the nodes (i, j, k) of a field staggered like E
+    and J (x component at (i+1/2, j, k), ...): backward differences."""
+    a = [np.asarray(F[c]).reshape(n[2], n[1], n[0]) for c in range(3)]
+    return ((a[0] - np.roll(a[0], 1, axis=2)) / d[0] + (a[1] - np.roll(a[1], 1, axis=1)) / d[1]
+            + (a[2] - np.roll(a[2], 1, axis=0)) / d[2]).ravel()
+
+
+def test_gauss_law_kept_by_the_field_update():
+    # random E, B (the curl B part of the update has no discrete divergence)
+    # and random charges moving less than a cell: the E update's current term
+    # -4 pi alpha J must change div E by 4 pi alpha (rho1 - rho0) node by node
+    rng = np.random.default_rng(8)
+    n, d, x0, dt = (6, 7, 5), (1.0, 0.8, 1.2), (0.0, 0.0, 0.0), 0.37
+    nc = int(np.prod(n))
+    f = [rng.standard_normal(nc) for _ in range(6)]
+    npart = 80
+    L = np.array(n) * np.array(d)
+    xa = rng.uniform(0, 1, (npart, 3)) * L
+    xb = xa + rng.uniform(-0.9, 0.9, (npart, 3)) * np.array(d)
+    qw = rng.uniform(-2, 2, npart) * 50.0
+    J = [np.zeros(nc) for _ in range(3)]
+    for p in range(npart):
+        o.deposit(n, d, x0, J, xa[p], xb[p], qw[p], dt)
+    rho0 = o.charge_density(n, d, x0, xa[:, 0], xa[:, 1], xa[:, 2], qw)
+    rho1 = o.charge_density(n, d, x0, xb[:, 0], xb[:, 1], xb[:, 2], qw)
+    div0 = div_nodes(n, d, f[:3])
+    o.yee_step(n, d, dt, f, J)
+    div1 = div_nodes(n, d, f[:3])
+    want = 4 * math.pi * 7.2973525693e-3 * (rho1 - rho0)
+    assert np.abs(want).max() > 1e-2                  # the charges do move
+    scale = max(np.abs(div0).max(), np.abs(want).max())
+    assert np.abs((div1 - div0) - want).max() < 1e-12 * scale

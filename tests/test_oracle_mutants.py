@@ -1,0 +1,149 @@
+"""Planted mistakes in the oracle, and the pins that catch them.
+
+Every parity claim rests on the oracle, and the oracle rests on its pins.
+This file checks the pins themselves.  Each case below copies
+oracle/qed_oracle.c, plants one plausible mistake: a dropped term, a wrong
+sign, a transposed operand or index, a wrong constant or Bessel order.  It
+builds the copy into a library of its own with the oracle's compiler flags,
+then runs the listed pins against it in a subprocess, with QED_ORACLE_LIB
+naming the copy.  Every pin set must fail on its mutant, and pass on an
+unmodified copy built the same way.  The CUDA library is not involved.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+from pathlib import Path
+
+import pytest
+
+from oracle import oracle as o
+
+ROOT = Path(__file__).resolve().parent.parent
+
+# (name, text in qed_oracle.c, its replacement, occurrences, pins that must fail)
+MUTANTS = [
+    # synchrotron functions (Sec. IV.E): the Bessel orders of F1 and F2
+    ("F1 from K_1/3", "cosh(5.0 * u / 3.0) / cosh(u)", "cosh(1.0 * u / 3.0) / cosh(u)", 1,
+     ["tests/test_oracle_special.py::test_F_against_scipy", "tests/test_oracle_golden.py"]),
+    ("F2 from K_1/3", "double t2 = e * cosh(2.0 * u / 3.0);", "double t2 = e * cosh(1.0 * u / 3.0);", 1,
+     ["tests/test_oracle_special.py::test_F_against_scipy"]),
+    # emission density, Eq. (24), and the modified generator, Eq. (25)
+    ("G: F2 term with the wrong sign", "(f1 + 1.5 * delta * chi * zq * f2)", "(f1 - 1.5 * delta * chi * zq * f2)", 1,
+     ["tests/test_oracle_rates.py::test_G_against_scipy"]),
+    ("G: F2 term dropped", "(f1 + 1.5 * delta * chi * zq * f2)", "(f1)", 1,
+     ["tests/test_oracle_rates.py::test_G_against_scipy", "tests/test_oracle_golden.py"]),
+    ("G: z_q with delta and 1 - delta transposed", "double zq = (2.0 / 3.0) / chi * delta / (1.0 - delta);",
+     "double zq = (2.0 / 3.0) / chi * (1.0 - delta) / delta;", 1,
+     ["tests/test_oracle_rates.py::test_G_against_scipy"]),
+    ("P without 1/gamma", "return OR_ALPHA * dt * or_G(delta, chi) / gamma;", "return OR_ALPHA * dt * or_G(delta, chi);", 1,
+     ["tests/test_oracle_golden.py", "tests/test_oracle_rates.py::test_small_delta_asymptote"]),
+    ("P_m with the Jacobian 2 r1^2", "return 3.0 * r1 * r1 * or_P(delta, chi, gamma, dt);",
+     "return 2.0 * r1 * r1 * or_P(delta, chi, gamma, dt);", 1,
+     ["tests/test_oracle_golden.py", "tests/test_oracle_generator.py::test_frozen_spectrum_gamma100_chi1"]),
+    # pair density, Eq. (30)
+    ("P_p: F2 term with the wrong sign", "(f1 - 1.5 * chig * zp * f2)", "(f1 + 1.5 * chig * zp * f2)", 1,
+     ["tests/test_oracle_rates.py::test_pair_rate_known_values"]),
+    ("P_p: chi_g eps_g for chi_g / eps_g", "chig / epsg * (de - 1.0) * de", "chig * epsg * (de - 1.0) * de", 1,
+     ["tests/test_oracle_rates.py::test_pair_rate_erber_limit", "tests/test_oracle_golden.py"]),
+    # chi and the effective fields, Eqs. (3)-(4), (31)-(32)
+    ("chi: p x B with the wrong sign", "double ax = g * E[0] + (p[1] * B[2] - p[2] * B[1]);",
+     "double ax = g * E[0] - (p[1] * B[2] - p[2] * B[1]);", 1,
+     ["tests/test_oracle_rates.py::test_chi_definitions"]),
+    ("H_eff without (p_hat . E)^2", "double pe = pm > 0.0 ? (p[0] * E[0] + p[1] * E[1] + p[2] * E[2]) / pm : 0.0;",
+     "double pe = 0.0;", 1, ["tests/test_oracle_rates.py::test_longitudinal_field_terms"]),
+    ("photon H_eff without (k_hat . E)^2", "double ke = nx * E[0] + ny * E[1] + nz * E[2];", "double ke = 0.0;", 1,
+     ["tests/test_oracle_rates.py::test_longitudinal_field_terms"]),
+    ("Esirkepov: current with the wrong sign", "acc -= qw * d[0] / (dt * dV) * W;", "acc += qw * d[0] / (dt * dV) * W;", 1,
+     ["tests/test_oracle_grid.py::test_esirkepov_continuity"]),
+    # sub-interval bounds, Eqs. (28) and (33), and their count (Sec. IV.H)
+    ("dt_q: 173 for 137", "return kappa * 137.0 * (a < b ? a : b);", "return kappa * 173.0 * (a < b ? a : b);", 1,
+     ["tests/test_oracle_golden.py"]),
+    ("dt_q: H^(-1/3) for H^(-2/3)", "double a = 0.67 * cbrt(gamma) * pow(1.0 / heff, 2.0 / 3.0);",
+     "double a = 0.67 * cbrt(gamma) * pow(1.0 / heff, 1.0 / 3.0);", 1, ["tests/test_oracle_golden.py"]),
+    ("dt_q of photons without lambda_C / c = 2 pi", "return kappa * 130.0 * 2.0 * OR_PI / heff_g;",
+     "return kappa * 130.0 / heff_g;", 1, ["tests/test_oracle_golden.py::test_time_step_bounds_match_the_rates"]),
+    ("sub-intervals longer than dt_q", "double n = ceil(ratio);", "double n = floor(ratio);", 1,
+     ["tests/test_oracle_rates.py::test_time_step_bounds"]),
+    # Boris push (Appendix A)
+    ("Boris: rotation operands transposed", "double up[3] = {um[0] + (um[1] * t[2] - um[2] * t[1]),",
+     "double up[3] = {um[0] + (um[2] * t[1] - um[1] * t[2]),", 1,
+     ["tests/test_oracle_push.py::test_uniform_B_rotation_exact"]),
+    ("Boris: s = 2t without 1/(1 + t^2)",
+     "double s[3] = {2.0 * t[0] / (1.0 + t2), 2.0 * t[1] / (1.0 + t2), 2.0 * t[2] / (1.0 + t2)};",
+     "double s[3] = {2.0 * t[0], 2.0 * t[1], 2.0 * t[2]};", 1,
+     ["tests/test_oracle_push.py::test_uniform_B_rotation_exact"]),
+    ("Boris: a whole E step on each side", "double a = 0.5 * q * h;", "double a = q * h;", 1,
+     ["tests/test_oracle_push.py::test_uniform_E_acceleration_exact"]),
+    # events (Sec. IV.G, V.A): momentum shares
+    ("photon takes r1^2", "double delta = a1 * a1 * a1;", "double delta = a1 * a1;", 1,
+     ["tests/test_oracle_step.py::test_momentum_conservation_uniform_E"]),
+    ("no recoil of the emitting lepton",
+     "for (int c = 0; c < 3; ++c) q->p[c] = (1.0 - delta) * p0[c];\n                C->D->emissions++;\n                double k[3]",
+     "for (int c = 0; c < 3; ++c) q->p[c] = p0[c];\n                C->D->emissions++;\n                double k[3]", 1,
+     ["tests/test_oracle_step.py::test_momentum_conservation_uniform_E"]),
+    ("positron takes r1 too", "po.p[c] = (1.0 - a1) * q->p[c];", "po.p[c] = a1 * q->p[c];", 1,
+     ["tests/test_oracle_step.py::test_momentum_conservation_uniform_E"]),
+    # mesh (Appendix C): FDTD, CIC, Esirkepov
+    ("FDTD: current term with the wrong sign", "E[c][q] += dt * (tmp[c][q] - 4.0 * OR_PI * OR_ALPHA * J[c][q]);",
+     "E[c][q] += dt * (tmp[c][q] + 4.0 * OR_PI * OR_ALPHA * J[c][q]);", 1,
+     ["tests/test_oracle_grid.py::test_gauss_law_kept_by_the_field_update"]),
+    ("FDTD: whole B steps", "B[c][q] -= 0.5 * dt * tmp[c][q];", "B[c][q] -= dt * tmp[c][q];", 2,
+     ["tests/test_oracle_grid.py::test_plane_wave_dispersion"]),
+    ("CIC: Ex and Ey staggers transposed", "{{0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 0.5},",
+     "{{0, 0.5, 0}, {0.5, 0, 0}, {0, 0, 0.5},", 1, ["tests/test_oracle_grid.py::test_cic_linear_exact"]),
+    ("Esirkepov: 1/2 for 1/3 in the Jx weight", "dS[1][j] * dS[2][k] / 3.0", "dS[1][j] * dS[2][k] / 2.0", 1,
+     ["tests/test_oracle_grid.py::test_esirkepov_continuity"]),
+    # vacuum pairs (Sec. V.B), thinning (Sec. VI), Philox
+    ("Schwinger rate exp(-1/E)", "exp(-OR_PI / Em)", "exp(-1.0 / Em)", 1,
+     ["tests/test_oracle_schwinger.py::test_pair_count_matches_the_si_rate"]),
+    ("thinning factor N/L instead of the weight ratio", "w = w * (wall[g] / wsurv[g]);",
+     "w = w * ((double)count[g] / (double)L);", 1,
+     ["tests/test_oracle_sec6.py::test_thinning_conserves_group_weight_and_is_binomial"]),
+    ("Philox: a Weyl constant off by one", "k[1] += 0xBB67AE85u;", "k[1] += 0xBB67AE86u;", 1,
+     ["tests/test_philox_pin.py::test_oracle_philox_matches_aten"]),
+]
+
+
+def build_copy(tmp: Path, name: str, text: str) -> Path:
+    d = tmp / name
+    d.mkdir()
+    src, out = d / "qed_oracle.c", d / "libqed_oracle.so"
+    src.write_text(text)
+    o.compile_library(str(src), str(out))
+    return out
+
+
+def run_pins(lib: Path, pins) -> subprocess.CompletedProcess:
+    env = dict(os.environ, QED_ORACLE_LIB=str(lib), PYTHONPATH=str(ROOT))
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", *pins],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+
+
+def test_every_mutant_is_caught(tmp_path):
+    source = Path(o.SRC).read_text()
+    # the pins pass on an unmodified copy built the same way
+    union = sorted({p for m in MUTANTS for p in m[4]})
+    base = run_pins(build_copy(tmp_path, "unmodified", source), union)
+    assert base.returncode == 0, base.stdout[-3000:]
+
+    def one(k, m):
+        name, old, new, count, pins = m
+        assert source.count(old) == count, (name, source.count(old))
+        lib = build_copy(tmp_path, f"mutant{k}", source.replace(old, new))
+        r = run_pins(lib, pins)
+        # 1: tests ran and failed (not a collection error or a crash)
+        return name, r.returncode, r.stdout[-1500:]
+
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        results = list(ex.map(lambda km: one(*km), enumerate(MUTANTS)))
+    survivors = [(name, rc, out) for name, rc, out in results if rc != 1]
+    assert not survivors, "\n\n".join(f"{name}: exit {rc}\n{out}" for name, rc, out in survivors)
+
+
+@pytest.mark.parametrize("m", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_text_is_in_the_source(m):
+    # a planted mistake must name text the oracle holds, so that an edit of
+    # the oracle cannot silently turn a case into a copy of the original
+    name, old, new, count, pins = m
+    assert Path(o.SRC).read_text().count(old) == count and old != new

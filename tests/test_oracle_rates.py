@@ -111,10 +111,11 @@ def test_pair_symmetry_and_positivity():
             assert a > 0 and abs(a / b - 1) < 1e-12
 
 
-@pytest.mark.parametrize("chig", [0.05, 0.02])
-def test_pair_rate_erber_limit(chig):
-    # total Breit-Wheeler rate * eps / alpha -> (3/16) sqrt(3/2) chi exp(-8/(3 chi))
-    tot = quad(lambda d: o.Pp(d, chig, 1.0, 1.0) / ALPHA, 0, 1, points=[0.5], limit=200, epsrel=1e-10)[0]
+@pytest.mark.parametrize("chig,eps", [(0.05, 1.0), (0.02, 1.0), (0.05, 37.0)])
+def test_pair_rate_erber_limit(chig, eps):
+    # total Breit-Wheeler rate * eps / alpha -> (3/16) sqrt(3/2) chi exp(-8/(3 chi)):
+    # at fixed chi_gamma the rate falls as 1/eps (Eq. (30)'s chi_g / eps_g)
+    tot = quad(lambda d: o.Pp(d, chig, eps, 1.0) * eps / ALPHA, 0, 1, points=[0.5], limit=200, epsrel=1e-10)[0]
     er = 3 / 16 * math.sqrt(1.5) * chig * math.exp(-8 / (3 * chig))
     assert abs(tot / er - 1) < 0.2 * chig
 
@@ -167,3 +168,17 @@ def test_chi_definitions():
     assert o.chi_photon((0, 0, -5.0), E, B) == pytest.approx(5.0 * 2e-3, rel=1e-14)
     # invariance: chi is a Lorentz scalar; pure E field, p perpendicular: chi = gamma E
     assert o.chi((3.0, 0, 0), (0, 0.01, 0), (0, 0, 0)) == pytest.approx(math.sqrt(10) * 0.01, rel=1e-14)
+
+
+def test_longitudinal_field_terms():
+    # the (p_hat . E)^2 term of Eq. (3) and the (k_hat . E)^2 term of Eq. (32),
+    # with a field component along the motion.  Lepton: chi = gamma H_eff
+    # (Sec. IV.C) holds up to relative terms of order 1/gamma^2 against the
+    # invariant form of Eq. (4); without the term H_eff is ~40% too large here
+    p, E, B = (1000.0, 0.0, 0.0), (1e-3, 2e-3, 0.0), (0.0, 0.0, 1e-3)
+    g = math.sqrt(1 + 1e6)
+    assert abs(o.chi(p, E, B) / (g * o.heff(p, E, B)) - 1) < 1e-5
+    # photon: chi_gamma is the massless limit of Eq. (4) with p = k
+    for k in ((1e6, 0.0, 0.0), (3e5, -4e5, 1e5)):
+        E, B = (2e-3, -1e-3, 5e-4), (1e-3, 3e-3, -2e-3)
+        assert abs(o.chi_photon(k, E, B) / o.chi(k, E, B) - 1) < 1e-9
