@@ -113,3 +113,36 @@ def test_generators_in_the_particle_step_conserve_what_they_should():
         expect = np.array([n * p0, -E * 2 * dt * n, 0.0])
         assert np.allclose(tot, expect, rtol=1e-11, atol=1e-9 * np.abs(expect).max()), gen
         assert D["photons_created"] == D["emissions"]
+
+
+def test_step_emits_the_generator_densities():
+    # the same spectra through the particle step itself (the code path of a
+    # run, not the frozen sampler): electrons with gamma = 100, perpendicular
+    # to a static B with chi = 1, one step of one sub-interval.  The push in B
+    # keeps |p|, so chi and gamma hold at the event and delta = |k| / |p0|.
+    # The standard generator integrates W(1) for every particle (about 5 ms
+    # each), so it runs fewer electrons at a larger P = W(1); an unbounded
+    # margin kappa keeps its step one sub-interval long
+    gamma, chi = 100.0, 1.0
+    p0 = math.sqrt(gamma ** 2 - 1)
+    lo, hi, nb = -10.0, 0.0, 20
+    edges = np.linspace(lo, hi, nb + 1)
+    for gen, h, n, kappa in ((o.GEN_MODIFIED, 0.1 * gamma / (ALPHA * 1.6), 200_000, 0.1),
+                             (o.GEN_ALTERNATIVE, 0.1 * gamma / (ALPHA * 1.6), 200_000, 0.1),
+                             (o.GEN_STANDARD, 0.5 * gamma / (ALPHA * 1.04), 2_000, 1e9)):
+        P = o.make_params(n=(4, 4, 4), d=(1e9,) * 3, x0=(-2e9,) * 3, periodic=(1, 1, 1),
+                          field_mode=o.FIELD_UNIFORM, fp=(0, 0, 0, 0, 0, chi / p0), kappa=kappa, pairs_on=0,
+                          generator=gen, seed=5)
+        run = o.Run(P, caps=(n, 1, n, 1))
+        x = np.zeros((n, 3))
+        p = np.zeros((n, 3))
+        p[:, 0] = p0
+        run.sp[0].set(x, p, np.ones(n), np.arange(n, dtype=np.uint64))
+        run.step(0, 0.0, h)
+        assert run.diag()["substeps_lepton"] == n              # one sub-interval each
+        _, k, _, _ = run.sp[2].get()
+        delta = np.linalg.norm(k, axis=1) / p0
+        hist, _ = np.histogram(np.log10(delta), bins=edges)
+        exp = _expected(gen, chi, gamma, h, n, edges)
+        sig = np.sqrt(np.maximum(exp, 1.0))
+        assert np.all(np.abs(hist - exp) <= 4 * sig + 1e-9), (gen, hist, exp)

@@ -84,6 +84,19 @@ MUTANTS = [
      ["tests/test_oracle_step.py::test_momentum_conservation_uniform_E"]),
     ("positron takes r1 too", "po.p[c] = (1.0 - a1) * q->p[c];", "po.p[c] = a1 * q->p[c];", 1,
      ["tests/test_oracle_step.py::test_momentum_conservation_uniform_E"]),
+    # the generators of Sec. IV.F through the particle step
+    ("alternative generator: delta from r2", "delta = r1;                          /* r2 < P(r1), delta = r1 */",
+     "delta = r2;                          /* r2 < P(r1), delta = r1 */", 1,
+     ["tests/test_oracle_generators.py::test_step_emits_the_generator_densities"]),
+    ("standard generator: fires on r2", "fire = r1 < pe;\n                    delta = fire ? or_delta_std(chi, r2)",
+     "fire = r2 < pe;\n                    delta = fire ? or_delta_std(chi, r2)", 1,
+     ["tests/test_oracle_generators.py::test_step_emits_the_generator_densities"]),
+    # the focused pulse of the collision (a paraxial Gaussian beam)
+    ("pulse: Rayleigh length k w0^2", "double zr = 0.5 * w * w0 * w0;", "double zr = w * w0 * w0;", 1,
+     ["tests/test_oracle_step.py::test_gaussian_pulse_solves_the_wave_equation"]),
+    ("pulse: Gouy phase with the wrong sign", "double phase = w * eta - 0.5 * w * r2 * invR + gouy + fp[8];",
+     "double phase = w * eta - 0.5 * w * r2 * invR - gouy + fp[8];", 1,
+     ["tests/test_oracle_step.py::test_gaussian_pulse_solves_the_wave_equation"]),
     # mesh (Appendix C): FDTD, CIC, Esirkepov
     ("FDTD: current term with the wrong sign", "E[c][q] += dt * (tmp[c][q] - 4.0 * OR_PI * OR_ALPHA * J[c][q]);",
      "E[c][q] += dt * (tmp[c][q] + 4.0 * OR_PI * OR_ALPHA * J[c][q]);", 1,
