@@ -107,6 +107,21 @@ MUTANTS = [
      "{{0, 0.5, 0}, {0.5, 0, 0}, {0, 0, 0.5},", 1, ["tests/test_oracle_grid.py::test_cic_linear_exact"]),
     ("Esirkepov: 1/2 for 1/3 in the Jx weight", "dS[1][j] * dS[2][k] / 3.0", "dS[1][j] * dS[2][k] / 2.0", 1,
      ["tests/test_oracle_grid.py::test_esirkepov_continuity"]),
+    # particle motion, ensembles, weights and placement
+    ("position update without the mass", "for (int c = 0; c < 3; ++c) q->x[c] += q->p[c] / (m * g) * h;",
+     "for (int c = 0; c < 3; ++c) q->x[c] += q->p[c] / g * h;", 1,
+     ["tests/test_oracle_step.py::test_free_streaming_velocity"]),
+    ("ensemble table: Bx and By swapped", "B[0] = q[6]; B[1] = q[7]; B[2] = q[8];",
+     "B[0] = q[7]; B[1] = q[6]; B[2] = q[8];", 1,
+     ["tests/test_oracle_sec6.py::test_one_ensemble_is_the_uniform_mode"]),
+    ("spectrum counts photons, not weights", "if (a >= 0.0 && a < P->nbins) C->D->spectrum[(long)a] += w;",
+     "if (a >= 0.0 && a < P->nbins) C->D->spectrum[(long)a] += 1.0;", 1,
+     ["tests/test_oracle_sec6.py::test_spectra_are_weighted"]),
+    ("pair products without 1/N_g", "el.w = po.w = q->w * (fg / (double)ng);", "el.w = po.w = q->w * fg;", 1,
+     ["tests/test_oracle_sec6.py::test_pair_factor_keeps_lepton_yield"]),
+    ("vacuum pair offsets: y from the x draw", "el.x[1] = po.x[1] = P->x0[1] + ((double)j + uy) * P->d[1];",
+     "el.x[1] = po.x[1] = P->x0[1] + ((double)j + ux) * P->d[1];", 1,
+     ["tests/test_oracle_schwinger.py::test_pairs_at_rest_colocated_uniform_in_cells"]),
     # vacuum pairs (Sec. V.B), thinning (Sec. VI), Philox
     ("Schwinger rate exp(-1/E)", "exp(-OR_PI / Em)", "exp(-1.0 / Em)", 1,
      ["tests/test_oracle_schwinger.py::test_pair_count_matches_the_si_rate"]),

@@ -57,6 +57,9 @@ def test_pairs_at_rest_colocated_uniform_in_cells():
     frac = (xe / d) % 1.0
     for c in range(3):
         assert kstest(frac[:, c], "uniform").pvalue > 1e-3
+    # the three offsets are independent draws
+    cc = np.corrcoef(frac.T)
+    assert np.all(np.abs(cc[np.triu_indices(3, 1)]) < 4 / math.sqrt(len(frac)))
 
 
 def test_only_the_field_strength_matters():

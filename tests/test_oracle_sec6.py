@@ -61,12 +61,13 @@ def ens_row(E0=0.0, omega=0.0, phase=0.0, Eu=(0.0, 0.0, 0.0), Bu=(0.0, 0.0, 0.0)
 # ---- ensembles -----------------------------------------------------------
 
 def test_one_ensemble_is_the_uniform_mode():
+    # a B along z alone, and a general field with six different components
     parts = {0: beam(200)}
-    B = 1e-3
-    a = run(parts, o.FIELD_UNIFORM, (0, 0, 0, 0, 0, B), 2e4, 4)[0]
-    b = run(parts, o.FIELD_ENSEMBLE, (), 2e4, 4, ens=np.array([ens_row(Bu=(0, 0, B))]))[0]
-    assert sum(len(a[s][3]) for s in range(4)) > 200
-    same(a, b)
+    for Eu, Bu in (((0, 0, 0), (0, 0, 1e-3)), ((2e-4, -1e-4, 3e-4), (4e-4, -6e-4, 1e-3))):
+        a = run(parts, o.FIELD_UNIFORM, (*Eu, *Bu), 2e4, 4)[0]
+        b = run(parts, o.FIELD_ENSEMBLE, (), 2e4, 4, ens=np.array([ens_row(Eu=Eu, Bu=Bu)]))[0]
+        assert sum(len(a[s][3]) for s in range(4)) > 200
+        same(a, b)
 
 
 def test_one_ensemble_is_the_rotating_mode():
@@ -182,6 +183,12 @@ def test_pair_factor_keeps_lepton_yield():
     w0, w1 = ref[1][2].sum(), out[1][2].sum()
     assert np.all(np.isin(out[1][2], [3.0, 9.0, 27.0]))
     assert abs(w1 - w0) < 5 * 3.0 * math.sqrt(max(d["pairs_created"], 1)) + 5 * math.sqrt(w0)
+    # N_g = 3 samples per photon sub-interval, each pair of weight w / 3
+    out, d, _, _ = run(parts, o.FIELD_UNIFORM, (0, 0, 0, 0, 0, 5e-3), 1e5, 6, pair_ng=3, **kw)
+    w3 = out[1][2]
+    assert d["pairs_created"] > 2 * d0["pairs"]
+    assert np.allclose(w3 * 3 ** np.round(-np.log(w3) / np.log(3)), 1.0, rtol=1e-12)   # powers of 1/3
+    assert abs(w3.sum() - w0) < 5 * math.sqrt(max(d["pairs_created"], 1)) / 3 + 5 * math.sqrt(w0)
 
 
 # ---- thinning -------------------------------------------------------------
@@ -282,3 +289,17 @@ def test_thinned_shower_keeps_weighted_yields():
     x, p, w, _ = out[2]
     assert abs(e1 - e0) < 5 * math.sqrt((w * w * np.linalg.norm(p, axis=1) ** 2).sum()) + 5 * math.sqrt(
         (np.linalg.norm(ref[2][1], axis=1) ** 2).sum())
+
+
+def test_spectra_are_weighted():
+    # the spectra sum the photons' weights (Sec. VI's weighted products):
+    # electrons of weights 0.5 .. 3, and a log range that holds every photon
+    rng = np.random.default_rng(4)
+    x, p, _, ids = beam(300)
+    w = rng.uniform(0.5, 3.0, 300)
+    out, d, spec, spec_e = run({0: (x, p, w, ids)}, o.FIELD_UNIFORM, (0, 0, 0, 0, 0, 1e-3), 2e4, 3,
+                               pairs_on=0, nbins=16, lg_lo=-60.0, lg_hi=4.0)
+    wph = out[2][2]
+    assert len(wph) > 100 and not np.all(wph == wph[0])
+    assert math.isclose(spec.sum(), wph.sum(), rel_tol=1e-12)
+    assert math.isclose(spec_e.sum(), wph.sum(), rel_tol=1e-12)

@@ -84,6 +84,23 @@ def test_energy_conservation_uniform_B():
     assert abs(D["energy_defect"]) < 1e-3 * e0
 
 
+def test_free_streaming_velocity():
+    # no field: each step moves a particle by p / sqrt(m^2 + p^2) dt (c = 1),
+    # for an electron (m = 1) and a proton (m = 1836.15)
+    P = o.make_params(field_mode=o.FIELD_UNIFORM, fp=(0,) * 6, kappa=0.1, **big_periodic_box())
+    run = o.Run(P, caps=(4, 1, 4, 4))
+    pv = np.array([[500.0, -300.0, 100.0]])
+    for sp in (0, 3):
+        run.sp[sp].set(np.zeros((1, 3)), pv, [1.0], [sp])
+    dt, n = 1e3, 5
+    for s in range(n):
+        run.step(s, s * dt, dt)
+    for sp, m in ((0, 1.0), (3, 1836.15267343)):
+        x, p, _, _ = run.sp[sp].get()
+        assert np.allclose(p, pv, rtol=0, atol=0)
+        assert np.allclose(x[0], n * dt * pv[0] / math.sqrt(m * m + pv[0] @ pv[0]), rtol=1e-13, atol=0), sp
+
+
 def test_boundaries_open_and_periodic():
     for periodic, alive in ((0, 0), (1, 1)):
         P = o.make_params(n=(10, 10, 10), d=(1.0, 1.0, 1.0), x0=(0.0, 0.0, 0.0), periodic=(periodic,) * 3,
