@@ -162,3 +162,46 @@ def test_gauss_law_kept_by_the_field_update():
     assert np.abs(want).max() > 1e-2                  # the charges do move
     scale = max(np.abs(div0).max(), np.abs(want).max())
     assert np.abs((div1 - div0) - want).max() < 1e-12 * scale
+
+
+def test_step_current_is_continuous():
+    # a whole step of the particle path on a mesh, deposit on: electrons
+    # (charge -1), positrons (+1) and ions (+1) of unequal weights, and the
+    # photons of an earlier step, some of which convert (pairs are born
+    # co-located, so they add no net charge at birth).  The current the step
+    # leaves in J obeys (rho_end - rho_start) / dt + div J = 0 at every node,
+    # with rho from the positions before the step and after it
+    from oracle import drive
+    rng = np.random.default_rng(21)
+    n, cell = (8, 8, 8), 2e4
+    d, x0 = (cell,) * 3, (0.0, 0.0, 0.0)
+    nc = int(np.prod(n))
+    dt = 0.45 * cell / math.sqrt(3)
+    f = [rng.standard_normal(nc) * 3e-2 for _ in range(6)]          # chi ~ 50
+    parts = {}
+    for sp, count in ((0, 400), (1, 400), (3, 150)):
+        x = rng.uniform(0, 1, (count, 3)) * np.array(n) * cell
+        u = rng.standard_normal((count, 3))
+        pm = 50.0 if sp == 3 else 1000.0
+        parts[sp] = (x, u / np.linalg.norm(u, axis=1)[:, None] * pm, rng.uniform(0.5, 2.0, count),
+                     np.arange(count, dtype=np.uint64) + 10_000 * sp)
+    common = dict(kappa=0.1, seed=2, caps=(20_000, 20_000, 40_000, 400))
+    first, _, _, _ = drive.run(n, d, x0, (1, 1, 1), o.FIELD_GRID, (), dt, 1, parts,
+                               fields=[a.copy() for a in f], **common)
+    J = [np.zeros(nc) for _ in range(3)]
+    out, D, _, _ = drive.run(n, d, x0, (1, 1, 1), o.FIELD_GRID, (), dt, 1, first, step0=1, t0=dt,
+                             fields=[a.copy() for a in f], J=J, deposit_on=1, **common)
+    assert D["emissions"] > 100 and D["pairs"] > 5, (D["emissions"], D["pairs"])
+    charge = {0: -1.0, 1: 1.0, 3: 1.0}
+
+    def rho(ps):
+        acc = np.zeros(nc)
+        for sp, q in charge.items():
+            x, _, w, _ = ps[sp]
+            if len(x):
+                acc += o.charge_density(n, d, x0, x[:, 0], x[:, 1], x[:, 2], q * np.asarray(w))
+        return acc
+    drho = rho(out) - rho(first)
+    res = drho / dt + div_nodes(n, d, J)
+    scale = np.abs(drho).max() / dt
+    assert scale > 0 and np.abs(res).max() < 1e-10 * scale, np.abs(res).max() / scale

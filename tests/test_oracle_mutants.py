@@ -122,6 +122,9 @@ MUTANTS = [
     ("vacuum pair offsets: y from the x draw", "el.x[1] = po.x[1] = P->x0[1] + ((double)j + uy) * P->d[1];",
      "el.x[1] = po.x[1] = P->x0[1] + ((double)j + ux) * P->d[1];", 1,
      ["tests/test_oracle_schwinger.py::test_pairs_at_rest_colocated_uniform_in_cells"]),
+    ("step deposits without the charge", "or_deposit(P->n, P->d, P->x0, C->J, xs, q->x, P->charge[sp] * q->w, C->dt);",
+     "or_deposit(P->n, P->d, P->x0, C->J, xs, q->x, q->w, C->dt);", 1,
+     ["tests/test_oracle_grid.py::test_step_current_is_continuous"]),
     # vacuum pairs (Sec. V.B), thinning (Sec. VI), Philox
     ("Schwinger rate exp(-1/E)", "exp(-OR_PI / Em)", "exp(-1.0 / Em)", 1,
      ["tests/test_oracle_schwinger.py::test_pair_count_matches_the_si_rate"]),
