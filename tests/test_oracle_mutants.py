@@ -91,6 +91,16 @@ MUTANTS = [
     ("standard generator: fires on r2", "fire = r1 < pe;\n                    delta = fire ? or_delta_std(chi, r2)",
      "fire = r2 < pe;\n                    delta = fire ? or_delta_std(chi, r2)", 1,
      ["tests/test_oracle_generators.py::test_step_emits_the_generator_densities"]),
+    ("standard generator: W without the Jacobian 3 s^2", "acc += or_gl8_w[k] * 3.0 * s * s * or_G(s * s * s, chi);",
+     "acc += or_gl8_w[k] * or_G(s * s * s, chi);", 1,
+     ["tests/test_oracle_generators.py::test_standard_total_and_cdf_against_scipy"]),
+    ("standard generator: delta = s^2", "    double sr = 0.5 * (a + b);\n    return sr * sr * sr;",
+     "    double sr = 0.5 * (a + b);\n    return sr * sr;", 1,
+     ["tests/test_oracle_generators.py::test_standard_energy_is_the_inverse_cdf"]),
+    ("sub-interval cap ignored", "    if (n > (double)nmax) { *capped = 1; return nmax; }",
+     "    if (0) { *capped = 1; return nmax; }", 1, ["tests/test_oracle_rates.py::test_time_step_bounds"]),
+    ("uniforms without the half offset (0 can occur)", "return (k + 0.5) * (1.0 / 4503599627370496.0);",
+     "return k * (1.0 / 4503599627370496.0);", 1, ["tests/test_oracle_generator.py::test_u52_range_edges"]),
     # the focused pulse of the collision (a paraxial Gaussian beam)
     ("pulse: Rayleigh length k w0^2", "double zr = 0.5 * w * w0 * w0;", "double zr = w * w0 * w0;", 1,
      ["tests/test_oracle_step.py::test_gaussian_pulse_solves_the_wave_equation"]),
