@@ -56,3 +56,24 @@ def test_pair_bound():
         f = bound_f2(zmin) if zmin > 0.42 else 0.6071
         b = ALPHA * h * K * (chig / eps) * f
         assert max(o.Pp(de, chig, eps, h) for de in des) <= b * (1 + 1e-12)
+
+
+def test_kernels_evaluate_the_verified_bounds():
+    # the constants above are the ones the step kernels' early exits use:
+    # read them from the kernel source, so that an edit there cannot leave
+    # these checks verifying a different bound
+    import re
+    from pathlib import Path
+    src = (Path(__file__).resolve().parent.parent / "paper_1412_6426_gb300" / "csrc" / "step_kernels.cuh").read_text()
+
+    def body(name):
+        m = re.search(r"__device__ __forceinline__ R " + name + r"\(.*?\n}\n", src, re.S)
+        assert m, name
+        return m.group(0)
+    emit, pair = body("emit_bound"), body("pair_bound")
+    assert "5.6336f * c23 + 1.8212f * c" in emit and "1.02 * kAlpha * kSqrt3Over2Pi" in emit
+    assert "0.6666667f * __log2f(c)" in emit                       # chi^(2/3)
+    assert "zmin = (8.0f / 3.0f) / c" in pair and "float f2 = 0.6071f;" in pair
+    assert "if (zmin > 0.42f)" in pair and "(1.0f + float(7.0 / 72.0) / zmin)" in pair
+    assert "sqrtf(float(kPi / 2) * zmin) * __expf(-zmin)" in pair
+    assert "1.02 * kAlpha * kSqrt3Over2Pi" in pair and "(c / (float)eps) * f2" in pair
