@@ -230,3 +230,18 @@ def test_device_gauss_legendre_constants():
         r = mpmath.findroot(P8, xi)
         wt = 2 / ((1 - r ** 2) * mpmath.diff(P8, r) ** 2)
         assert xi == float(r) and wi == float(wt)
+
+
+def test_fast_division_is_exact(tmp_path):
+    # the multiply-shift division that splits cell indices and forms the cell
+    # sort's keys, for the divisors the meshes give (edges, planes, cell-block
+    # counts), checked on the host against integer division for n < 2^31
+    from paper_1412_6426_gb300 import build
+    exe = str(tmp_path / "fast_div")
+    subprocess.run([build.nvcc(), "-O2", "-std=c++17", "-I", build.CSRC, "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "native", "fast_div_host.cu"), "-o", exe], check=True)
+    divisors = [1, 2, 3, 7, 8, 12, 16, 64, 100, 255, 256, 257, 511, 512, 513, 1000, 4096, 65536, 65537,
+                262144, 2 ** 20 - 1, 2 ** 24 + 3, 1_000_003, 2 ** 30, 2 ** 31 - 1]
+    out = subprocess.run([exe, *map(str, divisors)], capture_output=True, text=True, check=True).stdout.split()
+    misses, tried = int(out[0]), int(out[1])
+    assert tried > len(divisors) * (1 << 20) and misses == 0, (misses, tried)
