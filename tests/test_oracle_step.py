@@ -102,18 +102,26 @@ def test_free_streaming_velocity():
 
 
 def test_boundaries_open_and_periodic():
-    for periodic, alive in ((0, 0), (1, 1)):
+    # one photon leaves through each of the six faces of a 10^3 box in one
+    # step: an open box removes all six, a periodic one wraps each to the
+    # opposite face, half a cell inside
+    x0 = [[9.5, 5, 5], [0.5, 5, 5], [5, 9.5, 5], [5, 0.5, 5], [5, 5, 9.5], [5, 5, 0.5]]
+    k = [[2, 0, 0], [-2, 0, 0], [0, 2, 0], [0, -2, 0], [0, 0, 2], [0, 0, -2]]
+    wrapped = {7: [0.5, 5, 5], 8: [9.5, 5, 5], 9: [5, 0.5, 5], 10: [5, 9.5, 5], 11: [5, 5, 0.5], 12: [5, 5, 9.5]}
+    for periodic in (0, 1):
         P = o.make_params(n=(10, 10, 10), d=(1.0, 1.0, 1.0), x0=(0.0, 0.0, 0.0), periodic=(periodic,) * 3,
                           field_mode=o.FIELD_UNIFORM, fp=(0,) * 6, pairs_on=1)
-        run = o.Run(P, caps=(1, 1, 4, 1))
-        run.sp[2].set([[9.5, 5.0, 5.0]], [[2.0, 0.0, 0.0]], [1.0], [7])
+        run = o.Run(P, caps=(1, 1, 8, 1))
+        run.sp[2].set(np.array(x0, float), np.array(k, float), np.ones(6), np.arange(7, 13))
         run.step(0, 0.0, 1.0)
-        assert run.sp[2].n == alive
-        if alive:
-            x, _, _, _ = run.sp[2].get()
-            assert abs(x[0, 0] - 0.5) < 1e-14
+        if periodic:
+            x, _, _, ids = run.sp[2].get()
+            assert sorted(ids.tolist()) == list(range(7, 13))
+            for xi, i in zip(x, ids):
+                assert np.abs(xi - wrapped[int(i)]).max() < 1e-14, (i, xi)
         else:
-            assert run.diag()["absorbed"] == 1
+            assert run.sp[2].n == 0
+            assert run.diag()["absorbed"] == 6
 
 
 def run_stats(dt, nsteps, kappa, n=800, seed=11):
