@@ -36,6 +36,9 @@
  *   AEG             few large steps vs many unsubdivided small steps
  *   events          3-momentum exact in uniform E; energy up to the closed-
  *                   form defects in uniform B
+ *   pairs, products photons convert at 1 - (1 - int P_p)^N per step and split
+ *                   by P_p; products evolve for exactly the rest of the step
+ *   boundaries      open boxes absorb and periodic ones wrap on all six faces
  *   Yee, CIC,       discrete dispersion relation; div B; linear fields exact;
  *   Esirkepov       discrete continuity equation
  *   ensembles       one ensemble reproduces the single-field runs exactly;

@@ -141,6 +141,96 @@ MUTANTS = [
     ("thinning factor N/L instead of the weight ratio", "w = w * (wall[g] / wsurv[g]);",
      "w = w * ((double)count[g] / (double)L);", 1,
      ["tests/test_oracle_sec6.py::test_thinning_conserves_group_weight_and_is_binomial"]),
+    # photons in the step (Sec. V.A, Eqs. (31)-(33))
+    ("photon flies at |k| instead of c", "for (int c = 0; c < 3; ++c) q->x[c] += q->p[c] / eps * h;",
+     "for (int c = 0; c < 3; ++c) q->x[c] += q->p[c] * h;", 1,
+     ["tests/test_oracle_step.py::test_boundaries_open_and_periodic"]),
+    ("chi_gamma without the photon energy", "double chig = eps * hg;", "double chig = hg;", 1,
+     ["tests/test_oracle_step.py::test_pair_step_converts_at_the_rate_and_splits_by_its_density"]),
+    ("pair draw over the whole step", "double pp = or_Pp(r1, chig, eps, h);", "double pp = or_Pp(r1, chig, eps, t_span);", 1,
+     ["tests/test_oracle_step.py::test_pair_step_converts_at_the_rate_and_splits_by_its_density"]),
+    ("P_p: z_p without 1 - delta_e", "double zp = (2.0 / 3.0) / (chig * (1.0 - de) * de);",
+     "double zp = (2.0 / 3.0) / (chig * de);", 1,
+     ["tests/test_oracle_rates.py::test_pair_rate_known_values",
+      "tests/test_oracle_step.py::test_pair_step_converts_at_the_rate_and_splits_by_its_density"]),
+    ("photon sub-intervals from chi_gamma", "n = or_nsub(t_span, or_dtq_photon(hg, P->kappa), P->nsub_max, &capped);",
+     "n = or_nsub(t_span, or_dtq_photon(chig, P->kappa), P->nsub_max, &capped);", 1,
+     ["tests/test_oracle_step.py::test_pair_products_evolve_for_the_rest_of_the_step"]),
+    ("pair defect: positron takes r1", "ke[c] = r1 * q->p[c]; kp[c] = (1.0 - r1) * q->p[c];",
+     "ke[c] = r1 * q->p[c]; kp[c] = r1 * q->p[c];", 1,
+     ["tests/test_oracle_step.py::test_energy_conservation_uniform_B"]),
+    # products of a step evolve for its rest (reading of Sec. IV.H)
+    ("photon product flies one sub-interval too long",
+     "                or_emit_child(C, OR_PHOTON, &ph, (double)(n - 1 - s) * h, E, B);\n            }\n            if (r2 < pm)",
+     "                or_emit_child(C, OR_PHOTON, &ph, (double)(n - s) * h, E, B);\n            }\n            if (r2 < pm)", 1,
+     ["tests/test_oracle_step.py::test_children_modes"]),
+    ("pair products move one sub-interval too long", "double t_rem = (double)(n - 1 - s) * h;",
+     "double t_rem = (double)(n - s) * h;", 1,
+     ["tests/test_oracle_step.py::test_pair_products_evolve_for_the_rest_of_the_step"]),
+    # the lepton's time-step bound and effective field
+    ("dt_q: the larger of the two branches", "return kappa * 137.0 * (a < b ? a : b);",
+     "return kappa * 137.0 * (a > b ? a : b);", 1, ["tests/test_oracle_rates.py::test_time_step_bounds"]),
+    ("H_eff: p x B for v x B", "double vx = p[0] / g, vy = p[1] / g, vz = p[2] / g;",
+     "double vx = p[0], vy = p[1], vz = p[2];", 1, ["tests/test_oracle_rates.py::test_chi_definitions"]),
+    # the generators of Sec. IV.F
+    ("alternative generator: P at r2", "pe = or_P(r1, chi, g, h);", "pe = or_P(r2, chi, g, h);", 1,
+     ["tests/test_oracle_generators.py::test_step_emits_the_generator_densities"]),
+    ("standard generator: W(1) without 1/gamma", "return OR_ALPHA * dt / gamma * or_Wnorm(1.0, chi);",
+     "return OR_ALPHA * dt * or_Wnorm(1.0, chi);", 1,
+     ["tests/test_oracle_generators.py::test_three_generators_frozen_spectra"]),
+    # analytic fields
+    ("rotating E: cos and sin swapped", "E[0] = fp[0] * cos(fp[1] * t);\n        E[1] = fp[0] * sin(fp[1] * t);",
+     "E[0] = fp[0] * sin(fp[1] * t);\n        E[1] = fp[0] * cos(fp[1] * t);", 1,
+     ["tests/test_oracle_sec6.py::test_one_ensemble_is_the_rotating_mode"]),
+    ("standing wave: B_z with the wrong sign", "B[2] = -fp[0] * cos(fp[1] * x[0]) * sin(fp[1] * t);",
+     "B[2] = fp[0] * cos(fp[1] * x[0]) * sin(fp[1] * t);", 1,
+     ["tests/test_oracle_step.py::test_standing_wave_field"]),
+    ("pulse: envelope ln 2 for 2 ln 2", "double env = exp(-2.0 * log(2.0) * eta * eta / (tau * tau));",
+     "double env = exp(-log(2.0) * eta * eta / (tau * tau));", 1,
+     ["tests/test_oracle_step.py::test_gaussian_pulse_properties"]),
+    ("pulse: B along +E", "        B[2] = -E[1];\n    } else if (mode == OR_FIELD_ROTATING_E)",
+     "        B[2] = E[1];\n    } else if (mode == OR_FIELD_ROTATING_E)", 1,
+     ["tests/test_oracle_step.py::test_gaussian_pulse_properties"]),
+    ("ensemble: rotating E_x by sin", "E[0] = q[3] + q[0] * cos(ph);", "E[0] = q[3] + q[0] * sin(ph);", 1,
+     ["tests/test_oracle_sec6.py::test_rotating_field_closed_form_orbit"]),
+    # boundaries
+    ("open box: lower faces keep particles", "} else if (q->x[c] < lo || q->x[c] >= lo + L) {",
+     "} else if (q->x[c] >= lo + L) {", 1, ["tests/test_oracle_step.py::test_boundaries_open_and_periodic"]),
+    ("periodic wrap the wrong way", "q->x[c] -= u * L;", "q->x[c] += u * L;", 1,
+     ["tests/test_oracle_step.py::test_boundaries_open_and_periodic"]),
+    # mesh: curls, CIC, charge density, Esirkepov
+    ("curl B: (curl B)_z with dy for dx", "out[2][c] = (B[1][c] - B[1][or_idx(n, i - 1, j, k)]) / d[0]",
+     "out[2][c] = (B[1][c] - B[1][or_idx(n, i - 1, j, k)]) / d[1]", 1,
+     ["tests/test_oracle_grid.py::test_plane_wave_dispersion"]),
+    ("curl E: backward difference", "out[0][c] = (E[2][or_idx(n, i, j + 1, k)] - E[2][c]) / d[1]",
+     "out[0][c] = (E[2][c] - E[2][or_idx(n, i, j - 1, k)]) / d[1]", 1,
+     ["tests/test_oracle_grid.py::test_plane_wave_dispersion"]),
+    ("CIC: fraction from the node above", "        fr[c] = v[c] - (double)b[c];\n    }\n    double acc",
+     "        fr[c] = (double)b[c] + 1.0 - v[c];\n    }\n    double acc", 1,
+     ["tests/test_oracle_grid.py::test_cic_linear_exact"]),
+    ("charge density: x weights transposed",
+     "                    double wgt = (di ? fr[0] : 1.0 - fr[0]) * (dj ? fr[1] : 1.0 - fr[1])",
+     "                    double wgt = (di ? 1.0 - fr[0] : fr[0]) * (dj ? fr[1] : 1.0 - fr[1])", 1,
+     ["tests/test_oracle_grid.py::test_esirkepov_continuity"]),
+    ("Esirkepov: 1/2 for 1/3 in the Jz weight", "dS[0][i] * dS[1][j] / 3.0", "dS[0][i] * dS[1][j] / 2.0", 1,
+     ["tests/test_oracle_grid.py::test_esirkepov_continuity"]),
+    ("Esirkepov: Jy scaled by dx", "acc -= qw * d[1] / (dt * dV) * W;", "acc -= qw * d[0] / (dt * dV) * W;", 1,
+     ["tests/test_oracle_grid.py::test_esirkepov_continuity"]),
+    # ensembles, thinning, weights (Sec. VI)
+    ("products leave their parent's ensemble", "return (parent & hi) | (mix & ~hi);", "return mix;", 1,
+     ["tests/test_oracle_sec6.py::test_ensembles_together_equal_ensembles_alone"]),
+    ("thinning keeps the complement", "if (u < (double)L / (double)count[g]) wsurv[g] += s->w[i];",
+     "if (u >= (double)L / (double)count[g]) wsurv[g] += s->w[i];", 1,
+     ["tests/test_oracle_sec6.py::test_thinning_conserves_group_weight_and_is_binomial"]),
+    ("thinning limit without the ensemble's scale", "if (sc > 0.0) L = (int64_t)floor((double)L * sc);",
+     "if (sc > 0.0) L = L;", 1, ["tests/test_oracle_sec6.py::test_thinning_conserves_group_weight_and_is_binomial"]),
+    ("pair products at weight w N_g", "el.w = po.w = q->w * (fg / (double)ng);", "el.w = po.w = q->w * fg * (double)ng;", 1,
+     ["tests/test_oracle_sec6.py::test_pair_factor_keeps_lepton_yield"]),
+    # vacuum pairs (Sec. V.B)
+    ("Schwinger rate over 4 pi^2", "(4.0 * OR_PI * OR_PI * OR_PI)", "(4.0 * OR_PI * OR_PI)", 1,
+     ["tests/test_oracle_schwinger.py::test_pair_count_matches_the_si_rate"]),
+    ("Schwinger rate with E for E^2", "double ps = Em * Em * exp(", "double ps = Em * exp(", 1,
+     ["tests/test_oracle_schwinger.py::test_pair_count_matches_the_si_rate"]),
     ("Philox: a Weyl constant off by one", "k[1] += 0xBB67AE85u;", "k[1] += 0xBB67AE86u;", 1,
      ["tests/test_philox_pin.py::test_oracle_philox_matches_aten"]),
 ]

@@ -10,14 +10,17 @@
 * Adaptive sub-stepping (Sec. IV.H): a few large steps agree statistically with
   many small steps that never subdivide (brute force), the paper's own
   small-vs-large time step check (Sec. VII).
-* Boundaries: open boxes remove particles, periodic boxes wrap them.
+* Pairs in the step (Sec. V.A): photons convert at the rate of Eq. (30) over
+  the sub-intervals of Eq. (33), and split their momentum by its density.
+* Products of a step evolve for exactly the rest of it (N - 1 - s sub-intervals).
+* Boundaries: open boxes remove particles, periodic boxes wrap them, on all six faces.
 * Analytic fields: the Gaussian pulse peaks at E0 at the focus, halves its
   intensity at +-tau/2, falls to 1/e at r = w0 and travels along -x at c.
 """
 import math
 
 import numpy as np
-from scipy.stats import ks_2samp
+from scipy.stats import ks_2samp, kstest
 
 from oracle import oracle as o
 
@@ -154,22 +157,108 @@ def test_adaptive_substeps_match_brute_force():
 
 
 def test_children_modes():
-    # with products evolving in the same step, photons born in step 0 already move in step 0
+    # with products evolving in the same step, photons born in step 0 already
+    # move in step 0: a photon born in sub-interval s of N flies at c for the
+    # rest of the step, (N - 1 - s) h, along its momentum
     common = dict(field_mode=o.FIELD_UNIFORM, fp=(0, 0, 0, 0, 0, B_CHI1), kappa=0.1, pairs_on=0,
                   **big_periodic_box())
+    dt, n_e = 2e5, 300
     res = {}
     for mode in (0, 1):
         P = o.make_params(same_step_children=mode, **common)
-        run = o.Run(P, caps=(300, 1, 3000, 1))
-        run.sp[0].set(*electrons(300))
-        run.step(0, 0.0, 2e5)
-        x, p, _, _ = run.sp[2].get()
-        res[mode] = (x, p)
+        run = o.Run(P, caps=(n_e, 1, 3000, 1))
+        run.sp[0].set(*electrons(n_e))
+        run.step(0, 0.0, dt)
+        x, p, _, ids = run.sp[2].get()
+        order = np.argsort(ids)
+        res[mode] = (x[order], p[order], ids[order], run.diag())
     # identical events (same streams), only the photon positions differ
     assert len(res[0][0]) == len(res[1][0]) > 20
+    assert np.array_equal(res[0][2], res[1][2])
     assert np.array_equal(res[0][1], res[1][1])
-    moved = np.linalg.norm(res[1][0] - res[0][0], axis=1)
-    assert (moved > 0).sum() > 0.5 * len(moved)
+    # identical electrons take the same number N of sub-intervals
+    n_sub = res[1][3]["substeps_lepton"] / n_e
+    assert n_sub == int(n_sub) > 4
+    n_sub = int(n_sub)
+    flown = res[1][0] - res[0][0]
+    k_hat = res[1][1] / np.linalg.norm(res[1][1], axis=1)[:, None]
+    assert np.allclose(np.cross(flown, k_hat), 0.0, atol=1e-9 * dt)     # along k
+    rest = np.einsum("ij,ij->i", flown, k_hat) / (dt / n_sub)          # in sub-intervals
+    assert np.abs(rest - np.round(rest)).max() < 1e-9
+    assert rest.min() > -0.5 and rest.max() < n_sub - 0.5               # 0 .. N - 1
+    # births in the first and in the last sub-interval both occur
+    assert np.isclose(rest.max(), n_sub - 1) and np.isclose(rest.min(), 0.0)
+
+
+def test_pair_products_evolve_for_the_rest_of_the_step():
+    # photons along x in a uniform E along y convert; with emission off a
+    # lepton takes one push over its remaining time, which in a pure E field
+    # is exact: p gains q E t_rem.  A pair born in sub-interval s of the
+    # photon's N has t_rem = (N - 1 - s) h, so t_rem / h is an integer in
+    # 0 .. N - 1, and with products starting at the next step it is 0
+    E, eps, dt, n_g = 2e-3, 1e4, 4e5, 300
+    common = dict(field_mode=o.FIELD_UNIFORM, fp=(0, E, 0, 0, 0, 0), kappa=0.1, pairs_on=1, emission_on=0,
+                  **big_periodic_box())
+    out = {}
+    for mode in (0, 1):
+        P = o.make_params(same_step_children=mode, **common)
+        run = o.Run(P, caps=(2000, 2000, n_g, 1))
+        run.sp[2].set(np.zeros((n_g, 3)), np.tile([eps, 0.0, 0.0], (n_g, 1)), np.ones(n_g),
+                      np.arange(n_g, dtype=np.uint64))
+        run.step(0, 0.0, dt)
+        D = run.diag()
+        got = {}
+        for sp in (0, 1):
+            _, p, _, ids = run.sp[sp].get()
+            order = np.argsort(ids)
+            got[sp] = (p[order], ids[order])
+        out[mode] = (got, D)
+    D = out[1][1]
+    # k perpendicular to E, no B: H_eff of Eq. (32) is |E|, and Eq. (33)
+    # with lambda_C / c = 2 pi Compton times bounds the sub-interval
+    n_sub = math.ceil(dt / (0.1 * 130.0 * 2.0 * math.pi / E))
+    assert D["pairs"] > 50 and n_sub > 4
+    h = dt / n_sub
+    for sp, q in ((0, -1.0), (1, 1.0)):
+        (p0, i0), (p1, i1) = out[0][0][sp], out[1][0][sp]
+        assert np.array_equal(i0, i1)
+        # born with a share of the photon's momentum along x; E changes only p_y
+        assert np.array_equal(p0[:, [0, 2]], p1[:, [0, 2]]) and np.all(p0[:, 1] == 0.0)
+        rest = p1[:, 1] / (q * E * h)
+        assert np.abs(rest - np.round(rest)).max() < 1e-6
+        assert rest.min() > -0.5 and rest.max() < n_sub - 0.5
+        assert np.isclose(rest.max(), n_sub - 1) and np.isclose(rest.min(), 0.0)
+
+
+def test_pair_step_converts_at_the_rate_and_splits_by_its_density():
+    # photons of energy eps along x in a uniform E along y (chi_g = eps |E|,
+    # Eq. (31)): in each of the N sub-intervals of Eq. (33) a photon converts
+    # with probability w = int_0^1 P_p(d) dd (Eq. (30); P_p < 1 here, and the
+    # generator accepts r2 < P_p(r1)), so a fraction 1 - (1 - w)^N converts in
+    # the step, and the electron's share of the photon momentum is
+    # distributed as P_p
+    E, eps, dt, n_g = 2e-3, 1e4, 4e5, 4000
+    P = o.make_params(field_mode=o.FIELD_UNIFORM, fp=(0, E, 0, 0, 0, 0), kappa=0.1, pairs_on=1,
+                      emission_on=0, same_step_children=0, **big_periodic_box())
+    run = o.Run(P, caps=(n_g, n_g, n_g, 1))
+    run.sp[2].set(np.zeros((n_g, 3)), np.tile([eps, 0.0, 0.0], (n_g, 1)), np.ones(n_g),
+                  np.arange(n_g, dtype=np.uint64))
+    run.step(0, 0.0, dt)
+    D = run.diag()
+    n_sub = math.ceil(dt / (0.1 * 130.0 * 2.0 * math.pi / E))
+    h, chig = dt / n_sub, eps * E
+    grid = np.linspace(0.0, 1.0, 4001)
+    dens = np.array([o.Pp(d, chig, eps, h) for d in grid])
+    assert dens.max() < 1.0
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (dens[1:] + dens[:-1]) * np.diff(grid))])
+    w = cdf[-1]
+    expect = n_g * (1.0 - (1.0 - w) ** n_sub)
+    assert abs(D["pairs"] - expect) < 4.0 * math.sqrt(expect * (1.0 - expect / n_g)), (D["pairs"], expect)
+    _, pe, _, _ = run.sp[0].get()
+    _, pp, _, _ = run.sp[1].get()
+    assert len(pe) == len(pp) == D["pairs"] > 1000
+    assert np.allclose(pe[:, 0] + pp[:, 0], eps, rtol=1e-15, atol=0)
+    assert kstest(pe[:, 0] / eps, lambda x: np.interp(x, grid, cdf / w)).pvalue > 1e-3
 
 
 def test_gaussian_pulse_properties():
