@@ -32,13 +32,15 @@
  *                   (paper 0.52); scipy-K density; max P_m vs Eq. (27)
  *   P_p             Erber small-chi asymptote; delta_e <-> 1-delta_e symmetry
  *   generator       sampled spectrum vs the analytic one down to delta=1e-10
- *   Boris           exact rotation angle, exact E acceleration, E x B drift
+ *   Boris           exact rotation angle (electron, proton, a doubly charged
+ *                   ion), exact E acceleration, E x B drift
  *   AEG             few large steps vs many unsubdivided small steps
  *   events          3-momentum exact in uniform E; energy up to the closed-
  *                   form defects in uniform B
  *   pairs, products photons convert at 1 - (1 - int P_p)^N per step and split
  *                   by P_p; products evolve for exactly the rest of the step
  *   boundaries      open boxes absorb and periodic ones wrap on all six faces
+ *   ions            pushed only: no emission, no sub-intervals, |p| kept in B
  *   Yee, CIC,       discrete dispersion relation; div B; linear fields exact;
  *   Esirkepov       discrete continuity equation
  *   ensembles       one ensemble reproduces the single-field runs exactly;
@@ -50,7 +52,8 @@
  *   Schwinger pairs the pair count of a uniform-field box against the sum of
  *                   P_S (binomial), the unit conversion of R_S V c dt against
  *                   the formula evaluated in SI units, positions uniform in
- *                   the cells, pairs at rest, none in weak fields
+ *                   the cells, pairs at rest, none in weak fields; on a mesh
+ *                   the field at the cell centre
  *   generators      standard (inverse transform): W(x)/W(1) against scipy's
  *                   K-function quadrature, total W(1) against the number
  *                   rate; alternative: P(delta) against Eq. (24); the three

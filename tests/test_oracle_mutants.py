@@ -231,6 +231,45 @@ MUTANTS = [
      ["tests/test_oracle_schwinger.py::test_pair_count_matches_the_si_rate"]),
     ("Schwinger rate with E for E^2", "double ps = Em * Em * exp(", "double ps = Em * exp(", 1,
      ["tests/test_oracle_schwinger.py::test_pair_count_matches_the_si_rate"]),
+    ("Philox: nine rounds", "for (int r = 0; r < 10; ++r) {", "for (int r = 0; r < 9; ++r) {", 1,
+     ["tests/test_philox_pin.py::test_oracle_philox_matches_aten"]),
+    ("Philox: low words of the products swapped", "c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;",
+     "c[0] = n0; c[1] = lo0; c[2] = n2; c[3] = lo1;", 1, ["tests/test_philox_pin.py::test_oracle_philox_matches_aten"]),
+    # more of the push, the rates and the mesh
+    ("Boris: gamma without 1/m^2", "double gm = sqrt(1.0 + (um[0] * um[0] + um[1] * um[1] + um[2] * um[2]) / (m * m));",
+     "double gm = sqrt(1.0 + (um[0] * um[0] + um[1] * um[1] + um[2] * um[2]));", 1,
+     ["tests/test_oracle_push.py::test_uniform_B_rotation_exact"]),
+    ("Boris: rotation vector without 1/m", "double f = a / (m * gm);", "double f = a / gm;", 1,
+     ["tests/test_oracle_push.py::test_uniform_B_rotation_exact"]),
+    ("photon H_eff: k x B with the wrong sign", "double ax = E[0] + (ny * B[2] - nz * B[1]);",
+     "double ax = E[0] - (ny * B[2] - nz * B[1]);", 1, ["tests/test_oracle_rates.py::test_chi_definitions"]),
+    ("G without the factor 1 - delta", "return sqrt(3.0) / (2.0 * OR_PI) * chi * (1.0 - delta) / delta",
+     "return sqrt(3.0) / (2.0 * OR_PI) * chi / delta", 1, ["tests/test_oracle_rates.py::test_G_against_scipy"]),
+    ("spectrum binned in ln delta", "double a = (log10(delta) - P->lg_lo) / span * P->nbins;",
+     "double a = (log(delta) - P->lg_lo) / span * P->nbins;", 1,
+     ["tests/test_oracle_martingale.py::test_sampled_spectrum_matches_its_expectation_along_the_trajectories"]),
+    ("CIC: Bz staggered in z too", "{0, 0.5, 0.5}, {0.5, 0, 0.5}, {0.5, 0.5, 0}};",
+     "{0, 0.5, 0.5}, {0.5, 0, 0.5}, {0.5, 0.5, 0.5}};", 1, ["tests/test_oracle_grid.py::test_cic_linear_exact"]),
+    ("Esirkepov: stencil one node up", "base[c] = (long)floor(ua[c]) - 1;", "base[c] = (long)floor(ua[c]);", 1,
+     ["tests/test_oracle_grid.py::test_esirkepov_continuity"]),
+    ("ions emit", "int qed = (sp != OR_ION) && P->emission_on;", "int qed = P->emission_on;", 1,
+     ["tests/test_oracle_step.py::test_ions_never_emit"]),
+    ("vacuum pairs: field at the cell's corner", "double xc[3] = {P->x0[0] + (i + 0.5) * P->d[0],",
+     "double xc[3] = {P->x0[0] + (i + 0.0) * P->d[0],", 1,
+     ["tests/test_oracle_schwinger.py::test_mesh_field_taken_at_the_cell_centre"]),
+    # ensembles and the generator factors (Sec. VI)
+    ("ensemble: phase dropped", "double ph = q[1] * t + q[2];", "double ph = q[1] * t;", 1,
+     ["tests/test_oracle_sec6.py::test_rotating_field_closed_form_orbit"]),
+    ("ensemble from one bit too few", "return P->ens_bits > 0 ? (uint32_t)(id >> (64 - P->ens_bits)) : 0u;",
+     "return P->ens_bits > 0 ? (uint32_t)(id >> (63 - P->ens_bits)) : 0u;", 1,
+     ["tests/test_oracle_sec6.py::test_ensembles_together_equal_ensembles_alone"]),
+    ("thinning factor inverted", "if (u < (double)L / (double)count[g]) w = w * (wall[g] / wsurv[g]);",
+     "if (u < (double)L / (double)count[g]) w = w * (wsurv[g] / wall[g]);", 1,
+     ["tests/test_oracle_sec6.py::test_thinning_conserves_group_weight_and_is_binomial"]),
+    ("products kept with probability f_g", "return u < 1.0 / fg;", "return u < fg;", 1,
+     ["tests/test_oracle_sec6.py::test_emission_factor_fg_keeps_yields"]),
+    ("photon products without 1/N_g", "ph.w = q->w * (fg / (double)ng);", "ph.w = q->w * fg;", 1,
+     ["tests/test_oracle_sec6.py::test_emission_factor_ng_keeps_yields"]),
     ("Philox: a Weyl constant off by one", "k[1] += 0xBB67AE85u;", "k[1] += 0xBB67AE86u;", 1,
      ["tests/test_philox_pin.py::test_oracle_philox_matches_aten"]),
 ]

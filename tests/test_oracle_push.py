@@ -12,18 +12,23 @@ from oracle import oracle as o
 
 
 def test_uniform_B_rotation_exact():
-    B, gam0 = 1e-3, 1000.0
-    p = np.array([math.sqrt(gam0 ** 2 - 1), 0.0, 0.0])
-    h = 2 * math.pi * gam0 / B / 100.0
-    n = 37
-    for _ in range(n):
-        p = o.boris(p, (0, 0, 0), (0, 0, B), -1.0, 1.0, h)
-    assert abs(np.linalg.norm(p) / math.sqrt(gam0 ** 2 - 1) - 1) < 1e-14
-    theta = 2 * math.atan(B * h / (2 * gam0))
-    ang = math.atan2(p[1], p[0])
-    # electron (q=-1) in +z field rotates counter-clockwise
-    expect = math.remainder(n * theta, 2 * math.pi)
-    assert abs(math.remainder(ang - expect, 2 * math.pi)) < 1e-11
+    # the Boris rotation in a uniform B turns p by exactly 2 atan(q B h / (2 m gamma))
+    # per step, gamma = sqrt(1 + p^2/m^2), and keeps |p|: an electron at gamma = 1000,
+    # a proton and a doubly charged ion of four proton masses at gamma = 3
+    B, n = 1e-3, 37
+    m_p = 1836.15267343
+    for q, m, gam0 in ((-1.0, 1.0, 1000.0), (1.0, m_p, 3.0), (2.0, 4.0 * m_p, 3.0)):
+        p0 = m * math.sqrt(gam0 ** 2 - 1)
+        p = np.array([p0, 0.0, 0.0])
+        h = 2 * math.pi * m * gam0 / (abs(q) * B) / 100.0
+        for _ in range(n):
+            p = o.boris(p, (0, 0, 0), (0, 0, B), q, m, h)
+        assert abs(np.linalg.norm(p) / p0 - 1) < 1e-14
+        theta = 2 * math.atan(abs(q) * B * h / (2 * m * gam0))
+        ang = math.atan2(p[1], p[0])
+        # a negative charge in a +z field turns counter-clockwise, a positive one clockwise
+        expect = math.remainder(-math.copysign(1.0, q) * n * theta, 2 * math.pi)
+        assert abs(math.remainder(ang - expect, 2 * math.pi)) < 1e-11, (q, m)
 
 
 def test_uniform_E_acceleration_exact():

@@ -9,6 +9,9 @@
 * Pairs are at rest, co-located, with equal numbers of electrons and
   positrons; their positions are uniform inside the cells (KS test).
 * Weak fields make none; P_S > 1 is counted per cell.
+* On a mesh the cell's field is the CIC value at its centre (the paper takes
+  the field constant over a cell): with E_y alternating E0, 0 along x every
+  centre sees E0/2, so every cell draws at P_S(E0/2).
 """
 import math
 
@@ -77,3 +80,27 @@ def test_weak_field_none_strong_field_counted():
     assert D["schwinger_pairs"] == 0
     _, D, _, _ = run_box(o.FIELD_UNIFORM, (0, 2.0, 0, 0, 0, 0), n=6)
     assert D["schwinger_gt1"] == 6 ** 3 and D["schwinger_pairs"] == 6 ** 3
+
+
+def test_mesh_field_taken_at_the_cell_centre():
+    # E_y nodes (i, j + 1/2, k) hold E0 for even i and 0 for odd i; the CIC
+    # value at any cell centre is E0/2.  P_S(E0) > 1, so a field read at the
+    # cell's corner would make exactly one pair in every even cell and none
+    # in the odd ones
+    E0, n, d, dt = 0.5, 16, 60.0, 40.0
+    N = n ** 3
+    ey = np.zeros((n, n, n))
+    ey[:, :, 0::2] = E0                              # [k][j][i], x fastest
+    fields = [np.zeros(N), ey.ravel().copy(), np.zeros(N), np.zeros(N), np.zeros(N), np.zeros(N)]
+    J = [np.zeros(N) for _ in range(3)]
+    out, D, _, _ = drive.run((n, n, n), (d, d, d), (0.0, 0.0, 0.0), (1, 1, 1), o.FIELD_GRID, (), dt, 1, {},
+                             kappa=0.1, seed=9, caps=(N, N, 1, 1), schwinger_on=1, fields=fields, J=J)
+    p = p_schwinger_si(E0 / 2, (d * LAMBDA_C) ** 3, dt * TAU_C)
+    assert 0.005 < p < 0.5 and p_schwinger_si(E0, (d * LAMBDA_C) ** 3, dt * TAU_C) > 1.0
+    k = D["schwinger_pairs"]
+    assert abs(k - N * p) < 5 * math.sqrt(N * p * (1 - p)), (k, N * p)
+    assert D["schwinger_gt1"] == 0
+    # the pairs' cells, even and odd in x alike
+    ix = np.floor(out[0][0][:, 0] / d).astype(int)
+    even = int((ix % 2 == 0).sum())
+    assert abs(even - (k - even)) < 5 * math.sqrt(k)

@@ -104,6 +104,25 @@ def test_free_streaming_velocity():
         assert np.allclose(x[0], n * dt * pv[0] / math.sqrt(m * m + pv[0] @ pv[0]), rtol=1e-13, atol=0), sp
 
 
+def test_ions_never_emit():
+    # ions are pushed with their charge and mass and take no part in the
+    # event generators: a proton at p = 1e6 m_e c across a strong B (chi would
+    # be ~1e3 for an electron of that momentum) keeps |p| and makes nothing
+    P = o.make_params(field_mode=o.FIELD_UNIFORM, fp=(0, 0, 0, 0, 0, 1e-3), kappa=0.1, emission_on=1, pairs_on=1,
+                      **big_periodic_box())
+    run = o.Run(P, caps=(16, 16, 16, 64))
+    n = 64
+    run.sp[3].set(np.zeros((n, 3)), np.tile([1e6, 0.0, 0.0], (n, 1)), np.ones(n), np.arange(n, dtype=np.uint64))
+    for s in range(3):
+        run.step(s, s * 1e5, 1e5)
+    D = run.diag()
+    assert D["emissions"] == D["photons_created"] == D["substeps_lepton"] == 0
+    assert run.sp[0].n == run.sp[1].n == run.sp[2].n == 0 and run.sp[3].n == n
+    _, p, _, _ = run.sp[3].get()
+    assert np.allclose(np.linalg.norm(p, axis=1), 1e6, rtol=1e-13, atol=0)
+    assert np.all(p[:, 1] < -100.0)                   # it did turn in the field (q v x B along -y)
+
+
 def test_boundaries_open_and_periodic():
     # one photon leaves through each of the six faces of a 10^3 box in one
     # step: an open box removes all six, a periodic one wraps each to the
