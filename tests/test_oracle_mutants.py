@@ -270,6 +270,24 @@ MUTANTS = [
      ["tests/test_oracle_sec6.py::test_emission_factor_fg_keeps_yields"]),
     ("photon products without 1/N_g", "ph.w = q->w * (fg / (double)ng);", "ph.w = q->w * fg;", 1,
      ["tests/test_oracle_sec6.py::test_emission_factor_ng_keeps_yields"]),
+    ("energy spectrum binned by delta", "double b = (log10(eps) - P->lg_lo) / span * P->nbins;",
+     "double b = (log10(delta) - P->lg_lo) / span * P->nbins;", 1,
+     ["tests/test_oracle_step.py::test_energy_spectrum_is_the_photons_energies"]),
+    ("pulse: intensity waist for the field's", "double amp = E0 * (w0 / wz) * exp(-r2 / (wz * wz)) * env;",
+     "double amp = E0 * (w0 / wz) * exp(-2.0 * r2 / (wz * wz)) * env;", 1,
+     ["tests/test_oracle_step.py::test_gaussian_pulse_properties"]),
+    ("pulse: no w0/w(z) amplitude", "double amp = E0 * (w0 / wz) * exp(-r2 / (wz * wz)) * env;",
+     "double amp = E0 * exp(-r2 / (wz * wz)) * env;", 1,
+     ["tests/test_oracle_step.py::test_gaussian_pulse_solves_the_wave_equation"]),
+    ("pulse: wave-front curvature 1/zeta", "double invR = zeta / (zeta * zeta + zr * zr);",
+     "double invR = 1.0 / zeta;", 1, ["tests/test_oracle_step.py::test_gaussian_pulse_solves_the_wave_equation"]),
+    ("standing wave: cos(kx) for sin(kx)", "E[1] = fp[0] * sin(fp[1] * x[0]) * cos(fp[1] * t);",
+     "E[1] = fp[0] * cos(fp[1] * x[0]) * cos(fp[1] * t);", 1, ["tests/test_oracle_step.py::test_standing_wave_field"]),
+    ("uniform mode: Bx and By swapped", "B[0] = fp[3]; B[1] = fp[4]; B[2] = fp[5];",
+     "B[0] = fp[4]; B[1] = fp[3]; B[2] = fp[5];", 1,
+     ["tests/test_oracle_sec6.py::test_one_ensemble_is_the_uniform_mode"]),
+    ("boundary: periodic and open swapped", "if (P->periodic[c]) {", "if (!P->periodic[c]) {", 1,
+     ["tests/test_oracle_step.py::test_boundaries_open_and_periodic"]),
     ("Philox: a Weyl constant off by one", "k[1] += 0xBB67AE85u;", "k[1] += 0xBB67AE86u;", 1,
      ["tests/test_philox_pin.py::test_oracle_philox_matches_aten"]),
 ]

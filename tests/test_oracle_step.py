@@ -280,6 +280,25 @@ def test_pair_step_converts_at_the_rate_and_splits_by_its_density():
     assert kstest(pe[:, 0] / eps, lambda x: np.interp(x, grid, cdf / w)).pvalue > 1e-3
 
 
+def test_energy_spectrum_is_the_photons_energies():
+    # with pairs off every emitted photon stays in the store and keeps its
+    # momentum, so the diagnostic spectrum over log10(photon energy) is the
+    # weighted histogram of log10|k| of the stored photons, bin by bin
+    from oracle import drive
+    n_e, nbins, lo, hi = 400, 64, -12.0, 4.0
+    x, p, _, ids = electrons(n_e)
+    w = 1.0 + np.arange(n_e) % 3                       # unequal weights
+    out, D, spec, spec_e = drive.run(
+        (4, 4, 4), (1e9,) * 3, (-2e9,) * 3, (1, 1, 1), o.FIELD_UNIFORM, (0, 0, 0, 0, 0, B_CHI1),
+        2e5, 3, {0: (x, p, w, ids)}, kappa=0.1, seed=5, pairs_on=0, same_step_children=0,
+        caps=(n_e, 1, 40 * n_e, 1), nbins=nbins, lg_lo=lo, lg_hi=hi)
+    _, k, wk, _ = out[2]
+    assert D["emissions"] == len(k) > 200
+    hist, _ = np.histogram(np.log10(np.linalg.norm(k, axis=1)), bins=nbins, range=(lo, hi), weights=wk)
+    assert np.allclose(spec_e, hist, rtol=1e-12, atol=0)
+    assert spec_e.sum() == wk.sum()
+
+
 def test_gaussian_pulse_properties():
     E0, w, w0, tau = 6e-4, 3e-6, 5e6, 2e7
     fp = (E0, w, w0, tau, 0.0, 0.0, 0.0, 0.0, 0.0)
