@@ -215,6 +215,33 @@ def test_product_path_has_no_oracle_import():
     assert "raised" in out
 
 
+def test_oracle_and_library_share_no_code():
+    # the oracle includes only the C standard library, the library's sources
+    # and header name nothing under oracle/, and the oracle's Python side
+    # never loads the CUDA library or its package (only the seeded inputs of
+    # workloads.py serve both)
+    src = open(os.path.join(ROOT, "oracle", "qed_oracle.c")).read()
+    assert set(re.findall(r"#include\s*[<\"]([^>\"]+)[>\"]", src)) <= {"math.h", "stdint.h", "stdlib.h", "string.h"}
+    lib_files = [os.path.join(ROOT, "paper_1412_6426_gb300", "csrc", f)
+                 for f in os.listdir(os.path.join(ROOT, "paper_1412_6426_gb300", "csrc"))]
+    for f in lib_files + [HEADER]:
+        text = open(f).read()
+        assert "oracle" not in text.lower() and "qed_oracle" not in text, f
+        for inc in re.findall(r"#include\s*\"([^\"]+)\"", text):
+            assert os.path.exists(os.path.join(os.path.dirname(f), inc)) or inc == "qed.h", (f, inc)
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith(".py"):
+            code = re.sub(r'""".*?"""', "", open(os.path.join(ROOT, "oracle", f)).read(), flags=re.S)
+            for mod in re.findall(r"^\s*import\s+([\w.]+)", code, re.M):
+                assert not mod.startswith("paper_1412_6426_gb300") or mod == "paper_1412_6426_gb300.workloads", (f, mod)
+            for mod, names in re.findall(r"^\s*from\s+([\w.]+)\s+import\s+([\w, ]+)", code, re.M):
+                if mod == "paper_1412_6426_gb300":
+                    assert {n.strip() for n in names.split(",")} <= {"workloads"}, (f, names)
+                else:
+                    assert not mod.startswith("paper_1412_6426_gb300.") or mod == "paper_1412_6426_gb300.workloads", (f, mod)
+            assert "libqed_gb300" not in code and "qed.load" not in code, f
+
+
 def test_device_gauss_legendre_constants():
     # the 8-point Gauss-Legendre nodes and weights the FP64 standard generator
     # integrates with (written into the device header) against the roots of
