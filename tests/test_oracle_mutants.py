@@ -28,6 +28,10 @@ MUTANTS = [
      ["tests/test_oracle_special.py::test_F_against_scipy", "tests/test_oracle_golden.py"]),
     ("F2 from K_1/3", "double t2 = e * cosh(2.0 * u / 3.0);", "double t2 = e * cosh(1.0 * u / 3.0);", 1,
      ["tests/test_oracle_special.py::test_F_against_scipy"]),
+    ("F1, F2: the u = 0 term at full weight", "double s1 = 0.5 * e0, s2 = 0.5 * e0;", "double s1 = e0, s2 = e0;", 1,
+     ["tests/test_oracle_special.py::test_F_against_scipy"]),
+    ("F1 without its factor x", "    *f1 = x * h * s1;", "    *f1 = h * s1;", 1,
+     ["tests/test_oracle_special.py::test_F_against_scipy"]),
     # emission density, Eq. (24), and the modified generator, Eq. (25)
     ("G: F2 term with the wrong sign", "(f1 + 1.5 * delta * chi * zq * f2)", "(f1 - 1.5 * delta * chi * zq * f2)", 1,
      ["tests/test_oracle_rates.py::test_G_against_scipy"]),
@@ -72,6 +76,9 @@ MUTANTS = [
     ("Boris: s = 2t without 1/(1 + t^2)",
      "double s[3] = {2.0 * t[0] / (1.0 + t2), 2.0 * t[1] / (1.0 + t2), 2.0 * t[2] / (1.0 + t2)};",
      "double s[3] = {2.0 * t[0], 2.0 * t[1], 2.0 * t[2]};", 1,
+     ["tests/test_oracle_push.py::test_uniform_B_rotation_exact"]),
+    ("Boris: second rotation with the wrong sign", "double uq[3] = {um[0] + (up[1] * s[2] - up[2] * s[1]),",
+     "double uq[3] = {um[0] - (up[1] * s[2] - up[2] * s[1]),", 1,
      ["tests/test_oracle_push.py::test_uniform_B_rotation_exact"]),
     ("Boris: a whole E step on each side", "double a = 0.5 * q * h;", "double a = q * h;", 1,
      ["tests/test_oracle_push.py::test_uniform_E_acceleration_exact"]),
