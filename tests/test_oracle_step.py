@@ -123,6 +123,35 @@ def test_ions_never_emit():
     assert np.all(p[:, 1] < -100.0)                   # it did turn in the field (q v x B along -y)
 
 
+def test_radiated_power_at_small_chi():
+    # the modified generator emits the whole spectrum, so the radiation
+    # reaction of the low-energy limit needs no classical term (Sec. IV.G):
+    # electrons at chi = 0.01 in a uniform B lose energy at the quantum-
+    # corrected synchrotron power alpha (2/3) chi^2 (1 - 5.95 chi + 48 chi^2)
+    # per Compton time, 5.5% below the classical (2/3) alpha chi^2, which the
+    # sample resolves (its statistical error is 0.5%)
+    g0, chi0, n, dt, nsteps = 1000.0, 0.01, 80000, 1e6, 20
+    p0 = math.sqrt(g0 ** 2 - 1)
+    P = o.make_params(field_mode=o.FIELD_UNIFORM, fp=(0, 0, 0, 0, 0, chi0 / p0), kappa=1e9, pairs_on=0,
+                      same_step_children=0, **big_periodic_box())
+    run = o.Run(P, caps=(n, 1, 20 * n, 1))
+    run.sp[0].set(np.zeros((n, 3)), np.tile([p0, 0.0, 0.0], (n, 1)), np.ones(n), np.arange(n, dtype=np.uint64))
+    for s in range(nsteps):
+        run.step(s, s * dt, dt)
+    D = run.diag()
+    assert D["pm_gt1"] == 0 and D["emissions"] > 100000
+    _, pe, _, _ = run.sp[0].get()
+    _, k, _, _ = run.sp[2].get()
+    loss = g0 - np.sqrt(1 + (pe ** 2).sum(1))
+    assert np.isclose(loss.sum(), np.linalg.norm(k, axis=1).sum(), rtol=1e-6)   # carried off by photons
+    alpha = 7.2973525693e-3
+    chi_mid = chi0 * (1 - 0.5 * loss.mean() / g0)      # chi ~ gamma falls ~1% over the run
+    power = alpha * (2 / 3) * chi_mid ** 2 * (1 - 5.95 * chi_mid + 48 * chi_mid ** 2)
+    err = loss.std() / math.sqrt(n)
+    assert abs(loss.mean() - power * nsteps * dt) < 4 * err, (loss.mean(), power * nsteps * dt, err)
+    assert abs(loss.mean() - alpha * (2 / 3) * chi_mid ** 2 * nsteps * dt) > 8 * err
+
+
 def test_boundaries_open_and_periodic():
     # one photon leaves through each of the six faces of a 10^3 box in one
     # step: an open box removes all six, a periodic one wraps each to the
