@@ -11,7 +11,7 @@
 namespace qed {
 
 constexpr double kAlpha = 7.2973525693e-3;          // fine-structure constant
-constexpr double kSqrt3Over2Pi = 0.27566444771089600; // sqrt(3)/(2 pi)
+constexpr double kSqrt3Over2Pi = 0.27566444771089602; // sqrt(3)/(2 pi), correctly rounded
 constexpr double kTwoPi = 6.283185307179586;
 constexpr double kPi = 3.141592653589793;
 

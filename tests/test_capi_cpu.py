@@ -6,6 +6,7 @@ same sizes and field offsets as the C compiler gives them; argument
 validation rejects invalid descriptors before touching the device.
 """
 import ctypes
+import math
 import os
 import re
 import subprocess
@@ -257,6 +258,28 @@ def test_device_gauss_legendre_constants():
         r = mpmath.findroot(P8, xi)
         wt = 2 / ((1 - r ** 2) * mpmath.diff(P8, r) ** 2)
         assert xi == float(r) and wi == float(wt)
+
+
+def test_device_constants():
+    # the literal constants of the device header against their definitions:
+    # the CODATA 2018 fine-structure constant, sqrt(3)/(2 pi) correctly
+    # rounded, pi, and the
+    # standard generator's table rows, ln chi from ln 1e-6 in 4096 steps to
+    # ln 1e4
+    text = open(os.path.join(ROOT, "paper_1412_6426_gb300", "csrc", "qed_device.cuh")).read()
+
+    def const(name):
+        m = re.search(r"constexpr (?:double|int) (?:\w+ = [^,;]+, )*" + name + r" = ([^,;]+)[,;]", text)
+        return eval(m.group(1), {"__builtins__": {}})      # a literal or a literal quotient
+
+    assert const("kAlpha") == 7.2973525693e-3
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    assert const("kSqrt3Over2Pi") == float(mpmath.sqrt(3) / (2 * mpmath.pi))   # correctly rounded
+    assert const("kPi") == math.pi and const("kTwoPi") == 2 * math.pi
+    assert const("kStdLnChiLo") == math.log(1e-6)
+    assert abs(const("kStdDLn") * 4096 - math.log(1e10)) < 1e-14
+    assert const("kStdRows") == 4097 and const("kStdCols") == 1025
 
 
 def test_fast_division_is_exact(tmp_path):
