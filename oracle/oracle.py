@@ -135,6 +135,7 @@ def lib():
         _lib.or_schwinger.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Store), ctypes.POINTER(Diag),
                                       ctypes.POINTER(pd), u32, d, d]
         _lib.or_Wnorm.restype = d; _lib.or_Wnorm.argtypes = [d, d]
+        _lib.or_gauss_legendre8.argtypes = [pd, pd]
         _lib.or_Pstd.restype = d; _lib.or_Pstd.argtypes = [d, d, d]
         _lib.or_delta_std.restype = d; _lib.or_delta_std.argtypes = [d, d]
         _lib.or_sample_frozen_gen.restype = i64
@@ -273,6 +274,14 @@ def sample_frozen_gen(generator, chi_, gamma, h, ndraw, seed, lo, hi, nbins):
     acc = lib().or_sample_frozen_gen(int(generator), float(chi_), float(gamma), float(h), int(ndraw), int(seed),
                                      float(lo), float(hi), int(nbins), _dp(hist), ctypes.byref(viol))
     return acc, hist, viol.value
+
+
+def gauss_legendre8():
+    """The 8-point Gauss-Legendre nodes and weights on [-1, 1] that W is
+    integrated with."""
+    x, w = np.zeros(8), np.zeros(8)
+    lib().or_gauss_legendre8(_dp(x), _dp(w))
+    return x, w
 
 
 def Wnorm(x, chi_):

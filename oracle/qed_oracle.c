@@ -216,12 +216,47 @@ double or_Pm(double r1, double chi, double gamma, double dt)
  * it is finite at s = 0.  The integrals are 8-point Gauss-Legendre over
  * panels of width 1/256 in s (the integrand is smooth in s); the root is
  * found by bisection on s, integrating panel by panel. */
-static const double or_gl8_x[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290,
-                                   -0.1834346424956498, 0.1834346424956498, 0.5255324099163290,
-                                   0.7966664774136267, 0.9602898564975363};
-static const double or_gl8_w[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873,
-                                   0.3626837833783620, 0.3626837833783620, 0.3137066458778873,
-                                   0.2223810344533745, 0.1012285362903763};
+static double or_gl8_x[8], or_gl8_w[8];
+
+/* P_8(x) and P_8'(x): P_8 and P_7 from the three-term recurrence
+ * n P_n = (2n - 1) x P_{n-1} - (n - 1) P_{n-2}, and
+ * P_8' = 8 (x P_8 - P_7)/(x^2 - 1). */
+static void or_legendre8(double x, double *p8, double *dp8)
+{
+    double p0 = 1.0, p1 = x;
+    for (int n = 2; n <= 8; ++n) {
+        double p2 = ((2.0 * n - 1.0) * x * p1 - (n - 1.0) * p0) / n;
+        p0 = p1;
+        p1 = p2;
+    }
+    *p8 = p1;
+    *dp8 = 8.0 * (x * p1 - p0) / (x * x - 1.0);
+}
+
+/* The 8-point Gauss-Legendre rule on [-1, 1]: the nodes are the roots of
+ * P_8, found by Newton's method from cos(pi (i + 3/4)/(n + 1/2)); the
+ * weights are 2/((1 - x^2) P_8'(x)^2).  Filled once when the library is
+ * loaded. */
+__attribute__((constructor)) static void or_gl8_init(void)
+{
+    for (int i = 0; i < 4; ++i) {
+        double x = cos(OR_PI * (i + 0.75) / 8.5), p8, dp;
+        for (int it = 0; it < 10; ++it) {   /* quadratic convergence: 4 would do */
+            or_legendre8(x, &p8, &dp);
+            x -= p8 / dp;
+        }
+        or_legendre8(x, &p8, &dp);
+        or_gl8_x[7 - i] = x;
+        or_gl8_x[i] = -x;
+        or_gl8_w[7 - i] = or_gl8_w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+/* The rule, copied out for its pin. */
+void or_gauss_legendre8(double x[8], double w[8])
+{
+    for (int k = 0; k < 8; ++k) { x[k] = or_gl8_x[k]; w[k] = or_gl8_w[k]; }
+}
 
 /* int_a^b 3 s^2 G(s^3, chi) ds, Gauss-Legendre on [a, b] */
 static double or_W_piece(double a, double b, double chi)

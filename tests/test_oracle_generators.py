@@ -6,6 +6,8 @@ and of the three-generator comparison (Sec. IV.G, the paper's Fig.
   normalised W(x) = int_0^x G(delta, chi) d delta against scipy's Bessel-K
   quadrature (independent of the oracle), its total W(1) against the same,
   and the photon energy it returns for r2 against the root of scipy's CDF.
+  The 8-point Gauss-Legendre rule W is integrated with (its nodes found by
+  Newton's method on P_8) against mpmath's roots of P_8 and their weights.
 * Frozen spectra: for each generator the expected count per log-delta bin
   is known in closed form from the emission density P of Eq. (24):
     modified:    ndraw int_bin P,
@@ -17,6 +19,7 @@ and of the three-generator comparison (Sec. IV.G, the paper's Fig.
 import math
 
 import numpy as np
+import pytest
 from scipy.integrate import quad
 
 from oracle import oracle as o
@@ -146,3 +149,18 @@ def test_step_emits_the_generator_densities():
         exp = _expected(gen, chi, gamma, h, n, edges)
         sig = np.sqrt(np.maximum(exp, 1.0))
         assert np.all(np.abs(hist - exp) <= 4 * sig + 1e-9), (gen, hist, exp)
+
+
+def test_gauss_legendre_rule_of_the_standard_generator():
+    # the oracle's rule (nodes found by Newton's method on P_8) against
+    # mpmath's roots of P_8 and the weights 2 / ((1 - x^2) P_8'(x)^2)
+    mpmath = pytest.importorskip("mpmath")
+    xs, ws = o.gauss_legendre8()
+    mpmath.mp.dps = 30
+    P8 = lambda t: mpmath.legendre(8, t)
+    roots = sorted(float(mpmath.findroot(P8, math.cos(math.pi * (i + 0.75) / 8.5))) for i in range(4))
+    roots = [-r for r in roots[::-1]] + roots
+    for x, w, r in zip(xs, ws, roots):
+        wt = float(2 / ((1 - mpmath.mpf(r) ** 2) * mpmath.diff(P8, mpmath.mpf(r)) ** 2))
+        assert abs(x - r) <= math.ulp(r) and abs(w - wt) <= 8 * math.ulp(wt), (x, r, w, wt)
+    assert abs(ws.sum() - 2.0) < 1e-15

@@ -101,6 +101,12 @@ MUTANTS = [
     ("standard generator: W without the Jacobian 3 s^2", "acc += or_gl8_w[k] * 3.0 * s * s * or_G(s * s * s, chi);",
      "acc += or_gl8_w[k] * or_G(s * s * s, chi);", 1,
      ["tests/test_oracle_generators.py::test_standard_total_and_cdf_against_scipy"]),
+    ("Gauss-Legendre: recurrence with 2n + 1", "double p2 = ((2.0 * n - 1.0) * x * p1 - (n - 1.0) * p0) / n;",
+     "double p2 = ((2.0 * n + 1.0) * x * p1 - (n - 1.0) * p0) / n;", 1,
+     ["tests/test_oracle_generators.py::test_gauss_legendre_rule_of_the_standard_generator"]),
+    ("Gauss-Legendre: weights with 1 + x^2", "or_gl8_w[7 - i] = or_gl8_w[i] = 2.0 / ((1.0 - x * x) * dp * dp);",
+     "or_gl8_w[7 - i] = or_gl8_w[i] = 2.0 / ((1.0 + x * x) * dp * dp);", 1,
+     ["tests/test_oracle_generators.py::test_gauss_legendre_rule_of_the_standard_generator"]),
     ("standard generator: delta = s^2", "    double sr = 0.5 * (a + b);\n    return sr * sr * sr;",
      "    double sr = 0.5 * (a + b);\n    return sr * sr;", 1,
      ["tests/test_oracle_generators.py::test_standard_energy_is_the_inverse_cdf"]),
