@@ -241,6 +241,18 @@ def test_oracle_and_library_share_no_code():
                 else:
                     assert not mod.startswith("paper_1412_6426_gb300.") or mod == "paper_1412_6426_gb300.workloads", (f, mod)
             assert "libqed_gb300" not in code and "qed.load" not in code, f
+    # no table of numbers typed on both sides: the long literals they share
+    # are the published CODATA constants alone
+    num = re.compile(r"(?<![\w.])(\d+\.\d{6,}(?:e[+-]?\d+)?)")
+    oracle_lits = set(num.findall(src))
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith(".py"):
+            oracle_lits |= set(num.findall(open(os.path.join(ROOT, "oracle", f)).read()))
+    pkg = os.path.join(ROOT, "paper_1412_6426_gb300")
+    lib_lits = set()
+    for f in lib_files + [HEADER] + [os.path.join(pkg, g) for g in os.listdir(pkg) if g.endswith(".py")]:
+        lib_lits |= set(num.findall(open(f).read()))
+    assert oracle_lits & lib_lits <= {"7.2973525693e-3", "1836.15267343"}, oracle_lits & lib_lits
 
 
 def test_device_gauss_legendre_constants():
