@@ -232,6 +232,9 @@ MUTANTS = [
     # ensembles, thinning, weights (Sec. VI)
     ("products leave their parent's ensemble", "return (parent & hi) | (mix & ~hi);", "return mix;", 1,
      ["tests/test_oracle_sec6.py::test_ensembles_together_equal_ensembles_alone"]),
+    ("ensemble guard one row too lenient", "if (!P->ens || e >= (uint32_t)P->n_ens) return;",
+     "if (!P->ens || e > (uint32_t)P->n_ens) return;", 1,
+     ["tests/test_oracle_sec6.py::test_an_ensemble_without_a_row_sees_no_field"]),
     ("thinning keeps the complement", "if (u < (double)L / (double)count[g]) wsurv[g] += s->w[i];",
      "if (u >= (double)L / (double)count[g]) wsurv[g] += s->w[i];", 1,
      ["tests/test_oracle_sec6.py::test_thinning_conserves_group_weight_and_is_binomial"]),

@@ -78,6 +78,19 @@ def test_one_ensemble_is_the_rotating_mode():
     same(a, b)
 
 
+def test_an_ensemble_without_a_row_sees_no_field():
+    # a table of one row handed over in a buffer whose next, uncounted row
+    # holds a strong field: ensemble 0 sees its row, ensemble 1 has no row
+    # and sees nothing (its field is never read from beyond the table)
+    rows = np.array([ens_row(Eu=(1e-3, 0, 0), Bu=(0, 2e-3, 0)), ens_row(Eu=(5.0, 5.0, 5.0), Bu=(5.0, 5.0, 5.0))])
+    P = o.make_params(field_mode=o.FIELD_ENSEMBLE, ens_bits=1, ens=rows, **box())
+    P.n_ens = 1
+    E, B = o.field_ensemble(P, 7, 0.0)
+    assert np.array_equal(E, [1e-3, 0, 0]) and np.array_equal(B, [0, 2e-3, 0])
+    E, B = o.field_ensemble(P, (1 << 63) | 7, 0.0)
+    assert np.all(E == 0.0) and np.all(B == 0.0)
+
+
 def test_ensembles_together_equal_ensembles_alone():
     bits = 8
     table = np.array([ens_row(Bu=(0, 0, 1e-3)),

@@ -152,6 +152,19 @@ def test_radiated_power_at_small_chi():
     assert abs(loss.mean() - alpha * (2 / 3) * chi_mid ** 2 * nsteps * dt) > 8 * err
 
 
+def test_full_store_counts_what_it_drops():
+    # a photon store of capacity 5: emissions beyond it are lost and counted,
+    # and the store never holds more than its capacity
+    P = o.make_params(field_mode=o.FIELD_UNIFORM, fp=(0, 0, 0, 0, 0, B_CHI1), kappa=0.1, pairs_on=0,
+                      same_step_children=0, **big_periodic_box())
+    run = o.Run(P, caps=(200, 1, 5, 1))
+    run.sp[0].set(*electrons(200))
+    run.step(0, 0.0, 2e5)
+    D = run.diag()
+    assert D["emissions"] > 20
+    assert run.sp[2].n == 5 and D["overflow"] == D["photons_created"] - 5
+
+
 def test_boundaries_open_and_periodic():
     # one photon leaves through each of the six faces of a 10^3 box in one
     # step: an open box removes all six, a periodic one wraps each to the
